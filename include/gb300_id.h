@@ -1,0 +1,174 @@
+/*
+ * gb300_id.h -- C ABI of the GB300 column interpolative decomposition library.
+ *
+ * The column ID (Dunton & Fox, "Mixed precision matrix interpolative
+ * decompositions for model reduction", Sec. 1.1) approximates an m x n matrix
+ * by k of its own columns:
+ *
+ *     A ~= A(:, J[0:k]) P,   P(:, J[0:k]) = I_k,   P(:, J[k:n]) = T,
+ *
+ * where J is the column permutation Z of a column-pivoted QR  A Z = Q R  and
+ * T = R11^-1 R12 (Eq. (idconstruction); Algorithm 1).  This library computes
+ * it on one GPU, optionally on a Gaussian sketch Y = Omega A instead of A, in
+ * plain FP64 or in the mixed-precision form of Algorithm 2 (low-precision
+ * cast and sketch, FP32 pivoted QR, FP64 coefficient solve).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with an explicit leading dimension (ld >= rows);
+ *     columns are the unit of the ID.  Omega is row-major (ell x m, row i
+ *     contiguous).  Column indices are 0-based int32.
+ *   - Every array argument is a DEVICE pointer owned by the caller unless the
+ *     comment says "host".  The library allocates no device memory: scratch
+ *     comes from the caller's `work` buffer (size from id_workspace_size).
+ *   - `stream` is a cudaStream_t passed as void*.  Every call only enqueues
+ *     work on that stream and returns; outputs are valid once the stream has
+ *     reached that point.
+ *   - The return value reports only errors the host can see before launching
+ *     (bad arguments, too small a workspace, a CUDA launch error).  Numerical
+ *     problems are reported in the device `info` word:
+ *        0   success
+ *        j>0 the pivot at step j-1 had zero residual norm: the rank is j-1
+ *            and k_out = j-1
+ *        -1  A (or Omega A) holds a non-finite value
+ *        -2  a bounded device wait gave up (watchdog); outputs are invalid
+ *   - The complement J[k:n] is listed in ascending column index.
+ */
+#ifndef GB300_ID_H
+#define GB300_ID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ID_OK = 0,
+    ID_ERR_ARG = 1,          /* invalid argument (sizes, null pointer, unsupported combination) */
+    ID_ERR_WORKSPACE = 2,    /* work_bytes smaller than id_workspace_size() */
+    ID_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    ID_ERR_TIMEOUT = 4,      /* a synchronous check found the device watchdog fired */
+    ID_ERR_UNSUPPORTED = 5   /* shape or option outside what this build implements */
+} id_status_t;
+
+typedef enum {
+    ID_F64 = 0,              /* double */
+    ID_F32 = 1               /* float */
+} id_dtype_t;
+
+/* Arithmetic of the factorisation.
+ *   PLAIN_F64     everything in FP64 (Algorithm 1).  With a sketch, Omega is FP64.
+ *   PLAIN_F32     pivoted QR in FP32 of the given matrix (no sketch), T in FP64.
+ *   MIXED_BF16    Algorithm 2 re-cast for GB300: A is scaled by powers of two per
+ *                 (64-row block, column), rounded to bfloat16, sketched on the
+ *                 tensor cores with FP32 accumulation; pivoted QR of Y in FP32;
+ *                 T = R11^-1 R12 in FP64 with iterative refinement.
+ *                 Omega is bfloat16.
+ *   MIXED_F16     as MIXED_BF16 with IEEE half (Omega is half).
+ *   MIXED_BF16X2  A split into 2 bfloat16 pieces (hi + lo), both sketched.
+ *   MIXED_BF16X3  A split into 3 bfloat16 pieces: an FP32-accurate sketch at the
+ *                 same HBM traffic.                                              */
+typedef enum {
+    ID_PLAIN_F64 = 0,
+    ID_PLAIN_F32 = 1,
+    ID_MIXED_BF16 = 2,
+    ID_MIXED_F16 = 3,
+    ID_MIXED_BF16X2 = 4,
+    ID_MIXED_BF16X3 = 5
+} id_precision_t;
+
+/* Rows per power-of-two scaling block of the low-precision cast (a block of
+ * rows of one column shares one shift). */
+#define ID_SCALE_BLOCK_ROWS 64
+
+/* Largest sketch size ell (= k + oversampling) of the tensor-core sketch. */
+#define ID_MAX_ELL 256
+
+typedef struct {
+    int32_t k;               /* target rank when rel_tol == 0 (Algorithm 1 line 2) */
+    double rel_tol;          /* > 0: rank = smallest k with ||R22||_F <= rel_tol ||W||_F,
+                                W the matrix being pivoted (A or Y), capped by k_max */
+    int32_t k_max;           /* cap for rel_tol mode (and T's row capacity) */
+    int32_t sketch;          /* 0: pivot A itself; 1: pivot Y = Omega A */
+    int32_t ell;             /* rows of Omega (k + oversampling) when sketch = 1 */
+    int32_t precision;       /* id_precision_t */
+    const void* omega;       /* device, ell x m row-major: bfloat16 bits (MIXED_BF16*),
+                                half bits (MIXED_F16), double (PLAIN_F64) */
+    int32_t refine_steps;    /* iterative-refinement steps of the T solve (default 1) */
+    int32_t estimate_error;  /* 1: write err_out = ||A - A(:,J)P||_F / ||A||_F (FP64) */
+    int64_t watchdog_iters;  /* poll limit of every device wait; 0 = default (~4 s) */
+} id_opts_t;
+
+/* Fill opts with defaults: k = 0, rel_tol = 0, k_max = 0, sketch = 0,
+ * ell = 0, precision = PLAIN_F64, omega = NULL, refine_steps = 1,
+ * estimate_error = 0, watchdog_iters = 0. */
+void id_opts_default(id_opts_t* opts);
+
+/* Device bytes of scratch id_factor needs for this problem (host call, no
+ * GPU work).  Returns ID_ERR_ARG / ID_ERR_UNSUPPORTED for invalid options. */
+id_status_t id_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n,
+                              const id_opts_t* opts, size_t* bytes);
+
+/* One column ID of A (m x n, column-major, lda >= m; dtype a_dtype).
+ *   Sketch (optional, Sec. 5 future work): Y = Omega A, ell x n.
+ *   Pivoted QR (Sec. 1.1, Algorithm 1 line 3): truncated Householder QR with
+ *   Businger-Golub pivoting and column-norm downdating on W = Y or A.
+ *   Coefficients (Algorithm 1 line 4): T = R11^-1 R12 in FP64.
+ * Outputs (device):
+ *   J      [n]  int32, J[0:k] the skeleton in pivot order, J[k:n] the rest
+ *   T      k_cap x (n - k) doubles, column-major, ldt >= k_cap where
+ *          k_cap = k (fixed rank) or k_max (rel_tol mode); only the first
+ *          k_out rows and n - k_out columns are meaningful
+ *   k_out  [1]  the rank used
+ *   info   [1]  status word (see above)
+ *   err_out[1]  nullable; relative Frobenius residual when estimate_error = 1
+ * Errors: ID_ERR_ARG for m, n < 1, lda < m, k outside [1, min(rows, n)],
+ * ell outside [k, min(m, ID_MAX_ELL)], null outputs, precision / dtype
+ * combinations not listed above (mixed precisions require sketch = 1;
+ * PLAIN_F32 requires a_dtype = ID_F32 and sketch = 0). */
+id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                      const id_opts_t* opts,
+                      int32_t* J, double* T, int64_t ldt, int32_t* k_out, int32_t* info,
+                      double* err_out, void* work, size_t work_bytes, void* stream);
+
+/* The sketch step alone (Sec. 5 "matrix sketching"; Algorithm 2 line 1 for
+ * the cast): Y = Omega A (ell x n, column-major, ldy >= ell).
+ * PLAIN_F64: Omega and Y are double.  MIXED_*: Omega is bfloat16/half bits,
+ * A is scaled per (ID_SCALE_BLOCK_ROWS rows, column) by a power of two,
+ * rounded to nearest-even in the low format (1-3 pieces), multiplied on the
+ * tensor cores with FP32 accumulation, and Y is float.  info (device, nullable)
+ * is set to -1 if A holds a non-finite value, else 0. */
+id_status_t id_sketch(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                      const void* omega, int32_t ell, int32_t precision,
+                      void* Y, int64_t ldy, int32_t* info,
+                      void* work, size_t work_bytes, void* stream);
+
+/* Scratch bytes id_sketch needs. */
+id_status_t id_sketch_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, int32_t ell,
+                                     int32_t precision, size_t* bytes);
+
+/* The scaled low-precision cast of Algorithm 2 line 1 on its own, as the
+ * mixed sketch performs it: for every block of ID_SCALE_BLOCK_ROWS rows of a
+ * column, shift s = exponent that puts the block's largest magnitude in
+ * [0.5, 1) (bfloat16) or [2^13, 2^14) (half), zero block -> 0; each entry x
+ * becomes nsplit pieces q_t = fl(x 2^-s - q_0 - ... - q_{t-1}).
+ * Outputs: pieces, nsplit consecutive m x n column-major uint16 matrices
+ * (ld = m) of format bits; shifts, ceil(m / ID_SCALE_BLOCK_ROWS) x n int32
+ * column-major.  precision selects the format and nsplit (MIXED_BF16: 1,
+ * MIXED_BF16X2: 2, MIXED_BF16X3: 3, MIXED_F16: 1).  info as in id_sketch. */
+id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                          int32_t precision, uint16_t* pieces, int32_t* shifts,
+                          int32_t* info, void* stream);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* id_status_string(id_status_t status);
+
+/* Library version string (static). */
+const char* id_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_ID_H */

@@ -55,12 +55,12 @@ def _L():
             lib.orc_sketch_f64.argtypes = [p, i64, i64, p, i64, i64, p, i64]
             lib.orc_round_fmt.argtypes = [d, ctypes.c_int]
             lib.orc_round_fmt.restype = d
-            lib.orc_block_shift.argtypes = [d, ctypes.c_int]
+            lib.orc_block_shift.argtypes = [d, ctypes.c_int, ctypes.c_int]
             lib.orc_block_shift.restype = ctypes.c_int
-            lib.orc_quantize.argtypes = [p, i64, i64, i64, ctypes.c_int, ctypes.c_int, i64, p, p]
+            lib.orc_quantize.argtypes = [p, i64, i64, i64, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, p, p]
             lib.orc_quantize.restype = ctypes.c_int
             lib.orc_sketch_lowp.argtypes = [p, i64, i64, p, i64, i64, ctypes.c_int, ctypes.c_int,
-                                            i64, p, i64]
+                                            i64, ctypes.c_int, p, i64]
             lib.orc_sketch_lowp.restype = ctypes.c_int
             lib.orc_cpqr.argtypes = [p, i64, i64, i64, i32, d, i32, i32, p, p, i64, p, p]
             lib.orc_cpqr.restype = ctypes.c_int
@@ -101,35 +101,40 @@ def round_fmt(x: float, fmt: str) -> float:
     return _L().orc_round_fmt(float(x), _FMT[fmt])
 
 
-def block_shift(mx: float, fmt: str) -> int:
-    return _L().orc_block_shift(float(mx), _FMT[fmt])
+def block_shift(mx: float, fmt: str, in_f32: bool = False) -> int:
+    """Power-of-two shift of a scaling block from its largest magnitude."""
+    return _L().orc_block_shift(float(mx), _FMT[fmt], int(in_f32))
 
 
 def quantize(a: np.ndarray, fmt: str, block_rows: int, nsplit: int = 1):
     """Scaled cast of Algorithm 2 line 1 with per-(row block, column) power-of-two shifts.
 
-    Returns ``(pieces, shifts, rc)``: pieces (nsplit, m, n) float64 values of the
-    low-format pieces, shifts (nblocks, n) int32, rc = -1 on non-finite input.
+    Each scaled entry is taken at FP32 precision (round to nearest even) and split
+    into ``nsplit`` low-format pieces.  ``a`` of dtype float32 is treated as float
+    storage.  Returns ``(pieces, shifts, rc)``: pieces (nsplit, m, n) float64 values
+    of the low-format pieces, shifts (nblocks, n) int32, rc = -1 on non-finite input.
     """
+    in_f32 = int(np.asarray(a).dtype == np.float32)
     a = _f64(a)
     m, n = a.shape
     nb = (m + block_rows - 1) // block_rows
     q = np.zeros(nsplit * m * n, dtype=np.float64)
     s = np.zeros(nb * n, dtype=np.int32)
-    rc = _L().orc_quantize(_ptr(a), m, n, m, _FMT[fmt], nsplit, block_rows, _ptr(q), _ptr(s))
+    rc = _L().orc_quantize(_ptr(a), m, n, m, _FMT[fmt], nsplit, block_rows, in_f32, _ptr(q), _ptr(s))
     pieces = q.reshape(nsplit, n, m).transpose(0, 2, 1)
     return pieces, s.reshape(n, nb).T.copy(), rc
 
 
 def sketch_lowp(omega: np.ndarray, a: np.ndarray, fmt: str, nsplit: int, block_rows: int):
     """FP64 evaluation of the sketch of the scaled low-precision cast of A."""
+    in_f32 = int(np.asarray(a).dtype == np.float32)
     om = np.ascontiguousarray(omega, dtype=np.float64)
     a = _f64(a)
     ell, m = om.shape
     n = a.shape[1]
     y = np.zeros((ell, n), dtype=np.float64, order="F")
     rc = _L().orc_sketch_lowp(_ptr(om), ell, m, _ptr(a), m, n, _FMT[fmt], nsplit, block_rows,
-                              _ptr(y), ell)
+                              in_f32, _ptr(y), ell)
     if rc == -2:
         raise MemoryError("oracle sketch_lowp")
     return y, rc

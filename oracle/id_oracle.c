@@ -26,9 +26,10 @@
  *     future work in Sec. 5);
  *   - the low-precision cast of Algorithm 2 (A_L = fl(A)) as round-to-
  *     nearest-even to bfloat16 or IEEE half after an exact power-of-two
- *     scaling of each block of rows of each column, and the sketch of the
- *     cast matrix evaluated exactly enough (FP64) to bound an FP32-
- *     accumulated sketch.
+ *     scaling of each block of rows of each column (the scaled value is
+ *     taken at FP32 precision first, then split into 1-3 low-format
+ *     pieces), and the sketch of the cast matrix evaluated exactly enough
+ *     (FP64) to bound an FP32-accumulated sketch.
  *
  * Storage: matrices are column-major with an explicit leading dimension.
  * Omega is row-major (ell x m, row i contiguous).  Column indices are 0-based.
@@ -90,10 +91,13 @@ double orc_round_fmt(double x, int fmt)
 
 /* Power-of-two shift s for a block whose largest magnitude is mx:
  * bfloat16 places mx * 2^-s in [0.5, 1); half places it in [2^13, 2^14).
- * A zero block gets s = 0. */
-int orc_block_shift(double mx, int fmt)
+ * The shift is read from the binary exponent of mx, so a block whose largest
+ * magnitude is zero or subnormal in the input format (below 2^-1022 for
+ * double input, 2^-126 for float input) gets s = 0. */
+int orc_block_shift(double mx, int fmt, int in_f32)
 {
-    if (mx == 0.0) return 0;
+    double tiny = in_f32 ? ldexp(1.0, -126) : DBL_MIN;
+    if (!(mx >= tiny)) return 0;
     int e2;
     (void)frexp(mx, &e2);
     return fmt == 0 ? e2 : e2 - 14;
@@ -101,14 +105,17 @@ int orc_block_shift(double mx, int fmt)
 
 /* Scaled cast of A (Algorithm 2 line 1, A_L = fl(A)) with per-(block, column)
  * power-of-two scaling.  Rows are split in blocks of block_rows; block b of
- * column j gets shift s(b,j) from its largest magnitude and its entries become
- * pieces of x 2^-s(b,j): piece 0 = fl(x), piece 1 = fl(x - piece0), piece 2 =
- * fl(x - piece0 - piece1) (nsplit = 1, 2 or 3).  Outputs (as doubles):
+ * column j gets shift s(b,j) from its largest magnitude.  Each entry is scaled
+ * by 2^-s(b,j) and rounded to the nearest FP32 value (ties to even; exact for
+ * FP32 inputs), x32 = fl32(x 2^-s); x32 is then split into low-format pieces
+ * piece 0 = fl(x32), piece 1 = fl(x32 - piece0), piece 2 = fl(x32 - piece0 -
+ * piece1) (nsplit = 1, 2 or 3; three bfloat16 pieces sum to x32 exactly).
+ * in_f32 says the values of A came from float storage.  Outputs (doubles):
  *   Q: nsplit consecutive m x n col-major matrices (ld = m) of piece values,
  *   S: shifts, nblocks x n col-major (ld = nblocks).
  * Returns 0, or -1 if A holds a non-finite value. */
 int orc_quantize(const double* A, int64_t m, int64_t n, int64_t lda,
-                 int fmt, int nsplit, int64_t block_rows,
+                 int fmt, int nsplit, int64_t block_rows, int in_f32,
                  double* Q, int32_t* S)
 {
     int64_t nb = (m + block_rows - 1) / block_rows;
@@ -122,13 +129,13 @@ int orc_quantize(const double* A, int64_t m, int64_t n, int64_t lda,
                 if (!isfinite(a)) bad = 1;
                 if (fabs(a) > mx) mx = fabs(a);
             }
-            int s = orc_block_shift(mx, fmt);
+            int s = orc_block_shift(mx, fmt, in_f32);
             S[j * nb + b] = s;
             for (int64_t i = r0; i < r1; ++i) {
-                double x = ldexp(A_(A, lda, i, j), -s);
+                double x32 = (double)(float)ldexp(A_(A, lda, i, j), -s);
                 double acc = 0.0;
                 for (int t = 0; t < nsplit; ++t) {
-                    double piece = orc_round_fmt(x - acc, fmt);
+                    double piece = orc_round_fmt(x32 - acc, fmt);
                     Q[(int64_t)t * m * n + j * m + i] = piece;
                     acc += piece;
                 }
@@ -143,14 +150,14 @@ int orc_quantize(const double* A, int64_t m, int64_t n, int64_t lda,
  * evaluation of the same quantity. */
 int orc_sketch_lowp(const double* omega, int64_t ell, int64_t m,
                     const double* A, int64_t lda, int64_t n,
-                    int fmt, int nsplit, int64_t block_rows,
+                    int fmt, int nsplit, int64_t block_rows, int in_f32,
                     double* Y, int64_t ldy)
 {
     int64_t nb = (m + block_rows - 1) / block_rows;
     double* Q = (double*)malloc(sizeof(double) * (size_t)(nsplit * m * n));
     int32_t* S = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nb * n));
     if (!Q || !S) { free(Q); free(S); return -2; }
-    int rc = orc_quantize(A, m, n, lda, fmt, nsplit, block_rows, Q, S);
+    int rc = orc_quantize(A, m, n, lda, fmt, nsplit, block_rows, in_f32, Q, S);
     for (int64_t j = 0; j < n; ++j)
         for (int64_t i = 0; i < ell; ++i) {
             double y = 0.0;

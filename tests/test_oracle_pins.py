@@ -154,8 +154,8 @@ def test_block_shift_range(orc, fmt, lo, hi):
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
 def test_quantize_error_bounds(orc, fmt):
-    """Pieces reconstruct x 2^-s within the format's unit round-off (1 piece) and
-    within u^3-ish (3 pieces); shifts follow the block maxima."""
+    """Pieces reconstruct x 2^-s within the format's unit round-off (1 piece) and to
+    FP32 accuracy (3 pieces); shifts follow the block maxima."""
     rng = np.random.default_rng(4)
     a = np.asfortranarray(rng.standard_normal((70, 5)) * 10.0 ** rng.uniform(-3, 3, (70, 5)))
     u = 2.0 ** -8 if fmt == "bf16" else 2.0 ** -11
@@ -166,13 +166,37 @@ def test_quantize_error_bounds(orc, fmt):
         scale = np.repeat(2.0 ** shifts, 32, axis=0)[:70]
         back = pieces.sum(axis=0) * scale
         err = np.abs(back - a)
-        # bound: each piece adds a relative factor u (subnormal half values add an absolute term)
-        bound = (u ** nsplit) * np.abs(a) * 1.0001 + (2.0 ** -24) * scale * (fmt == "f16")
+        # each piece adds a relative factor u; the FP32 step adds 2^-24; subnormal
+        # half pieces add an absolute 2^-25 (half of the smallest subnormal)
+        bound = (u ** nsplit + 2.0 ** -24) * np.abs(a) * 1.0001 + 2.0 ** -25 * scale * (fmt == "f16")
         assert np.all(err <= bound)
         for b in range(3):
             mx = np.max(np.abs(a[b * 32:(b + 1) * 32]), axis=0)
             for j in range(5):
                 assert shifts[b, j] == orc.block_shift(mx[j], fmt)
+
+
+def test_quantize_three_bf16_pieces_are_fp32_value(orc):
+    """Reading of the cast: the scaled value is taken at FP32 first; three bfloat16
+    pieces then sum to fl32(x 2^-s) exactly, for double and float storage."""
+    rng = np.random.default_rng(14)
+    a = rng.standard_normal((128, 6)) * 10.0 ** rng.uniform(-5, 5, (128, 6))
+    for arr in (np.asfortranarray(a), np.asfortranarray(a.astype(np.float32))):
+        pieces, shifts, rc = orc.quantize(arr, "bf16", 64, 3)
+        scale = np.repeat(2.0 ** shifts, 64, axis=0)
+        x32 = (arr.astype(np.float64) / scale).astype(np.float32).astype(np.float64)
+        assert np.array_equal(pieces.sum(axis=0), x32)
+        # piece 0 is a bfloat16 value: its low 16 float bits are zero
+        p0 = pieces[0].astype(np.float32).view(np.uint32)
+        assert np.all(p0 & 0xFFFF == 0)
+
+
+def test_block_shift_zero_and_subnormal(orc):
+    """Zero or input-subnormal block maxima get shift 0."""
+    assert orc.block_shift(0.0, "bf16") == 0
+    assert orc.block_shift(2.0 ** -1070, "bf16") == 0
+    assert orc.block_shift(2.0 ** -130, "f16", in_f32=True) == 0
+    assert orc.block_shift(2.0 ** -130, "bf16") == -129
 
 
 def test_sketch_lowp_limits(orc):
