@@ -95,14 +95,17 @@ typedef struct {
     int32_t precision;       /* id_precision_t */
     const void* omega;       /* device, ell x m row-major: bfloat16 bits (MIXED_BF16*),
                                 half bits (MIXED_F16), double (PLAIN_F64) */
+    int64_t omega_ld;        /* row stride of omega in elements (>= m; 0 means m).  The
+                                tensor-core sketch reads omega with TMA: it needs
+                                omega 16-byte aligned and omega_ld a multiple of 8 */
     int32_t refine_steps;    /* iterative-refinement steps of the T solve (default 1) */
     int32_t estimate_error;  /* 1: write err_out = ||A - A(:,J)P||_F / ||A||_F (FP64) */
-    int64_t watchdog_iters;  /* poll limit of every device wait; 0 = default (~4 s) */
+    int64_t watchdog_ms;     /* time limit of every device wait in ms; 0 = default (4000) */
 } id_opts_t;
 
 /* Fill opts with defaults: k = 0, rel_tol = 0, k_max = 0, sketch = 0,
- * ell = 0, precision = PLAIN_F64, omega = NULL, refine_steps = 1,
- * estimate_error = 0, watchdog_iters = 0. */
+ * ell = 0, precision = PLAIN_F64, omega = NULL, omega_ld = 0,
+ * refine_steps = 1, estimate_error = 0, watchdog_ms = 0. */
 void id_opts_default(id_opts_t* opts);
 
 /* Device bytes of scratch id_factor needs for this problem (host call, no
@@ -140,7 +143,7 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
  * tensor cores with FP32 accumulation, and Y is float.  info (device, nullable)
  * is set to -1 if A holds a non-finite value, else 0. */
 id_status_t id_sketch(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
-                      const void* omega, int32_t ell, int32_t precision,
+                      const void* omega, int64_t omega_ld, int32_t ell, int32_t precision,
                       void* Y, int64_t ldy, int32_t* info,
                       void* work, size_t work_bytes, void* stream);
 

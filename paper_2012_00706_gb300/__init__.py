@@ -1,0 +1,235 @@
+"""GB300 column interpolative decomposition: thin Python binding over libgb300id.
+
+The column ID of Dunton & Fox (Sec. 1.1) approximates A (m x n) by k of its
+own columns, A ~= A(:, J[:k]) P with P(:, J[:k]) = I and P(:, J[k:]) = T.  All
+arithmetic runs in the hand-written sm_103a kernels of ``libgb300id.so``; this
+module only marshals torch tensors (device memory, the current stream, a
+workspace buffer) into the C ABI declared in ``include/gb300_id.h``.  There is
+no CPU fallback: if the native library is missing or there is no GPU, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import torch
+
+__all__ = [
+    "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
+    "status_string", "lib_path",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_NAME = "libgb300id.so"
+_lib = None
+_lock = threading.Lock()
+
+PRECISIONS = {
+    "plain_f64": 0, "plain_f32": 1, "mixed_bf16": 2, "mixed_f16": 3, "mixed_bf16x2": 4, "mixed_bf16x3": 5,
+}
+_DTYPE = {torch.float64: 0, torch.float32: 1}
+ID_SCALE_BLOCK_ROWS = 64
+ID_MAX_ELL = 256
+
+
+class IDOpts(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int32), ("rel_tol", ctypes.c_double), ("k_max", ctypes.c_int32),
+        ("sketch", ctypes.c_int32), ("ell", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("omega", ctypes.c_void_p), ("omega_ld", ctypes.c_int64), ("refine_steps", ctypes.c_int32),
+        ("estimate_error", ctypes.c_int32), ("watchdog_ms", ctypes.c_int64),
+    ]
+
+
+class IDError(RuntimeError):
+    pass
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, _LIB_NAME)
+
+
+def load():
+    """Load (building first if needed) the native library; raise if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+        lib = ctypes.CDLL(path)
+        p, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        lib.id_opts_default.argtypes = [ctypes.POINTER(IDOpts)]
+        lib.id_status_string.argtypes = [ctypes.c_int]
+        lib.id_status_string.restype = ctypes.c_char_p
+        lib.id_version.restype = ctypes.c_char_p
+        lib.id_workspace_size.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(IDOpts), ctypes.POINTER(sz)]
+        lib.id_factor.argtypes = [p, ctypes.c_int, i64, i64, i64, ctypes.POINTER(IDOpts), p, p, i64, p, p, p,
+                                  p, sz, p]
+        lib.id_sketch_workspace_size.argtypes = [ctypes.c_int, i64, i64, i32, i32, ctypes.POINTER(sz)]
+        lib.id_sketch.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i64, i32, i32, p, i64, p, p, sz, p]
+        lib.id_scale_cast.argtypes = [p, ctypes.c_int, i64, i64, i64, i32, p, p, p, p]
+        for name in ("id_workspace_size", "id_factor", "id_sketch_workspace_size", "id_sketch",
+                     "id_scale_cast"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def status_string(code: int) -> str:
+    return load().id_status_string(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise IDError(f"{what}: {status_string(code)}")
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _colmajor(a: torch.Tensor):
+    """(tensor, ld) with column-major storage of the (m, n) matrix a."""
+    if a.dim() != 2:
+        raise ValueError("expected a 2-D matrix")
+    m, n = a.shape
+    if a.stride(0) == 1 and (n == 1 or a.stride(1) >= max(m, 1)):
+        return a, max(a.stride(1), m) if n > 1 else m
+    return a.t().contiguous().t(), m
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("the GB300 ID library works on CUDA tensors only")
+
+
+@dataclasses.dataclass
+class IDResult:
+    J: torch.Tensor        # (n,) int32: skeleton J[:k] in pivot order, then the rest ascending
+    T: torch.Tensor        # (k, n - k) float64 interpolation coefficients
+    k: int                 # rank used
+    info: int              # 0 ok, j > 0 rank reduced, -1 non-finite input, -2 watchdog
+    err: float | None      # relative Frobenius residual when requested
+
+
+def _opts(k, tol, k_max, precision, sketch, ell, omega, omega_ld, refine_steps, estimate_error, watchdog_ms):
+    o = IDOpts()
+    load().id_opts_default(ctypes.byref(o))
+    o.k = int(k or 0)
+    o.rel_tol = float(tol or 0.0)
+    o.k_max = int(k_max or 0)
+    o.sketch = 1 if sketch else 0
+    o.ell = int(ell or 0)
+    o.precision = PRECISIONS[precision]
+    o.omega = omega.data_ptr() if omega is not None else None
+    o.omega_ld = int(omega_ld or 0)
+    o.refine_steps = int(refine_steps)
+    o.estimate_error = 1 if estimate_error else 0
+    o.watchdog_ms = int(watchdog_ms or 0)
+    return o
+
+
+def _omega_ld(omega):
+    if omega is None:
+        return 0
+    if omega.dim() != 2 or omega.stride(1) != 1:
+        raise ValueError("omega must be a row-major (ell, m) tensor")
+    return omega.stride(0)
+
+
+def id_workspace_size(m, n, dtype=torch.float64, **kw) -> int:
+    o = _opts(kw.get("k"), kw.get("tol"), kw.get("k_max"), kw.get("precision", "plain_f64"),
+              kw.get("sketch", False), kw.get("ell"), kw.get("omega"), _omega_ld(kw.get("omega")),
+              kw.get("refine_steps", 1), kw.get("estimate_error", False), 0)
+    nb = ctypes.c_size_t(0)
+    _check(load().id_workspace_size(_DTYPE[dtype], m, n, ctypes.byref(o), ctypes.byref(nb)), "id_workspace_size")
+    return nb.value
+
+
+def id_factor(A: torch.Tensor, k: int | None = None, *, tol: float | None = None, k_max: int | None = None,
+              precision: str = "plain_f64", omega: torch.Tensor | None = None, refine_steps: int = 1,
+              estimate_error: bool = False, watchdog_ms: int = 0, stream=None, workspace=None,
+              out=None, sync: bool = True) -> IDResult:
+    """Column ID of the CUDA matrix A (m, n); sketched when ``omega`` (ell, m) is given.
+
+    ``precision``: plain_f64 | plain_f32 | mixed_bf16 | mixed_f16 | mixed_bf16x2 | mixed_bf16x3
+    (mixed precisions need ``omega`` in bfloat16/half; plain_f64 sketches with a float64 omega).
+    With ``sync=False`` the result tensors are returned without waiting; k and info are then -1.
+    """
+    _require_cuda(A, omega)
+    if A.dtype not in _DTYPE:
+        raise ValueError("A must be float64 or float32")
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    sketch = omega is not None
+    ell = omega.shape[0] if sketch else 0
+    if tol is None and k is None:
+        raise ValueError("give a rank k or a tolerance tol")
+    kcap = int(k_max if tol is not None else k)
+    o = _opts(k, tol, k_max, precision, sketch, ell, omega, _omega_ld(omega), refine_steps, estimate_error,
+              watchdog_ms)
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.id_workspace_size(_DTYPE[A.dtype], m, n, ctypes.byref(o), ctypes.byref(nb)), "id_workspace_size")
+    dev = a.device
+    if workspace is None or workspace.numel() < nb.value:
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    if out is None:
+        J = torch.empty(n, dtype=torch.int32, device=dev)
+        T = torch.empty((max(n - 1, 1), kcap), dtype=torch.float64, device=dev).t()   # column-major, ld = kcap
+        small = torch.zeros(2, dtype=torch.int32, device=dev)
+        err = torch.zeros(1, dtype=torch.float64, device=dev)
+    else:
+        J, T, small, err = out
+    code = lib.id_factor(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, ctypes.byref(o), J.data_ptr(), T.data_ptr(),
+                         kcap, small.data_ptr(), small.data_ptr() + 4, err.data_ptr() if estimate_error else None,
+                         workspace.data_ptr(), workspace.numel(), _stream_ptr(stream))
+    _check(code, "id_factor")
+    if not sync:
+        return IDResult(J, T, -1, -1, None)
+    kk, info = (int(v) for v in small.cpu())
+    return IDResult(J, T[:kk, : n - kk], kk, info, float(err.item()) if estimate_error else None)
+
+
+def id_sketch(A: torch.Tensor, omega: torch.Tensor, precision: str = "mixed_bf16", stream=None) -> torch.Tensor:
+    """Y = Omega A (ell, n): float32 for the mixed precisions, float64 for plain_f64."""
+    _require_cuda(A, omega)
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    ell = omega.shape[0]
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.id_sketch_workspace_size(_DTYPE[A.dtype], m, n, ell, PRECISIONS[precision], ctypes.byref(nb)),
+           "id_sketch_workspace_size")
+    work = torch.empty(nb.value, dtype=torch.uint8, device=a.device)
+    ydt = torch.float64 if precision == "plain_f64" else torch.float32
+    Y = torch.empty((n, ell), dtype=ydt, device=a.device).t()      # column-major (ell, n)
+    info = torch.zeros(1, dtype=torch.int32, device=a.device)
+    _check(lib.id_sketch(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, omega.data_ptr(), _omega_ld(omega), ell,
+                         PRECISIONS[precision], Y.data_ptr(), ell, info.data_ptr(), work.data_ptr(), work.numel(),
+                         _stream_ptr(stream)), "id_sketch")
+    return Y
+
+
+def id_scale_cast(A: torch.Tensor, precision: str = "mixed_bf16", stream=None):
+    """The sketch's scaled cast on its own: (pieces (nsplit, m, n) uint16 bits, shifts (nblocks, n), info)."""
+    _require_cuda(A)
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    nsplit = {"mixed_bf16": 1, "mixed_f16": 1, "mixed_bf16x2": 2, "mixed_bf16x3": 3}[precision]
+    nb = (m + ID_SCALE_BLOCK_ROWS - 1) // ID_SCALE_BLOCK_ROWS
+    pieces = torch.empty((nsplit, n, m), dtype=torch.int16, device=a.device)
+    shifts = torch.empty((n, nb), dtype=torch.int32, device=a.device)
+    info = torch.zeros(1, dtype=torch.int32, device=a.device)
+    _check(load().id_scale_cast(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, PRECISIONS[precision],
+                                pieces.data_ptr(), shifts.data_ptr(), info.data_ptr(), _stream_ptr(stream)),
+           "id_scale_cast")
+    return pieces.transpose(1, 2), shifts.t(), info

@@ -1,0 +1,290 @@
+// C ABI of the GB300 column-ID library: argument checks, workspace planning
+// and the launch sequence of one ID (sketch -> pivoted QR -> coefficient solve
+// -> optional error estimate), all enqueued on the caller's stream.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+namespace gid {
+
+const DeviceInfo& device_info() {
+    static std::mutex mu;
+    static std::vector<DeviceInfo> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        dev = 0;
+        cudaGetLastError();
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (static_cast<int>(cache.size()) <= dev) cache.resize(dev + 1);
+    DeviceInfo& d = cache[dev];
+    if (d.sm_count == 0) {
+        cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+        // without a device (host-only planning) assume the GB300 target: 152 SMs, 227 KB
+        if (d.sm_count <= 0) d.sm_count = 152;
+        if (d.max_smem_optin <= 0) d.max_smem_optin = 232448;
+    }
+    return d;
+}
+
+namespace {
+
+uint64_t limit_ns_of(const id_opts_t& o) {
+    const int64_t ms = o.watchdog_ms > 0 ? o.watchdog_ms : 4000;
+    return static_cast<uint64_t>(ms) * 1000000ull;
+}
+
+bool is_mixed(int p) {
+    return p == ID_MIXED_BF16 || p == ID_MIXED_F16 || p == ID_MIXED_BF16X2 || p == ID_MIXED_BF16X3;
+}
+
+// Everything id_factor derives from its arguments before touching the GPU.
+struct FactorPlan {
+    int64_t rows = 0;       // rows of the matrix being pivoted (ell or m)
+    int kcap = 0;           // rank capacity (k or k_max)
+    int w_f64 = 1;          // working precision of the pivoted QR
+    int mixed = 0, sketch = 0;
+    int64_t omega_ld = 0;
+    SketchPlan sp;
+    SketchF64Plan sp64;
+    CpqrPlan cp;
+    size_t bytes = 0;
+};
+
+struct FactorPtrs {
+    void* ctrl;
+    uint8_t* sel;
+    void* nu;
+    void* nuref;
+    void* W;
+    void* partial;
+    double* R64;
+    double* tscr;
+    double* acc;
+};
+
+size_t carve_factor(void* base, int64_t n, const FactorPlan& p, FactorPtrs* out) {
+    Carver c(base);
+    const int elem = p.w_f64 ? 8 : 4;
+    FactorPtrs f{};
+    f.ctrl = c.take<uint8_t>(cpqr_ctrl_bytes(p.cp, p.rows, elem));
+    f.sel = c.take<uint8_t>(static_cast<size_t>(n));
+    f.nu = c.take<uint8_t>(static_cast<size_t>(n) * elem);
+    f.nuref = c.take<uint8_t>(static_cast<size_t>(n) * elem);
+    f.W = c.take<uint8_t>(static_cast<size_t>(p.rows) * n * elem);
+    if (p.sketch) {
+        if (p.mixed) f.partial = c.take<uint8_t>(sketch_partial_bytes_lowp(p.sp, n));
+        else f.partial = c.take<double>(static_cast<size_t>(p.sp64.kslabs) * n * p.sp64.lp);
+    }
+    f.R64 = c.take<double>(static_cast<size_t>(p.kcap) * n);
+    f.tscr = c.take<double>(solve_T_scratch_doubles(p.kcap, n));
+    f.acc = c.take<double>(4);
+    if (out) *out = f;
+    return c.off + 256;
+}
+
+id_status_t plan_factor(id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, const id_opts_t* o,
+                        FactorPlan* plan) {
+    if (!o || m < 1 || n < 1 || lda < m) return ID_ERR_ARG;
+    if (a_dtype != ID_F64 && a_dtype != ID_F32) return ID_ERR_ARG;
+    if (n > (int64_t(1) << 31) - 1) return ID_ERR_UNSUPPORTED;
+    FactorPlan p;
+    const int prec = o->precision;
+    if (prec < ID_PLAIN_F64 || prec > ID_MIXED_BF16X3) return ID_ERR_ARG;
+    p.mixed = is_mixed(prec);
+    p.sketch = o->sketch ? 1 : 0;
+    if (p.mixed && !p.sketch) return ID_ERR_ARG;
+    if (prec == ID_PLAIN_F32 && p.sketch) return ID_ERR_ARG;
+    p.w_f64 = (prec == ID_PLAIN_F64) ? 1 : 0;
+    if (p.sketch) {
+        if (o->ell < 1 || o->ell > m || !o->omega) return ID_ERR_ARG;
+        if (p.mixed && o->ell > ID_MAX_ELL) return ID_ERR_ARG;
+        if (prec == ID_PLAIN_F64 && a_dtype != ID_F64) return ID_ERR_ARG;
+        p.rows = o->ell;
+        p.omega_ld = o->omega_ld > 0 ? o->omega_ld : m;
+        if (p.omega_ld < m) return ID_ERR_ARG;
+        if (p.mixed && ((p.omega_ld % 8) != 0 || (reinterpret_cast<uintptr_t>(o->omega) & 15u) != 0))
+            return ID_ERR_ARG;
+    } else {
+        p.rows = m;
+    }
+    const int64_t kmax_possible = std::min<int64_t>(p.rows, n);
+    if (o->rel_tol > 0.0) {
+        if (o->k_max < 1 || o->k_max > kmax_possible) return ID_ERR_ARG;
+        p.kcap = o->k_max;
+    } else {
+        if (o->rel_tol < 0.0 || o->k < 1 || o->k > kmax_possible) return ID_ERR_ARG;
+        p.kcap = o->k;
+    }
+    if (o->refine_steps < 0) return ID_ERR_ARG;
+    if (p.sketch) {
+        if (p.mixed) {
+            if (!sketch_plan_lowp(m, n, o->ell, a_dtype == ID_F64, precision_nsplit(prec), &p.sp))
+                return ID_ERR_UNSUPPORTED;
+        } else {
+            sketch_plan_f64(m, n, o->ell, &p.sp64);
+        }
+    }
+    cpqr_plan(p.rows, n, p.w_f64 ? 8 : 4, &p.cp);
+    p.bytes = carve_factor(nullptr, n, p, nullptr);
+    *plan = p;
+    return ID_OK;
+}
+
+}  // namespace
+}  // namespace gid
+
+using namespace gid;
+
+extern "C" {
+
+void id_opts_default(id_opts_t* o) {
+    if (!o) return;
+    o->k = 0;
+    o->rel_tol = 0.0;
+    o->k_max = 0;
+    o->sketch = 0;
+    o->ell = 0;
+    o->precision = ID_PLAIN_F64;
+    o->omega = nullptr;
+    o->omega_ld = 0;
+    o->refine_steps = 1;
+    o->estimate_error = 0;
+    o->watchdog_ms = 0;
+}
+
+const char* id_status_string(id_status_t s) {
+    switch (s) {
+        case ID_OK: return "ID_OK: success";
+        case ID_ERR_ARG: return "ID_ERR_ARG: invalid argument";
+        case ID_ERR_WORKSPACE: return "ID_ERR_WORKSPACE: workspace smaller than id_workspace_size()";
+        case ID_ERR_CUDA: return "ID_ERR_CUDA: a CUDA runtime call failed";
+        case ID_ERR_TIMEOUT: return "ID_ERR_TIMEOUT: a device wait gave up (watchdog)";
+        case ID_ERR_UNSUPPORTED: return "ID_ERR_UNSUPPORTED: shape or option not supported";
+    }
+    return "unknown status";
+}
+
+const char* id_version(void) { return "gb300-id 0.1 (sm_103a)"; }
+
+id_status_t id_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts, size_t* bytes) {
+    if (!bytes) return ID_ERR_ARG;
+    FactorPlan p;
+    const id_status_t st = plan_factor(a_dtype, m, n, m, opts, &p);
+    if (st != ID_OK) return st;
+    *bytes = p.bytes;
+    return ID_OK;
+}
+
+id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, const id_opts_t* opts,
+                      int32_t* J, double* T, int64_t ldt, int32_t* k_out, int32_t* info, double* err_out,
+                      void* work, size_t work_bytes, void* stream) {
+    if (!A || !J || !T || !k_out || !info || !work) return ID_ERR_ARG;
+    FactorPlan p;
+    id_status_t st = plan_factor(a_dtype, m, n, lda, opts, &p);
+    if (st != ID_OK) return st;
+    if (ldt < p.kcap) return ID_ERR_ARG;
+    if (opts->estimate_error && !err_out) return ID_ERR_ARG;
+    if (work_bytes < p.bytes) return ID_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FactorPtrs f;
+    void* aligned = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
+    carve_factor(aligned, n, p, &f);
+    const uint64_t lim = limit_ns_of(*opts);
+    const int a_f64 = a_dtype == ID_F64;
+
+    cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(k_out, 0, sizeof(int32_t), s);
+    const void* cpqr_src = nullptr;
+    int64_t ldsrc = 0;
+    if (e == cudaSuccess && p.sketch) {
+        if (p.mixed) {
+            e = launch_sketch_lowp(A, a_f64, m, n, lda, static_cast<const uint16_t*>(opts->omega), p.omega_ld,
+                                   opts->ell, opts->precision, p.sp, static_cast<float*>(f.partial),
+                                   static_cast<float*>(f.W), opts->ell, info, lim, s);
+        } else {
+            e = launch_sketch_f64(static_cast<const double*>(A), m, n, lda,
+                                  static_cast<const double*>(opts->omega), p.omega_ld, opts->ell, p.sp64,
+                                  static_cast<double*>(f.partial), static_cast<double*>(f.W), opts->ell, info, s);
+        }
+    } else if (e == cudaSuccess) {
+        cpqr_src = A;
+        ldsrc = lda;
+    }
+    if (e == cudaSuccess)
+        e = launch_cpqr(f.W, p.w_f64, p.rows, n, p.rows, cpqr_src, a_f64, ldsrc, p.kcap,
+                        opts->rel_tol > 0.0 ? opts->rel_tol : 0.0, J, k_out, info, f.R64, p.kcap, f.nu,
+                        f.nuref, f.sel, f.ctrl, p.cp, lim, s);
+    if (e == cudaSuccess)
+        e = launch_solve_T(f.R64, p.kcap, J, k_out, p.kcap, n, T, ldt, f.tscr, opts->refine_steps, s);
+    if (e == cudaSuccess && opts->estimate_error)
+        e = launch_residual_fro(A, a_f64, m, n, lda, J, k_out, T, ldt, f.acc, err_out, s);
+    return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
+}
+
+id_status_t id_sketch_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, int32_t ell, int32_t precision,
+                                     size_t* bytes) {
+    if (!bytes || m < 1 || n < 1 || ell < 1 || ell > m) return ID_ERR_ARG;
+    if (precision == ID_PLAIN_F64) {
+        if (a_dtype != ID_F64) return ID_ERR_ARG;
+        SketchF64Plan sp;
+        sketch_plan_f64(m, n, ell, &sp);
+        *bytes = static_cast<size_t>(sp.kslabs) * n * sp.lp * sizeof(double) + 512;
+        return ID_OK;
+    }
+    if (!is_mixed(precision) || ell > ID_MAX_ELL) return ID_ERR_ARG;
+    SketchPlan sp;
+    if (!sketch_plan_lowp(m, n, ell, a_dtype == ID_F64, precision_nsplit(precision), &sp)) return ID_ERR_UNSUPPORTED;
+    *bytes = sketch_partial_bytes_lowp(sp, n) + 512;
+    return ID_OK;
+}
+
+id_status_t id_sketch(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, const void* omega,
+                      int64_t omega_ld, int32_t ell, int32_t precision, void* Y, int64_t ldy, int32_t* info,
+                      void* work, size_t work_bytes, void* stream) {
+    if (!A || !omega || !Y || !work || lda < m || ldy < ell) return ID_ERR_ARG;
+    size_t need = 0;
+    id_status_t st = id_sketch_workspace_size(a_dtype, m, n, ell, precision, &need);
+    if (st != ID_OK) return st;
+    if (work_bytes < need) return ID_ERR_WORKSPACE;
+    const int64_t ldo = omega_ld > 0 ? omega_ld : m;
+    if (ldo < m) return ID_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* aligned = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
+    cudaError_t e = cudaSuccess;
+    if (info) e = cudaMemsetAsync(info, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return ID_ERR_CUDA;
+    if (precision == ID_PLAIN_F64) {
+        SketchF64Plan sp;
+        sketch_plan_f64(m, n, ell, &sp);
+        e = launch_sketch_f64(static_cast<const double*>(A), m, n, lda, static_cast<const double*>(omega), ldo, ell,
+                              sp, static_cast<double*>(aligned), static_cast<double*>(Y), ldy, info, s);
+    } else {
+        if ((ldo % 8) != 0 || (reinterpret_cast<uintptr_t>(omega) & 15u) != 0) return ID_ERR_ARG;
+        SketchPlan sp;
+        sketch_plan_lowp(m, n, ell, a_dtype == ID_F64, precision_nsplit(precision), &sp);
+        e = launch_sketch_lowp(A, a_dtype == ID_F64, m, n, lda, static_cast<const uint16_t*>(omega), ldo, ell,
+                               precision, sp, static_cast<float*>(aligned), static_cast<float*>(Y), ldy, info,
+                               4000000000ull, s);
+    }
+    return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
+}
+
+id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t precision,
+                          uint16_t* pieces, int32_t* shifts, int32_t* info, void* stream) {
+    if (!A || !pieces || !shifts || m < 1 || n < 1 || lda < m || !is_mixed(precision)) return ID_ERR_ARG;
+    if (a_dtype != ID_F64 && a_dtype != ID_F32) return ID_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (info) e = cudaMemsetAsync(info, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_scale_cast(A, a_dtype == ID_F64, m, n, lda, precision, pieces, shifts, info, s);
+    return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gb300_id.h"
+
+namespace gid {
+
+// Rows of one scaling / pipeline chunk of the tensor-core sketch.
+constexpr int kChunkRows = ID_SCALE_BLOCK_ROWS;
+// Columns of A per sketch CTA (the MMA's M).
+constexpr int kTileCols = 128;
+
+struct DeviceInfo {
+    int sm_count = 0;
+    int max_smem_optin = 0;
+    int cc_major = 0, cc_minor = 0;
+};
+const DeviceInfo& device_info();   // current device, cached
+
+// Bump allocator over the caller's workspace (256-byte alignment).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// ---- sketch (sketch.cu)
+struct SketchPlan {
+    int lp = 0;             // MMA N: ell rounded up to 16
+    int tiles = 0;          // ceil(n / 128)
+    int64_t nchunks = 0;    // ceil(m / 64)
+    int64_t chunks_per_slab = 0;
+    int kslabs = 0;
+    int stages = 0, aop_bufs = 0, omega_bufs = 0, acc_bufs = 0;
+    size_t smem_bytes = 0;
+};
+int precision_nsplit(int precision);
+int precision_is_f16(int precision);
+bool sketch_plan_lowp(int64_t m, int64_t n, int ell, int a_f64, int nsplit, SketchPlan* plan);
+size_t sketch_partial_bytes_lowp(const SketchPlan& p, int64_t n);
+cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
+                               const uint16_t* omega, int64_t ldo, int ell, int precision,
+                               const SketchPlan& plan, float* partial, float* Y, int64_t ldy,
+                               int32_t* info, uint64_t limit_ns, cudaStream_t s);
+
+struct SketchF64Plan {
+    int kslabs = 0;
+    int64_t k_per_slab = 0;
+    int lp = 0;
+};
+void sketch_plan_f64(int64_t m, int64_t n, int ell, SketchF64Plan* plan);
+cudaError_t launch_sketch_f64(const double* A, int64_t m, int64_t n, int64_t lda,
+                              const double* omega, int64_t ldo, int ell,
+                              const SketchF64Plan& plan, double* partial, double* Y, int64_t ldy,
+                              int32_t* info, cudaStream_t s);
+cudaError_t launch_scale_cast(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
+                              int precision, uint16_t* pieces, int32_t* shifts, int32_t* info,
+                              cudaStream_t s);
+
+// ---- pivoted QR (cpqr.cu)
+struct CpqrPlan {
+    int grid = 0;
+    int threads = 0;
+    size_t smem = 0;
+};
+bool cpqr_plan(int64_t r, int64_t n, int elem_bytes, CpqrPlan* plan);
+size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes);
+cudaError_t launch_cpqr(void* W, int w_f64, int64_t r, int64_t n, int64_t ldw, const void* src,
+                        int src_f64, int64_t ldsrc, int kcap, double rel_tol, int32_t* J,
+                        int32_t* k_out, int32_t* info, double* R64, int64_t ldr, void* nu,
+                        void* nuref, uint8_t* sel, void* ctrl, const CpqrPlan& plan,
+                        uint64_t limit_ns, cudaStream_t s);
+
+// ---- coefficient solve and error estimate (trsm.cu)
+cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr,
+                           int kcap, int64_t n, double* T, int64_t ldt, double* scratch,
+                           int refine_steps, cudaStream_t s);
+size_t solve_T_scratch_doubles(int kcap, int64_t n);
+cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
+                                const int32_t* J, const int32_t* k_ptr, const double* T,
+                                int64_t ldt, double* acc2, double* err_out, cudaStream_t s);
+
+}  // namespace gid

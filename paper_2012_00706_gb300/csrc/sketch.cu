@@ -1,0 +1,715 @@
+// Sketch Y = Omega A on GB300.
+//
+// Mixed precision (Algorithm 2 line 1 cast + the sketching the paper names as
+// future work in Sec. 5): every 64-row block of every column of A is scaled by
+// a power of two chosen from the block's largest magnitude, taken at FP32
+// precision, split into 1-3 bfloat16/half pieces, and multiplied by the
+// low-precision Gaussian Omega on the 5th-generation tensor cores
+// (tcgen05.mma kind::f16, FP32 accumulation in tensor memory).  The kernel is
+// bound by the single HBM pass over A: one CTA per SM streams a 128-column
+// tile of A through shared memory with 1-D bulk copies, converter warps build
+// the swizzled K-major operand, one thread issues the MMAs, and epilogue warps
+// drain each chunk's accumulator, apply the block's 2^s and keep the running
+// sum in tensor memory.  Split-K partial sums are reduced by a second kernel.
+//
+// Plain FP64 twin: the same product with FP64 Omega by DFMA, register tiled.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <cudaTypedefs.h>
+
+namespace gid {
+
+// ---------------------------------------------------------------- cast helpers
+
+// Shift of a scaling block from the largest magnitude's biased exponent
+// (bits of |x|): bfloat16 puts the maximum in [0.5, 1), half in [2^13, 2^14).
+// A zero or subnormal maximum gives shift 0.
+__device__ __forceinline__ int shift_from_max_f64hi(uint32_t max_abs_hi, int f16) {
+    const int e = static_cast<int>(max_abs_hi >> 20);
+    if (e == 0) return 0;
+    const int e2 = e - 1022;
+    return f16 ? e2 - 14 : e2;
+}
+
+__device__ __forceinline__ int shift_from_max_f32(uint32_t max_abs, int f16) {
+    const int e = static_cast<int>(max_abs >> 23);
+    if (e == 0) return 0;
+    const int e2 = e - 126;
+    return f16 ? e2 - 14 : e2;
+}
+
+// x * 2^-s rounded once to float, through FP64 (rare path: results outside the
+// float normal range, zero/subnormal doubles).  Both factors are normal
+// doubles, so each FP64 product is exact while the result stays normal.
+__device__ __noinline__ float scaled_slow(double x, int s) {
+    const int a = -s / 2, b = -s - a;
+    const double fa = __hiloint2double((1023 + a) << 20, 0);
+    const double fb = __hiloint2double((1023 + b) << 20, 0);
+    return __double2float_rn(__dmul_rn(__dmul_rn(x, fa), fb));
+}
+
+// fl32(x 2^-s) for double x using integer operations only: the exponent is
+// rebiased and the 52-bit significand rounded to 23 bits, ties to even.
+__device__ __forceinline__ float scaled_f32_from_f64(double x, int s) {
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
+    const uint32_t sign = hi & 0x80000000u, ah = hi & 0x7fffffffu;
+    const int e = static_cast<int>(ah >> 20);
+    const int e32 = e - s - 896;
+    if (e != 0 && e32 >= 1 && e32 <= 253) {
+        uint32_t t = (static_cast<uint32_t>(e32) << 23) | ((ah & 0xFFFFFu) << 3) | (lo >> 29);
+        const uint32_t rb = (lo >> 28) & 1u;
+        const uint32_t st = (lo & 0x0FFFFFFFu) != 0u ? 1u : 0u;
+        t += rb & (st | (t & 1u));
+        return __uint_as_float(sign | t);
+    }
+    if ((ah | lo) == 0u) return __uint_as_float(sign);
+    return scaled_slow(x, s);
+}
+
+// fl32(x 2^-s) for float x: exponent adjust when both ends are normal.
+__device__ __forceinline__ float scaled_f32_from_f32(float x, int s) {
+    const uint32_t u = __float_as_uint(x);
+    const int e = static_cast<int>((u >> 23) & 0xFFu);
+    const int e2 = e - s;
+    if (e >= 1 && e <= 254 && e2 >= 1 && e2 <= 254)
+        return __uint_as_float(u - (static_cast<uint32_t>(s) << 23));
+    if ((u & 0x7fffffffu) == 0u) return x;
+    return scaled_slow(static_cast<double>(x), s);
+}
+
+// One low-format piece of r (round to nearest even) and the exact remainder.
+__device__ __forceinline__ uint16_t take_piece(float& r, int f16) {
+    if (f16) {
+        const __half h = __float2half_rn(r);
+        r = r - __half2float(h);
+        return __half_as_ushort(h);
+    }
+    const __nv_bfloat16 b = __float2bfloat16_rn(r);
+    r = r - __bfloat162float(b);
+    return __bfloat16_as_ushort(b);
+}
+
+int precision_nsplit(int precision) {
+    switch (precision) {
+        case ID_MIXED_BF16: return 1;
+        case ID_MIXED_F16: return 1;
+        case ID_MIXED_BF16X2: return 2;
+        case ID_MIXED_BF16X3: return 3;
+        default: return 0;
+    }
+}
+
+int precision_is_f16(int precision) { return precision == ID_MIXED_F16 ? 1 : 0; }
+
+// ------------------------------------------------------ tensor-core sketch
+
+struct LowpParams {
+    const void* A;
+    int64_t lda, m, n;
+    int a_f64, nsplit, f16, lp, lpa;
+    int64_t nchunks, chunks_per_slab;
+    int stages, aop_bufs, omega_bufs, acc_bufs;
+    uint32_t colstride, stage_bytes, omega_tile_bytes;
+    int direct_all;
+    float* partial;     // [kslabs][n][lp]
+    int32_t* info;
+    uint64_t limit_ns;
+};
+
+constexpr uint32_t kAopTileBytes = kTileCols * 128;   // 128 rows x 64 bf16
+
+struct LowpSmem {
+    uint8_t* aop;        // [aop_bufs][nsplit][16 KB]
+    uint8_t* omega;      // [omega_bufs][omega_tile_bytes]
+    uint8_t* stage;      // [stages][stage_bytes]
+    int32_t* shifts;     // [aop_bufs + acc_bufs][128]
+    uint64_t* bars;
+    uint32_t* tmem_holder;
+    int* abort;
+};
+
+__host__ __device__ inline size_t lowp_carve(uintptr_t base, const LowpParams& P, LowpSmem* S) {
+    uintptr_t p = base;
+    auto take = [&](size_t bytes, size_t align) {
+        p = (p + align - 1) & ~(uintptr_t)(align - 1);
+        uintptr_t r = p;
+        p += bytes;
+        return r;
+    };
+    const int H = P.aop_bufs + P.acc_bufs;
+    uintptr_t aop = take((size_t)P.aop_bufs * P.nsplit * kAopTileBytes, 1024);
+    uintptr_t om = take((size_t)P.omega_bufs * P.omega_tile_bytes, 1024);
+    uintptr_t st = take((size_t)P.stages * P.stage_bytes, 128);
+    uintptr_t sh = take((size_t)H * kTileCols * 4, 16);
+    const int nbars = 2 * P.stages + 2 * P.omega_bufs + 2 * P.aop_bufs + 2 * P.acc_bufs + 2 * H;
+    uintptr_t bars = take((size_t)nbars * 8, 8);
+    uintptr_t th = take(4, 4);
+    uintptr_t ab = take(4, 4);
+    if (S) {
+        S->aop = reinterpret_cast<uint8_t*>(aop);
+        S->omega = reinterpret_cast<uint8_t*>(om);
+        S->stage = reinterpret_cast<uint8_t*>(st);
+        S->shifts = reinterpret_cast<int32_t*>(sh);
+        S->bars = reinterpret_cast<uint64_t*>(bars);
+        S->tmem_holder = reinterpret_cast<uint32_t*>(th);
+        S->abort = reinterpret_cast<int*>(ab);
+    }
+    return static_cast<size_t>(p - base);
+}
+
+__global__ void __launch_bounds__(384, 1)
+k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) {
+    extern __shared__ uint8_t smem_raw[];
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
+    LowpSmem S;
+    lowp_carve(base, P, &S);
+    const int NS = P.stages, NO = P.omega_bufs, NA = P.aop_bufs, NC = P.acc_bufs, H = NA + NC;
+    uint64_t* stage_full = S.bars;
+    uint64_t* stage_free = stage_full + NS;
+    uint64_t* omg_full = stage_free + NS;
+    uint64_t* omg_free = omg_full + NO;
+    uint64_t* aop_full = omg_free + NO;
+    uint64_t* aop_free = aop_full + NA;
+    uint64_t* acc_full = aop_free + NA;
+    uint64_t* acc_empty = acc_full + NC;
+    uint64_t* sh_full = acc_empty + NC;
+    uint64_t* sh_free = sh_full + H;
+    volatile int* abort = S.abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * kTileCols;
+    const int64_t ch_begin = static_cast<int64_t>(blockIdx.y) * P.chunks_per_slab;
+    const int64_t ch_end = min(P.nchunks, ch_begin + P.chunks_per_slab);
+    const int nloc = static_cast<int>(ch_end - ch_begin);
+    const int elem = P.a_f64 ? 8 : 4;
+    const int ncols_valid = static_cast<int>(min(static_cast<int64_t>(kTileCols), P.n - col0));
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NS; ++i) { mbar_init(&stage_full[i], 1); mbar_init(&stage_free[i], 4); }
+        for (int i = 0; i < NO; ++i) { mbar_init(&omg_full[i], 1); mbar_init(&omg_free[i], 1); }
+        for (int i = 0; i < NA; ++i) { mbar_init(&aop_full[i], 4); mbar_init(&aop_free[i], 1); }
+        for (int i = 0; i < NC; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 4); }
+        for (int i = 0; i < H; ++i) { mbar_init(&sh_full[i], 4); mbar_init(&sh_free[i], 4); }
+        *S.abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 2) {
+        tmem_alloc(S.tmem_holder, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *S.tmem_holder;
+
+    if (warp == 0) {
+        // ---------------- producer: A column slices (bulk copies) + Omega tiles (TMA)
+        if (lane == 0) prefetch_tensormap(&tm_omega);
+        for (int i = 0; i < nloc && !*abort; ++i) {
+            const int64_t c = ch_begin + i;
+            const int s = i % NS, o = i % NO;
+            if (!mbar_wait(&omg_free[o], ((i / NO) & 1) ^ 1, abort, P.limit_ns)) break;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&omg_full[o], P.omega_tile_bytes);
+                tma_load_2d(S.omega + (size_t)o * P.omega_tile_bytes, &tm_omega,
+                            static_cast<int32_t>(c * kChunkRows), 0, &omg_full[o]);
+            }
+            if (!mbar_wait(&stage_free[s], ((i / NS) & 1) ^ 1, abort, P.limit_ns)) break;
+            const int64_t row0 = c * kChunkRows;
+            const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), P.m - row0));
+            const uint32_t bytes_col = P.direct_all ? 0u : (static_cast<uint32_t>(rows * elem) & ~15u);
+            const uint32_t total = bytes_col * static_cast<uint32_t>(ncols_valid);
+            if (lane == 0) {
+                if (total > 0) mbar_arrive_expect_tx(&stage_full[s], total);
+                else mbar_arrive(&stage_full[s]);
+            }
+            __syncwarp();
+            if (bytes_col > 0) {
+                uint8_t* dst = S.stage + (size_t)s * P.stage_bytes;
+                const uint8_t* A8 = static_cast<const uint8_t*>(P.A);
+                for (int q = lane; q < ncols_valid; q += 32) {
+                    const uint8_t* src = A8 + ((col0 + q) * P.lda + row0) * elem;
+                    bulk_g2s(dst + (size_t)q * P.colstride, src, bytes_col, &stage_full[s]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_f16(P.f16 ? 0u : 1u, 128u, static_cast<uint32_t>(P.lp));
+            int issued = 0;
+            for (int i = 0; i < nloc; ++i) {
+                const int a = i % NA, o = i % NO, b = i % NC;
+                if (!mbar_wait(&aop_full[a], (i / NA) & 1, abort, P.limit_ns)) break;
+                if (!mbar_wait(&omg_full[o], (i / NO) & 1, abort, P.limit_ns)) break;
+                if (!mbar_wait(&acc_empty[b], ((i / NC) & 1) ^ 1, abort, P.limit_ns)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + static_cast<uint32_t>(b * P.lpa);
+                const uint32_t bbase = smem_addr(S.omega + (size_t)o * P.omega_tile_bytes);
+                for (int p = 0; p < P.nsplit; ++p) {
+                    const uint32_t abase =
+                        smem_addr(S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_f16(d, umma_desc_sw128(abase + 32u * kk), umma_desc_sw128(bbase + 32u * kk),
+                                 idesc, (p | kk) != 0 ? 1u : 0u);
+                }
+                umma_commit(&aop_free[a]);
+                umma_commit(&omg_free[o]);
+                umma_commit(&acc_full[b]);
+                issued = i + 1;
+            }
+            if (*abort && issued > 0) {
+                // leave only after the MMAs already issued are done (bounded wait)
+                volatile int keep_waiting = 0;
+                const int b = (issued - 1) % NC;
+                mbar_wait(&acc_full[b], ((issued - 1) / NC) & 1, &keep_waiting, P.limit_ns);
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---------------- converters: thread t owns column col0 + t
+        const int t = threadIdx.x - 128;
+        const int64_t col = col0 + t;
+        const bool valid = t < ncols_valid;
+        const uint8_t* A8 = static_cast<const uint8_t*>(P.A);
+        for (int i = 0; i < nloc; ++i) {
+            const int64_t c = ch_begin + i;
+            const int s = i % NS, a = i % NA, h = i % H;
+            if (!mbar_wait(&stage_full[s], (i / NS) & 1, abort, P.limit_ns)) break;
+            if (!mbar_wait(&aop_free[a], ((i / NA) & 1) ^ 1, abort, P.limit_ns)) break;
+            if (!mbar_wait(&sh_free[h], ((i / H) & 1) ^ 1, abort, P.limit_ns)) break;
+            const int64_t row0 = c * kChunkRows;
+            const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), P.m - row0));
+            const int rows_smem = P.direct_all ? 0 : ((rows * elem) & ~15) / elem;
+            const uint8_t* scol = S.stage + (size_t)s * P.stage_bytes + (size_t)t * P.colstride;
+            const uint8_t* gcol = A8 + (col * P.lda + row0) * elem;
+            int shift = 0;
+            if (P.a_f64) {
+                const double* sd = reinterpret_cast<const double*>(scol);
+                const double* gd = reinterpret_cast<const double*>(gcol);
+                uint32_t mx = 0;
+                if (valid) {
+                    if (rows_smem == kChunkRows) {
+#pragma unroll 8
+                        for (int r = 0; r < kChunkRows; r += 2) {
+                            const double2 v = *reinterpret_cast<const double2*>(sd + r);
+                            mx = max(mx, static_cast<uint32_t>(__double2hiint(v.x)) & 0x7fffffffu);
+                            mx = max(mx, static_cast<uint32_t>(__double2hiint(v.y)) & 0x7fffffffu);
+                        }
+                    } else {
+                        for (int r = 0; r < rows; ++r) {
+                            const double x = r < rows_smem ? sd[r] : __ldg(gd + r);
+                            mx = max(mx, static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu);
+                        }
+                    }
+                    if ((mx >> 20) == 0x7FFu) set_info(P.info, kInfoNonFinite);
+                }
+                shift = shift_from_max_f64hi(mx, P.f16);
+#pragma unroll 1
+                for (int g = 0; g < 8; ++g) {
+                    float v[8];
+                    if (valid && rows_smem == kChunkRows) {
+#pragma unroll
+                        for (int q = 0; q < 8; q += 2) {
+                            const double2 d2 = *reinterpret_cast<const double2*>(sd + 8 * g + q);
+                            v[q] = scaled_f32_from_f64(d2.x, shift);
+                            v[q + 1] = scaled_f32_from_f64(d2.y, shift);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int r = 8 * g + q;
+                            double x = 0.0;
+                            if (valid && r < rows) x = r < rows_smem ? sd[r] : __ldg(gd + r);
+                            v[q] = scaled_f32_from_f64(x, shift);
+                        }
+                    }
+                    for (int p = 0; p < P.nsplit; ++p) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t lo16 = take_piece(v[2 * q], P.f16);
+                            const uint32_t hi16 = take_piece(v[2 * q + 1], P.f16);
+                            w[q] = lo16 | (hi16 << 16);
+                        }
+                        uint8_t* tile = S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes;
+                        const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
+                        *reinterpret_cast<uint4*>(tile + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+            } else {
+                const float* sf = reinterpret_cast<const float*>(scol);
+                const float* gf = reinterpret_cast<const float*>(gcol);
+                uint32_t mx = 0;
+                if (valid) {
+                    if (rows_smem == kChunkRows) {
+#pragma unroll 4
+                        for (int r = 0; r < kChunkRows; r += 4) {
+                            const float4 v = *reinterpret_cast<const float4*>(sf + r);
+                            mx = max(mx, __float_as_uint(v.x) & 0x7fffffffu);
+                            mx = max(mx, __float_as_uint(v.y) & 0x7fffffffu);
+                            mx = max(mx, __float_as_uint(v.z) & 0x7fffffffu);
+                            mx = max(mx, __float_as_uint(v.w) & 0x7fffffffu);
+                        }
+                    } else {
+                        for (int r = 0; r < rows; ++r) {
+                            const float x = r < rows_smem ? sf[r] : __ldg(gf + r);
+                            mx = max(mx, __float_as_uint(x) & 0x7fffffffu);
+                        }
+                    }
+                    if ((mx >> 23) == 0xFFu) set_info(P.info, kInfoNonFinite);
+                }
+                shift = shift_from_max_f32(mx, P.f16);
+#pragma unroll 1
+                for (int g = 0; g < 8; ++g) {
+                    float v[8];
+                    if (valid && rows_smem == kChunkRows) {
+                        const float4 x0 = *reinterpret_cast<const float4*>(sf + 8 * g);
+                        const float4 x1 = *reinterpret_cast<const float4*>(sf + 8 * g + 4);
+                        v[0] = scaled_f32_from_f32(x0.x, shift); v[1] = scaled_f32_from_f32(x0.y, shift);
+                        v[2] = scaled_f32_from_f32(x0.z, shift); v[3] = scaled_f32_from_f32(x0.w, shift);
+                        v[4] = scaled_f32_from_f32(x1.x, shift); v[5] = scaled_f32_from_f32(x1.y, shift);
+                        v[6] = scaled_f32_from_f32(x1.z, shift); v[7] = scaled_f32_from_f32(x1.w, shift);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int r = 8 * g + q;
+                            float x = 0.f;
+                            if (valid && r < rows) x = r < rows_smem ? sf[r] : __ldg(gf + r);
+                            v[q] = scaled_f32_from_f32(x, shift);
+                        }
+                    }
+                    for (int p = 0; p < P.nsplit; ++p) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t lo16 = take_piece(v[2 * q], P.f16);
+                            const uint32_t hi16 = take_piece(v[2 * q + 1], P.f16);
+                            w[q] = lo16 | (hi16 << 16);
+                        }
+                        uint8_t* tile = S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes;
+                        const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
+                        *reinterpret_cast<uint4*>(tile + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+            }
+            S.shifts[h * kTileCols + t] = shift;
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&stage_free[s]);
+                mbar_arrive(&aop_full[a]);
+                mbar_arrive(&sh_full[h]);
+            }
+        }
+    } else if (warp >= 8) {
+        // ---------------- epilogue: drain each chunk, scale by 2^s, accumulate in TMEM
+        const int q = warp & 3;
+        const int t = 32 * q + lane;
+        const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
+        const uint32_t run_col = static_cast<uint32_t>(NC * P.lpa);
+        const int nsl = P.lp / 16;
+        bool ok = true;
+        for (int i = 0; i < nloc; ++i) {
+            const int b = i % NC, h = i % H;
+            if (!mbar_wait(&acc_full[b], (i / NC) & 1, abort, P.limit_ns)) { ok = false; break; }
+            if (!mbar_wait(&sh_full[h], (i / H) & 1, abort, P.limit_ns)) { ok = false; break; }
+            tc_fence_after();
+            const float sc = ldexpf(1.0f, S.shifts[h * kTileCols + t]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh_free[h]);
+            for (int sl = 0; sl < nsl; ++sl) {
+                float acc[16], run[16];
+                tmem_ld16(lane_base + static_cast<uint32_t>(b * P.lpa + 16 * sl), acc);
+                if (i > 0) tmem_ld16(lane_base + run_col + 16u * sl, run);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) run[j] = (i > 0) ? fmaf(acc[j], sc, run[j]) : acc[j] * sc;
+                tmem_st16(lane_base + run_col + 16u * sl, run);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        if (ok && nloc > 0) {
+            // all lanes take part in the warp-wide loads; lanes past n do not store
+            float* dst = P.partial + (static_cast<int64_t>(blockIdx.y) * P.n + col0 + t) * P.lp;
+            for (int sl = 0; sl < nsl; ++sl) {
+                float run[16];
+                tmem_ld16(lane_base + run_col + 16u * sl, run);
+                tmem_ld_wait();
+                if (t < ncols_valid) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(dst + 16 * sl + j) =
+                            make_float4(run[j], run[j + 1], run[j + 2], run[j + 3]);
+                }
+            }
+        }
+    }
+    if (*abort) set_info(P.info, kInfoWatchdog);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 2) tmem_dealloc(tmem, 512);
+}
+
+// Y(l, j) = sum over split-K slabs of the partial sums (fixed slab order).
+__global__ void k_reduce_partials_f32(const float* __restrict__ partial, int kslabs, int64_t n,
+                                      int lp, int ell, float* __restrict__ Y, int64_t ldy) {
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n * ell) return;
+    const int64_t j = idx / ell;
+    const int l = static_cast<int>(idx - j * ell);
+    float s = 0.f;
+    for (int k = 0; k < kslabs; ++k) s += partial[(static_cast<int64_t>(k) * n + j) * lp + l];
+    Y[j * ldy + l] = s;
+}
+
+// ------------------------------------------------------------- host plans
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool sketch_plan_lowp(int64_t m, int64_t n, int ell, int a_f64, int nsplit, SketchPlan* plan) {
+    const DeviceInfo& dev = device_info();
+    SketchPlan p;
+    p.lp = (ell + 15) / 16 * 16;
+    if (p.lp > ID_MAX_ELL || ell < 1 || nsplit < 1 || nsplit > 3) return false;
+    const int lpa = (p.lp + 31) / 32 * 32;
+    p.acc_bufs = (3 * lpa <= 512) ? 2 : 1;
+    p.tiles = static_cast<int>((n + kTileCols - 1) / kTileCols);
+    p.nchunks = (m + kChunkRows - 1) / kChunkRows;
+    int target = std::max(1, dev.sm_count);
+    int64_t kslabs = std::max<int64_t>(1, std::min<int64_t>(p.nchunks, target / std::max(1, p.tiles)));
+    p.chunks_per_slab = (p.nchunks + kslabs - 1) / kslabs;
+    p.kslabs = static_cast<int>((p.nchunks + p.chunks_per_slab - 1) / p.chunks_per_slab);
+    const int elem = a_f64 ? 8 : 4;
+    const uint32_t colstride = kChunkRows * elem + 16;
+    const uint32_t stage_bytes = kTileCols * colstride;
+    const uint32_t omega_tile = (static_cast<uint32_t>(p.lp) * 128u + 1023u) & ~1023u;
+    LowpParams P{};
+    P.nsplit = nsplit;
+    P.colstride = colstride;
+    P.stage_bytes = stage_bytes;
+    P.omega_tile_bytes = omega_tile;
+    P.acc_bufs = p.acc_bufs;
+    const size_t budget = static_cast<size_t>(dev.max_smem_optin) - 1024;
+    auto fits = [&](int st, int na, int no) {
+        P.stages = st; P.aop_bufs = na; P.omega_bufs = no;
+        return lowp_carve(0, P, nullptr) <= budget;
+    };
+    int st = 2, na = 1, no = 1;
+    if (!fits(st, na, no)) return false;
+    if (fits(st, na, 2)) no = 2;
+    if (fits(st, 2, no)) na = 2;
+    const int max_st = a_f64 ? 3 : 4;
+    while (st < max_st && fits(st + 1, na, no)) ++st;
+    fits(st, na, no);
+    p.stages = st; p.aop_bufs = na; p.omega_bufs = no;
+    p.smem_bytes = lowp_carve(0, P, nullptr) + 1024;
+    *plan = p;
+    return true;
+}
+
+size_t sketch_partial_bytes_lowp(const SketchPlan& p, int64_t n) {
+    return static_cast<size_t>(p.kslabs) * static_cast<size_t>(n) * p.lp * sizeof(float);
+}
+
+cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
+                               const uint16_t* omega, int64_t ldo, int ell, int precision,
+                               const SketchPlan& plan, float* partial, float* Y, int64_t ldy,
+                               int32_t* info, uint64_t limit_ns, cudaStream_t s) {
+    auto encode = get_encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const int f16 = precision_is_f16(precision);
+    CUtensorMap tm;
+    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(ell)};
+    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ldo) * 2};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunkRows), static_cast<cuuint32_t>(plan.lp)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = encode(&tm, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                         const_cast<uint16_t*>(omega), gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+    LowpParams P{};
+    P.A = A; P.lda = lda; P.m = m; P.n = n; P.a_f64 = a_f64;
+    P.nsplit = precision_nsplit(precision); P.f16 = f16;
+    P.lp = plan.lp; P.lpa = (plan.lp + 31) / 32 * 32;
+    P.nchunks = plan.nchunks; P.chunks_per_slab = plan.chunks_per_slab;
+    P.stages = plan.stages; P.aop_bufs = plan.aop_bufs; P.omega_bufs = plan.omega_bufs;
+    P.acc_bufs = plan.acc_bufs;
+    const int elem = a_f64 ? 8 : 4;
+    P.colstride = kChunkRows * elem + 16;
+    P.stage_bytes = kTileCols * P.colstride;
+    P.omega_tile_bytes = (static_cast<uint32_t>(plan.lp) * 128u + 1023u) & ~1023u;
+    P.direct_all = ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || ((lda * elem) & 15) != 0) ? 1 : 0;
+    P.partial = partial; P.info = info; P.limit_ns = limit_ns;
+
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_lowp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(plan.smem_bytes));
+    if (e != cudaSuccess) return e;
+    dim3 grid(plan.tiles, plan.kslabs);
+    k_sketch_lowp<<<grid, 384, plan.smem_bytes, s>>>(tm, P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = n * ell;
+    k_reduce_partials_f32<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+        partial, plan.kslabs, n, plan.lp, ell, Y, ldy);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ plain FP64 sketch
+
+constexpr int kF64Tile = 64;
+constexpr int kF64K = 16;
+
+// Y partial for rows [64 by, +64) of Omega and columns [64 bx, +64) of A over a
+// K slab; 256 threads, 4 x 4 outputs each, FP64 FMAs.
+__global__ void __launch_bounds__(256)
+k_sketch_f64(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+             const double* __restrict__ omega, int64_t ldo, int ell, int64_t k_per_slab, int lp,
+             double* __restrict__ partial) {
+    __shared__ double Os[kF64K][kF64Tile + 1];
+    __shared__ double As[kF64K][kF64Tile + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kF64Tile;
+    const int r0 = blockIdx.y * kF64Tile;
+    const int64_t kb = static_cast<int64_t>(blockIdx.z) * k_per_slab;
+    const int64_t ke = min(m, kb + k_per_slab);
+    double acc[4][4] = {};
+    for (int64_t k0 = kb; k0 < ke; k0 += kF64K) {
+        for (int idx = threadIdx.x; idx < kF64K * kF64Tile; idx += 256) {
+            const int kk = idx % kF64K, i = idx / kF64K;
+            const int64_t kg = k0 + kk;
+            Os[kk][i] = (r0 + i < ell && kg < ke) ? omega[(r0 + i) * ldo + kg] : 0.0;
+            As[kk][i] = (c0 + i < n && kg < ke) ? A[(c0 + i) * lda + kg] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kF64K; ++kk) {
+            double o[4], a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { o[q] = Os[kk][ty * 4 + q]; a[q] = As[kk][tx * 4 + q]; }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fma(o[p], a[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t col = c0 + tx * 4 + q;
+        if (col >= n) continue;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int row = r0 + ty * 4 + p;
+            if (row < lp) partial[(static_cast<int64_t>(blockIdx.z) * n + col) * lp + row] = acc[p][q];
+        }
+    }
+}
+
+__global__ void k_reduce_partials_f64(const double* __restrict__ partial, int kslabs, int64_t n, int lp,
+                                      int ell, double* __restrict__ Y, int64_t ldy, int32_t* info) {
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n * ell) return;
+    const int64_t j = idx / ell;
+    const int l = static_cast<int>(idx - j * ell);
+    double s = 0.0;
+    for (int k = 0; k < kslabs; ++k) s += partial[(static_cast<int64_t>(k) * n + j) * lp + l];
+    if (!isfinite(s)) set_info(info, kInfoNonFinite);
+    Y[j * ldy + l] = s;
+}
+
+void sketch_plan_f64(int64_t m, int64_t n, int ell, SketchF64Plan* plan) {
+    const DeviceInfo& dev = device_info();
+    const int64_t tiles = ((n + kF64Tile - 1) / kF64Tile) * ((ell + kF64Tile - 1) / kF64Tile);
+    const int64_t want = std::max<int64_t>(1, (2LL * dev.sm_count + tiles - 1) / tiles);
+    int64_t kps = (m + want - 1) / want;
+    kps = std::max<int64_t>(kF64K, (kps + kF64K - 1) / kF64K * kF64K);
+    plan->k_per_slab = kps;
+    plan->kslabs = static_cast<int>((m + kps - 1) / kps);
+    plan->lp = ell;
+}
+
+cudaError_t launch_sketch_f64(const double* A, int64_t m, int64_t n, int64_t lda, const double* omega,
+                              int64_t ldo, int ell, const SketchF64Plan& plan, double* partial,
+                              double* Y, int64_t ldy, int32_t* info, cudaStream_t s) {
+    dim3 grid(static_cast<unsigned>((n + kF64Tile - 1) / kF64Tile),
+              static_cast<unsigned>((ell + kF64Tile - 1) / kF64Tile), static_cast<unsigned>(plan.kslabs));
+    k_sketch_f64<<<grid, 256, 0, s>>>(A, m, n, lda, omega, ldo, ell, plan.k_per_slab, plan.lp, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = n * ell;
+    k_reduce_partials_f64<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+        partial, plan.kslabs, n, plan.lp, ell, Y, ldy, info);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------- standalone scaled cast
+
+// One thread per (64-row block, column): the cast exactly as the sketch's
+// converter warps perform it, written out as format bits and shifts.
+__global__ void k_scale_cast(const void* __restrict__ A, int a_f64, int64_t m, int64_t n, int64_t lda,
+                             int nsplit, int f16, uint16_t* __restrict__ pieces,
+                             int32_t* __restrict__ shifts, int32_t* info) {
+    const int64_t nb = (m + kChunkRows - 1) / kChunkRows;
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= nb * n) return;
+    const int64_t j = idx / nb, b = idx - j * nb;
+    const int64_t r0 = b * kChunkRows;
+    const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), m - r0));
+    int shift;
+    if (a_f64) {
+        const double* col = static_cast<const double*>(A) + j * lda + r0;
+        uint32_t mx = 0;
+        for (int r = 0; r < rows; ++r)
+            mx = max(mx, static_cast<uint32_t>(__double2hiint(col[r])) & 0x7fffffffu);
+        if ((mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
+        shift = shift_from_max_f64hi(mx, f16);
+        for (int r = 0; r < rows; ++r) {
+            float v = scaled_f32_from_f64(col[r], shift);
+            for (int p = 0; p < nsplit; ++p) pieces[(p * n + j) * m + r0 + r] = take_piece(v, f16);
+        }
+    } else {
+        const float* col = static_cast<const float*>(A) + j * lda + r0;
+        uint32_t mx = 0;
+        for (int r = 0; r < rows; ++r) mx = max(mx, __float_as_uint(col[r]) & 0x7fffffffu);
+        if ((mx >> 23) == 0xFFu) set_info(info, kInfoNonFinite);
+        shift = shift_from_max_f32(mx, f16);
+        for (int r = 0; r < rows; ++r) {
+            float v = scaled_f32_from_f32(col[r], shift);
+            for (int p = 0; p < nsplit; ++p) pieces[(p * n + j) * m + r0 + r] = take_piece(v, f16);
+        }
+    }
+    shifts[j * nb + b] = shift;
+}
+
+cudaError_t launch_scale_cast(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, int precision,
+                              uint16_t* pieces, int32_t* shifts, int32_t* info, cudaStream_t s) {
+    const int64_t nb = (m + kChunkRows - 1) / kChunkRows;
+    const int64_t total = nb * n;
+    k_scale_cast<<<static_cast<unsigned>((total + 127) / 128), 128, 0, s>>>(
+        A, a_f64, m, n, lda, precision_nsplit(precision), precision_is_f16(precision), pieces, shifts,
+        info);
+    return cudaGetLastError();
+}
+
+}  // namespace gid

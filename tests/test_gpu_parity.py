@@ -1,0 +1,248 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived from the arithmetic):
+  * scaled cast: bit-exact (shifts are integers, pieces are format codes decided
+    in FP32 on both sides);
+  * mixed sketch: |Y_gpu - Y_oracle| <= 2 (c + 2 log2(kslab count)) u32 (|Omega| |A~|)
+    entrywise, c = 64 terms per chunk + chunks per slab (FP32 accumulation of exact
+    products; factor 2 allows truncating rather than rounding accumulation);
+  * plain FP64 sketch: 1e-12 relative to |Omega| |A|;
+  * plain FP64 ID: pivots bit-exact on separated inputs, T within 1e-9 relative,
+    relative reconstruction error within 1e-10 of the oracle's;
+  * mixed ID: e_M <= 1.1 e_D + 10 u_low (spec tolerance), e the relative
+    2-norm error of the reconstruction.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+U_LOW = {"mixed_bf16": 2.0 ** -8, "mixed_f16": 2.0 ** -11, "mixed_bf16x2": 2.0 ** -16,
+         "mixed_bf16x3": 2.0 ** -24}
+FMT = {"mixed_bf16": ("bf16", 1), "mixed_f16": ("f16", 1), "mixed_bf16x2": ("bf16", 2),
+       "mixed_bf16x3": ("bf16", 3)}
+
+
+@pytest.fixture(scope="module")
+def gid():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2012_00706_gb300 as g
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda:0")
+
+
+def omega_dev(bits, dev, fmt):
+    t = torch.from_numpy(np.ascontiguousarray(bits).view(np.int16)).to(dev)
+    return t.view(torch.bfloat16 if fmt == "bf16" else torch.float16)
+
+
+def bits_as_f64(bits, fmt):
+    if fmt == "f16":
+        return bits.view(np.float16).astype(np.float64)
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+# ------------------------------------------------------------------ scaled cast
+
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_f16", "mixed_bf16x2", "mixed_bf16x3"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_scale_cast_bit_exact(gid, dev, orc, precision, dtype):
+    """Shifts and piece bits equal the oracle's cast (ragged last block, zero column,
+    wide dynamic range, ties)."""
+    rng = np.random.default_rng(1)
+    m, n = 200, 37
+    a = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-6, 6, (m, n))
+    a[:, 3] = 0.0
+    a[10:20, 5] = 1e-30
+    a[:, 7] = 1.0 + 2.0 ** -9            # ties for bfloat16
+    a[::3, 8] = -(1.0 + 3 * 2.0 ** -12)  # ties for half
+    a = np.asfortranarray(a.astype(dtype))
+    fmt, nsplit = FMT[precision]
+    pieces, shifts, info = gid.id_scale_cast(torch.from_numpy(a).to(dev), precision)
+    ref_p, ref_s, rc = orc.quantize(a, fmt, 64, nsplit)
+    assert int(info.item()) == 0 and rc == 0
+    assert np.array_equal(shifts.cpu().numpy(), ref_s)
+    got = pieces.cpu().numpy().view(np.uint16)
+    for p in range(nsplit):
+        vals = bits_as_f64(np.ascontiguousarray(got[p]), fmt)
+        assert np.array_equal(vals, ref_p[p]), f"piece {p} differs"
+
+
+def test_scale_cast_nonfinite(gid, dev):
+    a = np.ones((70, 4))
+    a[65, 2] = np.inf
+    _, _, info = gid.id_scale_cast(torch.from_numpy(a).to(dev), "mixed_bf16")
+    assert int(info.item()) == -1
+
+
+# ----------------------------------------------------------------------- sketch
+
+def lowp_bound(om, pieces, shifts, block=64, kslabs=16):
+    """Entrywise bound of an FP32-accumulated evaluation: 2 (64 + nchunks + kslabs) u32 |Om| |A~| 2^s."""
+    scale = np.repeat(2.0 ** shifts, block, axis=0)[: pieces.shape[1]]
+    mag = np.abs(om) @ (np.abs(pieces).sum(axis=0) * scale)
+    nch = (pieces.shape[1] + block - 1) // block
+    return 2.0 * (64 + nch + kslabs) * U32 * mag
+
+
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_f16", "mixed_bf16x3"])
+@pytest.mark.parametrize("m,n,ell,dtype,pad", [
+    (1000, 300, 40, np.float64, 0),      # ragged rows (1000 = 15*64 + 40), 3 column tiles
+    (777, 129, 110, np.float64, 6),      # odd tail, lda = m + 6
+    (640, 200, 200, np.float32, 0),      # N > 128
+    (333, 70, 16, np.float32, 3),        # lda*4 not a multiple of 16 -> direct loads
+    (129, 5, 8, np.float64, 1),          # odd lda -> direct loads
+])
+def test_sketch_lowp_vs_oracle(gid, dev, orc, precision, m, n, ell, dtype, pad):
+    fmt, nsplit = FMT[precision]
+    rng = np.random.default_rng(m + n + ell)
+    a = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-2, 2, (1, n))
+    a = a.astype(dtype)
+    full = np.zeros((m + pad, n), dtype=dtype, order="F")
+    full[:m] = a
+    at = torch.from_numpy(full).to(dev)[:m]
+    ldo = (m + 7) // 8 * 8
+    om, bits = wl.gaussian_omega(ell, m, 3, fmt)
+    bits_pad = np.zeros((ell, ldo), dtype=np.uint16)
+    bits_pad[:, :m] = bits
+    omt = omega_dev(bits_pad, dev, fmt)[:, :m]
+    y = gid.id_sketch(at, omt, precision).cpu().numpy().astype(np.float64)
+    ref, rc = orc.sketch_lowp(om, np.asfortranarray(a), fmt, nsplit, 64)
+    pieces, shifts, _ = orc.quantize(np.asfortranarray(a), fmt, 64, nsplit)
+    bound = lowp_bound(om, pieces, shifts)
+    assert rc == 0
+    err = np.abs(y - ref)
+    assert np.all(err <= bound), float(np.max(err / np.maximum(bound, 1e-300)))
+
+
+def test_sketch_f64_vs_oracle(gid, dev, orc):
+    rng = np.random.default_rng(9)
+    m, n, ell = 3001, 150, 70
+    a = np.asfortranarray(rng.standard_normal((m, n)))
+    om = rng.standard_normal((ell, m))
+    y = gid.id_sketch(torch.from_numpy(a).to(dev), torch.from_numpy(om).to(dev), "plain_f64").cpu().numpy()
+    ref = orc.sketch_f64(om, a)
+    assert np.max(np.abs(y - ref) / (np.abs(om) @ np.abs(a))) <= 1e-12
+
+
+# -------------------------------------------------------------- plain FP64 ID
+
+@pytest.mark.parametrize("m,n,k", [(300, 140, 20), (1000, 500, 50), (97, 33, 33), (513, 260, 1), (64, 300, 40)])
+def test_plain_f64_id_matches_oracle(gid, dev, orc, m, n, k):
+    a = wl.separated_matrix(m, n, seed=m * 7 + n)
+    ref = orc.interp_decomp(a, k=k)
+    assert np.min(ref["gaps"]) >= 1e-8
+    res = gid.id_factor(torch.from_numpy(a).to(dev), k, precision="plain_f64", estimate_error=True)
+    assert res.info == 0 and res.k == k
+    J = res.J.cpu().numpy()
+    assert np.array_equal(J, ref["J"])
+    T = res.T.cpu().numpy()
+    assert T.shape == ref["T"].shape
+    if T.size:
+        assert np.max(np.abs(T - ref["T"])) <= 1e-9 * max(1.0, np.max(np.abs(ref["T"])))
+    e_gpu = orc.rel_err(a, J, T, k, "fro")
+    e_ref = orc.rel_err(a, ref["J"], ref["T"], k, "fro")
+    assert abs(e_gpu - e_ref) <= 1e-10
+    assert abs(res.err - e_ref) <= 1e-10
+
+
+def test_plain_f64_config1_full(gid, dev, orc):
+    """Config 1 (1000 x 500, sigma_i = 10^(-i/25), k = 50): pivots at separated steps,
+    reconstruction error within 1e-10 of the oracle's."""
+    c = wl.config1()
+    a = c["A"]
+    ref = orc.interp_decomp(a, k=c["k"])
+    res = gid.id_factor(torch.from_numpy(a).to(dev), c["k"], precision="plain_f64")
+    assert res.info == 0 and res.k == 50
+    J = res.J.cpu().numpy()
+    gaps = ref["gaps"]
+    first_tie = int(np.argmax(gaps < 1e-8)) if np.any(gaps < 1e-8) else 50
+    assert np.array_equal(J[:first_tie], ref["J"][:first_tie])
+    e_gpu = orc.rel_err(a, J, res.T.cpu().numpy(), 50)
+    e_ref = orc.rel_err(a, ref["J"], ref["T"], 50)
+    assert abs(e_gpu - e_ref) <= 1e-10 * max(1.0, e_ref) or first_tie < 50
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_plain_f32_id(gid, dev, orc, dtype):
+    a = wl.separated_matrix(400, 120, seed=31, decay=0.9)
+    ref = orc.interp_decomp(a, k=25)
+    res = gid.id_factor(torch.from_numpy(a.astype(dtype)).to(dev), 25, precision="plain_f32")
+    assert res.info == 0
+    assert np.array_equal(res.J.cpu().numpy()[:25], ref["J"][:25])
+    e = orc.rel_err(a, res.J.cpu().numpy(), res.T.cpu().numpy(), 25)
+    e_ref = orc.rel_err(a, ref["J"], ref["T"], 25)
+    assert e <= 1.1 * e_ref + 10 * U32
+
+
+def test_rank_by_tolerance(gid, dev, orc):
+    m, n = 400, 120
+    sigma = 10.0 ** (-np.arange(1, n + 1) / 6.0)
+    a = wl.lowrank(m, n, sigma, 31)
+    ref = orc.interp_decomp(a, tol=1e-5, k_max=80)
+    res = gid.id_factor(torch.from_numpy(a).to(dev), tol=1e-5, k_max=80, precision="plain_f64")
+    assert res.info == 0 and res.k == ref["k"]
+    assert np.array_equal(res.J.cpu().numpy(), ref["J"])
+
+
+def test_info_codes(gid, dev):
+    a = np.zeros((50, 9))
+    rng = np.random.default_rng(0)
+    a[:, [2, 5]] = rng.standard_normal((50, 2))
+    res = gid.id_factor(torch.from_numpy(a).to(dev), 4, precision="plain_f64")
+    assert res.info == 3 and res.k == 2
+    assert sorted(res.J.cpu().numpy()[:2].tolist()) == [2, 5]
+    b = rng.standard_normal((50, 9))
+    b[7, 3] = np.nan
+    res = gid.id_factor(torch.from_numpy(b).to(dev), 4, precision="plain_f64")
+    assert res.info == -1
+
+
+# ----------------------------------------------------------------- mixed ID
+
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_f16", "mixed_bf16x2", "mixed_bf16x3"])
+def test_mixed_id_tolerance(gid, dev, orc, precision):
+    """Config-2-shaped (smaller): e_M <= 1.1 e_D + 10 u_low with the same Omega."""
+    fmt, _ = FMT[precision]
+    m, n, k, ell = 4000, 400, 40, 50
+    sigma = np.arange(1, n + 1, dtype=np.float64) ** -2.0
+    a = wl.lowrank(m, n, sigma, 77)
+    om, bits = wl.gaussian_omega(ell, m, 78, fmt)
+    res = gid.id_factor(torch.from_numpy(a).to(dev), k, precision=precision, omega=omega_dev(bits, dev, fmt))
+    assert res.info == 0 and res.k == k
+    J, T = res.J.cpu().numpy(), res.T.cpu().numpy()
+    ref = orc.interp_decomp(a, k=k, omega=om)
+    e_m = orc.rel_err(a, J, T, k)
+    e_d = orc.rel_err(a, ref["J"], ref["T"], k)
+    assert e_m <= 1.1 * e_d + 10 * U_LOW[precision] * 1.0, (e_m, e_d)
+    if precision == "mixed_bf16x3":
+        # FP32-accurate sketch: same skeleton at separated steps
+        ok = ref["gaps"] >= 1e-3
+        first = int(np.argmax(~ok)) if np.any(~ok) else k
+        assert np.array_equal(J[:first], ref["J"][:first])
+
+
+def test_plain_f64_sketched_id(gid, dev, orc):
+    m, n, k, ell = 3000, 250, 30, 40
+    sigma = np.arange(1, n + 1, dtype=np.float64) ** -2.0
+    a = wl.lowrank(m, n, sigma, 90)
+    rng = np.random.default_rng(91)
+    om = rng.standard_normal((ell, m))
+    ref = orc.interp_decomp(a, k=k, omega=om)
+    res = gid.id_factor(torch.from_numpy(a).to(dev), k, precision="plain_f64", omega=torch.from_numpy(om).to(dev))
+    assert res.info == 0
+    sep = ref["gaps"] >= 1e-8
+    first = int(np.argmax(~sep)) if np.any(~sep) else k
+    assert np.array_equal(res.J.cpu().numpy()[:first], ref["J"][:first])
+    if first == k:
+        assert np.max(np.abs(res.T.cpu().numpy() - ref["T"])) <= 1e-8 * max(1.0, np.max(np.abs(ref["T"])))
