@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 column-ID hot path.
+
+Workload (one step = one full ID: sketch -> pivoted QR -> coefficient solve):
+A = U diag(sigma) V^T, 20000 x 2000 FP64, sigma_i = i^-2 (seeded orthonormal
+U, V); Gaussian Omega of 110 x 20000 rounded to bfloat16; rank k = 100.
+Mixed precision by default: power-of-two scaled bfloat16 sketch on the
+tensor cores with FP32 accumulation, FP32 pivoted QR of Y, FP64 T solve with
+one refinement step.  Inputs stay resident in HBM for the timed loop (A is
+320 MB, larger than the 129 MB L2, so no flush is needed); `e2e` repeats the
+measurement with A and Omega copied from pinned host memory each step and the
+result read back.
+
+Also reported: the plain FP64 GPU ID on the same matrix and Omega (FP64
+sketch by DFMA), the 3-piece bfloat16 sketch (the matched-error form), their
+errors, the roofline of the dominant kernel, sampled SM clocks, and the FP64
+CPU oracle timed on the host (`cpu_baseline`).  `--impl reference` times the
+oracle alone as the reference arm.
+
+Under torchrun (N > 1) every rank runs its own IDs (independent problems, no
+collective on the data path); value = all ranks' IDs / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IDs/sec and effective TFLOP/s, mixed vs plain FP64 GPU ID at rel.err ≤1e-6"
+M, N, K, P = 20000, 2000, 100, 10
+ELL = K + P
+WORKLOAD = ("randomized column ID, A 20000x2000 FP64 (sigma_i = i^-2, seeded orthonormal factors), "
+            "Gaussian Omega 110x20000, rank k=100")
+
+
+def id_flops(m, n, ell, k, sketch=True):
+    """Algorithmic flops of one ID: sketch 2 ell m n, truncated Householder CPQR on the
+    r x n pivoted matrix 4rnk - 2k^2(r+n) + 4k^3/3, triangular solve k^2 (n-k)."""
+    r = ell if sketch else m
+    f = 4.0 * r * n * k - 2.0 * k * k * (r + n) + 4.0 * k ** 3 / 3.0 + k * k * (n - k)
+    if sketch:
+        f += 2.0 * ell * m * n
+    return f
+
+
+def sketch_bytes(m, n, ell, a_bytes=8):
+    """Algorithmic bytes of the sketch kernel: read A and Omega once, write Y."""
+    return a_bytes * m * n + 2 * ell * m + 4 * ell * n
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in ("sketch.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2012_00706_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the sketch kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sketch_lowp_20000x2000.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            key, _, v = line.strip()[2:].partition(":")
+            vals[key.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_id_timed(cfg, rows=None):
+    """Time the FP64 oracle ID on the workload (optionally on a row sample of the
+    sketch; the sketch time is then scaled to all rows).  Returns (seconds per full
+    ID, result of the last run)."""
+    import oracle
+    a, om = cfg["A"], cfg["omega"]
+    m = a.shape[0]
+    rows = m if rows is None else min(rows, m)
+    t0 = time.perf_counter()
+    y = oracle.sketch_f64(om[:, :rows], a[:rows])
+    t_sketch = (time.perf_counter() - t0) * (m / rows)
+    t1 = time.perf_counter()
+    r = oracle.cpqr(y, k=K, norm_mode="downdate")
+    T = oracle.solve_T(r["R"], r["J"], r["k"])
+    t_rest = time.perf_counter() - t1
+    return t_sketch + t_rest, {"J": r["J"], "T": T, "k": r["k"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import workloads as wl
+    import oracle
+    oracle.build()
+    cfg = wl.config2()
+    # size each step so that warmup + steps take about two minutes of host time
+    probe_rows = 2000
+    t_probe, _ = oracle_id_timed(cfg, rows=probe_rows)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rows = int(min(M, max(500, M * budget / max(t_probe, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_id_timed(cfg, rows=rows)
+    ts = [oracle_id_timed(cfg, rows=rows)[0] for _ in range(args.steps)]
+    sec = statistics.mean(ts)
+    value = 1.0 / sec
+    sample = (f"each step: FP64 oracle ID (plain C, 1 thread) with the sketch over {rows} of {M} rows "
+              f"(time scaled to all rows) plus the full pivoted QR and T solve")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "IDs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "ell": ELL},
+        "cpu_baseline": {"value": value, "unit": "IDs/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "IDs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "tflops": id_flops(M, N, ELL, K) / sec / 1e12,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="mixed_bf16")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/matched/e2e/cpu legs")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2012_00706_gb300 as gid
+    import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    gid.load()
+    cfg = wl.config2()
+    a_np, bits = cfg["A"], cfg["omega_bits"]
+    A = torch.from_numpy(a_np).to(dev)                       # (m, n), column-major strides
+    assert A.stride(0) == 1
+    omega = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
+    omega64 = torch.from_numpy(cfg["omega"]).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def make_out(kcap):
+        J = torch.empty(N, dtype=torch.int32, device=dev)
+        T = torch.empty((N - 1, kcap), dtype=torch.float64, device=dev).t()
+        small = torch.zeros(2, dtype=torch.int32, device=dev)
+        err = torch.zeros(1, dtype=torch.float64, device=dev)
+        return J, T, small, err
+
+    def run_loop(precision, om, steps, warmup, stage=False, a_src=None, host=None):
+        ws = torch.empty(gid.id_workspace_size(M, N, torch.float64, k=K, precision=precision, sketch=True,
+                                               ell=ELL, omega=om), dtype=torch.uint8, device=dev)
+        out = make_out(K)
+        A_use = A if a_src is None else a_src
+
+        def one():
+            if host is not None:
+                A_use.copy_(host["A"], non_blocking=True)
+                om.copy_(host["omega"], non_blocking=True)
+            gid.id_factor(A_use, K, precision=precision, omega=om, workspace=ws, out=out, sync=False)
+            if host is not None:
+                host["J"].copy_(out[0], non_blocking=True)
+                host["T"].copy_(out[1][:, : N - K], non_blocking=True)
+                host["small"].copy_(out[2], non_blocking=True)
+
+        for _ in range(warmup):
+            one()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(steps)] if stage else None
+        barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(steps):
+            if stage:
+                gid.set_stage_events(evs[i])
+            one()
+        t1.record(stream)
+        gid.set_stage_events(None)
+        torch.cuda.synchronize()
+        barrier()
+        total_ms = t0.elapsed_time(t1)
+        stages = None
+        if stage:
+            names = ["sketch_kernel", "sketch_reduce", "cpqr", "solve_T", "tail"]
+            stages = {nm: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j, nm in enumerate(names)}
+        return total_ms, out, stages
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    gpu_uuid = None
+    try:
+        gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if gpu_uuid and not gpu_uuid.startswith("GPU-"):
+            gpu_uuid = "GPU-" + gpu_uuid
+    except Exception:
+        gpu_uuid = None
+    sampler = ClockSampler(gpu_uuid) if rank == 0 else None
+
+    # ---- main timed region: inputs resident in HBM
+    if sampler:
+        sampler.start()
+    total_ms, out_main, stages = run_loop(args.precision, omega, args.steps, args.warmup, stage=True)
+    clocks = sampler.stop() if sampler else None
+    total_ms = max_over_ranks(total_ms)
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    kernels_per_step = 4
+
+    hbm_peak, bf16_peak, peak_src = measured_peaks()
+    sk_ms = stages["sketch_kernel"]
+    alg_bytes = sketch_bytes(M, N, ELL)
+    achieved = alg_bytes / (sk_ms / 1e3) / 1e9
+    traffic = ncu_traffic()
+    roofline = {"kernel": "k_sketch_lowp", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                "algorithmic_bytes": alg_bytes, "kernel_ms": sk_ms,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "IDs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "ell": ELL, "precision": args.precision,
+                   "l2": "inputs larger than L2 (A is 320 MB vs 129 MB L2); no flush needed"},
+        "tflops": id_flops(M, N, ELL, K) * value / 1e12,
+        "stages_ms": stages, "roofline": roofline, "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clocks,
+    }
+
+    if not args.no_extras:
+        # ---- e2e: A and Omega from pinned host memory each step, outputs back to the host
+        host = {"A": torch.from_numpy(a_np).pin_memory(),
+                "omega": omega.cpu().pin_memory(),
+                "J": torch.empty(N, dtype=torch.int32).pin_memory(),
+                "T": torch.empty((K, N - K), dtype=torch.float64).pin_memory(),
+                "small": torch.empty(2, dtype=torch.int32).pin_memory()}
+        host["T"] = host["T"].t().contiguous().t()
+        A_e2e = torch.empty_like(A)
+        om_e2e = torch.empty_like(omega)
+        e2e_steps = max(3, min(args.steps, 10))
+        e2e_ms, _, _ = run_loop(args.precision, om_e2e, e2e_steps, 2, a_src=A_e2e, host=host)
+        e2e_ms = max_over_ranks(e2e_ms)
+        h2d = 8 * M * N + 2 * ELL * M
+        d2h = 4 * N + 8 * K * (N - K) + 8
+        line["e2e"] = {"value": world * e2e_steps / (e2e_ms / 1e3), "unit": "IDs/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+        # ---- plain FP64 GPU ID (same A, same Omega in FP64) and the matched-error form
+        p_steps = max(3, min(args.steps, 5))
+        p_ms, out_plain, p_stages = run_loop("plain_f64", omega64, p_steps, 1, stage=True)
+        x_ms, out_x3, _ = run_loop("mixed_bf16x3", omega, args.steps, 2)
+        plain_ids = p_steps / (p_ms / 1e3)
+        x3_ids = args.steps / (x_ms / 1e3)
+        line["plain_f64"] = {"ids_per_s": plain_ids, "ms_per_id": p_ms / p_steps, "stages_ms": p_stages,
+                             "tflops": id_flops(M, N, ELL, K) * plain_ids / 1e12}
+        line["mixed_bf16x3"] = {"ids_per_s": x3_ids, "ms_per_id": x_ms / args.steps}
+
+        # ---- accuracy (FP64 on the GPU): relative 2-norm errors and distances between IDs
+        def ahat(out):
+            J, T, small, _ = out
+            k = int(small[0].item())
+            Jn = J.long()
+            P_ = torch.zeros((k, N), dtype=torch.float64, device=dev)
+            P_[:, Jn[:k]] = torch.eye(k, dtype=torch.float64, device=dev)
+            P_[:, Jn[k:]] = T[:k, : N - k]
+            return A[:, Jn[:k]] @ P_
+
+        def norm2(X, iters=60):
+            g = torch.Generator(device=dev)
+            g.manual_seed(0)
+            v = torch.randn(X.shape[1], dtype=torch.float64, device=dev, generator=g)
+            v /= v.norm()
+            s = 0.0
+            for _ in range(iters):
+                w = X.T @ (X @ v)
+                s = float(w.norm().sqrt())
+                v = w / w.norm()
+            return s
+
+        na = norm2(A)
+        h_m, h_p, h_x = ahat(out_main), ahat(out_plain), ahat(out_x3)
+        line["accuracy"] = {
+            "e_mixed": norm2(A - h_m) / na, "e_plain_f64": norm2(A - h_p) / na, "e_bf16x3": norm2(A - h_x) / na,
+            "d_mixed_vs_plain": norm2(h_m - h_p) / na, "d_bf16x3_vs_plain": norm2(h_x - h_p) / na,
+            "same_skeleton_bf16x3": bool(torch.equal(out_x3[0][:K], out_plain[0][:K])),
+        }
+        d3 = line["accuracy"]["d_bf16x3_vs_plain"]
+        line["speedup_vs_plain_f64"] = {"mixed_bf16": value / world / plain_ids,
+                                        "mixed_bf16x3": x3_ids / plain_ids,
+                                        "matched_1e-6_form": "mixed_bf16x3" if d3 <= 1e-6 else None}
+        del h_m, h_p, h_x
+
+        # ---- the FP64 CPU oracle on the host (rank 0, N = 1 only)
+        if rank == 0 and world == 1:
+            import oracle
+            oracle.build()
+            ts = []
+            t_start = time.perf_counter()
+            while len(ts) < 3 and (time.perf_counter() - t_start) < 20.0:
+                ts.append(oracle_id_timed(cfg)[0])
+            line["cpu_baseline"] = {"value": 1.0 / statistics.mean(ts), "unit": "IDs/s", "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": f"{len(ts)} full IDs of this workload (FP64 oracle, plain C, "
+                                              f"1 thread: sketch, pivoted QR, T solve)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -164,6 +164,16 @@ id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t 
                           int32_t precision, uint16_t* pieces, int32_t* shifts,
                           int32_t* info, void* stream);
 
+/* Profiling aid (not part of the computation).  When set, the next id_factor
+ * calls made from this host thread record the caller's CUDA events (cudaEvent_t
+ * passed as void*) on their stream at the stage boundaries:
+ *   events[0] start, [1] after the sketch kernel, [2] after the sketch's
+ *   split-K reduction, [3] after the pivoted QR, [4] after the T solve,
+ *   [5] end.
+ * Stages a call does not run record at the same point as the previous one.
+ * count <= 0 or events == NULL switches recording off.  Always ID_OK. */
+id_status_t id_set_stage_events(void* const* events, int32_t count);
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char* id_status_string(id_status_t status);
 

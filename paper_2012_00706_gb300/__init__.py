@@ -19,7 +19,7 @@ import torch
 
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
-    "status_string", "lib_path",
+    "status_string", "lib_path", "set_stage_events",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,8 +74,9 @@ def load():
         lib.id_sketch_workspace_size.argtypes = [ctypes.c_int, i64, i64, i32, i32, ctypes.POINTER(sz)]
         lib.id_sketch.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i64, i32, i32, p, i64, p, p, sz, p]
         lib.id_scale_cast.argtypes = [p, ctypes.c_int, i64, i64, i64, i32, p, p, p, p]
+        lib.id_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         for name in ("id_workspace_size", "id_factor", "id_sketch_workspace_size", "id_sketch",
-                     "id_scale_cast"):
+                     "id_scale_cast", "id_set_stage_events"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -197,6 +198,19 @@ def id_factor(A: torch.Tensor, k: int | None = None, *, tol: float | None = None
         return IDResult(J, T, -1, -1, None)
     kk, info = (int(v) for v in small.cpu())
     return IDResult(J, T[:kk, : n - kk], kk, info, float(err.item()) if estimate_error else None)
+
+
+def set_stage_events(events) -> None:
+    """Record these torch.cuda.Event objects at id_factor's stage boundaries (None: stop)."""
+    lib = load()
+    if not events:
+        lib.id_set_stage_events(None, 0)
+        return
+    for e in events:
+        if not e.cuda_event:        # torch creates the CUDA event at its first record
+            e.record()
+    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    lib.id_set_stage_events(arr, len(events))
 
 
 def id_sketch(A: torch.Tensor, omega: torch.Tensor, precision: str = "mixed_bf16", stream=None) -> torch.Tensor:

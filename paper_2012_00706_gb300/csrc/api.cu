@@ -35,6 +35,15 @@ const DeviceInfo& device_info() {
 
 namespace {
 
+thread_local cudaEvent_t t_stage_events[8];
+thread_local int t_stage_count = 0;
+
+void record_stage(int i, cudaStream_t s) {
+    if (i < t_stage_count) cudaEventRecord(t_stage_events[i], s);
+}
+
+cudaEvent_t stage_event(int i) { return i < t_stage_count ? t_stage_events[i] : nullptr; }
+
 uint64_t limit_ns_of(const id_opts_t& o) {
     const int64_t ms = o.watchdog_ms > 0 ? o.watchdog_ms : 4000;
     return static_cast<uint64_t>(ms) * 1000000ull;
@@ -54,6 +63,8 @@ struct FactorPlan {
     SketchPlan sp;
     SketchF64Plan sp64;
     CpqrPlan cp;
+    ClusterCpqrPlan ccp;
+    int use_cluster = 0;    // FP32 pivoting of at most 128 rows: one thread-block cluster
     size_t bytes = 0;
 };
 
@@ -132,6 +143,9 @@ id_status_t plan_factor(id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, c
         }
     }
     cpqr_plan(p.rows, n, p.w_f64 ? 8 : 4, &p.cp);
+    // the cluster kernel reads A directly when it is a short float matrix (PLAIN_F32, no sketch)
+    const bool short_f32 = !p.w_f64 && (p.sketch || a_dtype == ID_F32);
+    p.use_cluster = short_f32 && cpqr_cluster_plan(p.rows, n, &p.ccp) ? 1 : 0;
     p.bytes = carve_factor(nullptr, n, p, nullptr);
     *plan = p;
     return ID_OK;
@@ -173,6 +187,16 @@ const char* id_status_string(id_status_t s) {
 
 const char* id_version(void) { return "gb300-id 0.1 (sm_103a)"; }
 
+id_status_t id_set_stage_events(void* const* events, int32_t count) {
+    if (!events || count <= 0) {
+        t_stage_count = 0;
+        return ID_OK;
+    }
+    t_stage_count = count > 8 ? 8 : count;
+    for (int i = 0; i < t_stage_count; ++i) t_stage_events[i] = static_cast<cudaEvent_t>(events[i]);
+    return ID_OK;
+}
+
 id_status_t id_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts, size_t* bytes) {
     if (!bytes) return ID_ERR_ARG;
     FactorPlan p;
@@ -201,30 +225,51 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
 
     cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(k_out, 0, sizeof(int32_t), s);
+    record_stage(0, s);
     const void* cpqr_src = nullptr;
     int64_t ldsrc = 0;
     if (e == cudaSuccess && p.sketch) {
         if (p.mixed) {
             e = launch_sketch_lowp(A, a_f64, m, n, lda, static_cast<const uint16_t*>(opts->omega), p.omega_ld,
                                    opts->ell, opts->precision, p.sp, static_cast<float*>(f.partial),
-                                   static_cast<float*>(f.W), opts->ell, info, lim, s);
+                                   static_cast<float*>(f.W), opts->ell, info, lim, s, stage_event(1));
         } else {
             e = launch_sketch_f64(static_cast<const double*>(A), m, n, lda,
                                   static_cast<const double*>(opts->omega), p.omega_ld, opts->ell, p.sp64,
-                                  static_cast<double*>(f.partial), static_cast<double*>(f.W), opts->ell, info, s);
+                                  static_cast<double*>(f.partial), static_cast<double*>(f.W), opts->ell, info, s,
+                                  stage_event(1));
         }
     } else if (e == cudaSuccess) {
+        record_stage(1, s);
         cpqr_src = A;
         ldsrc = lda;
     }
+    record_stage(2, s);
+    const double rel_tol = opts->rel_tol > 0.0 ? opts->rel_tol : 0.0;
+    if (e == cudaSuccess) {
+        if (p.use_cluster) {
+            // short FP32 matrix: the sketch Y (or a short A) goes straight to the cluster kernel
+            const float* Wf = static_cast<const float*>(f.W);
+            int64_t ldw = p.rows;
+            if (!p.sketch) {
+                Wf = static_cast<const float*>(A);
+                ldw = lda;
+            }
+            e = launch_cpqr_cluster(Wf, p.rows, n, ldw, p.kcap, rel_tol, J, k_out, info, f.R64, p.kcap, f.sel,
+                                    p.ccp, lim, s);
+        } else {
+            e = launch_cpqr(f.W, p.w_f64, p.rows, n, p.rows, cpqr_src, a_f64, ldsrc, p.kcap, rel_tol, J, k_out, info,
+                            f.R64, p.kcap, f.nu, f.nuref, f.sel, f.ctrl, p.cp, lim, s);
+        }
+    }
+    record_stage(3, s);
     if (e == cudaSuccess)
-        e = launch_cpqr(f.W, p.w_f64, p.rows, n, p.rows, cpqr_src, a_f64, ldsrc, p.kcap,
-                        opts->rel_tol > 0.0 ? opts->rel_tol : 0.0, J, k_out, info, f.R64, p.kcap, f.nu,
-                        f.nuref, f.sel, f.ctrl, p.cp, lim, s);
-    if (e == cudaSuccess)
-        e = launch_solve_T(f.R64, p.kcap, J, k_out, p.kcap, n, T, ldt, f.tscr, opts->refine_steps, s);
+        e = launch_solve_T(f.R64, p.kcap, J, k_out, p.kcap, n, T, ldt, f.tscr, opts->refine_steps, p.w_f64 ? 0 : 1,
+                           s);
+    record_stage(4, s);
     if (e == cudaSuccess && opts->estimate_error)
         e = launch_residual_fro(A, a_f64, m, n, lda, J, k_out, T, ldt, f.acc, err_out, s);
+    record_stage(5, s);
     return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
 }
 

@@ -1,0 +1,405 @@
+// Truncated column-pivoted Householder QR of a short FP32 matrix on one thread-block
+// cluster (Sec. 1.1 / Algorithm 1 line 3 applied to the sketch Y of the mixed path).
+//
+// The sketch Y has ell <= 128 rows, so a column fits in the registers of a few
+// threads: TPC threads own one column, each a contiguous block of MAXR / TPC
+// rows.  The n columns are split over the C CTAs of a cluster (up to 16).
+//
+// Every pivot step needs one global argmax.  Each CTA stages its best candidate
+// (norm, index, sum of norms) and that candidate's current column in its own
+// shared memory and bulk-copies the record into every peer's shared memory
+// (cp.async.bulk shared::cta -> shared::cluster), completing on the peer's
+// mbarrier in bytes.  Each CTA waits (bounded) on its own mbarrier, reduces the
+// C records in the same order, and so all CTAs agree on the pivot and hold its
+// column locally: one exchange per step, no grid barrier and no memory fences.
+//
+// Per step each column forms w = v^T x(j:r) with the reflector
+// v = x_p / (alpha - beta) (v_j = 1), applies x -= tau w v, records
+// R(j, i) = x_j, and downdates its squared norm with the Drmac-Bujanovic
+// recompute test.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+
+namespace gid {
+
+constexpr int kCqMaxCluster = 16;
+constexpr int kCqMaxThreads = 512;
+
+struct CqParams {
+    const float* Y;
+    int64_t r, n, ldy;
+    int kcap;
+    double rel_tol;
+    int32_t* J;
+    int32_t* k_out;
+    int32_t* info;
+    double* R;
+    int64_t ldr;
+    uint8_t* sel;
+    int64_t cpb;          // columns per CTA
+    uint64_t limit_ns;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_nrank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t map_peer(uint32_t local_addr, uint32_t rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(local_addr), "r"(rank));
+    return out;
+}
+
+// Bulk copy of `bytes` from this CTA's shared memory into a peer's shared memory,
+// counted in bytes on the peer's mbarrier.
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
+                                            uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_cluster),
+        "r"(src_cta), "r"(bytes), "r"(bar_cluster)
+        : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// (value, index) argmax with ties to the smaller index; -1 index marks "none".
+__device__ __forceinline__ void better(float& v, int& i, float ov, int oi) {
+    if (oi >= 0 && (i < 0 || ov > v || (ov == v && oi < i))) { v = ov; i = oi; }
+}
+
+template <int MAXR>
+struct CqRecord {
+    float4 head;          // (best norm, index bits, sum of norms, unused)
+    float col[MAXR];
+};
+
+template <int MAXR, int TPC>
+__global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParams P) {
+    constexpr int RPT = MAXR / TPC;
+    constexpr uint32_t REC = sizeof(CqRecord<MAXR>);
+    static_assert(REC % 16 == 0, "record size");
+    __shared__ __align__(128) CqRecord<MAXR> recv[2][kCqMaxCluster];
+    __shared__ __align__(128) CqRecord<MAXR> stg[2];
+    __shared__ float wv[32];
+    __shared__ int wi[32];
+    __shared__ float wsum[32];
+    __shared__ __align__(8) uint64_t recv_bar[2];
+
+    const uint32_t me = cluster_rank(), C = cluster_nrank();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    const int cl = t / TPC, qq = t % TPC;
+    const int64_t i = static_cast<int64_t>(me) * P.cpb + cl;
+    const bool valid = cl < P.cpb && i < P.n;
+    const int r = static_cast<int>(P.r);
+    const int rb = qq * RPT;                 // first row of this thread's block
+    const float sqrt_u = 2.44140625e-04f;    // sqrt of the FP32 unit round-off 2^-24
+
+    if (t == 0) {
+        mbar_init(&recv_bar[0], 1);
+        mbar_init(&recv_bar[1], 1);
+        fence_barrier_init();
+    }
+    cluster_sync_all();
+
+    float x[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) x[u] = (valid && rb + u < r) ? P.Y[i * P.ldy + rb + u] : 0.f;
+    float nu = 0.f;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) nu = fmaf(x[u], x[u], nu);
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) nu += __shfl_xor_sync(0xffffffffu, nu, o);
+    float nuref = nu;
+    bool selected = !valid;
+    if (valid && qq == 0) {
+        if (!isfinite(nu)) set_info(P.info, kInfoNonFinite);
+        P.sel[i] = 0;
+    }
+
+    // Exchange q: arm own barrier, stage the CTA's best candidate, bulk-copy it to every peer.
+    // Exchange q fills recv[q & 1] and completes phase q >> 1 of recv_bar[q & 1]; a peer can be
+    // at most one exchange ahead, so two alternating buffers and barriers never mix phases.
+    auto exchange = [&](int q) {
+        const int slot = q & 1;
+        if (t == 0) mbar_arrive_expect_tx(&recv_bar[slot], C * REC);
+        float bv = -1.f, part = 0.f;
+        int bi = -1;
+        if (!selected && qq == 0) { bv = nu; bi = static_cast<int>(i); part = nu; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            better(bv, bi, ov, oi);
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+        }
+        if (lane == 0) { wv[warp] = bv; wi[warp] = bi; wsum[warp] = part; }
+        __syncthreads();
+        float v0 = -1.f, s0 = 0.f;
+        int i0 = -1;
+        for (int w = 0; w < nw; ++w) { better(v0, i0, wv[w], wi[w]); s0 += wsum[w]; }
+        if (valid && i == i0) {
+#pragma unroll
+            for (int u = 0; u < RPT; u += 4)
+                *reinterpret_cast<float4*>(&stg[slot].col[rb + u]) = make_float4(x[u], x[u + 1], x[u + 2], x[u + 3]);
+        }
+        if (t == 0) stg[slot].head = make_float4(v0, __int_as_float(i0), s0, 0.f);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t < static_cast<int>(C)) {
+            const uint32_t d = static_cast<uint32_t>(t);
+            bulk_s2peer(map_peer(smem_addr(&recv[slot][me]), d), smem_addr(&stg[slot]), REC,
+                        map_peer(smem_addr(&recv_bar[slot]), d));
+        }
+    };
+    auto wait_exchange = [&](int q) -> bool {
+        volatile int keep = 0;
+        return mbar_wait(&recv_bar[q & 1], static_cast<uint32_t>((q >> 1) & 1), &keep, P.limit_ns);
+    };
+
+    exchange(0);
+    bool ok = wait_exchange(0);
+    int k = 0;
+    float total = 0.f;
+    for (int j = 0; ok && j < P.kcap; ++j) {
+        const int par = j & 1;
+        // ---- the pivot: identical reduction of the C records in every thread
+        float best = -1.f, sumnu = 0.f;
+        int p = -1, src = -1;
+        for (uint32_t c = 0; c < C; ++c) {
+            const float4 hv = recv[par][c].head;
+            const int ci = __float_as_int(hv.y);
+            if (ci >= 0 && (p < 0 || hv.x > best || (hv.x == best && ci < p))) { best = hv.x; p = ci; src = static_cast<int>(c); }
+            sumnu += hv.z;
+        }
+        if (j == 0) total = sumnu;
+        if (P.rel_tol > 0.0 && sqrtf(fmaxf(sumnu, 0.f)) <= static_cast<float>(P.rel_tol) * sqrtf(total)) break;
+        if (p < 0 || !(best > 0.f)) {
+            if (me == 0 && t == 0) set_info(P.info, j + 1);
+            break;
+        }
+        const float* xw = recv[par][src].col;
+        // ---- reflector scalars (every warp computes the same sum in the same order)
+        float s2 = 0.f;
+        for (int q = j + lane; q < r; q += 32) s2 = fmaf(xw[q], xw[q], s2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        const float alpha = xw[j];
+        const float snorm = sqrtf(s2);
+        const float beta = alpha >= 0.f ? -snorm : snorm;
+        const float tau = (beta - alpha) / beta;
+        const float inv = 1.f / (alpha - beta);
+        if (valid && i == p) {
+            selected = true;
+            if (qq == 0) {
+                P.R[i * P.ldr + j] = static_cast<double>(beta);
+                P.J[j] = p;
+                P.sel[i] = 1;
+            }
+        }
+        // w = x_j + inv * sum_{q > j} xw_q x_q over this thread's rows, then over the TPC threads
+        // of the column.  Every lane runs the shuffles (selected columns just discard the result).
+        float acc = 0.f, xj = 0.f;
+        if (!selected && rb + RPT > j) {
+#pragma unroll
+            for (int u = 0; u < RPT; u += 4) {
+                const float4 w4 = *reinterpret_cast<const float4*>(&xw[rb + u]);
+                const int q0 = rb + u;
+                acc = (q0 > j) ? fmaf(w4.x, x[u], acc) : acc;
+                acc = (q0 + 1 > j) ? fmaf(w4.y, x[u + 1], acc) : acc;
+                acc = (q0 + 2 > j) ? fmaf(w4.z, x[u + 2], acc) : acc;
+                acc = (q0 + 3 > j) ? fmaf(w4.w, x[u + 3], acc) : acc;
+                xj = (q0 == j) ? x[u] : xj;
+                xj = (q0 + 1 == j) ? x[u + 1] : xj;
+                xj = (q0 + 2 == j) ? x[u + 2] : xj;
+                xj = (q0 + 3 == j) ? x[u + 3] : xj;
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < TPC; o <<= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            xj += __shfl_xor_sync(0xffffffffu, xj, o);
+        }
+        const float wdot = fmaf(inv, acc, xj);
+        const float tw = tau * wdot;
+        const float sv = tw * inv;
+        const float rho = xj - tw;
+        bool recompute = false;
+        if (!selected) {
+            if (rb + RPT > j) {
+#pragma unroll
+                for (int u = 0; u < RPT; u += 4) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(&xw[rb + u]);
+                    const int q0 = rb + u;
+                    x[u] = (q0 > j) ? fmaf(-sv, w4.x, x[u]) : ((q0 == j) ? rho : x[u]);
+                    x[u + 1] = (q0 + 1 > j) ? fmaf(-sv, w4.y, x[u + 1]) : ((q0 + 1 == j) ? rho : x[u + 1]);
+                    x[u + 2] = (q0 + 2 > j) ? fmaf(-sv, w4.z, x[u + 2]) : ((q0 + 2 == j) ? rho : x[u + 2]);
+                    x[u + 3] = (q0 + 3 > j) ? fmaf(-sv, w4.w, x[u + 3]) : ((q0 + 3 == j) ? rho : x[u + 3]);
+                }
+            }
+            if (qq == 0) P.R[i * P.ldr + j] = static_cast<double>(rho);
+            if (nu > 0.f) {
+                const float t1 = fmaxf(1.f - (rho * rho) / nu, 0.f);
+                if (t1 * (nu / nuref) <= sqrt_u) recompute = true;   // same decision in all TPC threads
+                else nu = nu * t1;
+            }
+        }
+        if (__any_sync(0xffffffffu, recompute)) {
+            float s = 0.f;
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) s = (rb + u > j) ? fmaf(x[u], x[u], s) : s;
+#pragma unroll
+            for (int o = 1; o < TPC; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (recompute) {
+                nu = s;
+                nuref = s;
+            }
+        }
+        exchange(j + 1);
+        ok = wait_exchange(j + 1);
+        k = j + 1;
+    }
+    if (!ok && t == 0) set_info(P.info, kInfoWatchdog);
+    // no CTA leaves while a peer may still copy into its shared memory
+    cluster_sync_all();
+    if (me == 0) {
+        if (t == 0) *P.k_out = k;
+        __shared__ int s_base;
+        __shared__ int cnt[32];
+        if (t == 0) s_base = k;
+        __syncthreads();
+        for (int64_t i0 = 0; i0 < P.n; i0 += blockDim.x) {
+            const int64_t c = i0 + t;
+            const int flag = (c < P.n && !__ldcg(P.sel + c)) ? 1 : 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, flag);
+            const int wpre = __popc(bal & ((1u << lane) - 1u));
+            if (lane == 0) cnt[warp] = __popc(bal);
+            __syncthreads();
+            int off = 0;
+            for (int w = 0; w < warp; ++w) off += cnt[w];
+            if (flag) P.J[s_base + off + wpre] = static_cast<int32_t>(c);
+            __syncthreads();
+            if (t == 0) {
+                int tot = 0;
+                for (int w = 0; w < nw; ++w) tot += cnt[w];
+                s_base += tot;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int MAXR, int TPC>
+static cudaLaunchConfig_t cq_config(int csize, int threads, cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Can a cluster of csize CTAs of this kernel be resident at once?
+template <int MAXR, int TPC>
+static bool cq_cluster_fits(int csize, int threads) {
+    auto kern = k_cpqr_cluster<MAXR, TPC>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cq_config<MAXR, TPC>(csize, threads, nullptr, attr);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters > 0;
+}
+
+template <int MAXR, int TPC>
+static cudaError_t launch_cq(const CqParams& P, int csize, int threads, cudaStream_t s) {
+    auto kern = k_cpqr_cluster<MAXR, TPC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cq_config<MAXR, TPC>(csize, threads, s, attr);
+    return cudaLaunchKernelEx(&cfg, kern, P);
+}
+
+template <int MAXR>
+static bool cq_fits(int tpc, int csize, int threads) {
+    return tpc == 4 ? cq_cluster_fits<MAXR, 4>(csize, threads) : cq_cluster_fits<MAXR, 2>(csize, threads);
+}
+
+bool cpqr_cluster_plan(int64_t r, int64_t n, ClusterCpqrPlan* plan) {
+    if (r < 1 || r > 128 || n < 1) return false;
+    const int maxr = r <= 32 ? 32 : (r <= 64 ? 64 : 128);
+    int csize = static_cast<int>(std::min<int64_t>(kCqMaxCluster, std::max<int64_t>(1, (n + 63) / 64)));
+    for (; csize >= 1; csize = csize > 8 ? 8 : csize - 1) {
+        const int64_t cpb = (n + csize - 1) / csize;
+        int tpc = 0;
+        if (cpb * 4 <= kCqMaxThreads) tpc = 4;
+        else if (cpb * 2 <= kCqMaxThreads) tpc = 2;
+        else return false;
+        const int threads = static_cast<int>((cpb * tpc + 31) / 32 * 32);
+        const bool fits = maxr == 32 ? cq_fits<32>(tpc, csize, threads)
+                        : maxr == 64 ? cq_fits<64>(tpc, csize, threads)
+                                     : cq_fits<128>(tpc, csize, threads);
+        if (fits) {
+            plan->csize = csize;
+            plan->cpb = cpb;
+            plan->threads = threads;
+            plan->maxr = maxr;
+            plan->tpc = tpc;
+            return true;
+        }
+        if (csize == 1) break;
+    }
+    return false;
+}
+
+cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kcap, double rel_tol,
+                                int32_t* J, int32_t* k_out, int32_t* info, double* R64, int64_t ldr, uint8_t* sel,
+                                const ClusterCpqrPlan& plan, uint64_t limit_ns, cudaStream_t s) {
+    CqParams P{};
+    P.Y = Y; P.r = r; P.n = n; P.ldy = ldy;
+    P.kcap = kcap; P.rel_tol = rel_tol;
+    P.J = J; P.k_out = k_out; P.info = info;
+    P.R = R64; P.ldr = ldr; P.sel = sel;
+    P.cpb = plan.cpb;
+    P.limit_ns = limit_ns;
+    const int cs = plan.csize, th = plan.threads;
+    if (plan.tpc == 4) {
+        switch (plan.maxr) {
+            case 32: return launch_cq<32, 4>(P, cs, th, s);
+            case 64: return launch_cq<64, 4>(P, cs, th, s);
+            default: return launch_cq<128, 4>(P, cs, th, s);
+        }
+    }
+    switch (plan.maxr) {
+        case 32: return launch_cq<32, 2>(P, cs, th, s);
+        case 64: return launch_cq<64, 2>(P, cs, th, s);
+        default: return launch_cq<128, 2>(P, cs, th, s);
+    }
+}
+
+}  // namespace gid

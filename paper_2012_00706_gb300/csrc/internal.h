@@ -53,7 +53,8 @@ size_t sketch_partial_bytes_lowp(const SketchPlan& p, int64_t n);
 cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                                const uint16_t* omega, int64_t ldo, int ell, int precision,
                                const SketchPlan& plan, float* partial, float* Y, int64_t ldy,
-                               int32_t* info, uint64_t limit_ns, cudaStream_t s);
+                               int32_t* info, uint64_t limit_ns, cudaStream_t s,
+                               cudaEvent_t after_main = nullptr);
 
 struct SketchF64Plan {
     int kslabs = 0;
@@ -64,7 +65,7 @@ void sketch_plan_f64(int64_t m, int64_t n, int ell, SketchF64Plan* plan);
 cudaError_t launch_sketch_f64(const double* A, int64_t m, int64_t n, int64_t lda,
                               const double* omega, int64_t ldo, int ell,
                               const SketchF64Plan& plan, double* partial, double* Y, int64_t ldy,
-                              int32_t* info, cudaStream_t s);
+                              int32_t* info, cudaStream_t s, cudaEvent_t after_main = nullptr);
 cudaError_t launch_scale_cast(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                               int precision, uint16_t* pieces, int32_t* shifts, int32_t* info,
                               cudaStream_t s);
@@ -83,10 +84,23 @@ cudaError_t launch_cpqr(void* W, int w_f64, int64_t r, int64_t n, int64_t ldw, c
                         void* nuref, uint8_t* sel, void* ctrl, const CpqrPlan& plan,
                         uint64_t limit_ns, cudaStream_t s);
 
+// ---- pivoted QR of a short FP32 matrix on one thread-block cluster (cpqr_cluster.cu)
+struct ClusterCpqrPlan {
+    int csize = 0;
+    int64_t cpb = 0;
+    int threads = 0;
+    int maxr = 0;
+    int tpc = 0;          // threads per column
+};
+bool cpqr_cluster_plan(int64_t r, int64_t n, ClusterCpqrPlan* plan);
+cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kcap, double rel_tol,
+                                int32_t* J, int32_t* k_out, int32_t* info, double* R64, int64_t ldr, uint8_t* sel,
+                                const ClusterCpqrPlan& plan, uint64_t limit_ns, cudaStream_t s);
+
 // ---- coefficient solve and error estimate (trsm.cu)
 cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr,
                            int kcap, int64_t n, double* T, int64_t ldt, double* scratch,
-                           int refine_steps, cudaStream_t s);
+                           int refine_steps, int low_solve, cudaStream_t s);
 size_t solve_T_scratch_doubles(int kcap, int64_t n);
 cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                                 const int32_t* J, const int32_t* k_ptr, const double* T,

@@ -80,16 +80,21 @@ __device__ __forceinline__ float scaled_f32_from_f32(float x, int s) {
     return scaled_slow(static_cast<double>(x), s);
 }
 
-// One low-format piece of r (round to nearest even) and the exact remainder.
-__device__ __forceinline__ uint16_t take_piece(float& r, int f16) {
+// Two low-format pieces at once (packed round-to-nearest-even conversion) and
+// the exact remainders; the first value goes to the low 16 bits.
+__device__ __forceinline__ uint32_t take_piece2(float& a, float& b, int f16) {
     if (f16) {
-        const __half h = __float2half_rn(r);
-        r = r - __half2float(h);
-        return __half_as_ushort(h);
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 f = __half22float2(h);
+        a = a - f.x;
+        b = b - f.y;
+        return *reinterpret_cast<const uint32_t*>(&h);
     }
-    const __nv_bfloat16 b = __float2bfloat16_rn(r);
-    r = r - __bfloat162float(b);
-    return __bfloat16_as_ushort(b);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(&h);
+    a = a - __uint_as_float(w << 16);
+    b = b - __uint_as_float(w & 0xFFFF0000u);
+    return w;
 }
 
 int precision_nsplit(int precision) {
@@ -120,12 +125,20 @@ struct LowpParams {
 };
 
 constexpr uint32_t kAopTileBytes = kTileCols * 128;   // 128 rows x 64 bf16
+// warps: 0 producer, 1 MMA issuer, 2 TMEM allocator, 3 idle, 4..11 converters, 12..15 epilogue
+constexpr int kConvWarps = 8;
+// L2 prefetch: every kPrefetchGroup chunks the producer prefetches the next group of
+// chunks starting kPrefetchChunks ahead (4 chunks x 64 rows x 8 B = 2 KB per column).
+constexpr int kPrefetchGroup = 4;
+constexpr int kPrefetchChunks = 8;
+constexpr int kSketchThreads = (4 + kConvWarps + 4) * 32;
 
 struct LowpSmem {
     uint8_t* aop;        // [aop_bufs][nsplit][16 KB]
     uint8_t* omega;      // [omega_bufs][omega_tile_bytes]
     uint8_t* stage;      // [stages][stage_bytes]
     int32_t* shifts;     // [aop_bufs + acc_bufs][128]
+    uint32_t* xmax;      // [2 chunks][2 halves][128] partial block maxima
     uint64_t* bars;
     uint32_t* tmem_holder;
     int* abort;
@@ -144,6 +157,7 @@ __host__ __device__ inline size_t lowp_carve(uintptr_t base, const LowpParams& P
     uintptr_t om = take((size_t)P.omega_bufs * P.omega_tile_bytes, 1024);
     uintptr_t st = take((size_t)P.stages * P.stage_bytes, 128);
     uintptr_t sh = take((size_t)H * kTileCols * 4, 16);
+    uintptr_t xm = take((size_t)4 * kTileCols * 4, 16);
     const int nbars = 2 * P.stages + 2 * P.omega_bufs + 2 * P.aop_bufs + 2 * P.acc_bufs + 2 * H;
     uintptr_t bars = take((size_t)nbars * 8, 8);
     uintptr_t th = take(4, 4);
@@ -153,6 +167,7 @@ __host__ __device__ inline size_t lowp_carve(uintptr_t base, const LowpParams& P
         S->omega = reinterpret_cast<uint8_t*>(om);
         S->stage = reinterpret_cast<uint8_t*>(st);
         S->shifts = reinterpret_cast<int32_t*>(sh);
+        S->xmax = reinterpret_cast<uint32_t*>(xm);
         S->bars = reinterpret_cast<uint64_t*>(bars);
         S->tmem_holder = reinterpret_cast<uint32_t*>(th);
         S->abort = reinterpret_cast<int*>(ab);
@@ -160,7 +175,7 @@ __host__ __device__ inline size_t lowp_carve(uintptr_t base, const LowpParams& P
     return static_cast<size_t>(p - base);
 }
 
-__global__ void __launch_bounds__(384, 1)
+__global__ void __launch_bounds__(kSketchThreads, 1)
 k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) {
     extern __shared__ uint8_t smem_raw[];
     const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
@@ -188,11 +203,11 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
     const int ncols_valid = static_cast<int>(min(static_cast<int64_t>(kTileCols), P.n - col0));
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NS; ++i) { mbar_init(&stage_full[i], 1); mbar_init(&stage_free[i], 4); }
+        for (int i = 0; i < NS; ++i) { mbar_init(&stage_full[i], 1); mbar_init(&stage_free[i], kConvWarps); }
         for (int i = 0; i < NO; ++i) { mbar_init(&omg_full[i], 1); mbar_init(&omg_free[i], 1); }
-        for (int i = 0; i < NA; ++i) { mbar_init(&aop_full[i], 4); mbar_init(&aop_free[i], 1); }
+        for (int i = 0; i < NA; ++i) { mbar_init(&aop_full[i], kConvWarps); mbar_init(&aop_free[i], 1); }
         for (int i = 0; i < NC; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 4); }
-        for (int i = 0; i < H; ++i) { mbar_init(&sh_full[i], 4); mbar_init(&sh_free[i], 4); }
+        for (int i = 0; i < H; ++i) { mbar_init(&sh_full[i], kConvWarps); mbar_init(&sh_free[i], 4); }
         *S.abort = 0;
         fence_barrier_init();
     }
@@ -208,6 +223,20 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
     if (warp == 0) {
         // ---------------- producer: A column slices (bulk copies) + Omega tiles (TMA)
         if (lane == 0) prefetch_tensormap(&tm_omega);
+        // warm L2 with the first prefetch window of this CTA's slab
+        if (!P.direct_all) {
+            const int64_t prow0 = ch_begin * kChunkRows;
+            const int64_t prow1 = min(P.m, min(ch_end, ch_begin + kPrefetchChunks) * kChunkRows);
+            const uint32_t pbytes = static_cast<uint32_t>(((prow1 - prow0) * elem) & ~int64_t(15));
+            if (pbytes > 0) {
+                const uint8_t* A8p = static_cast<const uint8_t*>(P.A);
+                for (int q = lane; q < ncols_valid; q += 32) {
+                    const uint8_t* base = A8p + ((col0 + q) * P.lda + prow0) * elem;
+                    for (uint32_t off = 0; off < pbytes; off += 4096u)
+                        prefetch_l2(base + off, min(4096u, pbytes - off));
+                }
+            }
+        }
         for (int i = 0; i < nloc && !*abort; ++i) {
             const int64_t c = ch_begin + i;
             const int s = i % NS, o = i % NO;
@@ -216,6 +245,21 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
                 mbar_arrive_expect_tx(&omg_full[o], P.omega_tile_bytes);
                 tma_load_2d(S.omega + (size_t)o * P.omega_tile_bytes, &tm_omega,
                             static_cast<int32_t>(c * kChunkRows), 0, &omg_full[o]);
+            }
+            // L2 prefetch of the chunks kPrefetchChunks ahead as 2 KB-class contiguous column
+            // segments: long runs keep DRAM efficient while the shared-memory stages stay small.
+            if (!P.direct_all && (i % kPrefetchGroup) == 0) {
+                const int64_t pc = c + kPrefetchChunks;
+                if (pc < ch_end) {
+                    const int64_t prow0 = pc * kChunkRows;
+                    const int64_t prow1 = min(P.m, min(ch_end, pc + kPrefetchGroup) * kChunkRows);
+                    const uint32_t pbytes = static_cast<uint32_t>(((prow1 - prow0) * elem) & ~int64_t(15));
+                    if (pbytes > 0) {
+                        const uint8_t* A8p = static_cast<const uint8_t*>(P.A);
+                        for (int q = lane; q < ncols_valid; q += 32)
+                            prefetch_l2(A8p + ((col0 + q) * P.lda + prow0) * elem, pbytes);
+                    }
+                }
             }
             if (!mbar_wait(&stage_free[s], ((i / NS) & 1) ^ 1, abort, P.limit_ns)) break;
             const int64_t row0 = c * kChunkRows;
@@ -269,9 +313,12 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
                 mbar_wait(&acc_full[b], ((issued - 1) / NC) & 1, &keep_waiting, P.limit_ns);
             }
         }
-    } else if (warp >= 4 && warp < 8) {
-        // ---------------- converters: thread t owns column col0 + t
-        const int t = threadIdx.x - 128;
+    } else if (warp >= 4 && warp < 4 + kConvWarps) {
+        // ---------------- converters: two threads per column (rows 0-31 and 32-63 of the chunk);
+        // the block maximum is combined through shared memory with a named barrier.
+        const int u = threadIdx.x - 128;
+        const int t = u & (kTileCols - 1);
+        const int half = u >> 7;
         const int64_t col = col0 + t;
         const bool valid = t < ncols_valid;
         const uint8_t* A8 = static_cast<const uint8_t*>(P.A);
@@ -284,34 +331,39 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
             const int64_t row0 = c * kChunkRows;
             const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), P.m - row0));
             const int rows_smem = P.direct_all ? 0 : ((rows * elem) & ~15) / elem;
+            const bool full = valid && rows_smem == kChunkRows;
+            const int rb = 32 * half;
             const uint8_t* scol = S.stage + (size_t)s * P.stage_bytes + (size_t)t * P.colstride;
             const uint8_t* gcol = A8 + (col * P.lda + row0) * elem;
-            int shift = 0;
+            uint32_t* xmax = S.xmax + (i & 1) * 2 * kTileCols;
+            uint32_t mx = 0;
             if (P.a_f64) {
                 const double* sd = reinterpret_cast<const double*>(scol);
                 const double* gd = reinterpret_cast<const double*>(gcol);
-                uint32_t mx = 0;
-                if (valid) {
-                    if (rows_smem == kChunkRows) {
-#pragma unroll 8
-                        for (int r = 0; r < kChunkRows; r += 2) {
-                            const double2 v = *reinterpret_cast<const double2*>(sd + r);
-                            mx = max(mx, static_cast<uint32_t>(__double2hiint(v.x)) & 0x7fffffffu);
-                            mx = max(mx, static_cast<uint32_t>(__double2hiint(v.y)) & 0x7fffffffu);
-                        }
-                    } else {
-                        for (int r = 0; r < rows; ++r) {
-                            const double x = r < rows_smem ? sd[r] : __ldg(gd + r);
-                            mx = max(mx, static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu);
-                        }
+                if (full) {
+#pragma unroll
+                    for (int r = 0; r < 32; r += 2) {
+                        const double2 v = *reinterpret_cast<const double2*>(sd + rb + r);
+                        mx = max(mx, static_cast<uint32_t>(__double2hiint(v.x)) & 0x7fffffffu);
+                        mx = max(mx, static_cast<uint32_t>(__double2hiint(v.y)) & 0x7fffffffu);
                     }
-                    if ((mx >> 20) == 0x7FFu) set_info(P.info, kInfoNonFinite);
+                } else if (valid) {
+                    for (int r = rb; r < min(rb + 32, rows); ++r) {
+                        const double x = r < rows_smem ? sd[r] : __ldg(gd + r);
+                        mx = max(mx, static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu);
+                    }
                 }
-                shift = shift_from_max_f64hi(mx, P.f16);
+                xmax[half * kTileCols + t] = mx;
+                asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
+                mx = max(mx, xmax[(half ^ 1) * kTileCols + t]);
+                if (half == 0 && (mx >> 20) == 0x7FFu) set_info(P.info, kInfoNonFinite);
+                const int shift = shift_from_max_f64hi(mx, P.f16);
+                if (half == 0) S.shifts[h * kTileCols + t] = shift;
 #pragma unroll 1
-                for (int g = 0; g < 8; ++g) {
+                for (int gg = 0; gg < 4; ++gg) {
+                    const int g = 4 * half + gg;
                     float v[8];
-                    if (valid && rows_smem == kChunkRows) {
+                    if (full) {
 #pragma unroll
                         for (int q = 0; q < 8; q += 2) {
                             const double2 d2 = *reinterpret_cast<const double2*>(sd + 8 * g + q);
@@ -327,46 +379,44 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
                             v[q] = scaled_f32_from_f64(x, shift);
                         }
                     }
+                    const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
                     for (int p = 0; p < P.nsplit; ++p) {
                         uint32_t w[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint32_t lo16 = take_piece(v[2 * q], P.f16);
-                            const uint32_t hi16 = take_piece(v[2 * q + 1], P.f16);
-                            w[q] = lo16 | (hi16 << 16);
-                        }
+                        for (int q = 0; q < 4; ++q) w[q] = take_piece2(v[2 * q], v[2 * q + 1], P.f16);
                         uint8_t* tile = S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes;
-                        const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
                         *reinterpret_cast<uint4*>(tile + off) = make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
             } else {
                 const float* sf = reinterpret_cast<const float*>(scol);
                 const float* gf = reinterpret_cast<const float*>(gcol);
-                uint32_t mx = 0;
-                if (valid) {
-                    if (rows_smem == kChunkRows) {
-#pragma unroll 4
-                        for (int r = 0; r < kChunkRows; r += 4) {
-                            const float4 v = *reinterpret_cast<const float4*>(sf + r);
-                            mx = max(mx, __float_as_uint(v.x) & 0x7fffffffu);
-                            mx = max(mx, __float_as_uint(v.y) & 0x7fffffffu);
-                            mx = max(mx, __float_as_uint(v.z) & 0x7fffffffu);
-                            mx = max(mx, __float_as_uint(v.w) & 0x7fffffffu);
-                        }
-                    } else {
-                        for (int r = 0; r < rows; ++r) {
-                            const float x = r < rows_smem ? sf[r] : __ldg(gf + r);
-                            mx = max(mx, __float_as_uint(x) & 0x7fffffffu);
-                        }
+                if (full) {
+#pragma unroll
+                    for (int r = 0; r < 32; r += 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(sf + rb + r);
+                        mx = max(mx, __float_as_uint(v.x) & 0x7fffffffu);
+                        mx = max(mx, __float_as_uint(v.y) & 0x7fffffffu);
+                        mx = max(mx, __float_as_uint(v.z) & 0x7fffffffu);
+                        mx = max(mx, __float_as_uint(v.w) & 0x7fffffffu);
                     }
-                    if ((mx >> 23) == 0xFFu) set_info(P.info, kInfoNonFinite);
+                } else if (valid) {
+                    for (int r = rb; r < min(rb + 32, rows); ++r) {
+                        const float x = r < rows_smem ? sf[r] : __ldg(gf + r);
+                        mx = max(mx, __float_as_uint(x) & 0x7fffffffu);
+                    }
                 }
-                shift = shift_from_max_f32(mx, P.f16);
+                xmax[half * kTileCols + t] = mx;
+                asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
+                mx = max(mx, xmax[(half ^ 1) * kTileCols + t]);
+                if (half == 0 && (mx >> 23) == 0xFFu) set_info(P.info, kInfoNonFinite);
+                const int shift = shift_from_max_f32(mx, P.f16);
+                if (half == 0) S.shifts[h * kTileCols + t] = shift;
 #pragma unroll 1
-                for (int g = 0; g < 8; ++g) {
+                for (int gg = 0; gg < 4; ++gg) {
+                    const int g = 4 * half + gg;
                     float v[8];
-                    if (valid && rows_smem == kChunkRows) {
+                    if (full) {
                         const float4 x0 = *reinterpret_cast<const float4*>(sf + 8 * g);
                         const float4 x1 = *reinterpret_cast<const float4*>(sf + 8 * g + 4);
                         v[0] = scaled_f32_from_f32(x0.x, shift); v[1] = scaled_f32_from_f32(x0.y, shift);
@@ -382,21 +432,16 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
                             v[q] = scaled_f32_from_f32(x, shift);
                         }
                     }
+                    const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
                     for (int p = 0; p < P.nsplit; ++p) {
                         uint32_t w[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint32_t lo16 = take_piece(v[2 * q], P.f16);
-                            const uint32_t hi16 = take_piece(v[2 * q + 1], P.f16);
-                            w[q] = lo16 | (hi16 << 16);
-                        }
+                        for (int q = 0; q < 4; ++q) w[q] = take_piece2(v[2 * q], v[2 * q + 1], P.f16);
                         uint8_t* tile = S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes;
-                        const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
                         *reinterpret_cast<uint4*>(tile + off) = make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
             }
-            S.shifts[h * kTileCols + t] = shift;
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
@@ -405,7 +450,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
                 mbar_arrive(&sh_full[h]);
             }
         }
-    } else if (warp >= 8) {
+    } else if (warp >= 4 + kConvWarps) {
         // ---------------- epilogue: drain each chunk, scale by 2^s, accumulate in TMEM
         const int q = warp & 3;
         const int t = 32 * q + lane;
@@ -533,7 +578,7 @@ size_t sketch_partial_bytes_lowp(const SketchPlan& p, int64_t n) {
 cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                                const uint16_t* omega, int64_t ldo, int ell, int precision,
                                const SketchPlan& plan, float* partial, float* Y, int64_t ldy,
-                               int32_t* info, uint64_t limit_ns, cudaStream_t s) {
+                               int32_t* info, uint64_t limit_ns, cudaStream_t s, cudaEvent_t after_main) {
     auto encode = get_encode_tiled();
     if (!encode) return cudaErrorNotSupported;
     const int f16 = precision_is_f16(precision);
@@ -566,9 +611,10 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
                                          static_cast<int>(plan.smem_bytes));
     if (e != cudaSuccess) return e;
     dim3 grid(plan.tiles, plan.kslabs);
-    k_sketch_lowp<<<grid, 384, plan.smem_bytes, s>>>(tm, P);
+    k_sketch_lowp<<<grid, kSketchThreads, plan.smem_bytes, s>>>(tm, P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (after_main) cudaEventRecord(after_main, s);
     const int64_t total = n * ell;
     k_reduce_partials_f32<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
         partial, plan.kslabs, n, plan.lp, ell, Y, ldy);
@@ -651,12 +697,13 @@ void sketch_plan_f64(int64_t m, int64_t n, int ell, SketchF64Plan* plan) {
 
 cudaError_t launch_sketch_f64(const double* A, int64_t m, int64_t n, int64_t lda, const double* omega,
                               int64_t ldo, int ell, const SketchF64Plan& plan, double* partial,
-                              double* Y, int64_t ldy, int32_t* info, cudaStream_t s) {
+                              double* Y, int64_t ldy, int32_t* info, cudaStream_t s, cudaEvent_t after_main) {
     dim3 grid(static_cast<unsigned>((n + kF64Tile - 1) / kF64Tile),
               static_cast<unsigned>((ell + kF64Tile - 1) / kF64Tile), static_cast<unsigned>(plan.kslabs));
     k_sketch_f64<<<grid, 256, 0, s>>>(A, m, n, lda, omega, ldo, ell, plan.k_per_slab, plan.lp, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (after_main) cudaEventRecord(after_main, s);
     const int64_t total = n * ell;
     k_reduce_partials_f64<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
         partial, plan.kslabs, n, plan.lp, ell, Y, ldy, info);
@@ -684,9 +731,14 @@ __global__ void k_scale_cast(const void* __restrict__ A, int a_f64, int64_t m, i
             mx = max(mx, static_cast<uint32_t>(__double2hiint(col[r])) & 0x7fffffffu);
         if ((mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
         shift = shift_from_max_f64hi(mx, f16);
-        for (int r = 0; r < rows; ++r) {
-            float v = scaled_f32_from_f64(col[r], shift);
-            for (int p = 0; p < nsplit; ++p) pieces[(p * n + j) * m + r0 + r] = take_piece(v, f16);
+        for (int r = 0; r < rows; r += 2) {
+            float v0 = scaled_f32_from_f64(col[r], shift);
+            float v1 = r + 1 < rows ? scaled_f32_from_f64(col[r + 1], shift) : 0.f;
+            for (int p = 0; p < nsplit; ++p) {
+                const uint32_t w = take_piece2(v0, v1, f16);
+                pieces[(p * n + j) * m + r0 + r] = static_cast<uint16_t>(w & 0xFFFFu);
+                if (r + 1 < rows) pieces[(p * n + j) * m + r0 + r + 1] = static_cast<uint16_t>(w >> 16);
+            }
         }
     } else {
         const float* col = static_cast<const float*>(A) + j * lda + r0;
@@ -694,9 +746,14 @@ __global__ void k_scale_cast(const void* __restrict__ A, int a_f64, int64_t m, i
         for (int r = 0; r < rows; ++r) mx = max(mx, __float_as_uint(col[r]) & 0x7fffffffu);
         if ((mx >> 23) == 0xFFu) set_info(info, kInfoNonFinite);
         shift = shift_from_max_f32(mx, f16);
-        for (int r = 0; r < rows; ++r) {
-            float v = scaled_f32_from_f32(col[r], shift);
-            for (int p = 0; p < nsplit; ++p) pieces[(p * n + j) * m + r0 + r] = take_piece(v, f16);
+        for (int r = 0; r < rows; r += 2) {
+            float v0 = scaled_f32_from_f32(col[r], shift);
+            float v1 = r + 1 < rows ? scaled_f32_from_f32(col[r + 1], shift) : 0.f;
+            for (int p = 0; p < nsplit; ++p) {
+                const uint32_t w = take_piece2(v0, v1, f16);
+                pieces[(p * n + j) * m + r0 + r] = static_cast<uint16_t>(w & 0xFFFFu);
+                if (r + 1 < rows) pieces[(p * n + j) * m + r0 + r + 1] = static_cast<uint16_t>(w >> 16);
+            }
         }
     }
     shifts[j * nb + b] = shift;

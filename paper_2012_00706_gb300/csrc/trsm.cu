@@ -1,15 +1,15 @@
 // Coefficient matrix and error estimate of the column ID on GB300.
 //
 // T = R11^-1 R12 (Algorithm 1 line 4; R11 upper triangular and nonsingular, so
-// its pseudo-inverse of the paper's Remark is its inverse), in FP64 by
-// back-substitution, followed by `refine_steps` steps of iterative refinement
-// T += R11^-1 (R12 - R11 T) with the residual formed in FP64.  The pivoted QR
-// leaves R in FP64 storage (exactly, whatever precision it ran in), so the
-// solve is independent of the factorisation's precision.
+// the pseudo-inverse of the paper's Remark is its inverse), delivered in FP64,
+// followed by `refine_steps` steps of iterative refinement
+// T += R11^-1 (R12 - R11 T) with the residual formed in FP64.  The plain path
+// solves in FP64; the mixed path, whose R comes from the FP32 pivoted QR, solves
+// in FP32 and refines with the FP64 residual (mixed-precision iterative
+// refinement).  The pivoted QR leaves R in FP64 storage (exact for FP32 R).
 //
-// R11 sits in shared memory (read as warp-wide broadcasts); one thread owns
-// one column of T.  The work is FP64-ALU bound: about k^2 (n-k) flops per
-// solve pass.
+// k <= 128: one warp per column of T, the column in registers (lane l holds
+// rows l, l+32, ...), R11 in shared memory; otherwise one thread per column.
 #include "common.cuh"
 #include "internal.h"
 
@@ -18,7 +18,6 @@
 namespace gid {
 
 constexpr int kSolveThreads = 64;
-constexpr int kSmemR11MaxK = 150;
 
 template <bool kSmem>
 __global__ void __launch_bounds__(kSolveThreads)
@@ -67,24 +66,145 @@ k_solve_T(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__
 
 size_t solve_T_scratch_doubles(int kcap, int64_t n) { return static_cast<size_t>(kcap) * static_cast<size_t>(n); }
 
+// ---- warp-per-column solve for k <= 32*KQ: lane l holds rows l, l+32, ... of its column.
+//
+// Back-substitution is done column-oriented: for a = k-1 .. 0 the owner lane of
+// row a forms t_a = t_a / R(a,a) (times the stored reciprocal) and broadcasts it,
+// then every lane updates its rows b < a by t_b -= R(b,a) t_a (independent FMAs).
+// TS is the precision of the two solves: double for the plain path; float for
+// the mixed path, whose R is FP32, with the refinement residual
+// R12 - R11 T formed in FP64 (mixed-precision iterative refinement).
+constexpr int kWarpSolveWarps = 8;
+
+template <typename TS, int KQ>
+__device__ __forceinline__ void warp_backsub(TS (&t)[KQ], const TS* __restrict__ r11, const TS* __restrict__ rinv,
+                                             int k, int lane) {
+    for (int a = k - 1; a >= 0; --a) {
+        const int qa = a >> 5, owner = a & 31;
+        TS ta = t[0];
+#pragma unroll
+        for (int q = 1; q < KQ; ++q) ta = (qa == q) ? t[q] : ta;
+        ta = ta * rinv[a];
+        ta = __shfl_sync(0xffffffffu, ta, owner);
+        const TS* col = r11 + static_cast<int64_t>(a) * k;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            if (b < a) t[q] = fma(-col[b], ta, t[q]);
+            else if (b == a) t[q] = ta;
+        }
+    }
+}
+
+template <typename TS, int KQ>
+__global__ void __launch_bounds__(kWarpSolveWarps * 32)
+k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+               const int32_t* __restrict__ k_ptr, int64_t n, double* __restrict__ T, int64_t ldt,
+               int refine_steps) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int k = *k_ptr;
+    if (k <= 0) return;
+    double* r11d = reinterpret_cast<double*>(sm);                       // k x k, column-major
+    TS* r11s = reinterpret_cast<TS*>(r11d + static_cast<int64_t>(k) * k);
+    TS* rinv = r11s + static_cast<int64_t>(k) * k;
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int b = idx % k, a = idx / k;                               // row b, column a
+        const double v = (b <= a) ? R[static_cast<int64_t>(J[a]) * ldr + b] : 0.0;
+        r11d[idx] = v;
+        r11s[idx] = static_cast<TS>(v);
+    }
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+        rinv[a] = static_cast<TS>(1.0) / static_cast<TS>(R[static_cast<int64_t>(J[a]) * ldr + a]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n - k;
+         c += nwarps) {
+        const double* r12 = R + static_cast<int64_t>(J[k + c]) * ldr;
+        double rhs[KQ];
+        TS t[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            rhs[q] = b < k ? r12[b] : 0.0;
+            t[q] = static_cast<TS>(rhs[q]);
+        }
+        warp_backsub<TS, KQ>(t, r11s, rinv, k, lane);
+        double tt[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
+        for (int it = 0; it < refine_steps; ++it) {
+            // residual R12 - R11 T in FP64 (row-oriented: lane b sums over a >= b)
+            double res[KQ];
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) res[q] = rhs[q];
+            for (int a = 0; a < k; ++a) {
+                const int qa = a >> 5, owner = a & 31;
+                double ta = tt[0];
+#pragma unroll
+                for (int q = 1; q < KQ; ++q) ta = (qa == q) ? tt[q] : ta;
+                ta = __shfl_sync(0xffffffffu, ta, owner);
+                const double* col = r11d + static_cast<int64_t>(a) * k;
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) {
+                    const int b = lane + 32 * q;
+                    if (b <= a) res[q] = fma(-col[b], ta, res[q]);
+                }
+            }
+            TS d[KQ];
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) d[q] = static_cast<TS>(res[q]);
+            warp_backsub<TS, KQ>(d, r11s, rinv, k, lane);
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) tt[q] += static_cast<double>(d[q]);
+        }
+        double* out = T + c * ldt;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            if (b < k) out[b] = tt[q];
+        }
+    }
+}
+
+template <typename TS, int KQ>
+static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
+                                     int64_t n, double* T, int64_t ldt, int refine_steps, cudaStream_t s) {
+    const size_t smem = static_cast<size_t>(kcap) * kcap * (sizeof(double) + sizeof(TS)) + kcap * sizeof(TS) + 16;
+    auto kern = k_solve_T_warp<TS, KQ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t cols = std::max<int64_t>(1, n - 1);
+    const int64_t want = (cols + kWarpSolveWarps - 1) / kWarpSolveWarps;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, device_info().sm_count)));
+    kern<<<grid, kWarpSolveWarps * 32, smem, s>>>(R64, ldr, J, k_ptr, n, T, ldt, refine_steps);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
-                           int64_t n, double* T, int64_t ldt, double* scratch, int refine_steps,
+                           int64_t n, double* T, int64_t ldt, double* scratch, int refine_steps, int low_solve,
                            cudaStream_t s) {
+    if (kcap <= 128) {
+        const int kq = (kcap + 31) / 32;
+        if (low_solve) {
+            switch (kq) {
+                case 1: return launch_warp_solve<float, 1>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+                case 2: return launch_warp_solve<float, 2>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+                case 3: return launch_warp_solve<float, 3>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+                default: return launch_warp_solve<float, 4>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+            }
+        }
+        switch (kq) {
+            case 1: return launch_warp_solve<double, 1>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+            case 2: return launch_warp_solve<double, 2>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+            case 3: return launch_warp_solve<double, 3>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+            default: return launch_warp_solve<double, 4>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        }
+    }
+    // k > 128: thread per column, FP64 throughout, R11 read through L1/L2
     const int64_t cols = std::max<int64_t>(1, n - 1);
     const unsigned grid = static_cast<unsigned>((cols + kSolveThreads - 1) / kSolveThreads);
-    if (kcap <= kSmemR11MaxK) {
-        const size_t smem = static_cast<size_t>(kcap) * kcap * sizeof(double);
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_solve_T<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(smem));
-            if (e != cudaSuccess) return e;
-        }
-        k_solve_T<true><<<grid, kSolveThreads, smem, s>>>(R64, ldr, J, k_ptr, kcap, n, T, ldt, scratch,
-                                                          refine_steps);
-    } else {
-        k_solve_T<false><<<grid, kSolveThreads, 0, s>>>(R64, ldr, J, k_ptr, kcap, n, T, ldt, scratch,
-                                                        refine_steps);
-    }
+    k_solve_T<false><<<grid, kSolveThreads, 0, s>>>(R64, ldr, J, k_ptr, kcap, n, T, ldt, scratch, refine_steps);
     return cudaGetLastError();
 }
 

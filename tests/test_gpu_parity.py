@@ -246,3 +246,45 @@ def test_plain_f64_sketched_id(gid, dev, orc):
     assert np.array_equal(res.J.cpu().numpy()[:first], ref["J"][:first])
     if first == k:
         assert np.max(np.abs(res.T.cpu().numpy() - ref["T"])) <= 1e-8 * max(1.0, np.max(np.abs(ref["T"])))
+
+
+# --------------------------------------------------- cluster pivoted QR (FP32, <= 128 rows)
+
+@pytest.mark.parametrize("m,n,k", [(20, 300, 15), (50, 37, 30), (100, 700, 50), (110, 2000, 100), (128, 3000, 60)])
+def test_cluster_cpqr_f32_short_matrix(gid, dev, orc, m, n, k):
+    """PLAIN_F32 on a float matrix of <= 128 rows runs the thread-block-cluster kernel:
+    pivots equal the oracle's while the oracle's gaps stay above FP32 resolution,
+    and the ID error meets e <= 1.1 e_D + 10 u32."""
+    a = wl.separated_matrix(m, n, seed=m + 3 * n, decay=0.97).astype(np.float32)
+    ref = orc.interp_decomp(a.astype(np.float64), k=k)
+    res = gid.id_factor(torch.from_numpy(np.asfortranarray(a)).to(dev), k, precision="plain_f32")
+    assert res.info == 0 and res.k == k
+    J = res.J.cpu().numpy()
+    assert sorted(J.tolist()) == list(range(n))
+    sep = ref["gaps"] >= 1e-3
+    first = int(np.argmax(~sep)) if np.any(~sep) else k
+    assert first > 0
+    assert np.array_equal(J[:first], ref["J"][:first])
+    e = orc.rel_err(a.astype(np.float64), J, res.T.cpu().numpy(), k)
+    e_d = orc.rel_err(a.astype(np.float64), ref["J"], ref["T"], k)
+    assert e <= 1.1 * e_d + 10 * U32
+
+
+def test_cluster_cpqr_rank_by_tolerance(gid, dev, orc):
+    m, n = 96, 800
+    sigma = 10.0 ** (-np.arange(1, m + 1) / 8.0)
+    a = wl.lowrank(m, n, sigma, 12).astype(np.float32)
+    ref = orc.interp_decomp(a.astype(np.float64), tol=1e-3, k_max=90)
+    res = gid.id_factor(torch.from_numpy(np.asfortranarray(a)).to(dev), tol=1e-3, k_max=90, precision="plain_f32")
+    assert res.info == 0
+    assert abs(res.k - ref["k"]) <= 1
+
+
+def test_cluster_cpqr_zero_columns(gid, dev):
+    a = np.zeros((40, 500), dtype=np.float32)
+    rng = np.random.default_rng(2)
+    cols = [3, 77, 200, 499]
+    a[:, cols] = rng.standard_normal((40, 4))
+    res = gid.id_factor(torch.from_numpy(np.asfortranarray(a)).to(dev), 6, precision="plain_f32")
+    assert res.info == 5 and res.k == 4
+    assert sorted(res.J.cpu().numpy()[:4].tolist()) == cols
