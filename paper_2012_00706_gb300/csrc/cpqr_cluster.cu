@@ -86,16 +86,27 @@ struct CqRecord {
     float col[MAXR];
 };
 
+// Shared-memory index of row r of a per-step vector, padded by 16 bytes every 32
+// rows so that the TPC row blocks of a column read from different banks.
+__device__ __forceinline__ int vidx(int r) { return r + ((r >> 5) << 2); }
+
 template <int MAXR, int TPC>
 __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParams P) {
     constexpr int RPT = MAXR / TPC;
+    constexpr int VLEN = MAXR + MAXR / 8;          // padded vector length
+    constexpr int MAXW = kCqMaxThreads / 32;
     constexpr uint32_t REC = sizeof(CqRecord<MAXR>);
     static_assert(REC % 16 == 0, "record size");
+    static_assert(RPT % 4 == 0, "rows per thread");
     __shared__ __align__(128) CqRecord<MAXR> recv[2][kCqMaxCluster];
-    __shared__ __align__(128) CqRecord<MAXR> stg[2];
-    __shared__ float wv[32];
-    __shared__ int wi[32];
-    __shared__ float wsum[32];
+    __shared__ __align__(128) CqRecord<MAXR> wstg[2][MAXW];   // per-warp staged candidate
+    __shared__ __align__(16) float vp[VLEN];     // v' : 0 above row j, alpha - beta at j, pivot column below
+    __shared__ __align__(16) float ej[VLEN];     // unit vector e_j
+    __shared__ float wv[MAXW];
+    __shared__ int wi[MAXW];
+    __shared__ float wsum[MAXW];
+    __shared__ float s_sc[4];                    // tau, inv, beta, sum of norms
+    __shared__ int s_piv[2];                     // pivot column, stop flag
     __shared__ __align__(8) uint64_t recv_bar[2];
 
     const uint32_t me = cluster_rank(), C = cluster_nrank();
@@ -129,12 +140,13 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
         P.sel[i] = 0;
     }
 
-    // Exchange q: arm own barrier, stage the CTA's best candidate, bulk-copy it to every peer.
-    // Exchange q fills recv[q & 1] and completes phase q >> 1 of recv_bar[q & 1]; a peer can be
-    // at most one exchange ahead, so two alternating buffers and barriers never mix phases.
+    // Exchange q: each warp stages its best candidate column, warp 0 picks the CTA's best
+    // and bulk-copies that record to every peer.  Exchange q fills recv[q & 1] and
+    // completes phase q >> 1 of recv_bar[q & 1]; a peer can be at most one exchange ahead,
+    // so two alternating buffers and barriers never mix phases, and a staging slot is
+    // reused (two exchanges later) only after its copies have landed.
     auto exchange = [&](int q) {
         const int slot = q & 1;
-        if (t == 0) mbar_arrive_expect_tx(&recv_bar[slot], C * REC);
         float bv = -1.f, part = 0.f;
         int bi = -1;
         if (!selected && qq == 0) { bv = nu; bi = static_cast<int>(i); part = nu; }
@@ -145,23 +157,39 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
             better(bv, bi, ov, oi);
             part += __shfl_xor_sync(0xffffffffu, part, o);
         }
-        if (lane == 0) { wv[warp] = bv; wi[warp] = bi; wsum[warp] = part; }
-        __syncthreads();
-        float v0 = -1.f, s0 = 0.f;
-        int i0 = -1;
-        for (int w = 0; w < nw; ++w) { better(v0, i0, wv[w], wi[w]); s0 += wsum[w]; }
-        if (valid && i == i0) {
+        if (valid && i == bi) {
 #pragma unroll
             for (int u = 0; u < RPT; u += 4)
-                *reinterpret_cast<float4*>(&stg[slot].col[rb + u]) = make_float4(x[u], x[u + 1], x[u + 2], x[u + 3]);
+                *reinterpret_cast<float4*>(&wstg[slot][warp].col[rb + u]) = make_float4(x[u], x[u + 1], x[u + 2], x[u + 3]);
         }
-        if (t == 0) stg[slot].head = make_float4(v0, __int_as_float(i0), s0, 0.f);
+        if (lane == 0) { wv[warp] = bv; wi[warp] = bi; wsum[warp] = part; }
         fence_proxy_async_smem();
         __syncthreads();
-        if (t < static_cast<int>(C)) {
-            const uint32_t d = static_cast<uint32_t>(t);
-            bulk_s2peer(map_peer(smem_addr(&recv[slot][me]), d), smem_addr(&stg[slot]), REC,
-                        map_peer(smem_addr(&recv_bar[slot]), d));
+        if (warp == 0) {
+            float v0 = lane < nw ? wv[lane] : -1.f;
+            int i0 = lane < nw ? wi[lane] : -1;
+            int w0 = lane;
+            float s0 = lane < nw ? wsum[lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, v0, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, i0, o);
+                const int ow = __shfl_xor_sync(0xffffffffu, w0, o);
+                if (oi >= 0 && (i0 < 0 || ov > v0 || (ov == v0 && oi < i0))) { v0 = ov; i0 = oi; w0 = ow; }
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            }
+            const int wsrc = i0 >= 0 ? w0 : 0;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&recv_bar[slot], C * REC);
+                wstg[slot][wsrc].head = make_float4(v0, __int_as_float(i0), s0, 0.f);
+                fence_proxy_async_smem();
+            }
+            __syncwarp();
+            if (lane < static_cast<int>(C)) {
+                const uint32_t d = static_cast<uint32_t>(lane);
+                bulk_s2peer(map_peer(smem_addr(&recv[slot][me]), d), smem_addr(&wstg[slot][wsrc]), REC,
+                            map_peer(smem_addr(&recv_bar[slot]), d));
+            }
         }
     };
     auto wait_exchange = [&](int q) -> bool {
@@ -172,82 +200,103 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     exchange(0);
     bool ok = wait_exchange(0);
     int k = 0;
-    float total = 0.f;
+    float total = -1.f;
     for (int j = 0; ok && j < P.kcap; ++j) {
         const int par = j & 1;
-        // ---- the pivot: identical reduction of the C records in every thread
-        float best = -1.f, sumnu = 0.f;
-        int p = -1, src = -1;
-        for (uint32_t c = 0; c < C; ++c) {
-            const float4 hv = recv[par][c].head;
-            const int ci = __float_as_int(hv.y);
-            if (ci >= 0 && (p < 0 || hv.x > best || (hv.x == best && ci < p))) { best = hv.x; p = ci; src = static_cast<int>(c); }
-            sumnu += hv.z;
-        }
-        if (j == 0) total = sumnu;
-        if (P.rel_tol > 0.0 && sqrtf(fmaxf(sumnu, 0.f)) <= static_cast<float>(P.rel_tol) * sqrtf(total)) break;
-        if (p < 0 || !(best > 0.f)) {
-            if (me == 0 && t == 0) set_info(P.info, j + 1);
-            break;
-        }
-        const float* xw = recv[par][src].col;
-        // ---- reflector scalars (every warp computes the same sum in the same order)
-        float s2 = 0.f;
-        for (int q = j + lane; q < r; q += 32) s2 = fmaf(xw[q], xw[q], s2);
+        // ---- warp 0: the pivot (same reduction order in every CTA), reflector scalars,
+        // and the step vectors v' and e_j
+        if (warp == 0) {
+            float hv = -1.f, hs = 0.f;
+            int hi = -1, hsrc = lane;
+            if (lane < static_cast<int>(C)) {
+                const float4 h = recv[par][lane].head;
+                hv = h.x;
+                hi = __float_as_int(h.y);
+                hs = h.z;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        const float alpha = xw[j];
-        const float snorm = sqrtf(s2);
-        const float beta = alpha >= 0.f ? -snorm : snorm;
-        const float tau = (beta - alpha) / beta;
-        const float inv = 1.f / (alpha - beta);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, hv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, hi, o);
+                const int os = __shfl_xor_sync(0xffffffffu, hsrc, o);
+                if (oi >= 0 && (hi < 0 || ov > hv || (ov == hv && oi < hi))) { hv = ov; hi = oi; hsrc = os; }
+                hs += __shfl_xor_sync(0xffffffffu, hs, o);
+            }
+            if (total < 0.f) total = hs;
+            int stop = 0;
+            if (P.rel_tol > 0.0 && sqrtf(fmaxf(hs, 0.f)) <= static_cast<float>(P.rel_tol) * sqrtf(total)) stop = 1;
+            if (!stop && (hi < 0 || !(hv > 0.f))) {
+                stop = 2;
+                if (me == 0 && lane == 0) set_info(P.info, j + 1);
+            }
+            if (!stop) {
+                const float* xw = recv[par][hsrc].col;
+                float s2 = 0.f;
+                for (int q = j + lane; q < r; q += 32) s2 = fmaf(xw[q], xw[q], s2);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                const float alpha = xw[j];
+                const float snorm = sqrtf(s2);
+                const float beta = alpha >= 0.f ? -snorm : snorm;
+                const float amb = alpha - beta;
+                for (int q = lane; q < MAXR; q += 32) {
+                    vp[vidx(q)] = q < j ? 0.f : (q == j ? amb : xw[q]);
+                    ej[vidx(q)] = q == j ? 1.f : 0.f;
+                }
+                if (lane == 0) {
+                    s_sc[0] = (beta - alpha) / beta;   // tau
+                    s_sc[1] = 1.f / amb;               // inv
+                    s_sc[2] = beta;
+                }
+            }
+            if (lane == 0) { s_piv[0] = hi; s_piv[1] = stop; }
+        }
+        __syncthreads();
+        if (s_piv[1]) break;
+        const int p = s_piv[0];
+        const float tau = s_sc[0], inv = s_sc[1];
         if (valid && i == p) {
             selected = true;
             if (qq == 0) {
-                P.R[i * P.ldr + j] = static_cast<double>(beta);
+                P.R[i * P.ldr + j] = static_cast<double>(s_sc[2]);
                 P.J[j] = p;
                 P.sel[i] = 1;
             }
         }
-        // w = x_j + inv * sum_{q > j} xw_q x_q over this thread's rows, then over the TPC threads
-        // of the column.  Every lane runs the shuffles (selected columns just discard the result).
-        float acc = 0.f, xj = 0.f;
-        if (!selected && rb + RPT > j) {
+        // S = v'.x (= (alpha - beta) w),  X = e_j.x (= x_j): plain FMAs over this thread's rows
+        float S0 = 0.f, S1 = 0.f, X = 0.f;
 #pragma unroll
-            for (int u = 0; u < RPT; u += 4) {
-                const float4 w4 = *reinterpret_cast<const float4*>(&xw[rb + u]);
-                const int q0 = rb + u;
-                acc = (q0 > j) ? fmaf(w4.x, x[u], acc) : acc;
-                acc = (q0 + 1 > j) ? fmaf(w4.y, x[u + 1], acc) : acc;
-                acc = (q0 + 2 > j) ? fmaf(w4.z, x[u + 2], acc) : acc;
-                acc = (q0 + 3 > j) ? fmaf(w4.w, x[u + 3], acc) : acc;
-                xj = (q0 == j) ? x[u] : xj;
-                xj = (q0 + 1 == j) ? x[u + 1] : xj;
-                xj = (q0 + 2 == j) ? x[u + 2] : xj;
-                xj = (q0 + 3 == j) ? x[u + 3] : xj;
-            }
+        for (int u = 0; u < RPT; u += 4) {
+            const float4 v4 = *reinterpret_cast<const float4*>(&vp[vidx(rb + u)]);
+            const float4 e4 = *reinterpret_cast<const float4*>(&ej[vidx(rb + u)]);
+            S0 = fmaf(v4.x, x[u], S0);
+            S1 = fmaf(v4.y, x[u + 1], S1);
+            S0 = fmaf(v4.z, x[u + 2], S0);
+            S1 = fmaf(v4.w, x[u + 3], S1);
+            X = fmaf(e4.x, x[u], X);
+            X = fmaf(e4.y, x[u + 1], X);
+            X = fmaf(e4.z, x[u + 2], X);
+            X = fmaf(e4.w, x[u + 3], X);
         }
+        float S = S0 + S1;
 #pragma unroll
         for (int o = 1; o < TPC; o <<= 1) {
-            acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            xj += __shfl_xor_sync(0xffffffffu, xj, o);
+            S += __shfl_xor_sync(0xffffffffu, S, o);
+            X += __shfl_xor_sync(0xffffffffu, X, o);
         }
-        const float wdot = fmaf(inv, acc, xj);
-        const float tw = tau * wdot;
+        const float tw = tau * (inv * S);
         const float sv = tw * inv;
-        const float rho = xj - tw;
+        const float rho = X - tw;
         bool recompute = false;
         if (!selected) {
-            if (rb + RPT > j) {
+            // x -= (tau w / (alpha - beta)) v': rows above j unchanged, row j becomes rho
 #pragma unroll
-                for (int u = 0; u < RPT; u += 4) {
-                    const float4 w4 = *reinterpret_cast<const float4*>(&xw[rb + u]);
-                    const int q0 = rb + u;
-                    x[u] = (q0 > j) ? fmaf(-sv, w4.x, x[u]) : ((q0 == j) ? rho : x[u]);
-                    x[u + 1] = (q0 + 1 > j) ? fmaf(-sv, w4.y, x[u + 1]) : ((q0 + 1 == j) ? rho : x[u + 1]);
-                    x[u + 2] = (q0 + 2 > j) ? fmaf(-sv, w4.z, x[u + 2]) : ((q0 + 2 == j) ? rho : x[u + 2]);
-                    x[u + 3] = (q0 + 3 > j) ? fmaf(-sv, w4.w, x[u + 3]) : ((q0 + 3 == j) ? rho : x[u + 3]);
-                }
+            for (int u = 0; u < RPT; u += 4) {
+                const float4 v4 = *reinterpret_cast<const float4*>(&vp[vidx(rb + u)]);
+                x[u] = fmaf(-sv, v4.x, x[u]);
+                x[u + 1] = fmaf(-sv, v4.y, x[u + 1]);
+                x[u + 2] = fmaf(-sv, v4.z, x[u + 2]);
+                x[u + 3] = fmaf(-sv, v4.w, x[u + 3]);
             }
             if (qq == 0) P.R[i * P.ldr + j] = static_cast<double>(rho);
             if (nu > 0.f) {
@@ -257,14 +306,14 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
             }
         }
         if (__any_sync(0xffffffffu, recompute)) {
-            float s = 0.f;
+            float sq = 0.f;
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) s = (rb + u > j) ? fmaf(x[u], x[u], s) : s;
+            for (int u = 0; u < RPT; ++u) sq = (rb + u > j) ? fmaf(x[u], x[u], sq) : sq;
 #pragma unroll
-            for (int o = 1; o < TPC; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            for (int o = 1; o < TPC; o <<= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (recompute) {
-                nu = s;
-                nuref = s;
+                nu = sq;
+                nuref = sq;
             }
         }
         exchange(j + 1);
@@ -277,7 +326,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     if (me == 0) {
         if (t == 0) *P.k_out = k;
         __shared__ int s_base;
-        __shared__ int cnt[32];
+        __shared__ int cnt[MAXW];
         if (t == 0) s_base = k;
         __syncthreads();
         for (int64_t i0 = 0; i0 < P.n; i0 += blockDim.x) {

@@ -44,6 +44,7 @@ struct SketchPlan {
     int64_t chunks_per_slab = 0;
     int kslabs = 0;
     int stages = 0, aop_bufs = 0, omega_bufs = 0, acc_bufs = 0;
+    int aop_in_stage = 0;
     size_t smem_bytes = 0;
 };
 int precision_nsplit(int precision);

@@ -17,6 +17,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <cstring>
 #include <cudaTypedefs.h>
 
 namespace gid {
@@ -69,6 +70,25 @@ __device__ __forceinline__ float scaled_f32_from_f64(double x, int s) {
     return scaled_slow(x, s);
 }
 
+// Branch-free fast path of scaled_f32_from_f64 for the sketch's converter.
+// u holds the exponent's low 9 bits and the top 23 significand bits; adding
+// 2^30 - (s << 23) rebiases the exponent from 1023 to 127 and applies the
+// shift (exact modulo 2^32 whenever the result is a normal float), and `inc`
+// is the round-to-nearest-even increment from the 29 discarded bits.  Zeros
+// map to signed zeros.  Sets `slow` when the scaled value is not a normal
+// float; the caller then redoes the block with scaled_f32_from_f64.
+__device__ __forceinline__ float scaled_f32_from_f64_fast(double x, int s, uint32_t kbias, bool& slow) {
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
+    const uint32_t u = __funnelshift_l(lo, hi, 3);
+    const uint32_t inc = ((lo & 0x1FFFFFFFu) + 0x0FFFFFFFu + (u & 1u)) >> 29;
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    const bool zero = ((hi << 1) | lo) == 0u;
+    const uint32_t bits = zero ? 0u : (u + kbias + inc);
+    slow |= !zero && (static_cast<uint32_t>(static_cast<int>(e) - s - 897) > 252u);
+    return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
 // fl32(x 2^-s) for float x: exponent adjust when both ends are normal.
 __device__ __forceinline__ float scaled_f32_from_f32(float x, int s) {
     const uint32_t u = __float_as_uint(x);
@@ -78,6 +98,15 @@ __device__ __forceinline__ float scaled_f32_from_f32(float x, int s) {
         return __uint_as_float(u - (static_cast<uint32_t>(s) << 23));
     if ((u & 0x7fffffffu) == 0u) return x;
     return scaled_slow(static_cast<double>(x), s);
+}
+
+// Branch-free fast path for float input: exponent adjust of a normal float.
+__device__ __forceinline__ float scaled_f32_from_f32_fast(float x, int s, bool& slow) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const bool zero = (u << 1) == 0u;
+    slow |= !zero && ((e - 1u) > 253u || (static_cast<uint32_t>(static_cast<int>(e) - s - 1) > 253u));
+    return zero ? x : __uint_as_float(u - (static_cast<uint32_t>(s) << 23));
 }
 
 // Two low-format pieces at once (packed round-to-nearest-even conversion) and
@@ -111,34 +140,43 @@ int precision_is_f16(int precision) { return precision == ID_MIXED_F16 ? 1 : 0; 
 
 // ------------------------------------------------------ tensor-core sketch
 
+// Warp roles: 0 producer (TMA), 1 MMA issuer, 2 TMEM allocator, 3 idle,
+// 4..19 converters (four threads per column), 20..23 epilogue.
+constexpr int kConvWarps = 16;
+constexpr int kFirstConvWarp = 4;
+constexpr int kFirstEpiWarp = kFirstConvWarp + kConvWarps;
+constexpr int kSketchThreads = (kFirstEpiWarp + 4) * 32;
+constexpr uint32_t kAopTileBytes = kTileCols * 128;   // 128 rows x 64 bf16 (16 KB)
+constexpr uint32_t kSlabBytes = kTileCols * 128;      // one A box: 128 columns x 128 bytes
+// L2 prefetch: every kPrefetchGroup chunks, the next kPrefetchGroup chunks starting
+// kPrefetchAhead chunks ahead are prefetched with one tensor prefetch (2 KB per column).
+constexpr int kPrefetchGroup = 4;
+constexpr int kPrefetchAhead = 8;
+#ifndef GID_SKETCH_L2_PREFETCH
+#define GID_SKETCH_L2_PREFETCH 0
+#endif
+constexpr int kSketchL2Prefetch = GID_SKETCH_L2_PREFETCH;
+
 struct LowpParams {
     const void* A;
     int64_t lda, m, n;
     int a_f64, nsplit, f16, lp, lpa;
     int64_t nchunks, chunks_per_slab;
     int stages, aop_bufs, omega_bufs, acc_bufs;
-    uint32_t colstride, stage_bytes, omega_tile_bytes;
-    int direct_all;
-    float* partial;     // [kslabs][n][lp]
+    uint32_t stage_bytes, omega_tile_bytes;
+    int direct;          // A is not TMA-addressable: converters load it from global memory
+    int aop_in_stage;    // the MMA operand is built inside the consumed A stage (no separate buffers)
+    int prefetch;        // issue L2 tensor prefetches ahead of the loads
+    float* partial;      // [kslabs][n][lp]
     int32_t* info;
     uint64_t limit_ns;
 };
 
-constexpr uint32_t kAopTileBytes = kTileCols * 128;   // 128 rows x 64 bf16
-// warps: 0 producer, 1 MMA issuer, 2 TMEM allocator, 3 idle, 4..11 converters, 12..15 epilogue
-constexpr int kConvWarps = 8;
-// L2 prefetch: every kPrefetchGroup chunks the producer prefetches the next group of
-// chunks starting kPrefetchChunks ahead (4 chunks x 64 rows x 8 B = 2 KB per column).
-constexpr int kPrefetchGroup = 4;
-constexpr int kPrefetchChunks = 8;
-constexpr int kSketchThreads = (4 + kConvWarps + 4) * 32;
-
 struct LowpSmem {
-    uint8_t* aop;        // [aop_bufs][nsplit][16 KB]
-    uint8_t* omega;      // [omega_bufs][omega_tile_bytes]
-    uint8_t* stage;      // [stages][stage_bytes]
+    uint8_t* aop;        // [aop_bufs][nsplit][16 KB]   swizzled K-major MMA operand (A columns)
+    uint8_t* omega;      // [omega_bufs][omega tile]   swizzled K-major MMA operand (Omega rows)
+    uint8_t* stage;      // [stages][stage_bytes]      A chunks as landed by TMA (128-byte swizzle)
     int32_t* shifts;     // [aop_bufs + acc_bufs][128]
-    uint32_t* xmax;      // [2 chunks][2 halves][128] partial block maxima
     uint64_t* bars;
     uint32_t* tmem_holder;
     int* abort;
@@ -153,11 +191,10 @@ __host__ __device__ inline size_t lowp_carve(uintptr_t base, const LowpParams& P
         return r;
     };
     const int H = P.aop_bufs + P.acc_bufs;
-    uintptr_t aop = take((size_t)P.aop_bufs * P.nsplit * kAopTileBytes, 1024);
+    uintptr_t aop = take(P.aop_in_stage ? 0 : (size_t)P.aop_bufs * P.nsplit * kAopTileBytes, 1024);
     uintptr_t om = take((size_t)P.omega_bufs * P.omega_tile_bytes, 1024);
-    uintptr_t st = take((size_t)P.stages * P.stage_bytes, 128);
+    uintptr_t st = take((size_t)P.stages * P.stage_bytes, 1024);
     uintptr_t sh = take((size_t)H * kTileCols * 4, 16);
-    uintptr_t xm = take((size_t)4 * kTileCols * 4, 16);
     const int nbars = 2 * P.stages + 2 * P.omega_bufs + 2 * P.aop_bufs + 2 * P.acc_bufs + 2 * H;
     uintptr_t bars = take((size_t)nbars * 8, 8);
     uintptr_t th = take(4, 4);
@@ -167,7 +204,6 @@ __host__ __device__ inline size_t lowp_carve(uintptr_t base, const LowpParams& P
         S->omega = reinterpret_cast<uint8_t*>(om);
         S->stage = reinterpret_cast<uint8_t*>(st);
         S->shifts = reinterpret_cast<int32_t*>(sh);
-        S->xmax = reinterpret_cast<uint32_t*>(xm);
         S->bars = reinterpret_cast<uint64_t*>(bars);
         S->tmem_holder = reinterpret_cast<uint32_t*>(th);
         S->abort = reinterpret_cast<int*>(ab);
@@ -175,8 +211,28 @@ __host__ __device__ inline size_t lowp_carve(uintptr_t base, const LowpParams& P
     return static_cast<size_t>(p - base);
 }
 
+__device__ __forceinline__ void prefetch_tensor_2d(const CUtensorMap* map, int32_t c0, int32_t c1) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1)
+                 : "memory");
+}
+
+// Convert 8 scaled values into nsplit pieces and store them as one 16-byte chunk of
+// row t (K group g) of each swizzled operand tile.
+__device__ __forceinline__ void store_pieces(uint8_t* aop_buf, int nsplit, int f16, int t, int g, float (&v)[8]) {
+    const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
+    for (int p = 0; p < nsplit; ++p) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = take_piece2(v[2 * q], v[2 * q + 1], f16);
+        *reinterpret_cast<uint4*>(aop_buf + (size_t)p * kAopTileBytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 __global__ void __launch_bounds__(kSketchThreads, 1)
-k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) {
+k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constant__ CUtensorMap tm_a,
+              const __grid_constant__ CUtensorMap tm_pf, const LowpParams P) {
     extern __shared__ uint8_t smem_raw[];
     const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
     LowpSmem S;
@@ -200,10 +256,15 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
     const int64_t ch_end = min(P.nchunks, ch_begin + P.chunks_per_slab);
     const int nloc = static_cast<int>(ch_end - ch_begin);
     const int elem = P.a_f64 ? 8 : 4;
+    const int slab_rows = 128 / elem;                     // rows per 128-byte box line
+    const int nslabs = kChunkRows / slab_rows;            // boxes per chunk
     const int ncols_valid = static_cast<int>(min(static_cast<int64_t>(kTileCols), P.n - col0));
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NS; ++i) { mbar_init(&stage_full[i], 1); mbar_init(&stage_free[i], kConvWarps); }
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&stage_full[i], 1);
+            mbar_init(&stage_free[i], P.aop_in_stage ? 1 : kConvWarps);
+        }
         for (int i = 0; i < NO; ++i) { mbar_init(&omg_full[i], 1); mbar_init(&omg_free[i], 1); }
         for (int i = 0; i < NA; ++i) { mbar_init(&aop_full[i], kConvWarps); mbar_init(&aop_free[i], 1); }
         for (int i = 0; i < NC; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 4); }
@@ -221,63 +282,46 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
     const uint32_t tmem = *S.tmem_holder;
 
     if (warp == 0) {
-        // ---------------- producer: A column slices (bulk copies) + Omega tiles (TMA)
-        if (lane == 0) prefetch_tensormap(&tm_omega);
-        // warm L2 with the first prefetch window of this CTA's slab
-        if (!P.direct_all) {
-            const int64_t prow0 = ch_begin * kChunkRows;
-            const int64_t prow1 = min(P.m, min(ch_end, ch_begin + kPrefetchChunks) * kChunkRows);
-            const uint32_t pbytes = static_cast<uint32_t>(((prow1 - prow0) * elem) & ~int64_t(15));
-            if (pbytes > 0) {
-                const uint8_t* A8p = static_cast<const uint8_t*>(P.A);
-                for (int q = lane; q < ncols_valid; q += 32) {
-                    const uint8_t* base = A8p + ((col0 + q) * P.lda + prow0) * elem;
-                    for (uint32_t off = 0; off < pbytes; off += 4096u)
-                        prefetch_l2(base + off, min(4096u, pbytes - off));
+        // ---------------- A producer: the A boxes of each chunk (one thread issues TMA)
+        if (lane == 0) {
+            if (!P.direct) prefetch_tensormap(&tm_a);
+            if (P.prefetch && !P.direct) {
+                prefetch_tensormap(&tm_pf);
+                for (int g = 0; g < kPrefetchAhead; g += kPrefetchGroup)
+                    if (ch_begin + g < ch_end)
+                        prefetch_tensor_2d(&tm_pf, static_cast<int32_t>((ch_begin + g) * kChunkRows),
+                                           static_cast<int32_t>(col0));
+            }
+            for (int i = 0; i < nloc; ++i) {
+                const int64_t c = ch_begin + i;
+                const int s = i % NS;
+                if (P.prefetch && !P.direct && (i % kPrefetchGroup) == 0 && c + kPrefetchAhead < ch_end)
+                    prefetch_tensor_2d(&tm_pf, static_cast<int32_t>((c + kPrefetchAhead) * kChunkRows),
+                                       static_cast<int32_t>(col0));
+                if (!mbar_wait(&stage_free[s], ((i / NS) & 1) ^ 1, abort, P.limit_ns)) break;
+                if (P.direct) {
+                    mbar_arrive(&stage_full[s]);
+                } else {
+                    mbar_arrive_expect_tx(&stage_full[s], P.stage_bytes);
+                    uint8_t* dst = S.stage + (size_t)s * P.stage_bytes;
+                    for (int sl = 0; sl < nslabs; ++sl)
+                        tma_load_2d(dst + (size_t)sl * kSlabBytes, &tm_a,
+                                    static_cast<int32_t>(c * kChunkRows + sl * slab_rows),
+                                    static_cast<int32_t>(col0), &stage_full[s]);
                 }
             }
         }
-        for (int i = 0; i < nloc && !*abort; ++i) {
-            const int64_t c = ch_begin + i;
-            const int s = i % NS, o = i % NO;
-            if (!mbar_wait(&omg_free[o], ((i / NO) & 1) ^ 1, abort, P.limit_ns)) break;
-            if (lane == 0) {
+    } else if (warp == 3) {
+        // ---------------- Omega producer: one swizzled Omega tile per chunk
+        if (lane == 0) {
+            prefetch_tensormap(&tm_omega);
+            for (int i = 0; i < nloc; ++i) {
+                const int64_t c = ch_begin + i;
+                const int o = i % NO;
+                if (!mbar_wait(&omg_free[o], ((i / NO) & 1) ^ 1, abort, P.limit_ns)) break;
                 mbar_arrive_expect_tx(&omg_full[o], P.omega_tile_bytes);
                 tma_load_2d(S.omega + (size_t)o * P.omega_tile_bytes, &tm_omega,
                             static_cast<int32_t>(c * kChunkRows), 0, &omg_full[o]);
-            }
-            // L2 prefetch of the chunks kPrefetchChunks ahead as 2 KB-class contiguous column
-            // segments: long runs keep DRAM efficient while the shared-memory stages stay small.
-            if (!P.direct_all && (i % kPrefetchGroup) == 0) {
-                const int64_t pc = c + kPrefetchChunks;
-                if (pc < ch_end) {
-                    const int64_t prow0 = pc * kChunkRows;
-                    const int64_t prow1 = min(P.m, min(ch_end, pc + kPrefetchGroup) * kChunkRows);
-                    const uint32_t pbytes = static_cast<uint32_t>(((prow1 - prow0) * elem) & ~int64_t(15));
-                    if (pbytes > 0) {
-                        const uint8_t* A8p = static_cast<const uint8_t*>(P.A);
-                        for (int q = lane; q < ncols_valid; q += 32)
-                            prefetch_l2(A8p + ((col0 + q) * P.lda + prow0) * elem, pbytes);
-                    }
-                }
-            }
-            if (!mbar_wait(&stage_free[s], ((i / NS) & 1) ^ 1, abort, P.limit_ns)) break;
-            const int64_t row0 = c * kChunkRows;
-            const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), P.m - row0));
-            const uint32_t bytes_col = P.direct_all ? 0u : (static_cast<uint32_t>(rows * elem) & ~15u);
-            const uint32_t total = bytes_col * static_cast<uint32_t>(ncols_valid);
-            if (lane == 0) {
-                if (total > 0) mbar_arrive_expect_tx(&stage_full[s], total);
-                else mbar_arrive(&stage_full[s]);
-            }
-            __syncwarp();
-            if (bytes_col > 0) {
-                uint8_t* dst = S.stage + (size_t)s * P.stage_bytes;
-                const uint8_t* A8 = static_cast<const uint8_t*>(P.A);
-                for (int q = lane; q < ncols_valid; q += 32) {
-                    const uint8_t* src = A8 + ((col0 + q) * P.lda + row0) * elem;
-                    bulk_g2s(dst + (size_t)q * P.colstride, src, bytes_col, &stage_full[s]);
-                }
             }
         }
     } else if (warp == 1) {
@@ -293,15 +337,16 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
                 tc_fence_after();
                 const uint32_t d = tmem + static_cast<uint32_t>(b * P.lpa);
                 const uint32_t bbase = smem_addr(S.omega + (size_t)o * P.omega_tile_bytes);
+                uint8_t* aop_base = P.aop_in_stage ? S.stage + (size_t)a * P.stage_bytes
+                                                   : S.aop + (size_t)a * P.nsplit * kAopTileBytes;
                 for (int p = 0; p < P.nsplit; ++p) {
-                    const uint32_t abase =
-                        smem_addr(S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes);
+                    const uint32_t abase = smem_addr(aop_base + (size_t)p * kAopTileBytes);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        umma_f16(d, umma_desc_sw128(abase + 32u * kk), umma_desc_sw128(bbase + 32u * kk),
-                                 idesc, (p | kk) != 0 ? 1u : 0u);
+                        umma_f16(d, umma_desc_sw128(abase + 32u * kk), umma_desc_sw128(bbase + 32u * kk), idesc,
+                                 (p | kk) != 0 ? 1u : 0u);
                 }
-                umma_commit(&aop_free[a]);
+                umma_commit(P.aop_in_stage ? &stage_free[a] : &aop_free[a]);
                 umma_commit(&omg_free[o]);
                 umma_commit(&acc_full[b]);
                 issued = i + 1;
@@ -313,144 +358,106 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const LowpParams P) 
                 mbar_wait(&acc_full[b], ((issued - 1) / NC) & 1, &keep_waiting, P.limit_ns);
             }
         }
-    } else if (warp >= 4 && warp < 4 + kConvWarps) {
-        // ---------------- converters: two threads per column (rows 0-31 and 32-63 of the chunk);
-        // the block maximum is combined through shared memory with a named barrier.
-        const int u = threadIdx.x - 128;
-        const int t = u & (kTileCols - 1);
-        const int half = u >> 7;
+    } else if (warp >= kFirstConvWarp && warp < kFirstEpiWarp) {
+        // ---------------- converters: lane = column (8 per warp) + 8 * quarter (16 rows each)
+        const int cw = warp - kFirstConvWarp;
+        const int q = lane >> 3;
+        const int t = cw * 8 + (lane & 7);
         const int64_t col = col0 + t;
         const bool valid = t < ncols_valid;
-        const uint8_t* A8 = static_cast<const uint8_t*>(P.A);
         for (int i = 0; i < nloc; ++i) {
             const int64_t c = ch_begin + i;
-            const int s = i % NS, a = i % NA, h = i % H;
+            const int s = i % NS, a = P.aop_in_stage ? s : i % NA, h = i % H;
             if (!mbar_wait(&stage_full[s], (i / NS) & 1, abort, P.limit_ns)) break;
-            if (!mbar_wait(&aop_free[a], ((i / NA) & 1) ^ 1, abort, P.limit_ns)) break;
+            if (!P.aop_in_stage && !mbar_wait(&aop_free[a], ((i / NA) & 1) ^ 1, abort, P.limit_ns)) break;
             if (!mbar_wait(&sh_free[h], ((i / H) & 1) ^ 1, abort, P.limit_ns)) break;
             const int64_t row0 = c * kChunkRows;
             const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), P.m - row0));
-            const int rows_smem = P.direct_all ? 0 : ((rows * elem) & ~15) / elem;
-            const bool full = valid && rows_smem == kChunkRows;
-            const int rb = 32 * half;
-            const uint8_t* scol = S.stage + (size_t)s * P.stage_bytes + (size_t)t * P.colstride;
-            const uint8_t* gcol = A8 + (col * P.lda + row0) * elem;
-            uint32_t* xmax = S.xmax + (i & 1) * 2 * kTileCols;
+            const uint8_t* stg = S.stage + (size_t)s * P.stage_bytes;
+            uint8_t* aop_buf = P.aop_in_stage ? S.stage + (size_t)s * P.stage_bytes
+                                              : S.aop + (size_t)a * P.nsplit * kAopTileBytes;
             uint32_t mx = 0;
+            int shift;
+            float f[16];
+            bool slow = false;
             if (P.a_f64) {
-                const double* sd = reinterpret_cast<const double*>(scol);
-                const double* gd = reinterpret_cast<const double*>(gcol);
-                if (full) {
+                double v[16];
+                if (!P.direct) {
+                    // box q holds rows 16q..16q+15 of all 128 columns, 128 bytes per column, swizzled
+                    const uint8_t* line = stg + (size_t)q * kSlabBytes + (size_t)t * 128;
 #pragma unroll
-                    for (int r = 0; r < 32; r += 2) {
-                        const double2 v = *reinterpret_cast<const double2*>(sd + rb + r);
-                        mx = max(mx, static_cast<uint32_t>(__double2hiint(v.x)) & 0x7fffffffu);
-                        mx = max(mx, static_cast<uint32_t>(__double2hiint(v.y)) & 0x7fffffffu);
+                    for (int cc = 0; cc < 8; ++cc) {
+                        const double2 d2 = *reinterpret_cast<const double2*>(line + ((cc ^ (t & 7)) << 4));
+                        v[2 * cc] = d2.x;
+                        v[2 * cc + 1] = d2.y;
                     }
-                } else if (valid) {
-                    for (int r = rb; r < min(rb + 32, rows); ++r) {
-                        const double x = r < rows_smem ? sd[r] : __ldg(gd + r);
-                        mx = max(mx, static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu);
-                    }
+                } else {
+                    const double* g = static_cast<const double*>(P.A) + col * P.lda + row0;
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = (valid && 16 * q + r < rows) ? __ldg(g + 16 * q + r) : 0.0;
                 }
-                xmax[half * kTileCols + t] = mx;
-                asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
-                mx = max(mx, xmax[(half ^ 1) * kTileCols + t]);
-                if (half == 0 && (mx >> 20) == 0x7FFu) set_info(P.info, kInfoNonFinite);
-                const int shift = shift_from_max_f64hi(mx, P.f16);
-                if (half == 0) S.shifts[h * kTileCols + t] = shift;
-#pragma unroll 1
-                for (int gg = 0; gg < 4; ++gg) {
-                    const int g = 4 * half + gg;
-                    float v[8];
-                    if (full) {
+                // every converter has its values in registers before the stage is overwritten
+                if (P.aop_in_stage) asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
 #pragma unroll
-                        for (int q = 0; q < 8; q += 2) {
-                            const double2 d2 = *reinterpret_cast<const double2*>(sd + 8 * g + q);
-                            v[q] = scaled_f32_from_f64(d2.x, shift);
-                            v[q + 1] = scaled_f32_from_f64(d2.y, shift);
-                        }
-                    } else {
+                for (int r = 0; r < 16; ++r) mx = max(mx, static_cast<uint32_t>(__double2hiint(v[r])) & 0x7fffffffu);
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+                if (q == 0 && (mx >> 20) == 0x7FFu) set_info(P.info, kInfoNonFinite);
+                shift = shift_from_max_f64hi(mx, P.f16);
+                const uint32_t kbias = 0x40000000u - (static_cast<uint32_t>(shift) << 23);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int r = 8 * g + q;
-                            double x = 0.0;
-                            if (valid && r < rows) x = r < rows_smem ? sd[r] : __ldg(gd + r);
-                            v[q] = scaled_f32_from_f64(x, shift);
-                        }
-                    }
-                    const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
-                    for (int p = 0; p < P.nsplit; ++p) {
-                        uint32_t w[4];
+                for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64_fast(v[r], shift, kbias, slow);
+                if (__any_sync(0xffffffffu, slow) && slow) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) w[q] = take_piece2(v[2 * q], v[2 * q + 1], P.f16);
-                        uint8_t* tile = S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes;
-                        *reinterpret_cast<uint4*>(tile + off) = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
+                    for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64(v[r], shift);
                 }
             } else {
-                const float* sf = reinterpret_cast<const float*>(scol);
-                const float* gf = reinterpret_cast<const float*>(gcol);
-                if (full) {
+                float v[16];
+                if (!P.direct) {
+                    // box q/2 holds rows 32(q/2)..+31; this thread's 16 rows are 16-byte chunks 4(q&1)..+3
+                    const uint8_t* line = stg + (size_t)(q >> 1) * kSlabBytes + (size_t)t * 128;
 #pragma unroll
-                    for (int r = 0; r < 32; r += 4) {
-                        const float4 v = *reinterpret_cast<const float4*>(sf + rb + r);
-                        mx = max(mx, __float_as_uint(v.x) & 0x7fffffffu);
-                        mx = max(mx, __float_as_uint(v.y) & 0x7fffffffu);
-                        mx = max(mx, __float_as_uint(v.z) & 0x7fffffffu);
-                        mx = max(mx, __float_as_uint(v.w) & 0x7fffffffu);
+                    for (int k = 0; k < 4; ++k) {
+                        const int cc = 4 * (q & 1) + k;
+                        const float4 f4 = *reinterpret_cast<const float4*>(line + ((cc ^ (t & 7)) << 4));
+                        v[4 * k] = f4.x; v[4 * k + 1] = f4.y; v[4 * k + 2] = f4.z; v[4 * k + 3] = f4.w;
                     }
-                } else if (valid) {
-                    for (int r = rb; r < min(rb + 32, rows); ++r) {
-                        const float x = r < rows_smem ? sf[r] : __ldg(gf + r);
-                        mx = max(mx, __float_as_uint(x) & 0x7fffffffu);
-                    }
+                } else {
+                    const float* g = static_cast<const float*>(P.A) + col * P.lda + row0;
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = (valid && 16 * q + r < rows) ? __ldg(g + 16 * q + r) : 0.f;
                 }
-                xmax[half * kTileCols + t] = mx;
-                asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
-                mx = max(mx, xmax[(half ^ 1) * kTileCols + t]);
-                if (half == 0 && (mx >> 23) == 0xFFu) set_info(P.info, kInfoNonFinite);
-                const int shift = shift_from_max_f32(mx, P.f16);
-                if (half == 0) S.shifts[h * kTileCols + t] = shift;
-#pragma unroll 1
-                for (int gg = 0; gg < 4; ++gg) {
-                    const int g = 4 * half + gg;
-                    float v[8];
-                    if (full) {
-                        const float4 x0 = *reinterpret_cast<const float4*>(sf + 8 * g);
-                        const float4 x1 = *reinterpret_cast<const float4*>(sf + 8 * g + 4);
-                        v[0] = scaled_f32_from_f32(x0.x, shift); v[1] = scaled_f32_from_f32(x0.y, shift);
-                        v[2] = scaled_f32_from_f32(x0.z, shift); v[3] = scaled_f32_from_f32(x0.w, shift);
-                        v[4] = scaled_f32_from_f32(x1.x, shift); v[5] = scaled_f32_from_f32(x1.y, shift);
-                        v[6] = scaled_f32_from_f32(x1.z, shift); v[7] = scaled_f32_from_f32(x1.w, shift);
-                    } else {
+                if (P.aop_in_stage) asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int r = 8 * g + q;
-                            float x = 0.f;
-                            if (valid && r < rows) x = r < rows_smem ? sf[r] : __ldg(gf + r);
-                            v[q] = scaled_f32_from_f32(x, shift);
-                        }
-                    }
-                    const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
-                    for (int p = 0; p < P.nsplit; ++p) {
-                        uint32_t w[4];
+                for (int r = 0; r < 16; ++r) mx = max(mx, __float_as_uint(v[r]) & 0x7fffffffu);
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+                if (q == 0 && (mx >> 23) == 0xFFu) set_info(P.info, kInfoNonFinite);
+                shift = shift_from_max_f32(mx, P.f16);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) w[q] = take_piece2(v[2 * q], v[2 * q + 1], P.f16);
-                        uint8_t* tile = S.aop + ((size_t)a * P.nsplit + p) * kAopTileBytes;
-                        *reinterpret_cast<uint4*>(tile + off) = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
+                for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f32_fast(v[r], shift, slow);
+                if (__any_sync(0xffffffffu, slow) && slow) {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f32(v[r], shift);
                 }
             }
+#pragma unroll
+            for (int gg = 0; gg < 2; ++gg) {
+                float f8[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f8[k] = f[8 * gg + k];
+                store_pieces(aop_buf, P.nsplit, P.f16, t, 2 * q + gg, f8);
+            }
+            if (q == 0) S.shifts[h * kTileCols + t] = shift;
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(&stage_free[s]);
+                if (!P.aop_in_stage) mbar_arrive(&stage_free[s]);
                 mbar_arrive(&aop_full[a]);
                 mbar_arrive(&sh_full[h]);
             }
         }
-    } else if (warp >= 4 + kConvWarps) {
+    } else if (warp >= kFirstEpiWarp) {
         // ---------------- epilogue: drain each chunk, scale by 2^s, accumulate in TMEM
         const int q = warp & 3;
         const int t = 32 * q + lane;
@@ -543,13 +550,10 @@ bool sketch_plan_lowp(int64_t m, int64_t n, int ell, int a_f64, int nsplit, Sket
     int64_t kslabs = std::max<int64_t>(1, std::min<int64_t>(p.nchunks, target / std::max(1, p.tiles)));
     p.chunks_per_slab = (p.nchunks + kslabs - 1) / kslabs;
     p.kslabs = static_cast<int>((p.nchunks + p.chunks_per_slab - 1) / p.chunks_per_slab);
-    const int elem = a_f64 ? 8 : 4;
-    const uint32_t colstride = kChunkRows * elem + 16;
-    const uint32_t stage_bytes = kTileCols * colstride;
+    const uint32_t stage_bytes = static_cast<uint32_t>(kChunkRows * kTileCols * (a_f64 ? 8 : 4));
     const uint32_t omega_tile = (static_cast<uint32_t>(p.lp) * 128u + 1023u) & ~1023u;
     LowpParams P{};
     P.nsplit = nsplit;
-    P.colstride = colstride;
     P.stage_bytes = stage_bytes;
     P.omega_tile_bytes = omega_tile;
     P.acc_bufs = p.acc_bufs;
@@ -558,14 +562,21 @@ bool sketch_plan_lowp(int64_t m, int64_t n, int ell, int a_f64, int nsplit, Sket
         P.stages = st; P.aop_bufs = na; P.omega_bufs = no;
         return lowp_carve(0, P, nullptr) <= budget;
     };
+    // The MMA operand lives inside the consumed stage when the stage can hold its pieces,
+    // which frees room for more stages in flight.  Prefer two Omega buffers, then load
+    // depth (stages), then (separate operands only) a second operand buffer.
+    P.aop_in_stage = stage_bytes >= static_cast<uint32_t>(nsplit) * kAopTileBytes ? 1 : 0;
     int st = 2, na = 1, no = 1;
-    if (!fits(st, na, no)) return false;
-    if (fits(st, na, 2)) no = 2;
-    if (fits(st, 2, no)) na = 2;
-    const int max_st = a_f64 ? 3 : 4;
-    while (st < max_st && fits(st + 1, na, no)) ++st;
+    if (P.aop_in_stage) na = 2;
+    auto fits2 = [&](int st_, int no_) { return fits(st_, P.aop_in_stage ? st_ : na, no_); };
+    if (!fits2(st, no)) return false;
+    if (fits2(st, 2)) no = 2;
+    const int max_st = a_f64 ? 3 : 6;
+    while (st < max_st && fits2(st + 1, no)) ++st;
+    if (P.aop_in_stage) na = st;
+    else if (fits(st, 2, no)) na = 2;
     fits(st, na, no);
-    p.stages = st; p.aop_bufs = na; p.omega_bufs = no;
+    p.stages = st; p.aop_bufs = na; p.omega_bufs = no; p.aop_in_stage = P.aop_in_stage;
     p.smem_bytes = lowp_carve(0, P, nullptr) + 1024;
     *plan = p;
     return true;
@@ -582,16 +593,40 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
     auto encode = get_encode_tiled();
     if (!encode) return cudaErrorNotSupported;
     const int f16 = precision_is_f16(precision);
-    CUtensorMap tm;
-    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(ell)};
-    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ldo) * 2};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunkRows), static_cast<cuuint32_t>(plan.lp)};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult cr = encode(&tm, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                         const_cast<uint16_t*>(omega), gdim, gstride, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const int elem = a_f64 ? 8 : 4;
+    CUtensorMap tm_om, tm_a, tm_pf;
+    memset(&tm_a, 0, sizeof(tm_a));
+    memset(&tm_pf, 0, sizeof(tm_pf));
+    {
+        cuuint64_t gdim[2] = {static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(ell)};
+        cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ldo) * 2};
+        cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunkRows), static_cast<cuuint32_t>(plan.lp)};
+        cuuint32_t estr[2] = {1, 1};
+        if (encode(&tm_om, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<uint16_t*>(omega), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const int direct = ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || ((lda * elem) & 15) != 0) ? 1 : 0;
+    bool prefetch = false;
+    if (!direct) {
+        const CUtensorMapDataType dt = a_f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        cuuint64_t gdim[2] = {static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(n)};
+        cuuint64_t gstride[1] = {static_cast<cuuint64_t>(lda) * elem};
+        cuuint32_t estr[2] = {1, 1};
+        cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem), static_cast<cuuint32_t>(kTileCols)};
+        if (encode(&tm_a, dt, 2, const_cast<void*>(A), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        // prefetch boxes: kPrefetchGroup chunks of rows x 128 columns (2 KB-class runs per column)
+        cuuint32_t pbox[2] = {static_cast<cuuint32_t>(std::min<int64_t>(256, kPrefetchGroup * kChunkRows)),
+                              static_cast<cuuint32_t>(kTileCols)};
+        prefetch = encode(&tm_pf, dt, 2, const_cast<void*>(A), gdim, gstride, pbox, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
 
     LowpParams P{};
     P.A = A; P.lda = lda; P.m = m; P.n = n; P.a_f64 = a_f64;
@@ -600,18 +635,18 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
     P.nchunks = plan.nchunks; P.chunks_per_slab = plan.chunks_per_slab;
     P.stages = plan.stages; P.aop_bufs = plan.aop_bufs; P.omega_bufs = plan.omega_bufs;
     P.acc_bufs = plan.acc_bufs;
-    const int elem = a_f64 ? 8 : 4;
-    P.colstride = kChunkRows * elem + 16;
-    P.stage_bytes = kTileCols * P.colstride;
+    P.stage_bytes = static_cast<uint32_t>(kChunkRows * kTileCols * elem);
     P.omega_tile_bytes = (static_cast<uint32_t>(plan.lp) * 128u + 1023u) & ~1023u;
-    P.direct_all = ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || ((lda * elem) & 15) != 0) ? 1 : 0;
+    P.direct = direct;
+    P.aop_in_stage = plan.aop_in_stage;
+    P.prefetch = prefetch ? kSketchL2Prefetch : 0;
     P.partial = partial; P.info = info; P.limit_ns = limit_ns;
 
     cudaError_t e = cudaFuncSetAttribute(k_sketch_lowp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(plan.smem_bytes));
     if (e != cudaSuccess) return e;
     dim3 grid(plan.tiles, plan.kslabs);
-    k_sketch_lowp<<<grid, kSketchThreads, plan.smem_bytes, s>>>(tm, P);
+    k_sketch_lowp<<<grid, kSketchThreads, plan.smem_bytes, s>>>(tm_om, tm_a, tm_pf, P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (after_main) cudaEventRecord(after_main, s);
@@ -731,9 +766,16 @@ __global__ void k_scale_cast(const void* __restrict__ A, int a_f64, int64_t m, i
             mx = max(mx, static_cast<uint32_t>(__double2hiint(col[r])) & 0x7fffffffu);
         if ((mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
         shift = shift_from_max_f64hi(mx, f16);
+        const uint32_t kbias = 0x40000000u - (static_cast<uint32_t>(shift) << 23);
+        // the converter's fast path, with the exact routine for out-of-range values
+        auto conv = [&](double x) {
+            bool slow = false;
+            const float f = scaled_f32_from_f64_fast(x, shift, kbias, slow);
+            return slow ? scaled_f32_from_f64(x, shift) : f;
+        };
         for (int r = 0; r < rows; r += 2) {
-            float v0 = scaled_f32_from_f64(col[r], shift);
-            float v1 = r + 1 < rows ? scaled_f32_from_f64(col[r + 1], shift) : 0.f;
+            float v0 = conv(col[r]);
+            float v1 = r + 1 < rows ? conv(col[r + 1]) : 0.f;
             for (int p = 0; p < nsplit; ++p) {
                 const uint32_t w = take_piece2(v0, v1, f16);
                 pieces[(p * n + j) * m + r0 + r] = static_cast<uint16_t>(w & 0xFFFFu);
@@ -746,9 +788,14 @@ __global__ void k_scale_cast(const void* __restrict__ A, int a_f64, int64_t m, i
         for (int r = 0; r < rows; ++r) mx = max(mx, __float_as_uint(col[r]) & 0x7fffffffu);
         if ((mx >> 23) == 0xFFu) set_info(info, kInfoNonFinite);
         shift = shift_from_max_f32(mx, f16);
+        auto conv = [&](float x) {
+            bool slow = false;
+            const float f = scaled_f32_from_f32_fast(x, shift, slow);
+            return slow ? scaled_f32_from_f32(x, shift) : f;
+        };
         for (int r = 0; r < rows; r += 2) {
-            float v0 = scaled_f32_from_f32(col[r], shift);
-            float v1 = r + 1 < rows ? scaled_f32_from_f32(col[r + 1], shift) : 0.f;
+            float v0 = conv(col[r]);
+            float v1 = r + 1 < rows ? conv(col[r + 1]) : 0.f;
             for (int p = 0; p < nsplit; ++p) {
                 const uint32_t w = take_piece2(v0, v1, f16);
                 pieces[(p * n + j) * m + r0 + r] = static_cast<uint16_t>(w & 0xFFFFu);

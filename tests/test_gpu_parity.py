@@ -66,6 +66,14 @@ def test_scale_cast_bit_exact(gid, dev, orc, precision, dtype):
     a[10:20, 5] = 1e-30
     a[:, 7] = 1.0 + 2.0 ** -9            # ties for bfloat16
     a[::3, 8] = -(1.0 + 3 * 2.0 ** -12)  # ties for half
+    if dtype == np.float64:
+        # FP64 -> FP32 rounding edges: exact ties (to even), just above/below ties,
+        # a carry into the next binade, the smallest FP64 step, signed zeros
+        edges = np.array([1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 1.0 + 2.0 ** -24 + 2.0 ** -52,
+                          1.0 + 2.0 ** -24 - 2.0 ** -52, 2.0 - 2.0 ** -53, 1.0 + 2.0 ** -52, -0.0, 0.0,
+                          -(1.5 + 2.0 ** -25), 0.75 - 2.0 ** -54, 1.9999999403953552, 1.0000000596046448])
+        a[: len(edges), 9] = edges
+        a[len(edges):2 * len(edges), 10] = -edges * 2.0 ** 40
     a = np.asfortranarray(a.astype(dtype))
     fmt, nsplit = FMT[precision]
     pieces, shifts, info = gid.id_scale_cast(torch.from_numpy(a).to(dev), precision)
