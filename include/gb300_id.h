@@ -147,6 +147,28 @@ id_status_t id_sketch(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
                       void* Y, int64_t ldy, int32_t* info,
                       void* work, size_t work_bytes, void* stream);
 
+/* id_sketch without a workspace.  The paper has no counterpart: this entry
+ * point is for callers that cannot allocate device memory when they call the
+ * library (a plug-in whose host framework owns every device allocation, a
+ * service whose memory budget is fixed at start-up, code that must not
+ * allocate while it runs).  Same arguments and results as id_sketch, minus
+ * work/work_bytes: the split-K scratch lives in a static device array of
+ * ID_NOALLOC_SCRATCH_BYTES bytes that every GPU loading this library holds
+ * until the process exits.
+ *   - Returns ID_ERR_WORKSPACE, without launching anything, when the problem's
+ *     scratch would exceed ID_NOALLOC_SCRATCH_BYTES (id_sketch_workspace_size
+ *     gives the figure); other errors as id_sketch.
+ *   - The array is shared by all calls on a device and keeps the last call's
+ *     contents.  Calls that overlap on the GPU race on it: serialise them
+ *     (one stream, or explicit ordering between streams and host threads).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+#define ID_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+id_status_t id_sketch_noalloc(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                              const void* omega, int64_t omega_ld, int32_t ell, int32_t precision,
+                              void* Y, int64_t ldy, int32_t* info, void* stream);
+
 /* Scratch bytes id_sketch needs. */
 id_status_t id_sketch_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, int32_t ell,
                                      int32_t precision, size_t* bytes);
