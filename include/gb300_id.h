@@ -186,6 +186,37 @@ id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t 
                           int32_t precision, uint16_t* pieces, int32_t* shifts,
                           int32_t* info, void* stream);
 
+/* Adjoint of the column ID with the pivot set J held fixed (north-star
+ * differentiation; the paper does not differentiate the ID), FP32.
+ * The map is the fixed-pivot least-squares ID: X = A(:,J[0:k]),
+ * C = A(:,J[k:n]), T = X^+ C (what a column-pivoted QR of A gives as
+ * R11^-1 R12, Sec. 1.1), A_hat = A(:,J[0:k]) P (Algorithm 1 lines 4-5).
+ * Given dL/dA_hat (dAhat, nullable) and dL/dT (dT, nullable) it writes
+ * dA = dL/dA (every column).  With the thin QR X = Q R:
+ *   B1 = Q^T G_c + R^-T dT,  Z = G_c T^T + C (R^-1 B1)^T,
+ *   dA(:,J[0:k]) = G_s + Z - Q (Q^T Z + R^-T dT T^T),  dA(:,J[k:n]) = Q B1.
+ * Batched over `batch` matrices of equal shape: matrix b starts at
+ * A + b*strideA (column-major, lda), J + b*strideJ (a permutation of 0..n-1
+ * as id_factor returns it), T + b*strideT (k x (n-k) doubles, ldt), dAhat +
+ * b*strideG (m x n, ldg), dT + b*strideDT (k x (n-k) doubles, lddt), dA +
+ * b*strideD (m x n, ldd, must not alias the inputs).  1 <= k <= min(m, n, 128).
+ * X must have full column rank.  Errors: ID_ERR_ARG, ID_ERR_WORKSPACE,
+ * ID_ERR_CUDA. */
+id_status_t id_backward_workspace_size(int64_t batch, int64_t m, int64_t n, int32_t k, size_t* bytes);
+id_status_t id_backward(int64_t batch, const float* A, int64_t m, int64_t n, int64_t lda, int64_t strideA,
+                        const int32_t* J, int64_t strideJ, int32_t k, const double* T, int64_t ldt, int64_t strideT,
+                        const float* dAhat, int64_t ldg, int64_t strideG, const double* dT, int64_t lddt,
+                        int64_t strideDT, float* dA, int64_t ldd, int64_t strideD, void* work, size_t work_bytes,
+                        void* stream);
+
+/* Reconstruction A_hat = A(:,J[0:k]) P with P(:,J[0:k]) = I, P(:,J[k:n]) = T
+ * (Sec. 1.1; Algorithm 1 line 7), FP32, batched like id_backward.  Ahat is
+ * m x n (ldh) per matrix. */
+id_status_t id_reconstruct_workspace_size(int64_t batch, int64_t n, int32_t k, size_t* bytes);
+id_status_t id_reconstruct(int64_t batch, const float* A, int64_t m, int64_t n, int64_t lda, int64_t strideA,
+                           const int32_t* J, int64_t strideJ, int32_t k, const double* T, int64_t ldt, int64_t strideT,
+                           float* Ahat, int64_t ldh, int64_t strideH, void* work, size_t work_bytes, void* stream);
+
 /* Profiling aid (not part of the computation).  When set, the next id_factor
  * calls made from this host thread record the caller's CUDA events (cudaEvent_t
  * passed as void*) on their stream at the stage boundaries:

@@ -19,7 +19,7 @@ import torch
 
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
-    "status_string", "lib_path", "set_stage_events",
+    "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -75,6 +75,13 @@ def load():
         lib.id_sketch.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i64, i32, i32, p, i64, p, p, sz, p]
         lib.id_scale_cast.argtypes = [p, ctypes.c_int, i64, i64, i64, i32, p, p, p, p]
         lib.id_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
+        lib.id_backward_workspace_size.argtypes = [i64, i64, i64, i32, ctypes.POINTER(sz)]
+        lib.id_backward.argtypes = [i64, p, i64, i64, i64, i64, p, i64, i32, p, i64, i64, p, i64, i64, p, i64, i64,
+                                    p, i64, i64, p, sz, p]
+        lib.id_reconstruct_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(sz)]
+        lib.id_reconstruct.argtypes = [i64, p, i64, i64, i64, i64, p, i64, i32, p, i64, i64, p, i64, i64, p, sz, p]
+        for name in ("id_backward_workspace_size", "id_backward", "id_reconstruct_workspace_size", "id_reconstruct"):
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("id_workspace_size", "id_factor", "id_sketch_workspace_size", "id_sketch",
                      "id_scale_cast", "id_set_stage_events"):
             getattr(lib, name).restype = ctypes.c_int
@@ -247,3 +254,105 @@ def id_scale_cast(A: torch.Tensor, precision: str = "mixed_bf16", stream=None):
                                 pieces.data_ptr(), shifts.data_ptr(), info.data_ptr(), _stream_ptr(stream)),
            "id_scale_cast")
     return pieces.transpose(1, 2), shifts.t(), info
+
+
+# ------------------------------------------------------------------ fixed-pivot adjoint
+
+def _batched_colmajor(x: torch.Tensor, rows: int):
+    """(batch, rows, cols) view with column-major matrices: returns (tensor, ld, batch stride)."""
+    if x.dim() == 2:
+        x = x.unsqueeze(0)
+    b, r, c = x.shape
+    if not (x.stride(1) == 1 and (c == 1 or x.stride(2) >= r)):
+        x = x.transpose(1, 2).contiguous().transpose(1, 2)
+    return x, x.stride(2) if c > 1 else r, x.stride(0)
+
+
+def id_reconstruct(A: torch.Tensor, J: torch.Tensor, T: torch.Tensor, k: int, stream=None) -> torch.Tensor:
+    """A_hat = A(:, J[:k]) P for float32 A of shape (m, n) or (batch, m, n); T (.., k, n-k) float64."""
+    _require_cuda(A, J, T)
+    squeeze = A.dim() == 2
+    a, lda, sa = _batched_colmajor(A, A.shape[-2])
+    batch, m, n = a.shape
+    j = J.reshape(batch, n).contiguous()
+    t, ldt, st = _batched_colmajor(T.reshape(batch, k, n - k), k)
+    out = torch.empty((batch, n, m), dtype=torch.float32, device=a.device).transpose(1, 2)
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.id_reconstruct_workspace_size(batch, n, k, ctypes.byref(nb)), "id_reconstruct_workspace_size")
+    work = torch.empty(nb.value, dtype=torch.uint8, device=a.device)
+    _check(lib.id_reconstruct(batch, a.data_ptr(), m, n, lda, sa, j.data_ptr(), n, k, t.data_ptr(), ldt, st,
+                              out.data_ptr(), m, m * n, work.data_ptr(), work.numel(), _stream_ptr(stream)),
+           "id_reconstruct")
+    return out[0] if squeeze else out
+
+
+def id_backward(A: torch.Tensor, J: torch.Tensor, T: torch.Tensor, k: int, dAhat: torch.Tensor | None = None,
+                dT: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dL/dA of the fixed-pivot ID for float32 A (m, n) or (batch, m, n), given dL/dA_hat and/or dL/dT."""
+    _require_cuda(A, J, T, dAhat, dT)
+    squeeze = A.dim() == 2
+    a, lda, sa = _batched_colmajor(A, A.shape[-2])
+    batch, m, n = a.shape
+    j = J.reshape(batch, n).contiguous()
+    t, ldt, st = _batched_colmajor(T.reshape(batch, k, n - k), k)
+    g = ldg = sg = None
+    if dAhat is not None:
+        g, ldg, sg = _batched_colmajor(dAhat.reshape(batch, m, n).float(), m)
+    tb = ldtb = stb = None
+    if dT is not None:
+        tb, ldtb, stb = _batched_colmajor(dT.reshape(batch, k, n - k).double(), k)
+    out = torch.empty((batch, n, m), dtype=torch.float32, device=a.device).transpose(1, 2)
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.id_backward_workspace_size(batch, m, n, k, ctypes.byref(nb)), "id_backward_workspace_size")
+    work = torch.empty(nb.value, dtype=torch.uint8, device=a.device)
+    _check(lib.id_backward(batch, a.data_ptr(), m, n, lda, sa, j.data_ptr(), n, k, t.data_ptr(), ldt, st,
+                           g.data_ptr() if g is not None else None, ldg or m, sg or 0,
+                           tb.data_ptr() if tb is not None else None, ldtb or k, stb or 0,
+                           out.data_ptr(), m, m * n, work.data_ptr(), work.numel(), _stream_ptr(stream)),
+           "id_backward")
+    return out[0] if squeeze else out
+
+
+class IDFunction(torch.autograd.Function):
+    """Differentiable column ID with the pivots held fixed.
+
+    ``IDFunction.apply(A, k)`` for float32 A (m, n) or (batch, m, n) returns
+    ``(A_hat, T, J)``: the reconstruction A(:, J[:k]) P, the coefficients T (float64,
+    k x (n-k)) and the pivots (not differentiable).  The pivots and T come from the
+    column-pivoted QR of A (``precision='plain_f32'``), whose T = R11^-1 R12 is the
+    least-squares X^+ C that the adjoint differentiates.
+    """
+
+    @staticmethod
+    def forward(ctx, A, k):
+        squeeze = A.dim() == 2
+        a = A.unsqueeze(0) if squeeze else A
+        batch, m, n = a.shape
+        Js, Ts = [], []
+        for b in range(batch):
+            res = id_factor(a[b], k, precision="plain_f32")
+            if res.k != k:
+                raise IDError(f"matrix {b}: rank {res.k} < k = {k} (info {res.info})")
+            Js.append(res.J)
+            Ts.append(res.T)
+        Jt = torch.stack(Js)
+        Tt = torch.stack([t.t().contiguous().t() for t in Ts])
+        Ahat = id_reconstruct(a, Jt, Tt, k)
+        ctx.save_for_backward(a, Jt, Tt)
+        ctx.k = k
+        ctx.squeeze = squeeze
+        ctx.mark_non_differentiable(Jt)
+        if squeeze:
+            return Ahat[0], Tt[0], Jt[0]
+        return Ahat, Tt, Jt
+
+    @staticmethod
+    def backward(ctx, gAhat, gT, gJ):
+        a, Jt, Tt = ctx.saved_tensors
+        if ctx.squeeze:
+            gAhat = None if gAhat is None else gAhat.unsqueeze(0)
+            gT = None if gT is None else gT.unsqueeze(0)
+        dA = id_backward(a, Jt, Tt, ctx.k, gAhat, gT)
+        return (dA[0] if ctx.squeeze else dA), None

@@ -107,4 +107,15 @@ cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, 
                                 const int32_t* J, const int32_t* k_ptr, const double* T,
                                 int64_t ldt, double* acc2, double* err_out, cudaStream_t s);
 
+// ---- adjoint and reconstruction (backward.cu)
+size_t backward_workspace_bytes(int64_t batch, int64_t m, int64_t n, int k);
+size_t reconstruct_workspace_bytes(int64_t batch, int64_t n, int k);
+cudaError_t launch_backward(int64_t batch, const float* A, int64_t m, int64_t n, int64_t lda, int64_t strideA,
+                            const int32_t* J, int64_t strideJ, int k, const double* T, int64_t ldt, int64_t strideT,
+                            const float* G, int64_t ldg, int64_t strideG, const double* Tb, int64_t ldtb,
+                            int64_t strideTb, float* dA, int64_t ldd, int64_t strideD, void* work, cudaStream_t s);
+cudaError_t launch_reconstruct(int64_t batch, const float* A, int64_t m, int64_t n, int64_t lda, int64_t strideA,
+                               const int32_t* J, int64_t strideJ, int k, const double* T, int64_t ldt, int64_t strideT,
+                               float* Ahat, int64_t ldh, int64_t strideH, void* work, cudaStream_t s);
+
 }  // namespace gid
