@@ -31,6 +31,7 @@
  *            and k_out = j-1
  *        -1  A (or Omega A) holds a non-finite value
  *        -2  a bounded device wait gave up (watchdog); outputs are invalid
+ *        -3  (batched calls) a work-unit table entry did not fit its matrix
  *   - The complement J[k:n] is listed in ascending column index.
  */
 #ifndef GB300_ID_H
@@ -86,7 +87,7 @@ typedef enum {
 #define ID_MAX_ELL 256
 
 typedef struct {
-    int32_t k;               /* target rank when rel_tol == 0 (Algorithm 1 line 2) */
+    int32_t k;               /* target rank when rel_tol == 0 (Algorithm 1) */
     double rel_tol;          /* > 0: rank = smallest k with ||R22||_F <= rel_tol ||W||_F,
                                 W the matrix being pivoted (A or Y), capped by k_max */
     int32_t k_max;           /* cap for rel_tol mode (and T's row capacity) */
@@ -115,9 +116,9 @@ id_status_t id_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n,
 
 /* One column ID of A (m x n, column-major, lda >= m; dtype a_dtype).
  *   Sketch (optional, Sec. 5 future work): Y = Omega A, ell x n.
- *   Pivoted QR (Sec. 1.1, Algorithm 1 line 3): truncated Householder QR with
+ *   Pivoted QR (Sec. 1.1, Algorithm 1, the pivoted QR): truncated Householder QR with
  *   Businger-Golub pivoting and column-norm downdating on W = Y or A.
- *   Coefficients (Algorithm 1 line 4): T = R11^-1 R12 in FP64.
+ *   Coefficients (Algorithm 1, the coefficient solve): T = R11^-1 R12 in FP64.
  * Outputs (device):
  *   J      [n]  int32, J[0:k] the skeleton in pivot order, J[k:n] the rest
  *   T      k_cap x (n - k) doubles, column-major, ldt >= k_cap where
@@ -135,7 +136,7 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
                       int32_t* J, double* T, int64_t ldt, int32_t* k_out, int32_t* info,
                       double* err_out, void* work, size_t work_bytes, void* stream);
 
-/* The sketch step alone (Sec. 5 "matrix sketching"; Algorithm 2 line 1 for
+/* The sketch step alone (the sketching of Sec. 5; Algorithm 2 for
  * the cast): Y = Omega A (ell x n, column-major, ldy >= ell).
  * PLAIN_F64: Omega and Y are double.  MIXED_*: Omega is bfloat16/half bits,
  * A is scaled per (ID_SCALE_BLOCK_ROWS rows, column) by a power of two,
@@ -173,7 +174,7 @@ id_status_t id_sketch_noalloc(const void* A, id_dtype_t a_dtype, int64_t m, int6
 id_status_t id_sketch_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, int32_t ell,
                                      int32_t precision, size_t* bytes);
 
-/* The scaled low-precision cast of Algorithm 2 line 1 on its own, as the
+/* The scaled low-precision cast of Algorithm 2 on its own, as the
  * mixed sketch performs it: for every block of ID_SCALE_BLOCK_ROWS rows of a
  * column, shift s = exponent that puts the block's largest magnitude in
  * [0.5, 1) (bfloat16) or [2^13, 2^14) (half), zero block -> 0; each entry x
@@ -190,7 +191,7 @@ id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t 
  * differentiation; the paper does not differentiate the ID), FP32.
  * The map is the fixed-pivot least-squares ID: X = A(:,J[0:k]),
  * C = A(:,J[k:n]), T = X^+ C (what a column-pivoted QR of A gives as
- * R11^-1 R12, Sec. 1.1), A_hat = A(:,J[0:k]) P (Algorithm 1 lines 4-5).
+ * R11^-1 R12, Sec. 1.1), A_hat = A(:,J[0:k]) P (Algorithm 1).
  * Given dL/dA_hat (dAhat, nullable) and dL/dT (dT, nullable) it writes
  * dA = dL/dA (every column).  With the thin QR X = Q R:
  *   B1 = Q^T G_c + R^-T dT,  Z = G_c T^T + C (R^-1 B1)^T,
@@ -210,12 +211,116 @@ id_status_t id_backward(int64_t batch, const float* A, int64_t m, int64_t n, int
                         void* stream);
 
 /* Reconstruction A_hat = A(:,J[0:k]) P with P(:,J[0:k]) = I, P(:,J[k:n]) = T
- * (Sec. 1.1; Algorithm 1 line 7), FP32, batched like id_backward.  Ahat is
+ * (Sec. 1.1; Algorithm 1, the reconstruction), FP32, batched like id_backward.  Ahat is
  * m x n (ldh) per matrix. */
 id_status_t id_reconstruct_workspace_size(int64_t batch, int64_t n, int32_t k, size_t* bytes);
 id_status_t id_reconstruct(int64_t batch, const float* A, int64_t m, int64_t n, int64_t lda, int64_t strideA,
                            const int32_t* J, int64_t strideJ, int32_t k, const double* T, int64_t ldt, int64_t strideT,
                            float* Ahat, int64_t ldh, int64_t strideH, void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------ batched IDs
+ * Many independent mixed-precision IDs of uneven sizes in one stream-ordered
+ * launch sequence (spec batching; the paper factors one matrix at a
+ * time).  Matrix i is m[i] x n[i] (column-major, lda[i]) with target rank
+ * k[i]; it is sketched with the leading ell_i = min(k[i] + oversample, m[i])
+ * rows and m[i] columns of one shared low-precision Gaussian Omega, then
+ * pivoted (FP32) and solved (FP32 solves, FP64 refinement residual) as
+ * id_factor does for one matrix with the same precision and Omega.
+ *
+ * Shapes are fixed when the plan is made, because they set the launch shapes;
+ * the matrices' addresses are fixed when they are bound (each matrix gets its
+ * own TMA tensor map, stored in the workspace).  Work is split into units
+ * (128-column tiles times row slabs for the sketch, one cluster of CTAs per
+ * matrix for the pivoted QR, blocks of T columns for the solve), ordered
+ * largest first; the unit sizes come from id_batch_opts_t or from the
+ * autotuner's cache.  A captured CUDA graph of id_factor_batched replays on
+ * new values written to the bound matrices.
+ *
+ * Calls, in order:
+ *   id_batch_plan_create  host only: checks shapes, builds the tables.
+ *   id_batch_plan_query / id_batch_workspace_size
+ *   id_batch_bind         encodes the matrices' tensor maps and copies the
+ *                         plan's tables into the head of `work` (stream-
+ *                         ordered); again after id_batch_autotune only if the
+ *                         addresses change.
+ *   id_factor_batched     launches only (graph-capturable).
+ *   id_batch_plan_destroy
+ * One call of a plan may be in flight at a time (it owns the fork/join
+ * streams and events of its pivoted-QR launches). */
+typedef struct id_batch_plan id_batch_plan_t;
+
+typedef struct {
+    int32_t precision;       /* ID_MIXED_BF16, ID_MIXED_F16, ID_MIXED_BF16X2 or ID_MIXED_BF16X3 */
+    int32_t oversample;      /* p: ell_i = min(k_i + p, m_i) <= 160; default 10 */
+    int32_t refine_steps;    /* refinement steps of the T solve; default 1 */
+    double rel_tol;          /* 0: fixed ranks k_i; > 0: stop at the first step whose remaining
+                                norm is <= rel_tol times the initial one, k_i the cap */
+    int64_t watchdog_ms;     /* bound of every device wait; 0 = 4000 ms */
+    int32_t slab_chunks;     /* sketch unit height in 64-row chunks: 16, 32 or 64 (0 = 32) */
+    int32_t cpqr_tpc;        /* pivoted-QR threads per column, 2 or 4 (0 = 4) */
+    int32_t solve_warps;     /* warps per solve CTA, 1..16 (0 = 8) */
+    int32_t solve_cols;      /* T columns per solve CTA, >= 16 (0 = 32) */
+    const char* tune_cache;  /* host, nullable: autotuner cache (JSON lines) whose entry for this
+                                device and batch overrides the four shape fields above */
+} id_batch_opts_t;
+
+id_batch_opts_t id_batch_opts_default(void);
+
+/* m, n, lda, k: HOST arrays of length batch.  Requirements per matrix:
+ * 1 <= k[i] <= min(m[i], n[i], 128), lda[i] >= m[i], ell_i <= 160,
+ * n[i] <= 2048.  Errors: ID_ERR_ARG, ID_ERR_UNSUPPORTED (a shape the kernels
+ * do not cover). */
+id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_t* m, const int64_t* n,
+                                 const int64_t* lda, const int32_t* k, const id_batch_opts_t* opts,
+                                 id_batch_plan_t** plan);
+void id_batch_plan_destroy(id_batch_plan_t* plan);
+
+/* Sizes of the caller's buffers (all host outputs, each nullable):
+ *   work_bytes       workspace for id_batch_bind / id_factor_batched;
+ *   j_offsets[batch+1]  J of matrix i is J[j_offsets[i] .. +n[i]) (int32);
+ *   t_offsets[batch+1]  T of matrix i starts at T + t_offsets[i], k[i] x tcols_i
+ *                    doubles with ldt = k[i]; tcols_i = n[i] - k[i] for fixed
+ *                    ranks, n[i] - 1 under a tolerance (first n[i] - k_out[i] used);
+ *   ell_max, m_max   Omega must have at least ell_max rows and m_max columns. */
+id_status_t id_batch_plan_query(const id_batch_plan_t* plan, size_t* work_bytes, int64_t* j_offsets,
+                                int64_t* t_offsets, int32_t* ell_max, int64_t* m_max);
+
+/* The plan's unit shapes and counts as a one-line JSON object (host buffer;
+ * truncated to len - 1 characters).  Returns the length it needed. */
+int64_t id_batch_plan_describe(const id_batch_plan_t* plan, char* buf, int64_t len);
+
+id_status_t id_batch_workspace_size(const id_batch_plan_t* plan, size_t* bytes);
+
+/* A: HOST array of batch DEVICE pointers to the matrices (a_dtype of the plan).
+ * Every matrix must be addressable by TMA: its address and lda[i] * element
+ * size multiples of 16 bytes (ID_ERR_ARG otherwise).  work: 256-byte aligned,
+ * at least work_bytes; it holds the tables from now on. */
+id_status_t id_batch_bind(id_batch_plan_t* plan, const void* const* A, void* work, size_t work_bytes,
+                          void* stream);
+
+/* omega: bfloat16/half bits (per the precision), row-major with omega_ld >=
+ * m_max, omega_ld a multiple of 8, 16-byte aligned, >= ell_max rows.
+ * J (packed int32), T (packed double), k_out[batch], info[batch]: outputs as
+ * laid out by id_batch_plan_query; info per matrix as for id_factor, plus -3
+ * when a table entry does not fit its matrix (never expected; nothing of that
+ * matrix is computed).  Errors: ID_ERR_ARG (also: work not the buffer last
+ * bound), ID_ERR_WORKSPACE, ID_ERR_CUDA. */
+id_status_t id_factor_batched(const id_batch_plan_t* plan, const void* omega, int64_t omega_ld, int32_t* J,
+                              double* T, int32_t* k_out, int32_t* info, void* work, size_t work_bytes,
+                              void* stream);
+
+/* Autotuner: times id_factor_batched on the bound buffers for each candidate
+ * sketch unit height, pivoted-QR threads per column, and solve CTA shape
+ * (coordinate search, median of `reps` timed calls after one warm-up), keeps
+ * the fastest in the plan, rewrites the tables in `work`, and, when cache_path
+ * is not NULL, writes the choice under this device's and this batch's key as
+ * one JSON line of that file (replacing an older line with the same key).
+ * The device synchronises.  best_ms (host, nullable) receives the tuned time.
+ * Errors: as id_factor_batched, ID_ERR_ARG when the cache file cannot be
+ * written. */
+id_status_t id_batch_autotune(id_batch_plan_t* plan, const void* omega, int64_t omega_ld, int32_t* J, double* T,
+                              int32_t* k_out, int32_t* info, void* work, size_t work_bytes, void* stream,
+                              int32_t reps, const char* cache_path, double* best_ms);
 
 /* Profiling aid (not part of the computation).  When set, the next id_factor
  * calls made from this host thread record the caller's CUDA events (cudaEvent_t

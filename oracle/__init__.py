@@ -107,7 +107,7 @@ def block_shift(mx: float, fmt: str, in_f32: bool = False) -> int:
 
 
 def quantize(a: np.ndarray, fmt: str, block_rows: int, nsplit: int = 1):
-    """Scaled cast of Algorithm 2 line 1 with per-(row block, column) power-of-two shifts.
+    """Scaled low-precision cast of Algorithm 2 with per-(row block, column) power-of-two shifts.
 
     Each scaled entry is taken at FP32 precision (round to nearest even) and split
     into ``nsplit`` low-format pieces.  ``a`` of dtype float32 is treated as float
@@ -180,7 +180,7 @@ def mgs_cpqr(w: np.ndarray, k: int):
 
 
 def solve_T(R: np.ndarray, J: np.ndarray, k: int) -> np.ndarray:
-    """T = R11^-1 R12 by back-substitution (Algorithm 1 line 4)."""
+    """T = R11^-1 R12 by back-substitution (Algorithm 1, the coefficient solve)."""
     R = _f64(R)
     n = R.shape[1]
     T = np.zeros((max(k, 1), max(n - k, 1)), dtype=np.float64, order="F")
@@ -223,7 +223,7 @@ def interp_decomp(a: np.ndarray, k: int | None = None, tol: float | None = None,
 # ------------------------------------------------------------ reconstruction
 
 def coefficient_matrix(J: np.ndarray, T: np.ndarray, k: int, n: int) -> np.ndarray:
-    """P with P(:, J[0:k]) = I_k and P(:, J[k:n]) = T (Algorithm 1 line 5)."""
+    """P with P(:, J[0:k]) = I_k and P(:, J[k:n]) = T (Algorithm 1)."""
     P = np.zeros((k, n), dtype=np.float64)
     P[:, J[:k]] = np.eye(k)
     P[:, J[k:]] = T

@@ -103,7 +103,7 @@ int orc_block_shift(double mx, int fmt, int in_f32)
     return fmt == 0 ? e2 : e2 - 14;
 }
 
-/* Scaled cast of A (Algorithm 2 line 1, A_L = fl(A)) with per-(block, column)
+/* Scaled cast of A (Algorithm 2, A_L = fl(A)) with per-(block, column)
  * power-of-two scaling.  Rows are split in blocks of block_rows; block b of
  * column j gets shift s(b,j) from its largest magnitude.  Each entry is scaled
  * by 2^-s(b,j) and rounded to the nearest FP32 value (ties to even; exact for
@@ -352,7 +352,7 @@ int orc_mgs_cpqr(const double* W, int64_t r, int64_t n, int64_t ldw, int32_t k,
     return info;
 }
 
-/* T = R11^-1 R12 by back-substitution (Algorithm 1 line 4; R11 is upper
+/* T = R11^-1 R12 by back-substitution (Algorithm 1, the coefficient solve; R11 is upper
  * triangular and nonsingular, so its pseudo-inverse is its inverse).
  * R11(a,b) = R(a, J[b]), R12(a,c) = R(a, J[k+c]).  T: k x (n-k) col-major. */
 void orc_solve_T(int32_t k, int64_t n, const int32_t* J, const double* R, int64_t ldr,

@@ -20,6 +20,7 @@ import torch
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
     "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
+    "BatchPlan",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,6 +42,15 @@ class IDOpts(ctypes.Structure):
         ("sketch", ctypes.c_int32), ("ell", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("omega", ctypes.c_void_p), ("omega_ld", ctypes.c_int64), ("refine_steps", ctypes.c_int32),
         ("estimate_error", ctypes.c_int32), ("watchdog_ms", ctypes.c_int64),
+    ]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32), ("oversample", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+        ("rel_tol", ctypes.c_double), ("watchdog_ms", ctypes.c_int64), ("slab_chunks", ctypes.c_int32),
+        ("cpqr_tpc", ctypes.c_int32), ("solve_warps", ctypes.c_int32), ("solve_cols", ctypes.c_int32),
+        ("tune_cache", ctypes.c_char_p),
     ]
 
 
@@ -81,6 +91,22 @@ def load():
         lib.id_reconstruct_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(sz)]
         lib.id_reconstruct.argtypes = [i64, p, i64, i64, i64, i64, p, i64, i32, p, i64, i64, p, i64, i64, p, sz, p]
         for name in ("id_backward_workspace_size", "id_backward", "id_reconstruct_workspace_size", "id_reconstruct"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.id_batch_opts_default.restype = BatchOpts
+        lib.id_batch_plan_create.argtypes = [i32, ctypes.c_int, p, p, p, p, ctypes.POINTER(BatchOpts),
+                                             ctypes.POINTER(ctypes.c_void_p)]
+        lib.id_batch_plan_destroy.argtypes = [p]
+        lib.id_batch_plan_destroy.restype = None
+        lib.id_batch_plan_query.argtypes = [p, ctypes.POINTER(sz), p, p, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        lib.id_batch_plan_describe.argtypes = [p, ctypes.c_char_p, i64]
+        lib.id_batch_plan_describe.restype = i64
+        lib.id_batch_workspace_size.argtypes = [p, ctypes.POINTER(sz)]
+        lib.id_batch_bind.argtypes = [p, ctypes.POINTER(ctypes.c_void_p), p, sz, p]
+        lib.id_factor_batched.argtypes = [p, p, i64, p, p, p, p, p, sz, p]
+        lib.id_batch_autotune.argtypes = [p, p, i64, p, p, p, p, p, sz, p, i32, ctypes.c_char_p,
+                                          ctypes.POINTER(ctypes.c_double)]
+        for name in ("id_batch_plan_create", "id_batch_plan_query", "id_batch_workspace_size", "id_batch_bind",
+                     "id_factor_batched", "id_batch_autotune"):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("id_workspace_size", "id_factor", "id_sketch_workspace_size", "id_sketch",
                      "id_scale_cast", "id_set_stage_events"):
@@ -356,3 +382,129 @@ class IDFunction(torch.autograd.Function):
             gT = None if gT is None else gT.unsqueeze(0)
         dA = id_backward(a, Jt, Tt, ctx.k, gAhat, gT)
         return (dA[0] if ctx.squeeze else dA), None
+
+
+# ------------------------------------------------------------------ batched IDs
+
+class BatchPlan:
+    """Many mixed-precision IDs of fixed uneven shapes in one launch sequence.
+
+    ``shapes``: list of (m, n); ``ranks``: list of k.  Matrices are column-major
+    with leading dimensions ``lda`` (default m; lda * element size must be a
+    multiple of 16 bytes).  The plan owns the workspace and the packed outputs.
+    ``bind(mats)`` fixes the matrices (CUDA tensors, column-major views such as
+    ``buf.t()[:m]``); ``run(omega)`` factors them with the shared low-precision
+    Omega (at least ell_max x m_max, row-major).
+    """
+
+    def __init__(self, shapes, ranks, *, dtype=torch.float64, precision="mixed_bf16", oversample=10,
+                 refine_steps=1, tol=None, watchdog_ms=0, slab_chunks=0, cpqr_tpc=0, solve_warps=0,
+                 solve_cols=0, tune_cache=None, lda=None, device=None):
+        lib = load()
+        self._lib = lib
+        self.batch = len(shapes)
+        self.m = [int(s[0]) for s in shapes]
+        self.n = [int(s[1]) for s in shapes]
+        self.k = [int(r) for r in ranks]
+        self.lda = [int(v) for v in (lda if lda is not None else self.m)]
+        self.dtype = dtype
+        o = lib.id_batch_opts_default()
+        o.precision = PRECISIONS[precision]
+        o.oversample = oversample
+        o.refine_steps = refine_steps
+        o.rel_tol = float(tol) if tol else 0.0
+        o.watchdog_ms = watchdog_ms
+        o.slab_chunks, o.cpqr_tpc, o.solve_warps, o.solve_cols = slab_chunks, cpqr_tpc, solve_warps, solve_cols
+        self._cache = tune_cache.encode() if tune_cache else None
+        o.tune_cache = self._cache
+        i64a = ctypes.c_int64 * self.batch
+        m_, n_, l_ = i64a(*self.m), i64a(*self.n), i64a(*self.lda)
+        k_ = (ctypes.c_int32 * self.batch)(*self.k)
+        h = ctypes.c_void_p(0)
+        _check(lib.id_batch_plan_create(self.batch, _DTYPE[dtype], m_, n_, l_, k_, ctypes.byref(o), ctypes.byref(h)),
+               "id_batch_plan_create")
+        self._h = h
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._query()
+        self.mats = None
+        if self.device.type != "cuda":
+            return          # planning only (sizes, offsets, describe); nothing to run
+        self.k_out = torch.zeros(self.batch, dtype=torch.int32, device=self.device)
+        self.info = torch.zeros(self.batch, dtype=torch.int32, device=self.device)
+        self.J = torch.empty(max(self.j_off[-1], 1), dtype=torch.int32, device=self.device)
+        self.T = torch.empty(max(self.t_off[-1], 1), dtype=torch.float64, device=self.device)
+        self.work = torch.empty(max(self.work_bytes, 256), dtype=torch.uint8, device=self.device)
+
+    def _query(self):
+        nb = ctypes.c_size_t(0)
+        jo = (ctypes.c_int64 * (self.batch + 1))()
+        to = (ctypes.c_int64 * (self.batch + 1))()
+        em = ctypes.c_int32(0)
+        mm = ctypes.c_int64(0)
+        _check(self._lib.id_batch_plan_query(self._h, ctypes.byref(nb), jo, to, ctypes.byref(em), ctypes.byref(mm)),
+               "id_batch_plan_query")
+        self.work_bytes = nb.value
+        self.j_off = list(jo)
+        self.t_off = list(to)
+        self.ell_max = em.value
+        self.m_max = mm.value
+
+    def bind(self, mats, stream=None):
+        """Fix the matrices (kept referenced by the plan) and write the tables to the workspace."""
+        if len(mats) != self.batch:
+            raise ValueError("one matrix per plan entry")
+        for a, m, n in zip(mats, self.m, self.n):
+            if not a.is_cuda or a.dtype != self.dtype or tuple(a.shape) != (m, n) or a.stride(0) != 1:
+                raise ValueError("matrices must be column-major CUDA tensors of the planned shapes and dtype")
+        self.mats = list(mats)
+        arr = (ctypes.c_void_p * self.batch)(*[ctypes.c_void_p(a.data_ptr()) for a in mats])
+        _check(self._lib.id_batch_bind(self._h, arr, self.work.data_ptr(), self.work.numel(), _stream_ptr(stream)),
+               "id_batch_bind")
+
+    def describe(self) -> dict:
+        import json
+        need = self._lib.id_batch_plan_describe(self._h, None, 0)
+        buf = ctypes.create_string_buffer(int(need))
+        self._lib.id_batch_plan_describe(self._h, buf, need)
+        return json.loads(buf.value.decode())
+
+    def run(self, omega: torch.Tensor, stream=None):
+        """Enqueue the batch (no synchronisation); outputs land in self.J/T/k_out/info."""
+        ld = _omega_ld(omega)
+        _check(self._lib.id_factor_batched(self._h, omega.data_ptr(), ld, self.J.data_ptr(), self.T.data_ptr(),
+                                           self.k_out.data_ptr(), self.info.data_ptr(), self.work.data_ptr(),
+                                           self.work.numel(), _stream_ptr(stream)), "id_factor_batched")
+
+    def autotune(self, omega: torch.Tensor, reps: int = 5, cache_path=None, stream=None):
+        best = ctypes.c_double(0.0)
+        cp = cache_path.encode() if cache_path else None
+        _check(self._lib.id_batch_autotune(self._h, omega.data_ptr(), _omega_ld(omega), self.J.data_ptr(),
+                                           self.T.data_ptr(), self.k_out.data_ptr(), self.info.data_ptr(),
+                                           self.work.data_ptr(), self.work.numel(), _stream_ptr(stream), reps, cp,
+                                           ctypes.byref(best)), "id_batch_autotune")
+        return best.value
+
+    def results(self):
+        """Per-matrix IDResult list (synchronises)."""
+        ks = self.k_out.cpu().tolist()
+        infos = self.info.cpu().tolist()
+        out = []
+        for i in range(self.batch):
+            n, kc = self.n[i], self.k[i]
+            J = self.J[self.j_off[i]: self.j_off[i + 1]]
+            cols = (self.t_off[i + 1] - self.t_off[i]) // kc
+            T = self.T[self.t_off[i]: self.t_off[i] + kc * cols].view(cols, kc).t()
+            kk = ks[i]
+            out.append(IDResult(J, T[:kk, : max(n - kk, 0)], kk, infos[i], None))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.id_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

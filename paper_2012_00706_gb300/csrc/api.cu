@@ -33,16 +33,16 @@ const DeviceInfo& device_info() {
     return d;
 }
 
-namespace {
-
-thread_local cudaEvent_t t_stage_events[8];
-thread_local int t_stage_count = 0;
+static thread_local cudaEvent_t t_stage_events[8];
+static thread_local int t_stage_count = 0;
 
 void record_stage(int i, cudaStream_t s) {
     if (i < t_stage_count) cudaEventRecord(t_stage_events[i], s);
 }
 
 cudaEvent_t stage_event(int i) { return i < t_stage_count ? t_stage_events[i] : nullptr; }
+
+namespace {
 
 uint64_t limit_ns_of(const id_opts_t& o) {
     const int64_t ms = o.watchdog_ms > 0 ? o.watchdog_ms : 4000;

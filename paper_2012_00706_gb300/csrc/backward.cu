@@ -1,5 +1,5 @@
 // Adjoint of the column ID with the pivots held fixed, and the reconstruction
-// A_hat = A(:, J[0:k]) P (Algorithm 1 line 7), on GB300 in FP32.
+// A_hat = A(:, J[0:k]) P (Algorithm 1, the reconstruction), on GB300 in FP32.
 //
 // With X = A(:, J[0:k]), C = A(:, J[k:n]) and the least-squares coefficients
 // T = X^+ C (for a column-pivoted QR of A this is exactly R11^-1 R12), the

@@ -20,6 +20,7 @@ namespace gid {
 // info word codes (see gb300_id.h)
 constexpr int kInfoNonFinite = -1;
 constexpr int kInfoWatchdog = -2;
+constexpr int kInfoBadTable = -3;   // a batch table entry does not fit its matrix or the plan
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;

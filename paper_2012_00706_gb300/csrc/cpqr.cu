@@ -1,4 +1,4 @@
-// Truncated column-pivoted Householder QR (Sec. 1.1, Algorithm 1 line 3) on GB300.
+// Truncated column-pivoted Householder QR (Sec. 1.1, Algorithm 1, the pivoted QR) on GB300.
 //
 // Greedy Businger-Golub pivoting: step j picks the unselected column with the
 // largest residual norm, builds the Householder reflector that maps its

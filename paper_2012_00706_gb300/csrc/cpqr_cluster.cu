@@ -1,7 +1,7 @@
 // Truncated column-pivoted Householder QR of a short FP32 matrix on one thread-block
-// cluster (Sec. 1.1 / Algorithm 1 line 3 applied to the sketch Y of the mixed path).
+// cluster (Sec. 1.1 / Algorithm 1, its pivoted QR, applied to the sketch Y of the mixed path).
 //
-// The sketch Y has ell <= 128 rows, so a column fits in the registers of a few
+// The sketch Y has ell <= 160 rows, so a column fits in the registers of a few
 // threads: TPC threads own one column, each a contiguous block of MAXR / TPC
 // rows.  The n columns are split over the C CTAs of a cluster (up to 16).
 //
@@ -26,6 +26,7 @@ namespace gid {
 
 constexpr int kCqMaxCluster = 16;
 constexpr int kCqMaxThreads = 512;
+constexpr int kCqMaxRows = 160;
 
 struct CqParams {
     const float* Y;
@@ -40,7 +41,58 @@ struct CqParams {
     uint8_t* sel;
     int64_t cpb;          // columns per CTA
     uint64_t limit_ns;
+    // batch mode (tasks != nullptr): cluster c factors task order[c]; Y is the sketch's
+    // split-K partial sums, added in slab order while loading
+    const BatchTask* tasks;
+    const int32_t* order;
+    const float* partial;
+    double* R_base;
+    uint8_t* sel_base;
+    int32_t* J_base;
+    int32_t* k_out_base;
+    int32_t* infos;
+    int64_t ntasks, partial_total, r_total, j_total, sel_total;
 };
+
+// The matrix one cluster factors.
+struct CqTask {
+    const float* Y;
+    int64_t r, n, ldy, slab_stride;
+    int kslabs, kcap;
+    double rel_tol;
+    int32_t* J;
+    int32_t* k_out;
+    int32_t* info;
+    double* R;
+    int64_t ldr;
+    uint8_t* sel;
+    bool ok;              // the task fits its regions and this launch's shape
+};
+
+template <int MAXR>
+__device__ __forceinline__ CqTask cq_task(const CqParams& P, uint32_t C) {
+    CqTask W;
+    W.ok = true;
+    if (!P.tasks) {
+        W.Y = P.Y; W.r = P.r; W.n = P.n; W.ldy = P.ldy; W.slab_stride = 0; W.kslabs = 1;
+        W.kcap = P.kcap; W.rel_tol = P.rel_tol; W.J = P.J; W.k_out = P.k_out; W.info = P.info;
+        W.R = P.R; W.ldr = P.ldr; W.sel = P.sel;
+        return W;
+    }
+    const int task = P.order[blockIdx.x / C];
+    W.ok = task >= 0 && task < P.ntasks;
+    const BatchTask& bt = P.tasks[W.ok ? task : 0];
+    W.Y = P.partial + bt.partial_off; W.r = bt.ell; W.n = bt.n; W.ldy = bt.lp;
+    W.slab_stride = bt.n * bt.lp; W.kslabs = bt.kslabs;
+    W.kcap = bt.kcap; W.rel_tol = bt.rel_tol; W.J = P.J_base + bt.j_off; W.k_out = P.k_out_base + task;
+    W.info = P.infos + task; W.R = P.R_base + bt.r_off; W.ldr = bt.kcap; W.sel = P.sel_base + bt.sel_off;
+    W.ok = W.ok && bt.ell >= 1 && bt.ell <= MAXR && bt.ell <= bt.lp && bt.n >= 1 && bt.n <= C * P.cpb &&
+           bt.kcap >= 1 && bt.kcap <= bt.ell && bt.kcap <= bt.n && bt.kslabs >= 1 && bt.partial_off >= 0 &&
+           bt.partial_off + static_cast<int64_t>(bt.kslabs) * bt.n * bt.lp <= P.partial_total &&
+           bt.r_off >= 0 && bt.r_off + static_cast<int64_t>(bt.kcap) * bt.n <= P.r_total && bt.j_off >= 0 &&
+           bt.j_off + bt.n <= P.j_total && bt.sel_off >= 0 && bt.sel_off + bt.n <= P.sel_total;
+    return W;
+}
 
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -110,11 +162,18 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     __shared__ __align__(8) uint64_t recv_bar[2];
 
     const uint32_t me = cluster_rank(), C = cluster_nrank();
+    const CqTask W = cq_task<MAXR>(P, C);
+    if (!W.ok) {
+        // every CTA of the cluster reads the same entry and leaves before any cluster barrier
+        if (me == 0 && threadIdx.x == 0 && P.order[blockIdx.x / C] >= 0 && P.order[blockIdx.x / C] < P.ntasks)
+            set_info(W.info, kInfoBadTable);
+        return;
+    }
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     const int cl = t / TPC, qq = t % TPC;
     const int64_t i = static_cast<int64_t>(me) * P.cpb + cl;
-    const bool valid = cl < P.cpb && i < P.n;
-    const int r = static_cast<int>(P.r);
+    const bool valid = cl < P.cpb && i < W.n;
+    const int r = static_cast<int>(W.r);
     const int rb = qq * RPT;                 // first row of this thread's block
     const float sqrt_u = 2.44140625e-04f;    // sqrt of the FP32 unit round-off 2^-24
 
@@ -127,7 +186,12 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
 
     float x[RPT];
 #pragma unroll
-    for (int u = 0; u < RPT; ++u) x[u] = (valid && rb + u < r) ? P.Y[i * P.ldy + rb + u] : 0.f;
+    for (int u = 0; u < RPT; ++u) {
+        float s = 0.f;
+        if (valid && rb + u < r)
+            for (int ks = 0; ks < W.kslabs; ++ks) s += W.Y[ks * W.slab_stride + i * W.ldy + rb + u];
+        x[u] = s;
+    }
     float nu = 0.f;
 #pragma unroll
     for (int u = 0; u < RPT; ++u) nu = fmaf(x[u], x[u], nu);
@@ -136,8 +200,8 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     float nuref = nu;
     bool selected = !valid;
     if (valid && qq == 0) {
-        if (!isfinite(nu)) set_info(P.info, kInfoNonFinite);
-        P.sel[i] = 0;
+        if (!isfinite(nu)) set_info(W.info, kInfoNonFinite);
+        W.sel[i] = 0;
     }
 
     // Exchange q: each warp stages its best candidate column, warp 0 picks the CTA's best
@@ -201,7 +265,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     bool ok = wait_exchange(0);
     int k = 0;
     float total = -1.f;
-    for (int j = 0; ok && j < P.kcap; ++j) {
+    for (int j = 0; ok && j < W.kcap; ++j) {
         const int par = j & 1;
         // ---- warp 0: the pivot (same reduction order in every CTA), reflector scalars,
         // and the step vectors v' and e_j
@@ -224,10 +288,10 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
             }
             if (total < 0.f) total = hs;
             int stop = 0;
-            if (P.rel_tol > 0.0 && sqrtf(fmaxf(hs, 0.f)) <= static_cast<float>(P.rel_tol) * sqrtf(total)) stop = 1;
+            if (W.rel_tol > 0.0 && sqrtf(fmaxf(hs, 0.f)) <= static_cast<float>(W.rel_tol) * sqrtf(total)) stop = 1;
             if (!stop && (hi < 0 || !(hv > 0.f))) {
                 stop = 2;
-                if (me == 0 && lane == 0) set_info(P.info, j + 1);
+                if (me == 0 && lane == 0) set_info(W.info, j + 1);
             }
             if (!stop) {
                 const float* xw = recv[par][hsrc].col;
@@ -258,9 +322,9 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
         if (valid && i == p) {
             selected = true;
             if (qq == 0) {
-                P.R[i * P.ldr + j] = static_cast<double>(s_sc[2]);
-                P.J[j] = p;
-                P.sel[i] = 1;
+                W.R[i * W.ldr + j] = static_cast<double>(s_sc[2]);
+                W.J[j] = p;
+                W.sel[i] = 1;
             }
         }
         // S = v'.x (= (alpha - beta) w),  X = e_j.x (= x_j): plain FMAs over this thread's rows
@@ -298,7 +362,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
                 x[u + 2] = fmaf(-sv, v4.z, x[u + 2]);
                 x[u + 3] = fmaf(-sv, v4.w, x[u + 3]);
             }
-            if (qq == 0) P.R[i * P.ldr + j] = static_cast<double>(rho);
+            if (qq == 0) W.R[i * W.ldr + j] = static_cast<double>(rho);
             if (nu > 0.f) {
                 const float t1 = fmaxf(1.f - (rho * rho) / nu, 0.f);
                 if (t1 * (nu / nuref) <= sqrt_u) recompute = true;   // same decision in all TPC threads
@@ -320,25 +384,25 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
         ok = wait_exchange(j + 1);
         k = j + 1;
     }
-    if (!ok && t == 0) set_info(P.info, kInfoWatchdog);
+    if (!ok && t == 0) set_info(W.info, kInfoWatchdog);
     // no CTA leaves while a peer may still copy into its shared memory
     cluster_sync_all();
     if (me == 0) {
-        if (t == 0) *P.k_out = k;
+        if (t == 0) *W.k_out = k;
         __shared__ int s_base;
         __shared__ int cnt[MAXW];
         if (t == 0) s_base = k;
         __syncthreads();
-        for (int64_t i0 = 0; i0 < P.n; i0 += blockDim.x) {
+        for (int64_t i0 = 0; i0 < W.n; i0 += blockDim.x) {
             const int64_t c = i0 + t;
-            const int flag = (c < P.n && !__ldcg(P.sel + c)) ? 1 : 0;
+            const int flag = (c < W.n && !__ldcg(W.sel + c)) ? 1 : 0;
             const unsigned bal = __ballot_sync(0xffffffffu, flag);
             const int wpre = __popc(bal & ((1u << lane) - 1u));
             if (lane == 0) cnt[warp] = __popc(bal);
             __syncthreads();
             int off = 0;
             for (int w = 0; w < warp; ++w) off += cnt[w];
-            if (flag) P.J[s_base + off + wpre] = static_cast<int32_t>(c);
+            if (flag) W.J[s_base + off + wpre] = static_cast<int32_t>(c);
             __syncthreads();
             if (t == 0) {
                 int tot = 0;
@@ -351,9 +415,10 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
 }
 
 template <int MAXR, int TPC>
-static cudaLaunchConfig_t cq_config(int csize, int threads, cudaStream_t s, cudaLaunchAttribute* attr) {
+static cudaLaunchConfig_t cq_config(int csize, int nclusters, int threads, cudaStream_t s,
+                                    cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(csize);
+    cfg.gridDim = dim3(csize * nclusters);
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
@@ -369,13 +434,19 @@ static cudaLaunchConfig_t cq_config(int csize, int threads, cudaStream_t s, cuda
 // Can a cluster of csize CTAs of this kernel be resident at once?
 template <int MAXR, int TPC>
 static bool cq_cluster_fits(int csize, int threads) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        // host-only planning (no device): the GB300 target takes 16-CTA clusters of 512 threads
+        cudaGetLastError();
+        return csize <= kCqMaxCluster && threads <= kCqMaxThreads;
+    }
     auto kern = k_cpqr_cluster<MAXR, TPC>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cq_config<MAXR, TPC>(csize, threads, nullptr, attr);
+    cudaLaunchConfig_t cfg = cq_config<MAXR, TPC>(csize, 1, threads, nullptr, attr);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
         cudaGetLastError();
@@ -385,35 +456,48 @@ static bool cq_cluster_fits(int csize, int threads) {
 }
 
 template <int MAXR, int TPC>
-static cudaError_t launch_cq(const CqParams& P, int csize, int threads, cudaStream_t s) {
+static cudaError_t launch_cq(const CqParams& P, int csize, int nclusters, int threads, cudaStream_t s) {
     auto kern = k_cpqr_cluster<MAXR, TPC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cq_config<MAXR, TPC>(csize, threads, s, attr);
+    cudaLaunchConfig_t cfg = cq_config<MAXR, TPC>(csize, nclusters, threads, s, attr);
     return cudaLaunchKernelEx(&cfg, kern, P);
 }
 
 template <int MAXR>
 static bool cq_fits(int tpc, int csize, int threads) {
-    return tpc == 4 ? cq_cluster_fits<MAXR, 4>(csize, threads) : cq_cluster_fits<MAXR, 2>(csize, threads);
+    if constexpr (MAXR > 128) {
+        // two threads per column would hold 80 rows each and spill
+        return tpc == 4 && cq_cluster_fits<MAXR, 4>(csize, threads);
+    } else {
+        return tpc == 4 ? cq_cluster_fits<MAXR, 4>(csize, threads) : cq_cluster_fits<MAXR, 2>(csize, threads);
+    }
+}
+
+static int cq_maxr(int64_t r) { return r <= 32 ? 32 : (r <= 64 ? 64 : (r <= 128 ? 128 : 160)); }
+
+static bool cq_fits_any(int maxr, int tpc, int csize, int threads) {
+    switch (maxr) {
+        case 32: return cq_fits<32>(tpc, csize, threads);
+        case 64: return cq_fits<64>(tpc, csize, threads);
+        case 128: return cq_fits<128>(tpc, csize, threads);
+        default: return cq_fits<160>(tpc, csize, threads);
+    }
 }
 
 bool cpqr_cluster_plan(int64_t r, int64_t n, ClusterCpqrPlan* plan) {
-    if (r < 1 || r > 128 || n < 1) return false;
-    const int maxr = r <= 32 ? 32 : (r <= 64 ? 64 : 128);
+    if (r < 1 || r > kCqMaxRows || n < 1) return false;
+    const int maxr = cq_maxr(r);
     int csize = static_cast<int>(std::min<int64_t>(kCqMaxCluster, std::max<int64_t>(1, (n + 63) / 64)));
     for (; csize >= 1; csize = csize > 8 ? 8 : csize - 1) {
         const int64_t cpb = (n + csize - 1) / csize;
         int tpc = 0;
         if (cpb * 4 <= kCqMaxThreads) tpc = 4;
-        else if (cpb * 2 <= kCqMaxThreads) tpc = 2;
+        else if (cpb * 2 <= kCqMaxThreads && maxr <= 128) tpc = 2;
         else return false;
         const int threads = static_cast<int>((cpb * tpc + 31) / 32 * 32);
-        const bool fits = maxr == 32 ? cq_fits<32>(tpc, csize, threads)
-                        : maxr == 64 ? cq_fits<64>(tpc, csize, threads)
-                                     : cq_fits<128>(tpc, csize, threads);
-        if (fits) {
+        if (cq_fits_any(maxr, tpc, csize, threads)) {
             plan->csize = csize;
             plan->cpb = cpb;
             plan->threads = threads;
@@ -426,6 +510,37 @@ bool cpqr_cluster_plan(int64_t r, int64_t n, ClusterCpqrPlan* plan) {
     return false;
 }
 
+bool cpqr_cluster_shape(int64_t r, int csize, int64_t cpb, int tpc, ClusterCpqrPlan* plan) {
+    if (r < 1 || r > kCqMaxRows || csize < 1 || csize > kCqMaxCluster || cpb < 1) return false;
+    const int maxr = cq_maxr(r);
+    if (cpb * tpc > kCqMaxThreads || (tpc != 2 && tpc != 4)) return false;
+    const int threads = static_cast<int>((cpb * tpc + 31) / 32 * 32);
+    if (!cq_fits_any(maxr, tpc, csize, threads)) return false;
+    plan->csize = csize;
+    plan->cpb = cpb;
+    plan->threads = threads;
+    plan->maxr = maxr;
+    plan->tpc = tpc;
+    return true;
+}
+
+static cudaError_t launch_cq_any(const CqParams& P, const ClusterCpqrPlan& plan, int nclusters, cudaStream_t s) {
+    const int cs = plan.csize, th = plan.threads;
+    if (plan.tpc == 4) {
+        switch (plan.maxr) {
+            case 32: return launch_cq<32, 4>(P, cs, nclusters, th, s);
+            case 64: return launch_cq<64, 4>(P, cs, nclusters, th, s);
+            case 128: return launch_cq<128, 4>(P, cs, nclusters, th, s);
+            default: return launch_cq<160, 4>(P, cs, nclusters, th, s);
+        }
+    }
+    switch (plan.maxr) {
+        case 32: return launch_cq<32, 2>(P, cs, nclusters, th, s);
+        case 64: return launch_cq<64, 2>(P, cs, nclusters, th, s);
+        default: return launch_cq<128, 2>(P, cs, nclusters, th, s);
+    }
+}
+
 cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kcap, double rel_tol,
                                 int32_t* J, int32_t* k_out, int32_t* info, double* R64, int64_t ldr, uint8_t* sel,
                                 const ClusterCpqrPlan& plan, uint64_t limit_ns, cudaStream_t s) {
@@ -436,19 +551,21 @@ cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ld
     P.R = R64; P.ldr = ldr; P.sel = sel;
     P.cpb = plan.cpb;
     P.limit_ns = limit_ns;
-    const int cs = plan.csize, th = plan.threads;
-    if (plan.tpc == 4) {
-        switch (plan.maxr) {
-            case 32: return launch_cq<32, 4>(P, cs, th, s);
-            case 64: return launch_cq<64, 4>(P, cs, th, s);
-            default: return launch_cq<128, 4>(P, cs, th, s);
-        }
-    }
-    switch (plan.maxr) {
-        case 32: return launch_cq<32, 2>(P, cs, th, s);
-        case 64: return launch_cq<64, 2>(P, cs, th, s);
-        default: return launch_cq<128, 2>(P, cs, th, s);
-    }
+    return launch_cq_any(P, plan, 1, s);
+}
+
+cudaError_t launch_cpqr_cluster_batched(const BatchTask* tasks, const int32_t* order, int ntasks,
+                                        const float* partial, double* R_base, uint8_t* sel_base, int32_t* J_base,
+                                        int32_t* k_out_base, int32_t* infos, const BatchTotals& tot,
+                                        const ClusterCpqrPlan& plan, uint64_t limit_ns, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    CqParams P{};
+    P.cpb = plan.cpb;
+    P.limit_ns = limit_ns;
+    P.tasks = tasks; P.order = order; P.partial = partial; P.R_base = R_base; P.sel_base = sel_base;
+    P.J_base = J_base; P.k_out_base = k_out_base; P.infos = infos;
+    P.ntasks = tot.ntasks; P.partial_total = tot.partial; P.r_total = tot.r; P.j_total = tot.j; P.sel_total = tot.sel;
+    return launch_cq_any(P, plan, ntasks, s);
 }
 
 }  // namespace gid

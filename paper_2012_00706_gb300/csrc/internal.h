@@ -22,6 +22,10 @@ struct DeviceInfo {
 };
 const DeviceInfo& device_info();   // current device, cached
 
+// Stage-boundary events set with id_set_stage_events (this host thread): record event i.
+void record_stage(int i, cudaStream_t s);
+cudaEvent_t stage_event(int i);
+
 // Bump allocator over the caller's workspace (256-byte alignment).
 struct Carver {
     char* base;
@@ -34,6 +38,34 @@ struct Carver {
         off += count * sizeof(T);
         return p;
     }
+};
+
+// ---- batched ID: task and work-unit tables (device copies built by the batch plan)
+struct BatchTask {
+    int64_t m, n, lda;
+    int32_t kcap;          // fixed rank, or the rank cap under a tolerance
+    int32_t ell, lp;       // sketch rows and the MMA N (ell rounded up to 16)
+    int32_t kslabs;        // row slabs of the split-K sketch
+    int64_t partial_off;   // floats: sketch partial sums [kslabs][n][lp]
+    int64_t r_off;         // doubles: R rows 0..kcap-1 of every column (ldr = kcap)
+    int64_t j_off;         // int32: J (n entries)
+    int64_t t_off;         // doubles: T (ldt = kcap, tcols columns reserved)
+    int64_t tcols;
+    int64_t sel_off;       // bytes: selected-column flags (n)
+    double rel_tol;
+};
+// Element counts of the batch workspace regions and outputs (bounds the kernels check
+// every table entry against before using it).
+struct BatchTotals {
+    int64_t ntasks = 0, partial = 0, r = 0, j = 0, t = 0, sel = 0;
+};
+struct SolveUnit {
+    int32_t task, c0, ncols, pad;   // columns [c0, c0 + ncols) of T
+};
+struct SketchUnit {
+    int32_t task, tile;    // matrix and 128-column tile
+    int32_t c0, nloc;      // first 64-row chunk and chunk count
+    int32_t slab, pad;     // row slab (partial-sum slot)
 };
 
 // ---- sketch (sketch.cu)
@@ -56,6 +88,17 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
                                const SketchPlan& plan, float* partial, float* Y, int64_t ldy,
                                int32_t* info, uint64_t limit_ns, cudaStream_t s,
                                cudaEvent_t after_main = nullptr);
+// Pipeline depth and shared memory of the tensor-core sketch for MMA width lp.
+bool sketch_pipeline_plan(int lp, int a_f64, int nsplit, SketchPlan* plan);
+// Batched sketch: one CTA per unit of the table (units ordered largest first); matrix i
+// is read through maps[i] (encode_a_map), all matrices share the leading
+// ell_rows x m_rows part of Omega.
+bool encode_a_map(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, CUtensorMap* map);
+cudaError_t launch_sketch_lowp_batched(const SketchUnit* units, int64_t nunits, const BatchTask* tasks,
+                                       const CUtensorMap* maps, int a_f64, const uint16_t* omega, int64_t ldo,
+                                       int64_t m_rows, int ell_rows, int precision, const SketchPlan& plan,
+                                       float* partial, int64_t partial_total, int64_t ntasks, int32_t* infos,
+                                       uint64_t limit_ns, cudaStream_t s);
 
 struct SketchF64Plan {
     int kslabs = 0;
@@ -94,6 +137,14 @@ struct ClusterCpqrPlan {
     int tpc = 0;          // threads per column
 };
 bool cpqr_cluster_plan(int64_t r, int64_t n, ClusterCpqrPlan* plan);
+// A fixed shape (csize CTAs of cpb columns, tpc threads per column) for rows <= r.
+bool cpqr_cluster_shape(int64_t r, int csize, int64_t cpb, int tpc, ClusterCpqrPlan* plan);
+// One cluster per listed task: cluster c factors tasks[order[c]] from its sketch partial sums.
+cudaError_t launch_cpqr_cluster_batched(const BatchTask* tasks, const int32_t* order, int ntasks,
+                                        const float* partial, double* R_base, uint8_t* sel_base,
+                                        int32_t* J_base, int32_t* k_out_base, int32_t* infos,
+                                        const BatchTotals& tot, const ClusterCpqrPlan& plan,
+                                        uint64_t limit_ns, cudaStream_t s);
 cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kcap, double rel_tol,
                                 int32_t* J, int32_t* k_out, int32_t* info, double* R64, int64_t ldr, uint8_t* sel,
                                 const ClusterCpqrPlan& plan, uint64_t limit_ns, cudaStream_t s);
@@ -103,6 +154,13 @@ cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, con
                            int kcap, int64_t n, double* T, int64_t ldt, double* scratch,
                            int refine_steps, int low_solve, cudaStream_t s);
 size_t solve_T_scratch_doubles(int kcap, int64_t n);
+size_t solve_smem_bytes(int kcap, size_t ts_bytes);
+// Batched mixed-precision solve (FP32 solves, FP64 residual): one CTA of `warps` warps
+// per unit; kmax bounds the ranks of the listed tasks (<= 128).
+cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* units, int nunits, int kmax,
+                                   int warps, const double* R_base, const int32_t* J_base,
+                                   const int32_t* k_out, int32_t* infos, double* T_base,
+                                   const BatchTotals& tot, int refine_steps, cudaStream_t s);
 cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                                 const int32_t* J, const int32_t* k_ptr, const double* T,
                                 int64_t ldt, double* acc2, double* err_out, cudaStream_t s);

@@ -1,6 +1,6 @@
 // Sketch Y = Omega A on GB300.
 //
-// Mixed precision (Algorithm 2 line 1 cast + the sketching the paper names as
+// Mixed precision (Algorithm 2 cast + the sketching the paper names as
 // future work in Sec. 5): every 64-row block of every column of A is scaled by
 // a power of two chosen from the block's largest magnitude, taken at FP32
 // precision, split into 1-3 bfloat16/half pieces, and multiplied by the
@@ -170,6 +170,12 @@ struct LowpParams {
     float* partial;      // [kslabs][n][lp]
     int32_t* info;
     uint64_t limit_ns;
+    // batch mode: CTA b computes unit b of the table; matrix i is read through maps[i]
+    const SketchUnit* units;
+    const BatchTask* tasks;
+    const CUtensorMap* maps;
+    int32_t* infos;
+    int64_t ntasks, partial_total;
 };
 
 struct LowpSmem {
@@ -230,6 +236,10 @@ __device__ __forceinline__ void store_pieces(uint8_t* aop_buf, int nsplit, int f
     }
 }
 
+// BATCH = false: one ID, CTA (x, y) computes 128-column tile x over row slab y of A.
+// BATCH = true: CTA b computes unit b of the batch table (a tile and row slab of one
+// matrix), reading that matrix through its own tensor map in global memory.
+template <bool BATCH>
 __global__ void __launch_bounds__(kSketchThreads, 1)
 k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constant__ CUtensorMap tm_a,
               const __grid_constant__ CUtensorMap tm_pf, const LowpParams P) {
@@ -251,14 +261,46 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
     volatile int* abort = S.abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * kTileCols;
-    const int64_t ch_begin = static_cast<int64_t>(blockIdx.y) * P.chunks_per_slab;
-    const int64_t ch_end = min(P.nchunks, ch_begin + P.chunks_per_slab);
+    int64_t col0, ch_begin, ch_end;
+    int lp, ncols_valid;
+    float* dst_tile;                  // partial sums of column col0 (column stride lp)
+    int32_t* info;
+    const CUtensorMap* amap;
+    if constexpr (BATCH) {
+        const SketchUnit su = P.units[blockIdx.x];
+        // a unit that does not fit its matrix or the plan is reported, never executed
+        if (su.task < 0 || su.task >= P.ntasks) return;
+        const BatchTask& bt = P.tasks[su.task];
+        const int64_t nch = (bt.m + kChunkRows - 1) / kChunkRows;
+        if (su.tile < 0 || static_cast<int64_t>(su.tile) * kTileCols >= bt.n || su.c0 < 0 || su.nloc < 1 ||
+            su.c0 + su.nloc > nch || su.slab < 0 || su.slab >= bt.kslabs || bt.lp < 16 || bt.lp > P.lp ||
+            (bt.lp & 15) != 0 || bt.partial_off < 0 ||
+            bt.partial_off + static_cast<int64_t>(bt.kslabs) * bt.n * bt.lp > P.partial_total) {
+            if (threadIdx.x == 0) set_info(P.infos + su.task, kInfoBadTable);
+            return;
+        }
+        col0 = static_cast<int64_t>(su.tile) * kTileCols;
+        ch_begin = su.c0;
+        ch_end = static_cast<int64_t>(su.c0) + su.nloc;
+        lp = bt.lp;
+        ncols_valid = static_cast<int>(min(static_cast<int64_t>(kTileCols), bt.n - col0));
+        dst_tile = P.partial + bt.partial_off + (static_cast<int64_t>(su.slab) * bt.n + col0) * bt.lp;
+        info = P.infos + su.task;
+        amap = P.maps + su.task;
+    } else {
+        col0 = static_cast<int64_t>(blockIdx.x) * kTileCols;
+        ch_begin = static_cast<int64_t>(blockIdx.y) * P.chunks_per_slab;
+        ch_end = min(P.nchunks, ch_begin + P.chunks_per_slab);
+        lp = P.lp;
+        ncols_valid = static_cast<int>(min(static_cast<int64_t>(kTileCols), P.n - col0));
+        dst_tile = P.partial + (static_cast<int64_t>(blockIdx.y) * P.n + col0) * P.lp;
+        info = P.info;
+        amap = &tm_a;
+    }
     const int nloc = static_cast<int>(ch_end - ch_begin);
     const int elem = P.a_f64 ? 8 : 4;
     const int slab_rows = 128 / elem;                     // rows per 128-byte box line
     const int nslabs = kChunkRows / slab_rows;            // boxes per chunk
-    const int ncols_valid = static_cast<int>(min(static_cast<int64_t>(kTileCols), P.n - col0));
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) {
@@ -284,7 +326,14 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
     if (warp == 0) {
         // ---------------- A producer: the A boxes of each chunk (one thread issues TMA)
         if (lane == 0) {
-            if (!P.direct) prefetch_tensormap(&tm_a);
+            if constexpr (BATCH) {
+                // the map was written to global memory before the launch; order the
+                // tensor-map proxy's view of it after that write
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                 reinterpret_cast<uint64_t>(amap))
+                             : "memory");
+            }
+            if (!P.direct) prefetch_tensormap(amap);
             if (P.prefetch && !P.direct) {
                 prefetch_tensormap(&tm_pf);
                 for (int g = 0; g < kPrefetchAhead; g += kPrefetchGroup)
@@ -305,7 +354,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                     mbar_arrive_expect_tx(&stage_full[s], P.stage_bytes);
                     uint8_t* dst = S.stage + (size_t)s * P.stage_bytes;
                     for (int sl = 0; sl < nslabs; ++sl)
-                        tma_load_2d(dst + (size_t)sl * kSlabBytes, &tm_a,
+                        tma_load_2d(dst + (size_t)sl * kSlabBytes, amap,
                                     static_cast<int32_t>(c * kChunkRows + sl * slab_rows),
                                     static_cast<int32_t>(col0), &stage_full[s]);
                 }
@@ -327,7 +376,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
     } else if (warp == 1) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
-            const uint32_t idesc = umma_idesc_f16(P.f16 ? 0u : 1u, 128u, static_cast<uint32_t>(P.lp));
+            const uint32_t idesc = umma_idesc_f16(P.f16 ? 0u : 1u, 128u, static_cast<uint32_t>(lp));
             int issued = 0;
             for (int i = 0; i < nloc; ++i) {
                 const int a = i % NA, o = i % NO, b = i % NC;
@@ -402,7 +451,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 for (int r = 0; r < 16; ++r) mx = max(mx, static_cast<uint32_t>(__double2hiint(v[r])) & 0x7fffffffu);
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-                if (q == 0 && (mx >> 20) == 0x7FFu) set_info(P.info, kInfoNonFinite);
+                if (q == 0 && (mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
                 shift = shift_from_max_f64hi(mx, P.f16);
                 const uint32_t kbias = 0x40000000u - (static_cast<uint32_t>(shift) << 23);
 #pragma unroll
@@ -432,7 +481,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 for (int r = 0; r < 16; ++r) mx = max(mx, __float_as_uint(v[r]) & 0x7fffffffu);
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-                if (q == 0 && (mx >> 23) == 0xFFu) set_info(P.info, kInfoNonFinite);
+                if (q == 0 && (mx >> 23) == 0xFFu) set_info(info, kInfoNonFinite);
                 shift = shift_from_max_f32(mx, P.f16);
 #pragma unroll
                 for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f32_fast(v[r], shift, slow);
@@ -463,7 +512,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
         const int t = 32 * q + lane;
         const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
         const uint32_t run_col = static_cast<uint32_t>(NC * P.lpa);
-        const int nsl = P.lp / 16;
+        const int nsl = lp / 16;
         bool ok = true;
         for (int i = 0; i < nloc; ++i) {
             const int b = i % NC, h = i % H;
@@ -489,7 +538,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
         }
         if (ok && nloc > 0) {
             // all lanes take part in the warp-wide loads; lanes past n do not store
-            float* dst = P.partial + (static_cast<int64_t>(blockIdx.y) * P.n + col0 + t) * P.lp;
+            float* dst = dst_tile + static_cast<int64_t>(t) * lp;
             for (int sl = 0; sl < nsl; ++sl) {
                 float run[16];
                 tmem_ld16(lane_base + run_col + 16u * sl, run);
@@ -503,7 +552,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
             }
         }
     }
-    if (*abort) set_info(P.info, kInfoWatchdog);
+    if (*abort) set_info(info, kInfoWatchdog);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -537,21 +586,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode_tiled() {
     return fn;
 }
 
-bool sketch_plan_lowp(int64_t m, int64_t n, int ell, int a_f64, int nsplit, SketchPlan* plan) {
+bool sketch_pipeline_plan(int lp, int a_f64, int nsplit, SketchPlan* plan) {
     const DeviceInfo& dev = device_info();
-    SketchPlan p;
-    p.lp = (ell + 15) / 16 * 16;
-    if (p.lp > ID_MAX_ELL || ell < 1 || nsplit < 1 || nsplit > 3) return false;
-    const int lpa = (p.lp + 31) / 32 * 32;
+    if (lp < 16 || lp > ID_MAX_ELL || (lp % 16) != 0 || nsplit < 1 || nsplit > 3) return false;
+    SketchPlan p = *plan;
+    p.lp = lp;
+    const int lpa = (lp + 31) / 32 * 32;
     p.acc_bufs = (3 * lpa <= 512) ? 2 : 1;
-    p.tiles = static_cast<int>((n + kTileCols - 1) / kTileCols);
-    p.nchunks = (m + kChunkRows - 1) / kChunkRows;
-    int target = std::max(1, dev.sm_count);
-    int64_t kslabs = std::max<int64_t>(1, std::min<int64_t>(p.nchunks, target / std::max(1, p.tiles)));
-    p.chunks_per_slab = (p.nchunks + kslabs - 1) / kslabs;
-    p.kslabs = static_cast<int>((p.nchunks + p.chunks_per_slab - 1) / p.chunks_per_slab);
     const uint32_t stage_bytes = static_cast<uint32_t>(kChunkRows * kTileCols * (a_f64 ? 8 : 4));
-    const uint32_t omega_tile = (static_cast<uint32_t>(p.lp) * 128u + 1023u) & ~1023u;
+    const uint32_t omega_tile = (static_cast<uint32_t>(lp) * 128u + 1023u) & ~1023u;
     LowpParams P{};
     P.nsplit = nsplit;
     P.stage_bytes = stage_bytes;
@@ -578,6 +621,21 @@ bool sketch_plan_lowp(int64_t m, int64_t n, int ell, int a_f64, int nsplit, Sket
     fits(st, na, no);
     p.stages = st; p.aop_bufs = na; p.omega_bufs = no; p.aop_in_stage = P.aop_in_stage;
     p.smem_bytes = lowp_carve(0, P, nullptr) + 1024;
+    *plan = p;
+    return true;
+}
+
+bool sketch_plan_lowp(int64_t m, int64_t n, int ell, int a_f64, int nsplit, SketchPlan* plan) {
+    const DeviceInfo& dev = device_info();
+    if (ell < 1) return false;
+    SketchPlan p;
+    p.tiles = static_cast<int>((n + kTileCols - 1) / kTileCols);
+    p.nchunks = (m + kChunkRows - 1) / kChunkRows;
+    int target = std::max(1, dev.sm_count);
+    int64_t kslabs = std::max<int64_t>(1, std::min<int64_t>(p.nchunks, target / std::max(1, p.tiles)));
+    p.chunks_per_slab = (p.nchunks + kslabs - 1) / kslabs;
+    p.kslabs = static_cast<int>((p.nchunks + p.chunks_per_slab - 1) / p.chunks_per_slab);
+    if (!sketch_pipeline_plan((ell + 15) / 16 * 16, a_f64, nsplit, &p)) return false;
     *plan = p;
     return true;
 }
@@ -642,17 +700,76 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
     P.prefetch = prefetch ? kSketchL2Prefetch : 0;
     P.partial = partial; P.info = info; P.limit_ns = limit_ns;
 
-    cudaError_t e = cudaFuncSetAttribute(k_sketch_lowp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_lowp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(plan.smem_bytes));
     if (e != cudaSuccess) return e;
     dim3 grid(plan.tiles, plan.kslabs);
-    k_sketch_lowp<<<grid, kSketchThreads, plan.smem_bytes, s>>>(tm_om, tm_a, tm_pf, P);
+    k_sketch_lowp<false><<<grid, kSketchThreads, plan.smem_bytes, s>>>(tm_om, tm_a, tm_pf, P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (after_main) cudaEventRecord(after_main, s);
     const int64_t total = n * ell;
     k_reduce_partials_f32<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
         partial, plan.kslabs, n, plan.lp, ell, Y, ldy);
+    return cudaGetLastError();
+}
+
+bool encode_a_map(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, CUtensorMap* map) {
+    auto encode = get_encode_tiled();
+    if (!encode) return false;
+    const int elem = a_f64 ? 8 : 4;
+    if ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || ((lda * elem) & 15) != 0) return false;
+    const CUtensorMapDataType dt = a_f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(n)};
+    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(lda) * elem};
+    cuuint32_t estr[2] = {1, 1};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem), static_cast<cuuint32_t>(kTileCols)};
+    return encode(map, dt, 2, const_cast<void*>(A), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_sketch_lowp_batched(const SketchUnit* units, int64_t nunits, const BatchTask* tasks,
+                                       const CUtensorMap* maps, int a_f64, const uint16_t* omega, int64_t ldo,
+                                       int64_t m_rows, int ell_rows, int precision, const SketchPlan& plan,
+                                       float* partial, int64_t partial_total, int64_t ntasks, int32_t* infos,
+                                       uint64_t limit_ns, cudaStream_t s) {
+    auto encode = get_encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const int f16 = precision_is_f16(precision);
+    const int elem = a_f64 ? 8 : 4;
+    CUtensorMap tm_om, tm_unused;
+    memset(&tm_unused, 0, sizeof(tm_unused));
+    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(m_rows), static_cast<cuuint64_t>(ell_rows)};
+    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ldo) * 2};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunkRows), static_cast<cuuint32_t>(plan.lp)};
+    cuuint32_t estr[2] = {1, 1};
+    if (encode(&tm_om, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+               const_cast<uint16_t*>(omega), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    LowpParams P{};
+    P.a_f64 = a_f64;
+    P.nsplit = precision_nsplit(precision); P.f16 = f16;
+    P.lp = plan.lp; P.lpa = (plan.lp + 31) / 32 * 32;
+    P.stages = plan.stages; P.aop_bufs = plan.aop_bufs; P.omega_bufs = plan.omega_bufs;
+    P.acc_bufs = plan.acc_bufs;
+    P.stage_bytes = static_cast<uint32_t>(kChunkRows * kTileCols * elem);
+    P.omega_tile_bytes = (static_cast<uint32_t>(plan.lp) * 128u + 1023u) & ~1023u;
+    P.direct = 0;
+    P.aop_in_stage = plan.aop_in_stage;
+    P.prefetch = 0;
+    P.partial = partial;
+    P.limit_ns = limit_ns;
+    P.units = units; P.tasks = tasks; P.maps = maps; P.infos = infos;
+    P.ntasks = ntasks; P.partial_total = partial_total;
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_lowp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(plan.smem_bytes));
+    if (e != cudaSuccess) return e;
+    if (nunits <= 0) return cudaSuccess;
+    k_sketch_lowp<true><<<static_cast<unsigned>(nunits), kSketchThreads, plan.smem_bytes, s>>>(tm_om, tm_unused,
+                                                                                            tm_unused, P);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 // Coefficient matrix and error estimate of the column ID on GB300.
 //
-// T = R11^-1 R12 (Algorithm 1 line 4; R11 upper triangular and nonsingular, so
+// T = R11^-1 R12 (Algorithm 1, the coefficient solve; R11 upper triangular and nonsingular, so
 // the pseudo-inverse of the paper's Remark is its inverse), delivered in FP64,
 // followed by `refine_steps` steps of iterative refinement
 // T += R11^-1 (R12 - R11 T) with the residual formed in FP64.  The plain path
@@ -179,6 +179,142 @@ static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, device_info().sm_count)));
     kern<<<grid, kWarpSolveWarps * 32, smem, s>>>(R64, ldr, J, k_ptr, n, T, ldt, refine_steps);
     return cudaGetLastError();
+}
+
+// ---- batched solve: CTA b solves columns [c0, c0 + ncols) of T of task units[b].task,
+// with the warp-per-column scheme above (FP32 solves, FP64 refinement residual).
+constexpr int kBatchSolveMaxWarps = 16;
+
+template <int KQ>
+__global__ void __launch_bounds__(kBatchSolveMaxWarps * 32)
+k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restrict__ units,
+                  const double* __restrict__ R_base, const int32_t* __restrict__ J_base,
+                  const int32_t* __restrict__ k_out, int32_t* infos, double* __restrict__ T_base,
+                  BatchTotals tot, int kmax, int refine_steps) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int s_bad;
+    const SolveUnit su = units[blockIdx.x];
+    if (su.task < 0 || su.task >= tot.ntasks) return;
+    const BatchTask& bt = tasks[su.task];
+    const int k = k_out[su.task];
+    const int64_t c_end = min(min(static_cast<int64_t>(su.c0) + su.ncols, bt.n - k), bt.tcols);
+    if (k <= 0 || su.c0 < 0 || su.c0 >= c_end) return;
+    const double* R = R_base + bt.r_off;
+    const int32_t* J = J_base + bt.j_off;
+    const int ldr = bt.kcap;
+    // every index below stays inside this task's regions: check the entry and the
+    // pivot list before using them
+    if (threadIdx.x == 0)
+        s_bad = !(k <= bt.kcap && k <= kmax && bt.r_off >= 0 && bt.r_off + static_cast<int64_t>(bt.kcap) * bt.n <= tot.r &&
+                  bt.j_off >= 0 && bt.j_off + bt.n <= tot.j && bt.t_off >= 0 &&
+                  bt.t_off + static_cast<int64_t>(bt.kcap) * bt.tcols <= tot.t);
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0) set_info(infos + su.task, kInfoBadTable);
+        return;
+    }
+    for (int64_t a = threadIdx.x; a < bt.n; a += blockDim.x)
+        if (J[a] < 0 || J[a] >= bt.n) s_bad = 1;
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0) set_info(infos + su.task, kInfoBadTable);
+        return;
+    }
+    double* r11d = reinterpret_cast<double*>(sm);                       // k x k, column-major
+    float* r11s = reinterpret_cast<float*>(r11d + static_cast<int64_t>(k) * k);
+    float* rinv = r11s + static_cast<int64_t>(k) * k;
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int b = idx % k, a = idx / k;
+        const double v = (b <= a) ? R[static_cast<int64_t>(J[a]) * ldr + b] : 0.0;
+        r11d[idx] = v;
+        r11s[idx] = static_cast<float>(v);
+    }
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+        rinv[a] = 1.0f / static_cast<float>(R[static_cast<int64_t>(J[a]) * ldr + a]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double* T = T_base + bt.t_off;
+    for (int64_t c = su.c0 + (threadIdx.x >> 5); c < c_end; c += blockDim.x >> 5) {
+        const double* r12 = R + static_cast<int64_t>(J[k + c]) * ldr;
+        double rhs[KQ];
+        float t[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            rhs[q] = b < k ? r12[b] : 0.0;
+            t[q] = static_cast<float>(rhs[q]);
+        }
+        warp_backsub<float, KQ>(t, r11s, rinv, k, lane);
+        double tt[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
+        for (int it = 0; it < refine_steps; ++it) {
+            double res[KQ];
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) res[q] = rhs[q];
+            for (int a = 0; a < k; ++a) {
+                const int qa = a >> 5, owner = a & 31;
+                double ta = tt[0];
+#pragma unroll
+                for (int q = 1; q < KQ; ++q) ta = (qa == q) ? tt[q] : ta;
+                ta = __shfl_sync(0xffffffffu, ta, owner);
+                const double* col = r11d + static_cast<int64_t>(a) * k;
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) {
+                    const int b = lane + 32 * q;
+                    if (b <= a) res[q] = fma(-col[b], ta, res[q]);
+                }
+            }
+            float d[KQ];
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) d[q] = static_cast<float>(res[q]);
+            warp_backsub<float, KQ>(d, r11s, rinv, k, lane);
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) tt[q] += static_cast<double>(d[q]);
+        }
+        double* out = T + c * ldr;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            if (b < k) out[b] = tt[q];
+        }
+    }
+}
+
+size_t solve_smem_bytes(int kcap, size_t ts_bytes) {
+    return static_cast<size_t>(kcap) * kcap * (sizeof(double) + ts_bytes) + kcap * ts_bytes + 16;
+}
+
+template <int KQ>
+static cudaError_t launch_batched_solve(const BatchTask* tasks, const SolveUnit* units, int nunits, int kmax,
+                                        int warps, const double* R_base, const int32_t* J_base,
+                                        const int32_t* k_out, int32_t* infos, double* T_base,
+                                        const BatchTotals& tot, int refine_steps, cudaStream_t s) {
+    const size_t smem = solve_smem_bytes(kmax, sizeof(float));
+    auto kern = k_solve_T_batched<KQ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<nunits, warps * 32, smem, s>>>(tasks, units, R_base, J_base, k_out, infos, T_base, tot, kmax,
+                                          refine_steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* units, int nunits, int kmax, int warps,
+                                   const double* R_base, const int32_t* J_base, const int32_t* k_out,
+                                   int32_t* infos, double* T_base, const BatchTotals& tot, int refine_steps,
+                                   cudaStream_t s) {
+    if (nunits <= 0) return cudaSuccess;
+    if (kmax < 1 || kmax > 128 || warps < 1 || warps > kBatchSolveMaxWarps) return cudaErrorInvalidValue;
+    switch ((kmax + 31) / 32) {
+        case 1: return launch_batched_solve<1>(tasks, units, nunits, kmax, warps, R_base, J_base, k_out, infos,
+                                               T_base, tot, refine_steps, s);
+        case 2: return launch_batched_solve<2>(tasks, units, nunits, kmax, warps, R_base, J_base, k_out, infos,
+                                               T_base, tot, refine_steps, s);
+        case 3: return launch_batched_solve<3>(tasks, units, nunits, kmax, warps, R_base, J_base, k_out, infos,
+                                               T_base, tot, refine_steps, s);
+        default: return launch_batched_solve<4>(tasks, units, nunits, kmax, warps, R_base, J_base, k_out, infos,
+                                                T_base, tot, refine_steps, s);
+    }
 }
 
 cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,

@@ -1,0 +1,106 @@
+"""Host-side logic of the batched ID plan (no GPU needed): argument checks, output
+offsets, workspace sizing, and the unit tables the plan derives from the shapes."""
+import ctypes
+
+import pytest
+import torch
+
+import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def gid():
+    import paper_2012_00706_gb300 as g
+    g.load()
+    return g
+
+
+def plan_status(gid, m, n, k, lda=None, **opts):
+    lib = gid.load()
+    b = len(m)
+    o = lib.id_batch_opts_default()
+    for key, v in opts.items():
+        setattr(o, key, v)
+    i64a = ctypes.c_int64 * b
+    h = ctypes.c_void_p(0)
+    code = lib.id_batch_plan_create(b, 0, i64a(*m), i64a(*n), i64a(*(lda or m)), (ctypes.c_int32 * b)(*k),
+                                    ctypes.byref(o), ctypes.byref(h))
+    if h.value:
+        lib.id_batch_plan_destroy(h)
+    return code
+
+
+def test_plan_offsets_fixed_rank(gid):
+    shapes = [(300, 40), (1000, 700), (64, 64), (5000, 2048)]
+    ranks = [10, 128, 64, 1]
+    p = gid.BatchPlan(shapes, ranks, device="cpu")
+    j = [0]
+    t = [0]
+    for (m, n), k in zip(shapes, ranks):
+        j.append(j[-1] + n)
+        t.append(t[-1] + k * (n - k))
+    assert p.j_off == j
+    assert p.t_off == t
+    assert p.ell_max == 138          # 128 + 10
+    assert p.m_max == 5000
+    d = p.describe()
+    assert d["work_bytes"] == p.work_bytes > 0
+    # one unit per (128-column tile, 32-chunk row slab)
+    assert d["sketch_units"] == sum(((n + 127) // 128) * (((m + 63) // 64 + 31) // 32) for m, n in shapes)
+
+
+def test_plan_offsets_tolerance(gid):
+    shapes = [(300, 40), (100, 90)]
+    p = gid.BatchPlan(shapes, [20, 30], tol=1e-6, device="cpu")
+    assert p.t_off == [0, 20 * 39, 20 * 39 + 30 * 89]
+
+
+def test_plan_config4_shapes(gid):
+    """The 512-matrix uneven batch plans; every unit table is sized and the outputs
+    hold sum(n) pivots and sum(k (n - k)) coefficients."""
+    shapes = wl.config4_shapes(512, 4)
+    p = gid.BatchPlan([(m, n) for m, n, _ in shapes], [r for _, _, r in shapes], precision="mixed_bf16x3",
+                      device="cpu")
+    assert p.j_off[-1] == sum(n for _, n, _ in shapes)
+    assert p.t_off[-1] == sum(r * (n - r) for _, n, r in shapes)
+    d = p.describe()
+    # each (tile, 32-chunk slab) is one unit
+    assert d["sketch_units"] == sum(((n + 127) // 128) * (((m + 63) // 64 + 31) // 32) for m, n, _ in shapes)
+    assert d["solve_units"] == sum((n - r + 31) // 32 for _, n, r in shapes)
+
+
+@pytest.mark.parametrize("slab,units_of", [(16, 16), (64, 64)])
+def test_plan_slab_option(gid, slab, units_of):
+    shapes = [(4096, 1000), (300, 200)]
+    p = gid.BatchPlan(shapes, [50, 8], slab_chunks=slab, device="cpu")
+    d = p.describe()
+    assert d["slab_chunks"] == slab
+    assert d["sketch_units"] == sum(((n + 127) // 128) * (((m + 63) // 64 + units_of - 1) // units_of)
+                                    for m, n in shapes)
+
+
+def test_plan_argument_errors(gid):
+    ok = plan_status(gid, [100], [50], [5])
+    assert ok == 0
+    assert plan_status(gid, [100], [50], [0]) == 1            # k < 1
+    assert plan_status(gid, [100], [50], [51]) == 1           # k > n
+    assert plan_status(gid, [30], [50], [31]) == 1            # k > m
+    assert plan_status(gid, [100], [50], [5], lda=[99]) == 1  # lda < m
+    assert plan_status(gid, [1000], [500], [129]) == 5        # k > 128
+    assert plan_status(gid, [1000], [3000], [50]) == 5        # n > 2048
+    assert plan_status(gid, [1000], [500], [128], oversample=40) == 5   # ell > 160
+    assert plan_status(gid, [100], [50], [5], precision=0) == 1         # plain FP64 is not batched
+    assert plan_status(gid, [100], [50], [5], slab_chunks=7) == 1       # not a tuner candidate
+    assert plan_status(gid, [100], [50], [5], cpqr_tpc=3) == 1
+
+
+def test_plan_reads_tune_cache(gid, tmp_path):
+    """A cache line with this batch's key sets the unit shapes; other keys are ignored."""
+    shapes = [(500, 100), (800, 300)]
+    ranks = [10, 20]
+    base = gid.BatchPlan(shapes, ranks, device="cpu")
+    cache = tmp_path / "c.jsonl"
+    # no entry yet: defaults
+    cache.write_text('{"key": "other|sm1|f64|p2|os10|tol0|b2|0", "slab_chunks": 64}\n')
+    p = gid.BatchPlan(shapes, ranks, tune_cache=str(cache), device="cpu")
+    assert p.describe()["slab_chunks"] == base.describe()["slab_chunks"]
