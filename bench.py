@@ -212,6 +212,163 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- our arm
 
+def batched_leg(gid, wl, dev, stream):
+    """512 uneven FP64 IDs (exact rank r, sigma_i = 10^(-i/r), m in [256, 4096],
+    n in [64, 1024], k = r): the batched mixed path (default and autotuned unit
+    shapes, plain launches and a replayed CUDA graph) against one id_factor call
+    per matrix, mixed and plain FP64, with the errors of a sample of matrices."""
+    import tempfile
+    import torch
+    t_gen = time.perf_counter()
+    shapes, bufs = wl.config4_device(dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    views = [v for _, v in bufs]
+    ranks = [r for _, _, r in shapes]
+    ldas = [b.shape[1] for b, _ in bufs]
+    count = len(shapes)
+    a_bytes = sum(8 * m * n for m, n, _ in shapes)
+    flops = sum(id_flops(m, n, min(r + 10, m), r) for m, n, r in shapes)
+    m_pad = (max(m for m, _, _ in shapes) + 7) // 8 * 8
+    ell_max = max(min(r + 10, m) for m, _, r in shapes)
+    om64, bits = wl.gaussian_omega(ell_max, m_pad, 4004, "bf16")
+    omega = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
+    omega64 = torch.from_numpy(om64).to(dev)
+    out = {"workload": f"{count} FP64 matrices, m in [256,4096], n in [64,1024] (n <= m), exact rank r in "
+                       f"[8,128], sigma_i = 10^(-i/r), k = r, ell = r + 10; seed 4; drawn on the GPU",
+           "a_bytes": a_bytes, "flops_per_batch": flops, "generate_s": t_gen}
+
+    def time_calls(fn, reps, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / reps
+
+    for prec in ("mixed_bf16x3", "mixed_bf16"):
+        plan = gid.BatchPlan([(m, n) for m, n, _ in shapes], ranks, precision=prec, lda=ldas)
+        plan.bind(views)
+        ms_default = time_calls(lambda: plan.run(omega), 5)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        gid.set_stage_events(evs)
+        plan.run(omega)
+        gid.set_stage_events(None)
+        torch.cuda.synchronize()
+        stages = {"sketch": evs[0].elapsed_time(evs[1]), "cpqr": evs[2].elapsed_time(evs[3]),
+                  "solve_T": evs[3].elapsed_time(evs[4])}
+        info = plan.info.cpu()
+        with tempfile.TemporaryDirectory() as td:
+            best = plan.autotune(omega, reps=3, cache_path=os.path.join(td, "tune.jsonl"))
+        ms_tuned = time_calls(lambda: plan.run(omega), 5)
+        # one CUDA graph holding the whole launch sequence
+        gs = torch.cuda.Stream()
+        gs.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(gs):
+            plan.run(omega, stream=gs)
+            gs.synchronize()
+            with torch.cuda.graph(graph, stream=gs):
+                plan.run(omega, stream=gs)
+        torch.cuda.synchronize()
+        ms_graph = time_calls(graph.replay, 10)
+        best_ms = min(ms_tuned, ms_graph)
+        out[prec] = {"ms_default_shapes": ms_default, "ms_tuned": ms_tuned, "ms_graph_tuned": ms_graph,
+                     "tuner_ms": best, "ids_per_s": count / (best_ms / 1e3),
+                     "tflops": flops / (best_ms / 1e3) / 1e12,
+                     "hbm_gbs_whole_batch": a_bytes / (best_ms / 1e3) / 1e9,
+                     "stages_ms_default": stages, "tuned_shapes": plan.describe(),
+                     "info_nonzero": int((info != 0).sum())}
+        if prec == "mixed_bf16x3":
+            keep = plan
+        else:
+            del plan
+
+    # ---- one id_factor call per matrix (launch-per-matrix baseline), mixed and plain FP64
+    def per_matrix(precision, om):
+        ws_bytes = max(gid.id_workspace_size(m, n, torch.float64, k=r, precision=precision, sketch=True,
+                                             ell=min(r + 10, m), omega=om[: min(r + 10, m), :m])
+                       for m, n, r in shapes)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        outs = []
+        for (m, n, r) in shapes:
+            outs.append((torch.empty(n, dtype=torch.int32, device=dev),
+                         torch.empty((max(n - 1, 1), r), dtype=torch.float64, device=dev).t(),
+                         torch.zeros(2, dtype=torch.int32, device=dev),
+                         torch.zeros(1, dtype=torch.float64, device=dev)))
+
+        def loop():
+            for (m, n, r), v, o in zip(shapes, views, outs):
+                gid.id_factor(v, r, precision=precision, omega=om[: min(r + 10, m), :m], workspace=ws, out=o,
+                              sync=False)
+        ms = time_calls(loop, 1, warm=1)
+        return ms, outs
+
+    ms_loop_mixed, _ = per_matrix("mixed_bf16x3", omega)
+    ms_loop_plain, outs_plain = per_matrix("plain_f64", omega64)
+    out["per_matrix_loop"] = {"mixed_bf16x3_ms": ms_loop_mixed, "plain_f64_ms": ms_loop_plain,
+                              "plain_f64_ids_per_s": count / (ms_loop_plain / 1e3),
+                              "plain_f64_tflops": flops / (ms_loop_plain / 1e3) / 1e12}
+    best_x3 = min(out["mixed_bf16x3"]["ms_tuned"], out["mixed_bf16x3"]["ms_graph_tuned"])
+    out["speedup"] = {"batched_bf16x3_vs_plain_f64_loop": ms_loop_plain / best_x3,
+                      "batched_bf16x3_vs_mixed_loop": ms_loop_mixed / best_x3,
+                      "tuned_vs_default_bf16x3": out["mixed_bf16x3"]["ms_default_shapes"] /
+                      out["mixed_bf16x3"]["ms_tuned"]}
+
+    # ---- errors on a sample of the matrices (FP64 on the GPU, 2-norms by power iteration)
+    keep.run(omega)
+    res = keep.results()
+
+    def norm2(X, iters=50):
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        v = torch.randn(X.shape[1], dtype=torch.float64, device=dev, generator=g)
+        v /= v.norm()
+        s = 0.0
+        for _ in range(iters):
+            w = X.T @ (X @ v)
+            nw = w.norm()
+            if nw == 0:
+                return 0.0
+            s = float(nw.sqrt())
+            v = w / nw
+        return s
+
+    def ahat(A, J, T, k):
+        n = A.shape[1]
+        Jl = J.long()
+        P_ = torch.zeros((k, n), dtype=torch.float64, device=dev)
+        P_[:, Jl[:k]] = torch.eye(k, dtype=torch.float64, device=dev)
+        if k < n:
+            P_[:, Jl[k:]] = T[:k, : n - k]
+        return A[:, Jl[:k]] @ P_
+
+    sample = list(range(0, count, count // 8))[:8]
+    e_m, e_p, d_mp = [], [], []
+    for i in sample:
+        m, n, r = shapes[i]
+        A = views[i]
+        na = norm2(A)
+        Jp, Tp, sp, _ = outs_plain[i]
+        kp = int(sp[0].item())
+        hm = ahat(A, res[i].J, res[i].T, res[i].k)
+        hp = ahat(A, Jp, Tp, kp)
+        e_m.append(norm2(A - hm) / na)
+        e_p.append(norm2(A - hp) / na)
+        d_mp.append(norm2(hm - hp) / na)
+    out["accuracy_sample"] = {"matrices": sample, "e_batched_bf16x3_max": max(e_m), "e_plain_f64_max": max(e_p),
+                              "d_batched_bf16x3_vs_plain_max": max(d_mp),
+                              "matched_1e-6": max(d_mp) <= 1e-6}
+    del keep, bufs, views
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,6 +377,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="mixed_bf16")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/matched/e2e/cpu legs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -408,6 +566,10 @@ def main():
                                         "mixed_bf16x3": x3_ids / plain_ids,
                                         "matched_1e-6_form": "mixed_bf16x3" if d3 <= 1e-6 else None}
         del h_m, h_p, h_x
+
+        # ---- the uneven batch: 512 FP64 matrices in one launch sequence (graph-captured)
+        if not args.no_batched:
+            line["batched"] = batched_leg(gid, wl, dev, stream)
 
         # ---- the FP64 CPU oracle on the host (rank 0, N = 1 only)
         if rank == 0 and world == 1:

@@ -14,6 +14,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace gid {
 
@@ -104,14 +105,16 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
     extern __shared__ __align__(16) uint8_t sm[];
     const int k = *k_ptr;
     if (k <= 0) return;
+    // R11 in FP64, and a TS copy for the solves (the FP64 copy itself when TS is double)
+    constexpr bool kOneCopy = std::is_same<TS, double>::value;
     double* r11d = reinterpret_cast<double*>(sm);                       // k x k, column-major
-    TS* r11s = reinterpret_cast<TS*>(r11d + static_cast<int64_t>(k) * k);
+    TS* r11s = kOneCopy ? reinterpret_cast<TS*>(r11d) : reinterpret_cast<TS*>(r11d + static_cast<int64_t>(k) * k);
     TS* rinv = r11s + static_cast<int64_t>(k) * k;
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
         const int b = idx % k, a = idx / k;                               // row b, column a
         const double v = (b <= a) ? R[static_cast<int64_t>(J[a]) * ldr + b] : 0.0;
         r11d[idx] = v;
-        r11s[idx] = static_cast<TS>(v);
+        if (!kOneCopy) r11s[idx] = static_cast<TS>(v);
     }
     for (int a = threadIdx.x; a < k; a += blockDim.x)
         rinv[a] = static_cast<TS>(1.0) / static_cast<TS>(R[static_cast<int64_t>(J[a]) * ldr + a]);
@@ -170,7 +173,8 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
 template <typename TS, int KQ>
 static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
                                      int64_t n, double* T, int64_t ldt, int refine_steps, cudaStream_t s) {
-    const size_t smem = static_cast<size_t>(kcap) * kcap * (sizeof(double) + sizeof(TS)) + kcap * sizeof(TS) + 16;
+    const size_t copies = std::is_same<TS, double>::value ? sizeof(double) : sizeof(double) + sizeof(TS);
+    const size_t smem = static_cast<size_t>(kcap) * kcap * copies + kcap * sizeof(TS) + 16;
     auto kern = k_solve_T_warp<TS, KQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;

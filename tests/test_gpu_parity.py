@@ -256,6 +256,26 @@ def test_plain_f64_sketched_id(gid, dev, orc):
         assert np.max(np.abs(res.T.cpu().numpy() - ref["T"])) <= 1e-8 * max(1.0, np.max(np.abs(ref["T"])))
 
 
+def test_plain_f64_rank_128(gid, dev, orc):
+    """The largest rank of the warp-per-column solve (k = 128) in FP64: one FP64 copy
+    of R11 fits shared memory."""
+    m, n, k, ell = 1500, 400, 128, 138
+    a = wl.separated_matrix(m, n, seed=128, decay=0.97)
+    rng = np.random.default_rng(129)
+    om = rng.standard_normal((ell, m))
+    ref = orc.interp_decomp(a, k=k, omega=om)
+    res = gid.id_factor(torch.from_numpy(a).to(dev), k, precision="plain_f64", omega=torch.from_numpy(om).to(dev))
+    assert res.info == 0 and res.k == k
+    sep = ref["gaps"] >= 1e-8
+    first = int(np.argmax(~sep)) if np.any(~sep) else k
+    assert np.array_equal(res.J.cpu().numpy()[:first], ref["J"][:first])
+    if first == k:
+        assert np.max(np.abs(res.T.cpu().numpy() - ref["T"])) <= 1e-8 * max(1.0, np.max(np.abs(ref["T"])))
+    e = orc.rel_err(a, res.J.cpu().numpy(), res.T.cpu().numpy(), k)
+    e_d = orc.rel_err(a, ref["J"], ref["T"], k)
+    assert abs(e - e_d) <= 1e-10
+
+
 # --------------------------------------------------- cluster pivoted QR (FP32, <= 128 rows)
 
 @pytest.mark.parametrize("m,n,k", [(20, 300, 15), (50, 37, 30), (100, 700, 50), (110, 2000, 100), (128, 3000, 60)])

@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "orthonormal", "lowrank", "paper_sigma", "paper_dataset", "gaussian_omega",
     "config1", "config2", "config3", "config4", "config5", "BatchItem",
-    "separated_matrix", "to_bf16_bits", "to_f16_bits",
+    "separated_matrix", "to_bf16_bits", "to_f16_bits", "lowrank_device", "config4_device",
 ]
 
 
@@ -186,6 +186,42 @@ def config4(count: int = 512, seed: int = 4, **kw):
         sigma = 10.0 ** (-np.arange(1, r + 1) / r)
         items.append(BatchItem(m, n, r, lowrank(m, n, sigma, seed * 100003 + idx)))
     return items
+
+
+def lowrank_device(m: int, n: int, sigma, seed: int, device, lda: int | None = None):
+    """``lowrank`` drawn directly in GPU memory with torch (for the full-size batch,
+    whose 4.7 GB the host would take minutes to draw).  Same distribution, not the
+    same draws as ``lowrank``.  Returns (buffer, view): the buffer is n x lda
+    row-major, i.e. the m x n view is column-major with leading dimension lda."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    sig = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=device)
+    r = sig.numel()
+
+    def orth(rows):
+        x = torch.randn(rows, r, dtype=torch.float64, device=device, generator=g)
+        q, rr = torch.linalg.qr(x)
+        sgn = torch.sign(torch.diagonal(rr))
+        sgn[sgn == 0] = 1.0
+        return q * sgn
+    u, v = orth(m), orth(n)
+    lda = lda or m
+    buf = torch.zeros((n, lda), dtype=torch.float64, device=device)
+    buf[:, :m] = (v * sig) @ u.T
+    return buf, buf.t()[:m]
+
+
+def config4_device(device, count: int = 512, seed: int = 4, lda_multiple: int = 2, **kw):
+    """The uneven batch of ``config4`` drawn on the GPU, leading dimensions rounded up to
+    a multiple of ``lda_multiple`` (2 doubles = 16 bytes, what TMA needs)."""
+    shapes = config4_shapes(count, seed, **kw)
+    bufs = []
+    for idx, (m, n, r) in enumerate(shapes):
+        sigma = 10.0 ** (-np.arange(1, r + 1) / r)
+        lda = (m + lda_multiple - 1) // lda_multiple * lda_multiple
+        bufs.append(lowrank_device(m, n, sigma, seed * 100003 + idx, device, lda))
+    return shapes, bufs
 
 
 def config5(count: int = 64, m: int = 2048, n: int = 512, rank: int = 32, seed: int = 5):
