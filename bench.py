@@ -69,18 +69,18 @@ def measured_peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-def source_hash():
+def source_hash(files=("sketch.cu", "common.cuh")):
     h = hashlib.sha256()
-    for name in ("sketch.cu", "common.cuh"):
+    for name in files:
         with open(os.path.join(ROOT, "paper_2012_00706_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """Per-launch DRAM bytes of the sketch kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "sketch_lowp_20000x2000.md")
+def ncu_traffic(profile="sketch_lowp_20000x2000.md", files=("sketch.cu", "common.cuh")):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if the summary
+    was taken on the current kernel source (its `source_sha` line)."""
+    path = os.path.join(ROOT, "profiles", profile)
     try:
         text = open(path).read()
     except OSError:
@@ -90,12 +90,23 @@ def ncu_traffic():
         if ":" in line and line.strip().startswith("- "):
             key, _, v = line.strip()[2:].partition(":")
             vals[key.strip()] = v.strip().strip("`")
-    if vals.get("source_sha") != source_hash():
+    if vals.get("source_sha") != source_hash(files):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+# FP32 and FP64 ALU peaks derived from the unit counts and the maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz, and the FP64 rate of 1.2 TFLOP/s
+# measured on this GPU with a DFMA loop (the nominal figure is 1.25).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.2
+
+
+def cpqr_flops(r, n, k):
+    return 4.0 * r * n * k - 2.0 * k * k * (r + n) + 4.0 * k ** 3 / 3.0
 
 
 class ClockSampler:
@@ -212,7 +223,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- our arm
 
-def batched_leg(gid, wl, dev, stream):
+def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0):
     """512 uneven FP64 IDs (exact rank r, sigma_i = 10^(-i/r), m in [256, 4096],
     n in [64, 1024], k = r): the batched mixed path (default and autotuned unit
     shapes, plain launches and a replayed CUDA graph) against one id_factor call
@@ -220,7 +231,7 @@ def batched_leg(gid, wl, dev, stream):
     import tempfile
     import torch
     t_gen = time.perf_counter()
-    shapes, bufs = wl.config4_device(dev)
+    shapes, bufs = wl.config4_device(dev, count=count)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     views = [v for _, v in bufs]
@@ -251,6 +262,14 @@ def batched_leg(gid, wl, dev, stream):
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / reps
 
+    if lean_steps:
+        # profiling case: default unit shapes, plain launches only
+        plan = gid.BatchPlan([(m, n) for m, n, _ in shapes], ranks, precision="mixed_bf16x3", lda=ldas)
+        plan.bind(views)
+        ms = time_calls(lambda: plan.run(omega), lean_steps)
+        out["mixed_bf16x3"] = {"ms_default_shapes": ms, "ids_per_s": count / (ms / 1e3),
+                               "shapes": plan.describe()}
+        return out
     for prec in ("mixed_bf16x3", "mixed_bf16"):
         plan = gid.BatchPlan([(m, n) for m, n, _ in shapes], ranks, precision=prec, lda=ldas)
         plan.bind(views)
@@ -288,6 +307,9 @@ def batched_leg(gid, wl, dev, stream):
             keep = plan
         else:
             del plan
+
+    if not loops:
+        return out
 
     # ---- one id_factor call per matrix (launch-per-matrix baseline), mixed and plain FP64
     def per_matrix(precision, om):
@@ -378,6 +400,9 @@ def main():
     ap.add_argument("--precision", default="mixed_bf16")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/matched/e2e/cpu legs")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched leg")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched leg (a profiling case) and print its JSON")
+    ap.add_argument("--batch-count", type=int, default=512, help="matrices in the batched leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -402,6 +427,12 @@ def main():
             dist.barrier()
 
     gid.load()
+    if args.batched_only:
+        line = {"batched": batched_leg(gid, wl, dev, torch.cuda.current_stream(), count=args.batch_count,
+                                       loops=False, lean_steps=args.steps)}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
     cfg = wl.config2()
     a_np, bits = cfg["A"], cfg["omega_bits"]
     A = torch.from_numpy(a_np).to(dev)                       # (m, n), column-major strides
@@ -487,11 +518,22 @@ def main():
     sk_ms = stages["sketch_kernel"]
     alg_bytes = sketch_bytes(M, N, ELL)
     achieved = alg_bytes / (sk_ms / 1e3) / 1e9
-    traffic = ncu_traffic()
-    roofline = {"kernel": "k_sketch_lowp", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                "algorithmic_bytes": alg_bytes, "kernel_ms": sk_ms,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
+    sketch_roof = {"kernel": "k_sketch_lowp", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                   "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": ncu_traffic(),
+                   "algorithmic_bytes": alg_bytes, "kernel_ms": sk_ms,
+                   "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                   else peak_src}
+    cq_ms = stages["cpqr"]
+    cq_flops = cpqr_flops(ELL, N, K)
+    cq_ach = cq_flops / (cq_ms / 1e3) / 1e12
+    cpqr_roof = {"kernel": "k_cpqr_cluster", "bound": "alu", "achieved": cq_ach, "peak": FP32_PEAK_TFLOPS,
+                 "unit": "TFLOP/s", "frac": cq_ach / FP32_PEAK_TFLOPS,
+                 "traffic": ncu_traffic("cpqr_solve_110x2000.md", ("cpqr_cluster.cu", "common.cuh")),
+                 "algorithmic_flops": cq_flops, "kernel_ms": cq_ms,
+                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                 "note": "latency-bound: k sequential cluster-wide pivot steps"}
+    # the roofline object describes the stage that takes the longest
+    roofline = cpqr_roof if cq_ms >= sk_ms else sketch_roof
 
     line = {
         "metric": METRIC, "value": value, "unit": "IDs/s", "n_gpus": world, "steps": args.steps,
@@ -500,7 +542,8 @@ def main():
         "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "ell": ELL, "precision": args.precision,
                    "l2": "inputs larger than L2 (A is 320 MB vs 129 MB L2); no flush needed"},
         "tflops": id_flops(M, N, ELL, K) * value / 1e12,
-        "stages_ms": stages, "roofline": roofline, "gpu_launches": kernels_per_step * args.steps,
+        "stages_ms": stages, "roofline": roofline, "sketch_roofline": sketch_roof, "cpqr_roofline": cpqr_roof,
+        "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks,
     }
 
@@ -569,7 +612,7 @@ def main():
 
         # ---- the uneven batch: 512 FP64 matrices in one launch sequence (graph-captured)
         if not args.no_batched:
-            line["batched"] = batched_leg(gid, wl, dev, stream)
+            line["batched"] = batched_leg(gid, wl, dev, stream, count=args.batch_count)
 
         # ---- the FP64 CPU oracle on the host (rank 0, N = 1 only)
         if rank == 0 and world == 1:

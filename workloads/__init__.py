@@ -189,26 +189,21 @@ def config4(count: int = 512, seed: int = 4, **kw):
 
 
 def lowrank_device(m: int, n: int, sigma, seed: int, device, lda: int | None = None):
-    """``lowrank`` drawn directly in GPU memory with torch (for the full-size batch,
-    whose 4.7 GB the host would take minutes to draw).  Same distribution, not the
-    same draws as ``lowrank``.  Returns (buffer, view): the buffer is n x lda
-    row-major, i.e. the m x n view is column-major with leading dimension lda."""
+    """``lowrank`` with the product formed in GPU memory (for the full-size batch, whose
+    4.7 GB the host would take minutes to multiply out).  The orthonormal factors are
+    the same numpy draws as ``lowrank``'s; only the product U diag(sigma) V^T runs on
+    the device.  Returns (buffer, view): the buffer is n x lda row-major, i.e. the
+    m x n view is column-major with leading dimension lda."""
     import torch
-    g = torch.Generator(device=device)
-    g.manual_seed(int(seed))
-    sig = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=device)
-    r = sig.numel()
-
-    def orth(rows):
-        x = torch.randn(rows, r, dtype=torch.float64, device=device, generator=g)
-        q, rr = torch.linalg.qr(x)
-        sgn = torch.sign(torch.diagonal(rr))
-        sgn[sgn == 0] = 1.0
-        return q * sgn
-    u, v = orth(m), orth(n)
+    rng = np.random.default_rng(seed)
+    r = len(sigma)
+    u = orthonormal(rng, m, r)
+    v = orthonormal(rng, n, r)
+    su = torch.from_numpy(np.ascontiguousarray(u * np.asarray(sigma, dtype=np.float64)[None, :])).to(device)
+    tv = torch.from_numpy(np.ascontiguousarray(v)).to(device)
     lda = lda or m
     buf = torch.zeros((n, lda), dtype=torch.float64, device=device)
-    buf[:, :m] = (v * sig) @ u.T
+    buf[:, :m] = tv @ su.T
     return buf, buf.t()[:m]
 
 
