@@ -127,38 +127,231 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// (value, index) argmax with ties to the smaller index; -1 index marks "none".
-__device__ __forceinline__ void better(float& v, int& i, float ov, int oi) {
-    if (oi >= 0 && (i < 0 || ov > v || (ov == v && oi < i))) { v = ov; i = oi; }
+// Candidate key: larger residual norm first, ties to the smaller column index.  Norms
+// are non-negative, so their float bits order like the values; 0 means "none".
+__device__ __forceinline__ uint64_t cand_key(float nu, int64_t i) {
+    return (static_cast<uint64_t>(__float_as_uint(nu)) << 32) | static_cast<uint32_t>(0x7FFFFFFF - static_cast<int>(i));
 }
+__device__ __forceinline__ int key_index(uint64_t key) {
+    return key ? 0x7FFFFFFF - static_cast<int>(static_cast<uint32_t>(key)) : -1;
+}
+__device__ __forceinline__ float key_norm(uint64_t key) { return __uint_as_float(static_cast<uint32_t>(key >> 32)); }
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int o) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint32_t>(v), o);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint32_t>(v >> 32), o);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+// 16 bytes from registers into a peer CTA's shared memory, counted in bytes on the
+// peer's mbarrier.
+__device__ __forceinline__ void st_async_peer(uint32_t dst_cluster, float4 v, uint32_t bar_cluster) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     dst_cluster),
+                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                 "r"(__float_as_uint(v.w)), "r"(bar_cluster)
+                 : "memory");
+}
+
+// x[u] for a warp-uniform u (a uniform switch, no local memory).
+template <int RPT>
+__device__ __forceinline__ float pick_row(const float (&x)[RPT], int u) {
+    switch (u) {
+        case 0: if constexpr (RPT > 0) return x[0]; else return 0.f;
+        case 1: if constexpr (RPT > 1) return x[1]; else return 0.f;
+        case 2: if constexpr (RPT > 2) return x[2]; else return 0.f;
+        case 3: if constexpr (RPT > 3) return x[3]; else return 0.f;
+        case 4: if constexpr (RPT > 4) return x[4]; else return 0.f;
+        case 5: if constexpr (RPT > 5) return x[5]; else return 0.f;
+        case 6: if constexpr (RPT > 6) return x[6]; else return 0.f;
+        case 7: if constexpr (RPT > 7) return x[7]; else return 0.f;
+        case 8: if constexpr (RPT > 8) return x[8]; else return 0.f;
+        case 9: if constexpr (RPT > 9) return x[9]; else return 0.f;
+        case 10: if constexpr (RPT > 10) return x[10]; else return 0.f;
+        case 11: if constexpr (RPT > 11) return x[11]; else return 0.f;
+        case 12: if constexpr (RPT > 12) return x[12]; else return 0.f;
+        case 13: if constexpr (RPT > 13) return x[13]; else return 0.f;
+        case 14: if constexpr (RPT > 14) return x[14]; else return 0.f;
+        case 15: if constexpr (RPT > 15) return x[15]; else return 0.f;
+        case 16: if constexpr (RPT > 16) return x[16]; else return 0.f;
+        case 17: if constexpr (RPT > 17) return x[17]; else return 0.f;
+        case 18: if constexpr (RPT > 18) return x[18]; else return 0.f;
+        case 19: if constexpr (RPT > 19) return x[19]; else return 0.f;
+        case 20: if constexpr (RPT > 20) return x[20]; else return 0.f;
+        case 21: if constexpr (RPT > 21) return x[21]; else return 0.f;
+        case 22: if constexpr (RPT > 22) return x[22]; else return 0.f;
+        case 23: if constexpr (RPT > 23) return x[23]; else return 0.f;
+        case 24: if constexpr (RPT > 24) return x[24]; else return 0.f;
+        case 25: if constexpr (RPT > 25) return x[25]; else return 0.f;
+        case 26: if constexpr (RPT > 26) return x[26]; else return 0.f;
+        case 27: if constexpr (RPT > 27) return x[27]; else return 0.f;
+        case 28: if constexpr (RPT > 28) return x[28]; else return 0.f;
+        case 29: if constexpr (RPT > 29) return x[29]; else return 0.f;
+        case 30: if constexpr (RPT > 30) return x[30]; else return 0.f;
+        case 31: if constexpr (RPT > 31) return x[31]; else return 0.f;
+        case 32: if constexpr (RPT > 32) return x[32]; else return 0.f;
+        case 33: if constexpr (RPT > 33) return x[33]; else return 0.f;
+        case 34: if constexpr (RPT > 34) return x[34]; else return 0.f;
+        case 35: if constexpr (RPT > 35) return x[35]; else return 0.f;
+        case 36: if constexpr (RPT > 36) return x[36]; else return 0.f;
+        case 37: if constexpr (RPT > 37) return x[37]; else return 0.f;
+        case 38: if constexpr (RPT > 38) return x[38]; else return 0.f;
+        case 39: if constexpr (RPT > 39) return x[39]; else return 0.f;
+        case 40: if constexpr (RPT > 40) return x[40]; else return 0.f;
+        case 41: if constexpr (RPT > 41) return x[41]; else return 0.f;
+        case 42: if constexpr (RPT > 42) return x[42]; else return 0.f;
+        case 43: if constexpr (RPT > 43) return x[43]; else return 0.f;
+        case 44: if constexpr (RPT > 44) return x[44]; else return 0.f;
+        case 45: if constexpr (RPT > 45) return x[45]; else return 0.f;
+        case 46: if constexpr (RPT > 46) return x[46]; else return 0.f;
+        case 47: if constexpr (RPT > 47) return x[47]; else return 0.f;
+        case 48: if constexpr (RPT > 48) return x[48]; else return 0.f;
+        case 49: if constexpr (RPT > 49) return x[49]; else return 0.f;
+        case 50: if constexpr (RPT > 50) return x[50]; else return 0.f;
+        case 51: if constexpr (RPT > 51) return x[51]; else return 0.f;
+        case 52: if constexpr (RPT > 52) return x[52]; else return 0.f;
+        case 53: if constexpr (RPT > 53) return x[53]; else return 0.f;
+        case 54: if constexpr (RPT > 54) return x[54]; else return 0.f;
+        case 55: if constexpr (RPT > 55) return x[55]; else return 0.f;
+        case 56: if constexpr (RPT > 56) return x[56]; else return 0.f;
+        case 57: if constexpr (RPT > 57) return x[57]; else return 0.f;
+        case 58: if constexpr (RPT > 58) return x[58]; else return 0.f;
+        case 59: if constexpr (RPT > 59) return x[59]; else return 0.f;
+        case 60: if constexpr (RPT > 60) return x[60]; else return 0.f;
+        case 61: if constexpr (RPT > 61) return x[61]; else return 0.f;
+        case 62: if constexpr (RPT > 62) return x[62]; else return 0.f;
+        case 63: if constexpr (RPT > 63) return x[63]; else return 0.f;
+        case 64: if constexpr (RPT > 64) return x[64]; else return 0.f;
+        case 65: if constexpr (RPT > 65) return x[65]; else return 0.f;
+        case 66: if constexpr (RPT > 66) return x[66]; else return 0.f;
+        case 67: if constexpr (RPT > 67) return x[67]; else return 0.f;
+        case 68: if constexpr (RPT > 68) return x[68]; else return 0.f;
+        case 69: if constexpr (RPT > 69) return x[69]; else return 0.f;
+        case 70: if constexpr (RPT > 70) return x[70]; else return 0.f;
+        case 71: if constexpr (RPT > 71) return x[71]; else return 0.f;
+        case 72: if constexpr (RPT > 72) return x[72]; else return 0.f;
+        case 73: if constexpr (RPT > 73) return x[73]; else return 0.f;
+        case 74: if constexpr (RPT > 74) return x[74]; else return 0.f;
+        case 75: if constexpr (RPT > 75) return x[75]; else return 0.f;
+        case 76: if constexpr (RPT > 76) return x[76]; else return 0.f;
+        case 77: if constexpr (RPT > 77) return x[77]; else return 0.f;
+        case 78: if constexpr (RPT > 78) return x[78]; else return 0.f;
+        case 79: if constexpr (RPT > 79) return x[79]; else return 0.f;
+        default: return 0.f;
+    }
+}
+
+// x[u] = 0 where `own` holds (u warp-uniform).
+template <int RPT>
+__device__ __forceinline__ void zero_row(float (&x)[RPT], int u, bool own) {
+    switch (u) {
+        case 0: if constexpr (RPT > 0) x[0] = own ? 0.f : x[0]; break;
+        case 1: if constexpr (RPT > 1) x[1] = own ? 0.f : x[1]; break;
+        case 2: if constexpr (RPT > 2) x[2] = own ? 0.f : x[2]; break;
+        case 3: if constexpr (RPT > 3) x[3] = own ? 0.f : x[3]; break;
+        case 4: if constexpr (RPT > 4) x[4] = own ? 0.f : x[4]; break;
+        case 5: if constexpr (RPT > 5) x[5] = own ? 0.f : x[5]; break;
+        case 6: if constexpr (RPT > 6) x[6] = own ? 0.f : x[6]; break;
+        case 7: if constexpr (RPT > 7) x[7] = own ? 0.f : x[7]; break;
+        case 8: if constexpr (RPT > 8) x[8] = own ? 0.f : x[8]; break;
+        case 9: if constexpr (RPT > 9) x[9] = own ? 0.f : x[9]; break;
+        case 10: if constexpr (RPT > 10) x[10] = own ? 0.f : x[10]; break;
+        case 11: if constexpr (RPT > 11) x[11] = own ? 0.f : x[11]; break;
+        case 12: if constexpr (RPT > 12) x[12] = own ? 0.f : x[12]; break;
+        case 13: if constexpr (RPT > 13) x[13] = own ? 0.f : x[13]; break;
+        case 14: if constexpr (RPT > 14) x[14] = own ? 0.f : x[14]; break;
+        case 15: if constexpr (RPT > 15) x[15] = own ? 0.f : x[15]; break;
+        case 16: if constexpr (RPT > 16) x[16] = own ? 0.f : x[16]; break;
+        case 17: if constexpr (RPT > 17) x[17] = own ? 0.f : x[17]; break;
+        case 18: if constexpr (RPT > 18) x[18] = own ? 0.f : x[18]; break;
+        case 19: if constexpr (RPT > 19) x[19] = own ? 0.f : x[19]; break;
+        case 20: if constexpr (RPT > 20) x[20] = own ? 0.f : x[20]; break;
+        case 21: if constexpr (RPT > 21) x[21] = own ? 0.f : x[21]; break;
+        case 22: if constexpr (RPT > 22) x[22] = own ? 0.f : x[22]; break;
+        case 23: if constexpr (RPT > 23) x[23] = own ? 0.f : x[23]; break;
+        case 24: if constexpr (RPT > 24) x[24] = own ? 0.f : x[24]; break;
+        case 25: if constexpr (RPT > 25) x[25] = own ? 0.f : x[25]; break;
+        case 26: if constexpr (RPT > 26) x[26] = own ? 0.f : x[26]; break;
+        case 27: if constexpr (RPT > 27) x[27] = own ? 0.f : x[27]; break;
+        case 28: if constexpr (RPT > 28) x[28] = own ? 0.f : x[28]; break;
+        case 29: if constexpr (RPT > 29) x[29] = own ? 0.f : x[29]; break;
+        case 30: if constexpr (RPT > 30) x[30] = own ? 0.f : x[30]; break;
+        case 31: if constexpr (RPT > 31) x[31] = own ? 0.f : x[31]; break;
+        case 32: if constexpr (RPT > 32) x[32] = own ? 0.f : x[32]; break;
+        case 33: if constexpr (RPT > 33) x[33] = own ? 0.f : x[33]; break;
+        case 34: if constexpr (RPT > 34) x[34] = own ? 0.f : x[34]; break;
+        case 35: if constexpr (RPT > 35) x[35] = own ? 0.f : x[35]; break;
+        case 36: if constexpr (RPT > 36) x[36] = own ? 0.f : x[36]; break;
+        case 37: if constexpr (RPT > 37) x[37] = own ? 0.f : x[37]; break;
+        case 38: if constexpr (RPT > 38) x[38] = own ? 0.f : x[38]; break;
+        case 39: if constexpr (RPT > 39) x[39] = own ? 0.f : x[39]; break;
+        case 40: if constexpr (RPT > 40) x[40] = own ? 0.f : x[40]; break;
+        case 41: if constexpr (RPT > 41) x[41] = own ? 0.f : x[41]; break;
+        case 42: if constexpr (RPT > 42) x[42] = own ? 0.f : x[42]; break;
+        case 43: if constexpr (RPT > 43) x[43] = own ? 0.f : x[43]; break;
+        case 44: if constexpr (RPT > 44) x[44] = own ? 0.f : x[44]; break;
+        case 45: if constexpr (RPT > 45) x[45] = own ? 0.f : x[45]; break;
+        case 46: if constexpr (RPT > 46) x[46] = own ? 0.f : x[46]; break;
+        case 47: if constexpr (RPT > 47) x[47] = own ? 0.f : x[47]; break;
+        case 48: if constexpr (RPT > 48) x[48] = own ? 0.f : x[48]; break;
+        case 49: if constexpr (RPT > 49) x[49] = own ? 0.f : x[49]; break;
+        case 50: if constexpr (RPT > 50) x[50] = own ? 0.f : x[50]; break;
+        case 51: if constexpr (RPT > 51) x[51] = own ? 0.f : x[51]; break;
+        case 52: if constexpr (RPT > 52) x[52] = own ? 0.f : x[52]; break;
+        case 53: if constexpr (RPT > 53) x[53] = own ? 0.f : x[53]; break;
+        case 54: if constexpr (RPT > 54) x[54] = own ? 0.f : x[54]; break;
+        case 55: if constexpr (RPT > 55) x[55] = own ? 0.f : x[55]; break;
+        case 56: if constexpr (RPT > 56) x[56] = own ? 0.f : x[56]; break;
+        case 57: if constexpr (RPT > 57) x[57] = own ? 0.f : x[57]; break;
+        case 58: if constexpr (RPT > 58) x[58] = own ? 0.f : x[58]; break;
+        case 59: if constexpr (RPT > 59) x[59] = own ? 0.f : x[59]; break;
+        case 60: if constexpr (RPT > 60) x[60] = own ? 0.f : x[60]; break;
+        case 61: if constexpr (RPT > 61) x[61] = own ? 0.f : x[61]; break;
+        case 62: if constexpr (RPT > 62) x[62] = own ? 0.f : x[62]; break;
+        case 63: if constexpr (RPT > 63) x[63] = own ? 0.f : x[63]; break;
+        case 64: if constexpr (RPT > 64) x[64] = own ? 0.f : x[64]; break;
+        case 65: if constexpr (RPT > 65) x[65] = own ? 0.f : x[65]; break;
+        case 66: if constexpr (RPT > 66) x[66] = own ? 0.f : x[66]; break;
+        case 67: if constexpr (RPT > 67) x[67] = own ? 0.f : x[67]; break;
+        case 68: if constexpr (RPT > 68) x[68] = own ? 0.f : x[68]; break;
+        case 69: if constexpr (RPT > 69) x[69] = own ? 0.f : x[69]; break;
+        case 70: if constexpr (RPT > 70) x[70] = own ? 0.f : x[70]; break;
+        case 71: if constexpr (RPT > 71) x[71] = own ? 0.f : x[71]; break;
+        case 72: if constexpr (RPT > 72) x[72] = own ? 0.f : x[72]; break;
+        case 73: if constexpr (RPT > 73) x[73] = own ? 0.f : x[73]; break;
+        case 74: if constexpr (RPT > 74) x[74] = own ? 0.f : x[74]; break;
+        case 75: if constexpr (RPT > 75) x[75] = own ? 0.f : x[75]; break;
+        case 76: if constexpr (RPT > 76) x[76] = own ? 0.f : x[76]; break;
+        case 77: if constexpr (RPT > 77) x[77] = own ? 0.f : x[77]; break;
+        case 78: if constexpr (RPT > 78) x[78] = own ? 0.f : x[78]; break;
+        case 79: if constexpr (RPT > 79) x[79] = own ? 0.f : x[79]; break;
+        default: break;
+    }
+}
+
+// Shared-memory index of row r of a column record, padded by 16 bytes every 32 rows
+// so that the TPC row blocks of a column read from different banks.
+__device__ __forceinline__ int vidx(int r) { return r + ((r >> 5) << 2); }
 
 template <int MAXR>
 struct CqRecord {
-    float4 head;          // (best norm, index bits, sum of norms, unused)
-    float col[MAXR];
+    float4 head;                       // (residual norm, index bits, sum of norms, exact ||x||^2)
+    float col[MAXR + MAXR / 8];        // the candidate column, padded rows (vidx)
 };
-
-// Shared-memory index of row r of a per-step vector, padded by 16 bytes every 32
-// rows so that the TPC row blocks of a column read from different banks.
-__device__ __forceinline__ int vidx(int r) { return r + ((r >> 5) << 2); }
 
 template <int MAXR, int TPC>
 __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParams P) {
     constexpr int RPT = MAXR / TPC;
-    constexpr int VLEN = MAXR + MAXR / 8;          // padded vector length
     constexpr int MAXW = kCqMaxThreads / 32;
     constexpr uint32_t REC = sizeof(CqRecord<MAXR>);
+    constexpr int NCH = REC / 16;                       // 16-byte chunks of a record
     static_assert(REC % 16 == 0, "record size");
-    static_assert(RPT % 4 == 0, "rows per thread");
+    static_assert(RPT % 4 == 0 && RPT <= 80, "rows per thread");
     __shared__ __align__(128) CqRecord<MAXR> recv[2][kCqMaxCluster];
     __shared__ __align__(128) CqRecord<MAXR> wstg[2][MAXW];   // per-warp staged candidate
-    __shared__ __align__(16) float vp[VLEN];     // v' : 0 above row j, alpha - beta at j, pivot column below
-    __shared__ __align__(16) float ej[VLEN];     // unit vector e_j
-    __shared__ float wv[MAXW];
-    __shared__ int wi[MAXW];
+    __shared__ uint64_t wkey[MAXW];
     __shared__ float wsum[MAXW];
-    __shared__ float s_sc[4];                    // tau, inv, beta, sum of norms
-    __shared__ int s_piv[2];                     // pivot column, stop flag
+    __shared__ float wnorm[MAXW];
     __shared__ __align__(8) uint64_t recv_bar[2];
 
     const uint32_t me = cluster_rank(), C = cluster_nrank();
@@ -171,11 +364,14 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     }
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     const int cl = t / TPC, qq = t % TPC;
+    const int gbase = lane & ~(TPC - 1);     // first lane of this column's thread group
+    const unsigned gmask = ((1u << TPC) - 1u) << gbase;
     const int64_t i = static_cast<int64_t>(me) * P.cpb + cl;
     const bool valid = cl < P.cpb && i < W.n;
     const int r = static_cast<int>(W.r);
     const int rb = qq * RPT;                 // first row of this thread's block
     const float sqrt_u = 2.44140625e-04f;    // sqrt of the FP32 unit round-off 2^-24
+    const bool need_sum = W.rel_tol > 0.0;
 
     if (t == 0) {
         mbar_init(&recv_bar[0], 1);
@@ -184,6 +380,8 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     }
     cluster_sync_all();
 
+    // x: this thread's rows of its column.  Rows of earlier pivot steps are set to zero
+    // once their R entry is out, so dot products and norms need no row masks.
     float x[RPT];
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
@@ -204,55 +402,56 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
         W.sel[i] = 0;
     }
 
-    // Exchange q: each warp stages its best candidate column, warp 0 picks the CTA's best
-    // and bulk-copies that record to every peer.  Exchange q fills recv[q & 1] and
-    // completes phase q >> 1 of recv_bar[q & 1]; a peer can be at most one exchange ahead,
-    // so two alternating buffers and barriers never mix phases, and a staging slot is
-    // reused (two exchanges later) only after its copies have landed.
+    // Exchange q: each warp finds its best candidate, whose threads stage the column and
+    // its exact squared norm; after one CTA barrier every warp finds the CTA's best, and
+    // warp w writes that record into peers w, w + nw, ... with st.async, completing on
+    // the peer's mbarrier in bytes.  Exchange q fills recv[q & 1] and completes phase
+    // q >> 1 of recv_bar[q & 1]; a peer can be at most one exchange ahead, so two
+    // alternating buffers and barriers never mix phases.
     auto exchange = [&](int q) {
         const int slot = q & 1;
-        float bv = -1.f, part = 0.f;
-        int bi = -1;
-        if (!selected && qq == 0) { bv = nu; bi = static_cast<int>(i); part = nu; }
+        uint64_t key = (!selected && qq == 0) ? cand_key(nu, i) : 0ull;
+        float part = (!selected && qq == 0) ? nu : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            better(bv, bi, ov, oi);
-            part += __shfl_xor_sync(0xffffffffu, part, o);
+            const uint64_t ok2 = shfl_xor_u64(key, o);
+            key = ok2 > key ? ok2 : key;
         }
-        if (valid && i == bi) {
+        if (need_sum || q == 0) part = warp_sum(part);
+        if (key != 0ull && i == key_index(key)) {
+            // the TPC threads of the warp's candidate column
+            float s = 0.f;
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) s = fmaf(x[u], x[u], s);
+#pragma unroll
+            for (int o = 1; o < TPC; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
 #pragma unroll
             for (int u = 0; u < RPT; u += 4)
-                *reinterpret_cast<float4*>(&wstg[slot][warp].col[rb + u]) = make_float4(x[u], x[u + 1], x[u + 2], x[u + 3]);
+                *reinterpret_cast<float4*>(&wstg[slot][warp].col[vidx(rb + u)]) =
+                    make_float4(x[u], x[u + 1], x[u + 2], x[u + 3]);
+            if (qq == 0) wnorm[warp] = s;
         }
-        if (lane == 0) { wv[warp] = bv; wi[warp] = bi; wsum[warp] = part; }
-        fence_proxy_async_smem();
+        if (lane == 0) { wkey[warp] = key; wsum[warp] = part; }
         __syncthreads();
-        if (warp == 0) {
-            float v0 = lane < nw ? wv[lane] : -1.f;
-            int i0 = lane < nw ? wi[lane] : -1;
-            int w0 = lane;
-            float s0 = lane < nw ? wsum[lane] : 0.f;
+        uint64_t ck = lane < nw ? wkey[lane] : 0ull;
+        float cs = lane < nw ? wsum[lane] : 0.f;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, v0, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, i0, o);
-                const int ow = __shfl_xor_sync(0xffffffffu, w0, o);
-                if (oi >= 0 && (i0 < 0 || ov > v0 || (ov == v0 && oi < i0))) { v0 = ov; i0 = oi; w0 = ow; }
-                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            }
-            const int wsrc = i0 >= 0 ? w0 : 0;
-            if (lane == 0) {
-                mbar_arrive_expect_tx(&recv_bar[slot], C * REC);
-                wstg[slot][wsrc].head = make_float4(v0, __int_as_float(i0), s0, 0.f);
-                fence_proxy_async_smem();
-            }
-            __syncwarp();
-            if (lane < static_cast<int>(C)) {
-                const uint32_t d = static_cast<uint32_t>(lane);
-                bulk_s2peer(map_peer(smem_addr(&recv[slot][me]), d), smem_addr(&wstg[slot][wsrc]), REC,
-                            map_peer(smem_addr(&recv_bar[slot]), d));
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t ok2 = shfl_xor_u64(ck, o);
+            ck = ok2 > ck ? ok2 : ck;
+        }
+        if (need_sum || q == 0) cs = warp_sum(cs);
+        const unsigned hit = __ballot_sync(0xffffffffu, lane < nw && wkey[lane] == ck && ck != 0ull);
+        const int wsrc = hit ? __ffs(hit) - 1 : 0;
+        if (t == 0) mbar_arrive_expect_tx(&recv_bar[slot], C * REC);
+        const float4 head = make_float4(key_norm(ck), __int_as_float(key_index(ck)), cs, wnorm[wsrc]);
+        const float* src = wstg[slot][wsrc].col;
+        for (uint32_t d = warp; d < C; d += nw) {
+            const uint32_t dst = map_peer(smem_addr(&recv[slot][me]), d);
+            const uint32_t bar = map_peer(smem_addr(&recv_bar[slot]), d);
+            for (int c = lane; c < NCH; c += 32) {
+                const float4 v = c == 0 ? head : *reinterpret_cast<const float4*>(src + 4 * (c - 1));
+                st_async_peer(dst + 16u * c, v, bar);
             }
         }
     };
@@ -267,96 +466,75 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     float total = -1.f;
     for (int j = 0; ok && j < W.kcap; ++j) {
         const int par = j & 1;
-        // ---- warp 0: the pivot (same reduction order in every CTA), reflector scalars,
-        // and the step vectors v' and e_j
-        if (warp == 0) {
-            float hv = -1.f, hs = 0.f;
-            int hi = -1, hsrc = lane;
-            if (lane < static_cast<int>(C)) {
-                const float4 h = recv[par][lane].head;
-                hv = h.x;
-                hi = __float_as_int(h.y);
-                hs = h.z;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, hv, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, hi, o);
-                const int os = __shfl_xor_sync(0xffffffffu, hsrc, o);
-                if (oi >= 0 && (hi < 0 || ov > hv || (ov == hv && oi < hi))) { hv = ov; hi = oi; hsrc = os; }
-                hs += __shfl_xor_sync(0xffffffffu, hs, o);
-            }
-            if (total < 0.f) total = hs;
-            int stop = 0;
-            if (W.rel_tol > 0.0 && sqrtf(fmaxf(hs, 0.f)) <= static_cast<float>(W.rel_tol) * sqrtf(total)) stop = 1;
-            if (!stop && (hi < 0 || !(hv > 0.f))) {
-                stop = 2;
-                if (me == 0 && lane == 0) set_info(W.info, j + 1);
-            }
-            if (!stop) {
-                const float* xw = recv[par][hsrc].col;
-                float s2 = 0.f;
-                for (int q = j + lane; q < r; q += 32) s2 = fmaf(xw[q], xw[q], s2);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                const float alpha = xw[j];
-                const float snorm = sqrtf(s2);
-                const float beta = alpha >= 0.f ? -snorm : snorm;
-                const float amb = alpha - beta;
-                for (int q = lane; q < MAXR; q += 32) {
-                    vp[vidx(q)] = q < j ? 0.f : (q == j ? amb : xw[q]);
-                    ej[vidx(q)] = q == j ? 1.f : 0.f;
-                }
-                if (lane == 0) {
-                    s_sc[0] = (beta - alpha) / beta;   // tau
-                    s_sc[1] = 1.f / amb;               // inv
-                    s_sc[2] = beta;
-                }
-            }
-            if (lane == 0) { s_piv[0] = hi; s_piv[1] = stop; }
+        // ---- the pivot: every warp reduces the C records in the same order
+        uint64_t hk = lane < static_cast<int>(C) ? cand_key(recv[par][lane].head.x, 0) : 0ull;
+        float hs = 0.f;
+        if (lane < static_cast<int>(C)) {
+            const float4 h = recv[par][lane].head;
+            const int hi = __float_as_int(h.y);
+            hk = hi >= 0 ? cand_key(h.x, hi) : 0ull;
+            hs = h.z;
         }
-        __syncthreads();
-        if (s_piv[1]) break;
-        const int p = s_piv[0];
-        const float tau = s_sc[0], inv = s_sc[1];
+        uint64_t best = hk;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t ok2 = shfl_xor_u64(best, o);
+            best = ok2 > best ? ok2 : best;
+        }
+        if (need_sum || j == 0) hs = warp_sum(hs);
+        const unsigned hit = __ballot_sync(0xffffffffu, lane < static_cast<int>(C) && hk == best && best != 0ull);
+        const int hsrc = hit ? __ffs(hit) - 1 : 0;
+        const int p = key_index(best);
+        const float hv = best ? key_norm(best) : -1.f;
+        if (total < 0.f) total = hs;
+        if (need_sum && sqrtf(fmaxf(hs, 0.f)) <= static_cast<float>(W.rel_tol) * sqrtf(total)) break;
+        if (p < 0 || !(hv > 0.f)) {
+            if (me == 0 && t == 0) set_info(W.info, j + 1);
+            break;
+        }
+        const float* pc = recv[par][hsrc].col;
+        const float s2 = recv[par][hsrc].head.w;
+        const float alpha = pc[vidx(j)];
+        const float snorm = sqrtf(s2);
+        const float beta = alpha >= 0.f ? -snorm : snorm;
+        const float amb = alpha - beta;
+        const float tau = (beta - alpha) / beta;
+        const float inv = 1.f / amb;
         if (valid && i == p) {
             selected = true;
             if (qq == 0) {
-                W.R[i * W.ldr + j] = static_cast<double>(s_sc[2]);
+                W.R[i * W.ldr + j] = static_cast<double>(beta);
                 W.J[j] = p;
                 W.sel[i] = 1;
             }
         }
-        // S = v'.x (= (alpha - beta) w),  X = e_j.x (= x_j): plain FMAs over this thread's rows
-        float S0 = 0.f, S1 = 0.f, X = 0.f;
+        // S = v'.x with v' = (0 above j, alpha - beta at j, pivot column below):
+        // pc.x - beta x_j, rows above j being zero in both
+        float S0 = 0.f, S1 = 0.f;
 #pragma unroll
         for (int u = 0; u < RPT; u += 4) {
-            const float4 v4 = *reinterpret_cast<const float4*>(&vp[vidx(rb + u)]);
-            const float4 e4 = *reinterpret_cast<const float4*>(&ej[vidx(rb + u)]);
+            const float4 v4 = *reinterpret_cast<const float4*>(&pc[vidx(rb + u)]);
             S0 = fmaf(v4.x, x[u], S0);
             S1 = fmaf(v4.y, x[u + 1], S1);
             S0 = fmaf(v4.z, x[u + 2], S0);
             S1 = fmaf(v4.w, x[u + 3], S1);
-            X = fmaf(e4.x, x[u], X);
-            X = fmaf(e4.y, x[u + 1], X);
-            X = fmaf(e4.z, x[u + 2], X);
-            X = fmaf(e4.w, x[u + 3], X);
         }
         float S = S0 + S1;
 #pragma unroll
-        for (int o = 1; o < TPC; o <<= 1) {
-            S += __shfl_xor_sync(0xffffffffu, S, o);
-            X += __shfl_xor_sync(0xffffffffu, X, o);
-        }
+        for (int o = 1; o < TPC; o <<= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+        // X = x_j, held by thread qj of the group at register uj
+        const int qj = j / RPT, uj = j - qj * RPT;
+        const float X = __shfl_sync(0xffffffffu, pick_row<RPT>(x, uj), gbase + qj);
+        S = fmaf(-beta, X, S);
         const float tw = tau * (inv * S);
         const float sv = tw * inv;
         const float rho = X - tw;
         bool recompute = false;
         if (!selected) {
-            // x -= (tau w / (alpha - beta)) v': rows above j unchanged, row j becomes rho
+            // x -= (tau w / (alpha - beta)) v'; row j leaves as rho and is then zeroed
 #pragma unroll
             for (int u = 0; u < RPT; u += 4) {
-                const float4 v4 = *reinterpret_cast<const float4*>(&vp[vidx(rb + u)]);
+                const float4 v4 = *reinterpret_cast<const float4*>(&pc[vidx(rb + u)]);
                 x[u] = fmaf(-sv, v4.x, x[u]);
                 x[u + 1] = fmaf(-sv, v4.y, x[u + 1]);
                 x[u + 2] = fmaf(-sv, v4.z, x[u + 2]);
@@ -369,10 +547,11 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
                 else nu = nu * t1;
             }
         }
+        zero_row<RPT>(x, uj, qq == qj);
         if (__any_sync(0xffffffffu, recompute)) {
             float sq = 0.f;
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) sq = (rb + u > j) ? fmaf(x[u], x[u], sq) : sq;
+            for (int u = 0; u < RPT; ++u) sq = fmaf(x[u], x[u], sq);
 #pragma unroll
             for (int o = 1; o < TPC; o <<= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (recompute) {
@@ -385,7 +564,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
         k = j + 1;
     }
     if (!ok && t == 0) set_info(W.info, kInfoWatchdog);
-    // no CTA leaves while a peer may still copy into its shared memory
+    // no CTA leaves while a peer may still write into its shared memory
     cluster_sync_all();
     if (me == 0) {
         if (t == 0) *W.k_out = k;
