@@ -97,6 +97,54 @@ __device__ __forceinline__ void warp_backsub(TS (&t)[KQ], const TS* __restrict__
     }
 }
 
+// Refinement residual R12 - R11 T of the mixed path on the FP32 pipe.  R11, R12 and
+// the first solve are FP32 values, so every product R(b,a) t_a splits exactly into
+// two floats (p = fl(R t), e = fma(R, t, -p)); the sums are kept as unevaluated float
+// pairs (TwoSum), which carries about 48 significant bits, well beyond the FP32
+// round-off the refinement corrects.  t is passed as a float pair (hi, lo); lo is zero
+// in the first refinement step.  Lane b accumulates rows b, b + 32, ... over a >= b.
+template <int KQ>
+__device__ __forceinline__ void residual_pairs(const double (&rhs)[KQ], const float (&th)[KQ], const float (&tl)[KQ],
+                                               bool use_lo, const float* __restrict__ r11s, int k, int lane,
+                                               double (&res)[KQ]) {
+    float sh[KQ], sl[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        sh[q] = static_cast<float>(rhs[q]);
+        sl[q] = 0.f;
+    }
+    for (int a = 0; a < k; ++a) {
+        const int qa = a >> 5, owner = a & 31;
+        float ah = th[0], al = tl[0];
+#pragma unroll
+        for (int q = 1; q < KQ; ++q) {
+            ah = (qa == q) ? th[q] : ah;
+            al = (qa == q) ? tl[q] : al;
+        }
+        ah = __shfl_sync(0xffffffffu, ah, owner);
+        if (use_lo) al = __shfl_sync(0xffffffffu, al, owner);
+        const float* col = r11s + static_cast<int64_t>(a) * k;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            if (b <= a) {
+                // explicit round-to-nearest operations: no contraction into FMAs
+                const float rv = -col[b];
+                const float p = __fmul_rn(rv, ah);
+                const float e = fmaf(rv, ah, -p);
+                const float s = __fadd_rn(sh[q], p);             // TwoSum(sh, p)
+                const float bp = __fsub_rn(s, sh[q]);
+                const float err = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(s, bp)), __fsub_rn(p, bp));
+                sh[q] = s;
+                sl[q] = __fadd_rn(sl[q], __fadd_rn(err, e));
+                if (use_lo) sl[q] = fmaf(rv, al, sl[q]);       // R t_lo is below the pair's resolution
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) res[q] = static_cast<double>(sh[q]) + static_cast<double>(sl[q]);
+}
+
 template <typename TS, int KQ>
 __global__ void __launch_bounds__(kWarpSolveWarps * 32)
 k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
@@ -105,16 +153,15 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
     extern __shared__ __align__(16) uint8_t sm[];
     const int k = *k_ptr;
     if (k <= 0) return;
-    // R11 in FP64, and a TS copy for the solves (the FP64 copy itself when TS is double)
-    constexpr bool kOneCopy = std::is_same<TS, double>::value;
-    double* r11d = reinterpret_cast<double*>(sm);                       // k x k, column-major
-    TS* r11s = kOneCopy ? reinterpret_cast<TS*>(r11d) : reinterpret_cast<TS*>(r11d + static_cast<int64_t>(k) * k);
+    // R11 (k x k, column-major) in the solve precision TS: FP64 for the plain path; FP32
+    // for the mixed path, whose R is FP32 (its refinement residual works on float pairs)
+    double* r11d = reinterpret_cast<double*>(sm);
+    TS* r11s = reinterpret_cast<TS*>(sm);
     TS* rinv = r11s + static_cast<int64_t>(k) * k;
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
         const int b = idx % k, a = idx / k;                               // row b, column a
         const double v = (b <= a) ? R[static_cast<int64_t>(J[a]) * ldr + b] : 0.0;
-        r11d[idx] = v;
-        if (!kOneCopy) r11s[idx] = static_cast<TS>(v);
+        r11s[idx] = static_cast<TS>(v);
     }
     for (int a = threadIdx.x; a < k; a += blockDim.x)
         rinv[a] = static_cast<TS>(1.0) / static_cast<TS>(R[static_cast<int64_t>(J[a]) * ldr + a]);
@@ -137,21 +184,32 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
 #pragma unroll
         for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
         for (int it = 0; it < refine_steps; ++it) {
-            // residual R12 - R11 T in FP64 (row-oriented: lane b sums over a >= b)
             double res[KQ];
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) res[q] = rhs[q];
-            for (int a = 0; a < k; ++a) {
-                const int qa = a >> 5, owner = a & 31;
-                double ta = tt[0];
-#pragma unroll
-                for (int q = 1; q < KQ; ++q) ta = (qa == q) ? tt[q] : ta;
-                ta = __shfl_sync(0xffffffffu, ta, owner);
-                const double* col = r11d + static_cast<int64_t>(a) * k;
+            if constexpr (std::is_same<TS, float>::value) {
+                // R is FP32 (mixed path): exact products, float-pair sums
+                float th[KQ], tl[KQ];
 #pragma unroll
                 for (int q = 0; q < KQ; ++q) {
-                    const int b = lane + 32 * q;
-                    if (b <= a) res[q] = fma(-col[b], ta, res[q]);
+                    th[q] = static_cast<float>(tt[q]);
+                    tl[q] = static_cast<float>(tt[q] - static_cast<double>(th[q]));
+                }
+                residual_pairs<KQ>(rhs, th, tl, it > 0, r11s, k, lane, res);
+            } else {
+                // residual R12 - R11 T in FP64 (row-oriented: lane b sums over a >= b)
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) res[q] = rhs[q];
+                for (int a = 0; a < k; ++a) {
+                    const int qa = a >> 5, owner = a & 31;
+                    double ta = tt[0];
+#pragma unroll
+                    for (int q = 1; q < KQ; ++q) ta = (qa == q) ? tt[q] : ta;
+                    ta = __shfl_sync(0xffffffffu, ta, owner);
+                    const double* col = r11d + static_cast<int64_t>(a) * k;
+#pragma unroll
+                    for (int q = 0; q < KQ; ++q) {
+                        const int b = lane + 32 * q;
+                        if (b <= a) res[q] = fma(-col[b], ta, res[q]);
+                    }
                 }
             }
             TS d[KQ];
@@ -173,8 +231,7 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
 template <typename TS, int KQ>
 static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
                                      int64_t n, double* T, int64_t ldt, int refine_steps, cudaStream_t s) {
-    const size_t copies = std::is_same<TS, double>::value ? sizeof(double) : sizeof(double) + sizeof(TS);
-    const size_t smem = static_cast<size_t>(kcap) * kcap * copies + kcap * sizeof(TS) + 16;
+    const size_t smem = static_cast<size_t>(kcap) * kcap * sizeof(TS) + kcap * sizeof(TS) + 16;
     auto kern = k_solve_T_warp<TS, KQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -224,14 +281,11 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
         if (threadIdx.x == 0) set_info(infos + su.task, kInfoBadTable);
         return;
     }
-    double* r11d = reinterpret_cast<double*>(sm);                       // k x k, column-major
-    float* r11s = reinterpret_cast<float*>(r11d + static_cast<int64_t>(k) * k);
+    float* r11s = reinterpret_cast<float*>(sm);                         // k x k, column-major
     float* rinv = r11s + static_cast<int64_t>(k) * k;
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
         const int b = idx % k, a = idx / k;
-        const double v = (b <= a) ? R[static_cast<int64_t>(J[a]) * ldr + b] : 0.0;
-        r11d[idx] = v;
-        r11s[idx] = static_cast<float>(v);
+        r11s[idx] = (b <= a) ? static_cast<float>(R[static_cast<int64_t>(J[a]) * ldr + b]) : 0.f;
     }
     for (int a = threadIdx.x; a < k; a += blockDim.x)
         rinv[a] = 1.0f / static_cast<float>(R[static_cast<int64_t>(J[a]) * ldr + a]);
@@ -254,21 +308,13 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
         for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
         for (int it = 0; it < refine_steps; ++it) {
             double res[KQ];
+            float th[KQ], tl[KQ];
 #pragma unroll
-            for (int q = 0; q < KQ; ++q) res[q] = rhs[q];
-            for (int a = 0; a < k; ++a) {
-                const int qa = a >> 5, owner = a & 31;
-                double ta = tt[0];
-#pragma unroll
-                for (int q = 1; q < KQ; ++q) ta = (qa == q) ? tt[q] : ta;
-                ta = __shfl_sync(0xffffffffu, ta, owner);
-                const double* col = r11d + static_cast<int64_t>(a) * k;
-#pragma unroll
-                for (int q = 0; q < KQ; ++q) {
-                    const int b = lane + 32 * q;
-                    if (b <= a) res[q] = fma(-col[b], ta, res[q]);
-                }
+            for (int q = 0; q < KQ; ++q) {
+                th[q] = static_cast<float>(tt[q]);
+                tl[q] = static_cast<float>(tt[q] - static_cast<double>(th[q]));
             }
+            residual_pairs<KQ>(rhs, th, tl, it > 0, r11s, k, lane, res);
             float d[KQ];
 #pragma unroll
             for (int q = 0; q < KQ; ++q) d[q] = static_cast<float>(res[q]);
@@ -294,7 +340,7 @@ static cudaError_t launch_batched_solve(const BatchTask* tasks, const SolveUnit*
                                         int warps, const double* R_base, const int32_t* J_base,
                                         const int32_t* k_out, int32_t* infos, double* T_base,
                                         const BatchTotals& tot, int refine_steps, cudaStream_t s) {
-    const size_t smem = solve_smem_bytes(kmax, sizeof(float));
+    const size_t smem = static_cast<size_t>(kmax) * kmax * sizeof(float) + kmax * sizeof(float) + 16;
     auto kern = k_solve_T_batched<KQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
