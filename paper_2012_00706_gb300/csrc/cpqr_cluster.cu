@@ -408,16 +408,20 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
     // the peer's mbarrier in bytes.  Exchange q fills recv[q & 1] and completes phase
     // q >> 1 of recv_bar[q & 1]; a peer can be at most one exchange ahead, so two
     // alternating buffers and barriers never mix phases.
-    auto exchange = [&](int q) {
-        const int slot = q & 1;
-        uint64_t key = (!selected && qq == 0) ? cand_key(nu, i) : 0ull;
-        float part = (!selected && qq == 0) ? nu : 0.f;
+    // warp-level best candidate of this warp's columns, and the warp's sum of norms
+    auto warp_best = [&](int q, uint64_t& key, float& part) {
+        key = (!selected && qq == 0) ? cand_key(nu, i) : 0ull;
+        part = (!selected && qq == 0) ? nu : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const uint64_t ok2 = shfl_xor_u64(key, o);
             key = ok2 > key ? ok2 : key;
         }
         if (need_sum || q == 0) part = warp_sum(part);
+    };
+    // Stage the warp candidates, find the CTA's best and send it to the peers.
+    auto send_best = [&](int q, uint64_t key, float part) {
+        const int slot = q & 1;
         if (key != 0ull && i == key_index(key)) {
             // the TPC threads of the warp's candidate column
             float s = 0.f;
@@ -460,7 +464,12 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
         return mbar_wait(&recv_bar[q & 1], static_cast<uint32_t>((q >> 1) & 1), &keep, P.limit_ns);
     };
 
-    exchange(0);
+    {
+        uint64_t key0;
+        float part0;
+        warp_best(0, key0, part0);
+        send_best(0, key0, part0);
+    }
     bool ok = wait_exchange(0);
     int k = 0;
     float total = -1.f;
@@ -527,10 +536,19 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
         const float X = __shfl_sync(0xffffffffu, pick_row<RPT>(x, uj), gbase + qj);
         S = fmaf(-beta, X, S);
         const float tw = tau * (inv * S);
-        const float sv = tw * inv;
+        const float sv = selected ? 0.f : tw * inv;       // the pivot column itself stays
         const float rho = X - tw;
+        if (!selected && qq == 0) W.R[i * W.ldr + j] = static_cast<double>(rho);
+        // norm downdate; an exact recompute where cancellation has eaten sqrt(u)
         bool recompute = false;
-        if (!selected) {
+        if (!selected && nu > 0.f) {
+            const float t1 = fmaxf(1.f - (rho * rho) / nu, 0.f);
+            if (t1 * (nu / nuref) <= sqrt_u) recompute = true;   // same decision in all TPC threads
+            else nu = nu * t1;
+        }
+        uint64_t key;
+        float part;
+        if (__any_sync(0xffffffffu, recompute)) {
             // x -= (tau w / (alpha - beta)) v'; row j leaves as rho and is then zeroed
 #pragma unroll
             for (int u = 0; u < RPT; u += 4) {
@@ -540,15 +558,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
                 x[u + 2] = fmaf(-sv, v4.z, x[u + 2]);
                 x[u + 3] = fmaf(-sv, v4.w, x[u + 3]);
             }
-            if (qq == 0) W.R[i * W.ldr + j] = static_cast<double>(rho);
-            if (nu > 0.f) {
-                const float t1 = fmaxf(1.f - (rho * rho) / nu, 0.f);
-                if (t1 * (nu / nuref) <= sqrt_u) recompute = true;   // same decision in all TPC threads
-                else nu = nu * t1;
-            }
-        }
-        zero_row<RPT>(x, uj, qq == qj);
-        if (__any_sync(0xffffffffu, recompute)) {
+            zero_row<RPT>(x, uj, qq == qj);
             float sq = 0.f;
 #pragma unroll
             for (int u = 0; u < RPT; ++u) sq = fmaf(x[u], x[u], sq);
@@ -558,8 +568,21 @@ __global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParam
                 nu = sq;
                 nuref = sq;
             }
+            warp_best(j + 1, key, part);
+        } else {
+            // the next candidate search does not depend on x: its shuffles overlap the update
+            warp_best(j + 1, key, part);
+#pragma unroll
+            for (int u = 0; u < RPT; u += 4) {
+                const float4 v4 = *reinterpret_cast<const float4*>(&pc[vidx(rb + u)]);
+                x[u] = fmaf(-sv, v4.x, x[u]);
+                x[u + 1] = fmaf(-sv, v4.y, x[u + 1]);
+                x[u + 2] = fmaf(-sv, v4.z, x[u + 2]);
+                x[u + 3] = fmaf(-sv, v4.w, x[u + 3]);
+            }
+            zero_row<RPT>(x, uj, qq == qj);
         }
-        exchange(j + 1);
+        send_best(j + 1, key, part);
         ok = wait_exchange(j + 1);
         k = j + 1;
     }
