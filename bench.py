@@ -223,7 +223,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- our arm
 
-def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0):
+def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0, world=1, rank=0):
     """512 uneven FP64 IDs (exact rank r, sigma_i = 10^(-i/r), m in [256, 4096],
     n in [64, 1024], k = r): the batched mixed path (default and autotuned unit
     shapes, plain launches and a replayed CUDA graph) against one id_factor call
@@ -231,7 +231,13 @@ def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0):
     import tempfile
     import torch
     t_gen = time.perf_counter()
-    shapes, bufs = wl.config4_device(dev, count=count)
+    share = None
+    if world > 1:
+        # this process's longest-processing-time share (every rank computes the same split)
+        all_shapes = wl.config4_shapes(count, 4)
+        rank_of, _ = gid.shard_batch([(m, n) for m, n, _ in all_shapes], [r for _, _, r in all_shapes], world)
+        share = [i for i, r in enumerate(rank_of) if r == rank]
+    shapes, bufs = wl.config4_device(dev, count=count, indices=share)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     views = [v for _, v in bufs]
@@ -612,7 +618,7 @@ def main():
 
         # ---- the uneven batch: 512 FP64 matrices in one launch sequence (graph-captured)
         if not args.no_batched:
-            line["batched"] = batched_leg(gid, wl, dev, stream, count=args.batch_count)
+            line["batched"] = batched_leg(gid, wl, dev, stream, count=args.batch_count, world=world, rank=rank)
 
         # ---- the FP64 CPU oracle on the host (rank 0, N = 1 only)
         if rank == 0 and world == 1:

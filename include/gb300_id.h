@@ -322,6 +322,17 @@ id_status_t id_batch_autotune(id_batch_plan_t* plan, const void* omega, int64_t 
                               int32_t* k_out, int32_t* info, void* work, size_t work_bytes, void* stream,
                               int32_t reps, const char* cache_path, double* best_ms);
 
+/* Split a batch over `world` GPUs (one process each) by longest-processing-time:
+ * matrices in decreasing order of their sketch + pivoted-QR + solve work, each
+ * to the least loaded rank so far (ties to the lower rank).  Host only and
+ * deterministic, so every rank computes the same split without communication.
+ * m, n, k: HOST arrays of length batch; rank_of (HOST, length batch) receives
+ * the rank of each matrix; load (HOST, length world, nullable) receives each
+ * rank's modelled work in flop.  ell_i = min(k_i + oversample, m_i) as in
+ * id_batch_plan_create.  Errors: ID_ERR_ARG. */
+id_status_t id_batch_shard(int32_t batch, const int64_t* m, const int64_t* n, const int32_t* k, int32_t oversample,
+                           int32_t world, int32_t* rank_of, double* load);
+
 /* Profiling aid (not part of the computation).  When set, the next id_factor
  * calls made from this host thread record the caller's CUDA events (cudaEvent_t
  * passed as void*) on their stream at the stage boundaries:

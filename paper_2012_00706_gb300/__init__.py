@@ -20,7 +20,7 @@ import torch
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
     "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
-    "BatchPlan",
+    "BatchPlan", "shard_batch",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,8 +105,9 @@ def load():
         lib.id_factor_batched.argtypes = [p, p, i64, p, p, p, p, p, sz, p]
         lib.id_batch_autotune.argtypes = [p, p, i64, p, p, p, p, p, sz, p, i32, ctypes.c_char_p,
                                           ctypes.POINTER(ctypes.c_double)]
+        lib.id_batch_shard.argtypes = [i32, p, p, p, i32, i32, p, p]
         for name in ("id_batch_plan_create", "id_batch_plan_query", "id_batch_workspace_size", "id_batch_bind",
-                     "id_factor_batched", "id_batch_autotune"):
+                     "id_factor_batched", "id_batch_autotune", "id_batch_shard"):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("id_workspace_size", "id_factor", "id_sketch_workspace_size", "id_sketch",
                      "id_scale_cast", "id_set_stage_events"):
@@ -508,3 +509,17 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def shard_batch(shapes, ranks, world: int, oversample: int = 10):
+    """(rank_of, work): the library's longest-processing-time split of a batch over
+    ``world`` processes (host only, deterministic) and each rank's modelled flop."""
+    lib = load()
+    b = len(shapes)
+    m_ = (ctypes.c_int64 * b)(*[int(s[0]) for s in shapes])
+    n_ = (ctypes.c_int64 * b)(*[int(s[1]) for s in shapes])
+    k_ = (ctypes.c_int32 * b)(*[int(r) for r in ranks])
+    rank_of = (ctypes.c_int32 * b)()
+    work = (ctypes.c_double * world)()
+    _check(lib.id_batch_shard(b, m_, n_, k_, oversample, world, rank_of, work), "id_batch_shard")
+    return list(rank_of), list(work)

@@ -625,6 +625,35 @@ id_status_t id_factor_batched(const id_batch_plan_t* p, const void* omega, int64
     return enqueue(p, omega, omega_ld, J, T, k_out, info, work, static_cast<cudaStream_t>(stream));
 }
 
+id_status_t id_batch_shard(int32_t batch, const int64_t* m, const int64_t* n, const int32_t* k, int32_t oversample,
+                           int32_t world, int32_t* rank_of, double* load) {
+    if (batch < 0 || world < 1 || (batch > 0 && (!m || !n || !k || !rank_of)) || oversample < 0) return ID_ERR_ARG;
+    std::vector<std::pair<double, int32_t>> work(batch);
+    for (int32_t i = 0; i < batch; ++i) {
+        if (m[i] < 1 || n[i] < 1 || k[i] < 1) return ID_ERR_ARG;
+        const double ell = static_cast<double>(std::min<int64_t>(k[i] + oversample, m[i]));
+        const double kk = k[i], nn = static_cast<double>(n[i]), mm = static_cast<double>(m[i]);
+        const double f = 2.0 * ell * mm * nn + 4.0 * ell * nn * kk - 2.0 * kk * kk * (ell + nn) +
+                         4.0 * kk * kk * kk / 3.0 + kk * kk * std::max(0.0, nn - kk);
+        work[i] = {f, i};
+    }
+    std::stable_sort(work.begin(), work.end(),
+                     [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+                         return a.first > b.first;
+                     });
+    std::vector<double> acc(world, 0.0);
+    for (const auto& w : work) {
+        int best = 0;
+        for (int r = 1; r < world; ++r)
+            if (acc[r] < acc[best]) best = r;
+        rank_of[w.second] = best;
+        acc[best] += w.first;
+    }
+    if (load)
+        for (int r = 0; r < world; ++r) load[r] = acc[r];
+    return ID_OK;
+}
+
 id_status_t id_batch_autotune(id_batch_plan_t* p, const void* omega, int64_t omega_ld, int32_t* J, double* T,
                               int32_t* k_out, int32_t* info, void* work, size_t work_bytes, void* stream, int32_t reps,
                               const char* cache_path, double* best_ms) {

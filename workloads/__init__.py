@@ -207,12 +207,15 @@ def lowrank_device(m: int, n: int, sigma, seed: int, device, lda: int | None = N
     return buf, buf.t()[:m]
 
 
-def config4_device(device, count: int = 512, seed: int = 4, lda_multiple: int = 2, **kw):
+def config4_device(device, count: int = 512, seed: int = 4, lda_multiple: int = 2, indices=None, **kw):
     """The uneven batch of ``config4`` drawn on the GPU, leading dimensions rounded up to
-    a multiple of ``lda_multiple`` (2 doubles = 16 bytes, what TMA needs)."""
-    shapes = config4_shapes(count, seed, **kw)
+    a multiple of ``lda_multiple`` (2 doubles = 16 bytes, what TMA needs).  ``indices``
+    keeps a subset (one process's share); matrix i is the same whichever subset holds it."""
+    all_shapes = config4_shapes(count, seed, **kw)
+    keep = list(range(count)) if indices is None else list(indices)
+    shapes = [all_shapes[i] for i in keep]
     bufs = []
-    for idx, (m, n, r) in enumerate(shapes):
+    for idx, (m, n, r) in zip(keep, shapes):
         sigma = 10.0 ** (-np.arange(1, r + 1) / r)
         lda = (m + lda_multiple - 1) // lda_multiple * lda_multiple
         bufs.append(lowrank_device(m, n, sigma, seed * 100003 + idx, device, lda))
