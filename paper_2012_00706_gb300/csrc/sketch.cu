@@ -224,14 +224,26 @@ __device__ __forceinline__ void prefetch_tensor_2d(const CUtensorMap* map, int32
                  : "memory");
 }
 
-// Convert 8 scaled values into nsplit pieces and store them as one 16-byte chunk of
-// row t (K group g) of each swizzled operand tile.
-__device__ __forceinline__ void store_pieces(uint8_t* aop_buf, int nsplit, int f16, int t, int g, float (&v)[8]) {
+// Convert 8 scaled values into NSPLIT pieces and store them as one 16-byte chunk of
+// row t (K group g) of each swizzled operand tile; the last piece needs no remainder.
+template <int NSPLIT, bool F16>
+__device__ __forceinline__ void store_pieces(uint8_t* aop_buf, int t, int g, float (&v)[8]) {
     const uint32_t off = (t >> 3) * 1024u + (t & 7) * 128u + ((g ^ (t & 7)) << 4);
-    for (int p = 0; p < nsplit; ++p) {
+#pragma unroll
+    for (int p = 0; p < NSPLIT; ++p) {
         uint32_t w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = take_piece2(v[2 * q], v[2 * q + 1], f16);
+        for (int q = 0; q < 4; ++q) {
+            if (p + 1 < NSPLIT) {
+                w[q] = take_piece2(v[2 * q], v[2 * q + 1], F16 ? 1 : 0);
+            } else if (F16) {
+                const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+                w[q] = *reinterpret_cast<const uint32_t*>(&h);
+            } else {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                w[q] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+        }
         *reinterpret_cast<uint4*>(aop_buf + (size_t)p * kAopTileBytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
@@ -239,7 +251,7 @@ __device__ __forceinline__ void store_pieces(uint8_t* aop_buf, int nsplit, int f
 // BATCH = false: one ID, CTA (x, y) computes 128-column tile x over row slab y of A.
 // BATCH = true: CTA b computes unit b of the batch table (a tile and row slab of one
 // matrix), reading that matrix through its own tensor map in global memory.
-template <bool BATCH>
+template <bool BATCH, bool F64, int NSPLIT, bool F16>
 __global__ void __launch_bounds__(kSketchThreads, 1)
 k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constant__ CUtensorMap tm_a,
               const __grid_constant__ CUtensorMap tm_pf, const LowpParams P) {
@@ -298,7 +310,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
         amap = &tm_a;
     }
     const int nloc = static_cast<int>(ch_end - ch_begin);
-    const int elem = P.a_f64 ? 8 : 4;
+    constexpr int elem = F64 ? 8 : 4;
     const int slab_rows = 128 / elem;                     // rows per 128-byte box line
     const int nslabs = kChunkRows / slab_rows;            // boxes per chunk
 
@@ -376,7 +388,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
     } else if (warp == 1) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
-            const uint32_t idesc = umma_idesc_f16(P.f16 ? 0u : 1u, 128u, static_cast<uint32_t>(lp));
+            const uint32_t idesc = umma_idesc_f16(F16 ? 0u : 1u, 128u, static_cast<uint32_t>(lp));
             int issued = 0;
             for (int i = 0; i < nloc; ++i) {
                 const int a = i % NA, o = i % NO, b = i % NC;
@@ -387,8 +399,9 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 const uint32_t d = tmem + static_cast<uint32_t>(b * P.lpa);
                 const uint32_t bbase = smem_addr(S.omega + (size_t)o * P.omega_tile_bytes);
                 uint8_t* aop_base = P.aop_in_stage ? S.stage + (size_t)a * P.stage_bytes
-                                                   : S.aop + (size_t)a * P.nsplit * kAopTileBytes;
-                for (int p = 0; p < P.nsplit; ++p) {
+                                                   : S.aop + (size_t)a * NSPLIT * kAopTileBytes;
+#pragma unroll
+                for (int p = 0; p < NSPLIT; ++p) {
                     const uint32_t abase = smem_addr(aop_base + (size_t)p * kAopTileBytes);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
@@ -424,12 +437,12 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
             const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), P.m - row0));
             const uint8_t* stg = S.stage + (size_t)s * P.stage_bytes;
             uint8_t* aop_buf = P.aop_in_stage ? S.stage + (size_t)s * P.stage_bytes
-                                              : S.aop + (size_t)a * P.nsplit * kAopTileBytes;
+                                              : S.aop + (size_t)a * NSPLIT * kAopTileBytes;
             uint32_t mx = 0;
             int shift;
             float f[16];
             bool slow = false;
-            if (P.a_f64) {
+            if constexpr (F64) {
                 double v[16];
                 if (!P.direct) {
                     // box q holds rows 16q..16q+15 of all 128 columns, 128 bytes per column, swizzled
@@ -452,7 +465,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
                 if (q == 0 && (mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
-                shift = shift_from_max_f64hi(mx, P.f16);
+                shift = shift_from_max_f64hi(mx, F16 ? 1 : 0);
                 const uint32_t kbias = 0x40000000u - (static_cast<uint32_t>(shift) << 23);
 #pragma unroll
                 for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64_fast(v[r], shift, kbias, slow);
@@ -482,7 +495,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
                 if (q == 0 && (mx >> 23) == 0xFFu) set_info(info, kInfoNonFinite);
-                shift = shift_from_max_f32(mx, P.f16);
+                shift = shift_from_max_f32(mx, F16 ? 1 : 0);
 #pragma unroll
                 for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f32_fast(v[r], shift, slow);
                 if (__any_sync(0xffffffffu, slow) && slow) {
@@ -495,7 +508,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 float f8[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) f8[k] = f[8 * gg + k];
-                store_pieces(aop_buf, P.nsplit, P.f16, t, 2 * q + gg, f8);
+                store_pieces<NSPLIT, F16>(aop_buf, t, 2 * q + gg, f8);
             }
             if (q == 0) S.shifts[h * kTileCols + t] = shift;
             fence_proxy_async_smem();
@@ -584,6 +597,35 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode_tiled() {
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
     return fn;
+}
+
+// The kernel instance for an input type and precision (pieces, format).
+template <bool BATCH>
+static void* sketch_kernel(int a_f64, int precision) {
+    const int nsplit = precision_nsplit(precision), f16 = precision_is_f16(precision);
+    if (a_f64) {
+        if (f16) return reinterpret_cast<void*>(k_sketch_lowp<BATCH, true, 1, true>);
+        switch (nsplit) {
+            case 1: return reinterpret_cast<void*>(k_sketch_lowp<BATCH, true, 1, false>);
+            case 2: return reinterpret_cast<void*>(k_sketch_lowp<BATCH, true, 2, false>);
+            default: return reinterpret_cast<void*>(k_sketch_lowp<BATCH, true, 3, false>);
+        }
+    }
+    if (f16) return reinterpret_cast<void*>(k_sketch_lowp<BATCH, false, 1, true>);
+    switch (nsplit) {
+        case 1: return reinterpret_cast<void*>(k_sketch_lowp<BATCH, false, 1, false>);
+        case 2: return reinterpret_cast<void*>(k_sketch_lowp<BATCH, false, 2, false>);
+        default: return reinterpret_cast<void*>(k_sketch_lowp<BATCH, false, 3, false>);
+    }
+}
+
+static cudaError_t launch_sketch_kernel(void* kern, dim3 grid, size_t smem, cudaStream_t s, const CUtensorMap& tm_om,
+                                        const CUtensorMap& tm_a, const CUtensorMap& tm_pf, const LowpParams& P) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    void* args[] = {const_cast<CUtensorMap*>(&tm_om), const_cast<CUtensorMap*>(&tm_a), const_cast<CUtensorMap*>(&tm_pf),
+                    const_cast<LowpParams*>(&P)};
+    return cudaLaunchKernel(kern, grid, dim3(kSketchThreads), args, smem, s);
 }
 
 bool sketch_pipeline_plan(int lp, int a_f64, int nsplit, SketchPlan* plan) {
@@ -700,12 +742,8 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
     P.prefetch = prefetch ? kSketchL2Prefetch : 0;
     P.partial = partial; P.info = info; P.limit_ns = limit_ns;
 
-    cudaError_t e = cudaFuncSetAttribute(k_sketch_lowp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(plan.smem_bytes));
-    if (e != cudaSuccess) return e;
-    dim3 grid(plan.tiles, plan.kslabs);
-    k_sketch_lowp<false><<<grid, kSketchThreads, plan.smem_bytes, s>>>(tm_om, tm_a, tm_pf, P);
-    e = cudaGetLastError();
+    cudaError_t e = launch_sketch_kernel(sketch_kernel<false>(a_f64, precision), dim3(plan.tiles, plan.kslabs),
+                                         plan.smem_bytes, s, tm_om, tm_a, tm_pf, P);
     if (e != cudaSuccess) return e;
     if (after_main) cudaEventRecord(after_main, s);
     const int64_t total = n * ell;
@@ -764,12 +802,11 @@ cudaError_t launch_sketch_lowp_batched(const SketchUnit* units, int64_t nunits, 
     P.limit_ns = limit_ns;
     P.units = units; P.tasks = tasks; P.maps = maps; P.infos = infos;
     P.ntasks = ntasks; P.partial_total = partial_total;
-    cudaError_t e = cudaFuncSetAttribute(k_sketch_lowp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(plan.smem_bytes));
-    if (e != cudaSuccess) return e;
     if (nunits <= 0) return cudaSuccess;
-    k_sketch_lowp<true><<<static_cast<unsigned>(nunits), kSketchThreads, plan.smem_bytes, s>>>(tm_om, tm_unused,
-                                                                                            tm_unused, P);
+    const cudaError_t e = launch_sketch_kernel(sketch_kernel<true>(a_f64, precision),
+                                               dim3(static_cast<unsigned>(nunits)), plan.smem_bytes, s, tm_om,
+                                               tm_unused, tm_unused, P);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

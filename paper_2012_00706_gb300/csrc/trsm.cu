@@ -235,9 +235,11 @@ static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32
     auto kern = k_solve_T_warp<TS, KQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
+    // one warp per column where possible: the solves are chains of k dependent steps, so
+    // more resident warps (several CTAs per SM; R11 is small) hide their latency
     const int64_t cols = std::max<int64_t>(1, n - 1);
     const int64_t want = (cols + kWarpSolveWarps - 1) / kWarpSolveWarps;
-    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, device_info().sm_count)));
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, 8LL * device_info().sm_count)));
     kern<<<grid, kWarpSolveWarps * 32, smem, s>>>(R64, ldr, J, k_ptr, n, T, ldt, refine_steps);
     return cudaGetLastError();
 }
