@@ -35,10 +35,11 @@ constexpr int kSlabCandidates[] = {16, 32, 64};
 constexpr int kMinSlabChunks = 16;
 constexpr int kMaxAuxStreams = 8;
 constexpr int kMaxClusterBatch = 16;    // CTAs of one matrix's pivoted QR (non-portable cluster size)
-constexpr int kRowClasses[] = {32, 64, 128, 160};
+constexpr int kRowClasses[] = {32, 64, 96, 128, 160};
+constexpr int kNumRowClasses = 5;
 
 int row_class(int ell) {
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < kNumRowClasses; ++i)
         if (ell <= kRowClasses[i]) return i;
     return -1;
 }
@@ -51,7 +52,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Tuning {
     int slab_chunks = 32;
-    int tpc[4] = {4, 4, 4, 4};   // per row class
+    int tpc[kNumRowClasses] = {4, 4, 4, 4, 4};   // per row class
     int solve_warps = 8;
     int solve_cols = 32;
 };
@@ -141,7 +142,7 @@ void build_sketch_units(id_batch_plan* p) {
 bool build_cq_groups(id_batch_plan* p) {
     p->cq_order.clear();
     p->cq_groups.clear();
-    std::vector<std::vector<int32_t>> buckets(4 * (kMaxClusterBatch + 1));
+    std::vector<std::vector<int32_t>> buckets(kNumRowClasses * (kMaxClusterBatch + 1));
     for (int32_t i = 0; i < p->batch; ++i) {
         const BatchTask& t = p->tasks[i];
         const int rc = row_class(t.ell);
@@ -151,7 +152,7 @@ bool build_cq_groups(id_batch_plan* p) {
         if (cs > kMaxClusterBatch) return false;
         buckets[rc * (kMaxClusterBatch + 1) + cs].push_back(i);
     }
-    for (int rc = 0; rc < 4; ++rc)
+    for (int rc = 0; rc < kNumRowClasses; ++rc)
         for (int cs = 1; cs <= kMaxClusterBatch; ++cs) {
             auto& v = buckets[rc * (kMaxClusterBatch + 1) + cs];
             if (v.empty()) continue;
@@ -359,9 +360,9 @@ bool json_key_is(const std::string& line, const std::string& key) {
 std::string tuning_json(const id_batch_plan* p, double ms) {
     char buf[512];
     snprintf(buf, sizeof(buf),
-             "\"slab_chunks\": %d, \"tpc32\": %d, \"tpc64\": %d, \"tpc128\": %d, \"tpc160\": %d, "
-             "\"solve_warps\": %d, \"solve_cols\": %d, \"ms\": %.4f",
-             p->tune.slab_chunks, p->tune.tpc[0], p->tune.tpc[1], p->tune.tpc[2], p->tune.tpc[3],
+             "\"slab_chunks\": %d, \"tpc32\": %d, \"tpc64\": %d, \"tpc96\": %d, \"tpc128\": %d, "
+             "\"tpc160\": %d, \"solve_warps\": %d, \"solve_cols\": %d, \"ms\": %.4f",
+             p->tune.slab_chunks, p->tune.tpc[0], p->tune.tpc[1], p->tune.tpc[2], p->tune.tpc[3], p->tune.tpc[4],
              p->tune.solve_warps, p->tune.solve_cols, ms);
     return std::string(buf);
 }
@@ -370,9 +371,9 @@ bool valid_tuning(const Tuning& t) {
     bool slab_ok = false;
     for (int S : kSlabCandidates) slab_ok |= (t.slab_chunks == S);
     if (!slab_ok) return false;
-    for (int rc = 0; rc < 4; ++rc)
+    for (int rc = 0; rc < kNumRowClasses; ++rc)
         if (t.tpc[rc] != 2 && t.tpc[rc] != 4) return false;
-    if (t.tpc[3] != 4) return false;
+    if (t.tpc[kNumRowClasses - 1] != 4) return false;   // 160 rows: 2 threads per column would spill
     return t.solve_warps >= 1 && t.solve_warps <= 16 && t.solve_cols >= 16 && t.solve_cols <= 4096;
 }
 
@@ -387,8 +388,9 @@ void read_cache(id_batch_plan* p, const char* path) {
         json_int(line, "slab_chunks", &t.slab_chunks);
         json_int(line, "tpc32", &t.tpc[0]);
         json_int(line, "tpc64", &t.tpc[1]);
-        json_int(line, "tpc128", &t.tpc[2]);
-        json_int(line, "tpc160", &t.tpc[3]);
+        json_int(line, "tpc96", &t.tpc[2]);
+        json_int(line, "tpc128", &t.tpc[3]);
+        json_int(line, "tpc160", &t.tpc[4]);
         json_int(line, "solve_warps", &t.solve_warps);
         json_int(line, "solve_cols", &t.solve_cols);
         if (valid_tuning(t)) p->tune = t;
@@ -544,7 +546,7 @@ id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_
     }
     if (o.slab_chunks > 0) p->tune.slab_chunks = o.slab_chunks;
     if (o.cpqr_tpc > 0)
-        for (int rc = 0; rc < 3; ++rc) p->tune.tpc[rc] = o.cpqr_tpc;
+        for (int rc = 0; rc < kNumRowClasses - 1; ++rc) p->tune.tpc[rc] = o.cpqr_tpc;
     if (o.solve_warps > 0) p->tune.solve_warps = o.solve_warps;
     if (o.solve_cols > 0) p->tune.solve_cols = o.solve_cols;
     if (!valid_tuning(p->tune)) {
@@ -718,9 +720,9 @@ id_status_t id_batch_autotune(id_batch_plan_t* p, const void* omega, int64_t ome
         c.slab_chunks = S;
         if (S != best.slab_chunks && (st = consider(c)) != ID_OK) return fail(st);
     }
-    bool present[4] = {false, false, false, false};
+    bool present[kNumRowClasses] = {};
     for (const BatchTask& t : p->tasks) present[row_class(t.ell)] = true;
-    for (int rc = 0; rc < 3; ++rc) {
+    for (int rc = 0; rc < kNumRowClasses - 1; ++rc) {
         if (!present[rc]) continue;
         Tuning c = best;
         c.tpc[rc] = best.tpc[rc] == 4 ? 2 : 4;

@@ -339,8 +339,10 @@ struct CqRecord {
     float col[MAXR + MAXR / 8];        // the candidate column, padded rows (vidx)
 };
 
+// Short columns (MAXR <= 64, TPC = 4: 16 rows per thread) fit 64 registers, so two
+// CTAs share an SM; that doubles the clusters a batch keeps in flight.
 template <int MAXR, int TPC>
-__global__ void __launch_bounds__(kCqMaxThreads, 1) k_cpqr_cluster(const CqParams P) {
+__global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 1) k_cpqr_cluster(const CqParams P) {
     constexpr int RPT = MAXR / TPC;
     constexpr int MAXW = kCqMaxThreads / 32;
     constexpr uint32_t REC = sizeof(CqRecord<MAXR>);
@@ -677,12 +679,13 @@ static bool cq_fits(int tpc, int csize, int threads) {
     }
 }
 
-static int cq_maxr(int64_t r) { return r <= 32 ? 32 : (r <= 64 ? 64 : (r <= 128 ? 128 : 160)); }
+static int cq_maxr(int64_t r) { return r <= 32 ? 32 : (r <= 64 ? 64 : (r <= 96 ? 96 : (r <= 128 ? 128 : 160))); }
 
 static bool cq_fits_any(int maxr, int tpc, int csize, int threads) {
     switch (maxr) {
         case 32: return cq_fits<32>(tpc, csize, threads);
         case 64: return cq_fits<64>(tpc, csize, threads);
+        case 96: return cq_fits<96>(tpc, csize, threads);
         case 128: return cq_fits<128>(tpc, csize, threads);
         default: return cq_fits<160>(tpc, csize, threads);
     }
@@ -732,6 +735,7 @@ static cudaError_t launch_cq_any(const CqParams& P, const ClusterCpqrPlan& plan,
         switch (plan.maxr) {
             case 32: return launch_cq<32, 4>(P, cs, nclusters, th, s);
             case 64: return launch_cq<64, 4>(P, cs, nclusters, th, s);
+            case 96: return launch_cq<96, 4>(P, cs, nclusters, th, s);
             case 128: return launch_cq<128, 4>(P, cs, nclusters, th, s);
             default: return launch_cq<160, 4>(P, cs, nclusters, th, s);
         }
@@ -739,6 +743,7 @@ static cudaError_t launch_cq_any(const CqParams& P, const ClusterCpqrPlan& plan,
     switch (plan.maxr) {
         case 32: return launch_cq<32, 2>(P, cs, nclusters, th, s);
         case 64: return launch_cq<64, 2>(P, cs, nclusters, th, s);
+        case 96: return launch_cq<96, 2>(P, cs, nclusters, th, s);
         default: return launch_cq<128, 2>(P, cs, nclusters, th, s);
     }
 }
