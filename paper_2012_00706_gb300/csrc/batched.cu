@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kSlabCandidates[] = {16, 32, 64};
 constexpr int kMinSlabChunks = 16;
-constexpr int kMaxAuxStreams = 8;
+constexpr int kMaxAuxStreams = 32;
 constexpr int kMaxClusterBatch = 16;    // CTAs of one matrix's pivoted QR (non-portable cluster size)
 constexpr int kRowClasses[] = {32, 64, 96, 128, 160};
 constexpr int kNumRowClasses = 5;
@@ -469,10 +469,26 @@ id_status_t enqueue(const id_batch_plan* p, const void* omega, int64_t omega_ld,
         }
     }
     record_stage(3, s);
-    for (const SolveClass& c : p->solve_classes) {
+    // solve classes (by rank) run concurrently on the plan's streams as well
+    const int nsc = static_cast<int>(p->solve_classes.size());
+    const int naux2 = std::min(nsc, kMaxAuxStreams);
+    if (naux2 > 1) {
+        if (cudaEventRecord(p->fork, s) != cudaSuccess) return ID_ERR_CUDA;
+        for (int i = 0; i < naux2; ++i)
+            if (cudaStreamWaitEvent(p->aux[i], p->fork, 0) != cudaSuccess) return ID_ERR_CUDA;
+    }
+    for (int ci = 0; ci < nsc; ++ci) {
+        const SolveClass& c = p->solve_classes[ci];
+        cudaStream_t cs = naux2 > 1 ? p->aux[ci % naux2] : s;
         e = launch_solve_T_batched(d_tasks, d_solve + c.first, c.count, c.kmax, p->tune.solve_warps, R, J, k_out,
-                                   info, T, p->tot, p->opts.refine_steps, s);
+                                   info, T, p->tot, p->opts.refine_steps, cs);
         if (e != cudaSuccess) return ID_ERR_CUDA;
+    }
+    if (naux2 > 1) {
+        for (int i = 0; i < naux2; ++i) {
+            if (cudaEventRecord(p->join[i], p->aux[i]) != cudaSuccess) return ID_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, p->join[i], 0) != cudaSuccess) return ID_ERR_CUDA;
+        }
     }
     record_stage(4, s);
     record_stage(5, s);
