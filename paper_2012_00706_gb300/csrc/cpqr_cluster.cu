@@ -137,9 +137,12 @@ __device__ __forceinline__ int key_index(uint64_t key) {
 }
 __device__ __forceinline__ float key_norm(uint64_t key) { return __uint_as_float(static_cast<uint32_t>(key >> 32)); }
 
-__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int o) {
-    const uint32_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint32_t>(v), o);
-    const uint32_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint32_t>(v >> 32), o);
+// Warp maximum of candidate keys with two 32-bit warp reductions (norm bits, then the
+// index word among the lanes holding the largest norm).
+__device__ __forceinline__ uint64_t warp_max_key(uint64_t key) {
+    const uint32_t kh = static_cast<uint32_t>(key >> 32);
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, kh);
+    const uint32_t lo = __reduce_max_sync(0xffffffffu, kh == hi ? static_cast<uint32_t>(key) : 0u);
     return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 
@@ -412,13 +415,8 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
     // alternating buffers and barriers never mix phases.
     // warp-level best candidate of this warp's columns, and the warp's sum of norms
     auto warp_best = [&](int q, uint64_t& key, float& part) {
-        key = (!selected && qq == 0) ? cand_key(nu, i) : 0ull;
+        key = warp_max_key((!selected && qq == 0) ? cand_key(nu, i) : 0ull);
         part = (!selected && qq == 0) ? nu : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t ok2 = shfl_xor_u64(key, o);
-            key = ok2 > key ? ok2 : key;
-        }
         if (need_sum || q == 0) part = warp_sum(part);
     };
     // Stage the warp candidates, find the CTA's best and send it to the peers.
@@ -426,9 +424,15 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         const int slot = q & 1;
         if (key != 0ull && i == key_index(key)) {
             // the TPC threads of the warp's candidate column
-            float s = 0.f;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) s = fmaf(x[u], x[u], s);
+            for (int u = 0; u < RPT; u += 4) {
+                s0 = fmaf(x[u], x[u], s0);
+                s1 = fmaf(x[u + 1], x[u + 1], s1);
+                s2 = fmaf(x[u + 2], x[u + 2], s2);
+                s3 = fmaf(x[u + 3], x[u + 3], s3);
+            }
+            float s = (s0 + s1) + (s2 + s3);
 #pragma unroll
             for (int o = 1; o < TPC; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
 #pragma unroll
@@ -439,13 +443,8 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         }
         if (lane == 0) { wkey[warp] = key; wsum[warp] = part; }
         __syncthreads();
-        uint64_t ck = lane < nw ? wkey[lane] : 0ull;
+        const uint64_t ck = warp_max_key(lane < nw ? wkey[lane] : 0ull);
         float cs = lane < nw ? wsum[lane] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t ok2 = shfl_xor_u64(ck, o);
-            ck = ok2 > ck ? ok2 : ck;
-        }
         if (need_sum || q == 0) cs = warp_sum(cs);
         const unsigned hit = __ballot_sync(0xffffffffu, lane < nw && wkey[lane] == ck && ck != 0ull);
         const int wsrc = hit ? __ffs(hit) - 1 : 0;
@@ -478,7 +477,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
     for (int j = 0; ok && j < W.kcap; ++j) {
         const int par = j & 1;
         // ---- the pivot: every warp reduces the C records in the same order
-        uint64_t hk = lane < static_cast<int>(C) ? cand_key(recv[par][lane].head.x, 0) : 0ull;
+        uint64_t hk = 0ull;
         float hs = 0.f;
         if (lane < static_cast<int>(C)) {
             const float4 h = recv[par][lane].head;
@@ -486,12 +485,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
             hk = hi >= 0 ? cand_key(h.x, hi) : 0ull;
             hs = h.z;
         }
-        uint64_t best = hk;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t ok2 = shfl_xor_u64(best, o);
-            best = ok2 > best ? ok2 : best;
-        }
+        const uint64_t best = warp_max_key(hk);
         if (need_sum || j == 0) hs = warp_sum(hs);
         const unsigned hit = __ballot_sync(0xffffffffu, lane < static_cast<int>(C) && hk == best && best != 0ull);
         const int hsrc = hit ? __ffs(hit) - 1 : 0;
@@ -521,16 +515,16 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         }
         // S = v'.x with v' = (0 above j, alpha - beta at j, pivot column below):
         // pc.x - beta x_j, rows above j being zero in both
-        float S0 = 0.f, S1 = 0.f;
+        float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
 #pragma unroll
         for (int u = 0; u < RPT; u += 4) {
             const float4 v4 = *reinterpret_cast<const float4*>(&pc[vidx(rb + u)]);
             S0 = fmaf(v4.x, x[u], S0);
             S1 = fmaf(v4.y, x[u + 1], S1);
-            S0 = fmaf(v4.z, x[u + 2], S0);
-            S1 = fmaf(v4.w, x[u + 3], S1);
+            S2 = fmaf(v4.z, x[u + 2], S2);
+            S3 = fmaf(v4.w, x[u + 3], S3);
         }
-        float S = S0 + S1;
+        float S = (S0 + S1) + (S2 + S3);
 #pragma unroll
         for (int o = 1; o < TPC; o <<= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
         // X = x_j, held by thread qj of the group at register uj
