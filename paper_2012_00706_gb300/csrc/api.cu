@@ -230,6 +230,8 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
     int64_t ldsrc = 0;
     if (e == cudaSuccess && p.sketch) {
         if (p.mixed) {
+            // the split-K partial sums are reduced by a whole-GPU pass: the pivoted QR runs on
+            // one cluster, too few SMs to gather the slabs quickly itself
             e = launch_sketch_lowp(A, a_f64, m, n, lda, static_cast<const uint16_t*>(opts->omega), p.omega_ld,
                                    opts->ell, opts->precision, p.sp, static_cast<float*>(f.partial),
                                    static_cast<float*>(f.W), opts->ell, info, lim, s, stage_event(1));
@@ -255,7 +257,7 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
                 Wf = static_cast<const float*>(A);
                 ldw = lda;
             }
-            e = launch_cpqr_cluster(Wf, p.rows, n, ldw, p.kcap, rel_tol, J, k_out, info, f.R64, p.kcap, f.sel,
+            e = launch_cpqr_cluster(Wf, p.rows, n, ldw, 1, 0, p.kcap, rel_tol, J, k_out, info, f.R64, p.kcap, f.sel,
                                     p.ccp, lim, s);
         } else {
             e = launch_cpqr(f.W, p.w_f64, p.rows, n, p.rows, cpqr_src, a_f64, ldsrc, p.kcap, rel_tol, J, k_out, info,

@@ -41,6 +41,8 @@ struct CqParams {
     uint8_t* sel;
     int64_t cpb;          // columns per CTA
     uint64_t limit_ns;
+    int kslabs;           // Y given as kslabs split-K partial sums, slab_stride apart (1: Y itself)
+    int64_t slab_stride;
     // batch mode (tasks != nullptr): cluster c factors task order[c]; Y is the sketch's
     // split-K partial sums, added in slab order while loading
     const BatchTask* tasks;
@@ -74,7 +76,8 @@ __device__ __forceinline__ CqTask cq_task(const CqParams& P, uint32_t C) {
     CqTask W;
     W.ok = true;
     if (!P.tasks) {
-        W.Y = P.Y; W.r = P.r; W.n = P.n; W.ldy = P.ldy; W.slab_stride = 0; W.kslabs = 1;
+        W.Y = P.Y; W.r = P.r; W.n = P.n; W.ldy = P.ldy; W.slab_stride = P.slab_stride;
+        W.kslabs = P.kslabs > 0 ? P.kslabs : 1;
         W.kcap = P.kcap; W.rel_tol = P.rel_tol; W.J = P.J; W.k_out = P.k_out; W.info = P.info;
         W.R = P.R; W.ldr = P.ldr; W.sel = P.sel;
         return W;
@@ -505,14 +508,6 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         const float amb = alpha - beta;
         const float tau = (beta - alpha) / beta;
         const float inv = 1.f / amb;
-        if (valid && i == p) {
-            selected = true;
-            if (qq == 0) {
-                W.R[i * W.ldr + j] = static_cast<double>(beta);
-                W.J[j] = p;
-                W.sel[i] = 1;
-            }
-        }
         // S = v'.x with v' = (0 above j, alpha - beta at j, pivot column below):
         // pc.x - beta x_j, rows above j being zero in both
         float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
@@ -531,6 +526,14 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         const int qj = j / RPT, uj = j - qj * RPT;
         const float X = __shfl_sync(0xffffffffu, pick_row<RPT>(x, uj), gbase + qj);
         S = fmaf(-beta, X, S);
+        if (valid && i == p) {
+            selected = true;
+            if (qq == 0) {
+                W.R[i * W.ldr + j] = static_cast<double>(beta);
+                W.J[j] = p;
+                W.sel[i] = 1;
+            }
+        }
         const float tw = tau * (inv * S);
         const float sv = selected ? 0.f : tw * inv;       // the pivot column itself stays
         const float rho = X - tw;
@@ -742,11 +745,13 @@ static cudaError_t launch_cq_any(const CqParams& P, const ClusterCpqrPlan& plan,
     }
 }
 
-cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kcap, double rel_tol,
-                                int32_t* J, int32_t* k_out, int32_t* info, double* R64, int64_t ldr, uint8_t* sel,
-                                const ClusterCpqrPlan& plan, uint64_t limit_ns, cudaStream_t s) {
+cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kslabs, int64_t slab_stride,
+                                int kcap, double rel_tol, int32_t* J, int32_t* k_out, int32_t* info, double* R64,
+                                int64_t ldr, uint8_t* sel, const ClusterCpqrPlan& plan, uint64_t limit_ns,
+                                cudaStream_t s) {
     CqParams P{};
     P.Y = Y; P.r = r; P.n = n; P.ldy = ldy;
+    P.kslabs = kslabs; P.slab_stride = slab_stride;
     P.kcap = kcap; P.rel_tol = rel_tol;
     P.J = J; P.k_out = k_out; P.info = info;
     P.R = R64; P.ldr = ldr; P.sel = sel;

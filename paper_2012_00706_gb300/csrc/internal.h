@@ -68,7 +68,7 @@ struct SketchUnit {
     int32_t slab, pad;     // row slab (partial-sum slot)
 };
 
-// ---- sketch (sketch.cu)
+// ---- sketch (sketch.cu); launch_sketch_lowp with Y == nullptr leaves only the partial sums
 struct SketchPlan {
     int lp = 0;             // MMA N: ell rounded up to 16
     int tiles = 0;          // ceil(n / 128)
@@ -145,9 +145,12 @@ cudaError_t launch_cpqr_cluster_batched(const BatchTask* tasks, const int32_t* o
                                         int32_t* J_base, int32_t* k_out_base, int32_t* infos,
                                         const BatchTotals& tot, const ClusterCpqrPlan& plan,
                                         uint64_t limit_ns, cudaStream_t s);
-cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kcap, double rel_tol,
-                                int32_t* J, int32_t* k_out, int32_t* info, double* R64, int64_t ldr, uint8_t* sel,
-                                const ClusterCpqrPlan& plan, uint64_t limit_ns, cudaStream_t s);
+// Y: r x n (ldy), or the sum of kslabs such arrays slab_stride floats apart (the
+// sketch's split-K partial sums, added in slab order while loading).
+cudaError_t launch_cpqr_cluster(const float* Y, int64_t r, int64_t n, int64_t ldy, int kslabs, int64_t slab_stride,
+                                int kcap, double rel_tol, int32_t* J, int32_t* k_out, int32_t* info, double* R64,
+                                int64_t ldr, uint8_t* sel, const ClusterCpqrPlan& plan, uint64_t limit_ns,
+                                cudaStream_t s);
 
 // ---- coefficient solve and error estimate (trsm.cu)
 cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr,

@@ -746,6 +746,7 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
                                          plan.smem_bytes, s, tm_om, tm_a, tm_pf, P);
     if (e != cudaSuccess) return e;
     if (after_main) cudaEventRecord(after_main, s);
+    if (!Y) return cudaSuccess;   // the consumer adds the partial sums itself
     const int64_t total = n * ell;
     k_reduce_partials_f32<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
         partial, plan.kslabs, n, plan.lp, ell, Y, ldy);
