@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "IDs/sec and effective TFLOP/s, mixed vs plain FP64 GPU ID at rel.err ≤1e-6"
 M, N, K, P = 20000, 2000, 100, 10
+INFLIGHT = 8        # IDs in flight in the timed stream of IDs
 ELL = K + P
 WORKLOAD = ("randomized column ID, A 20000x2000 FP64 (sigma_i = i^-2, seeded orthonormal factors), "
             "Gaussian Omega 110x20000, rank k=100")
@@ -409,6 +410,7 @@ def main():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched leg (a profiling case) and print its JSON")
     ap.add_argument("--batch-count", type=int, default=512, help="matrices in the batched leg")
+    ap.add_argument("--inflight", type=int, default=INFLIGHT, help="IDs in flight in the timed stream")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -510,6 +512,56 @@ def main():
             stages = {nm: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j, nm in enumerate(names)}
         return total_ms, out, stages
 
+    def run_inflight(precision, om, steps, warmup, depth):
+        """`steps` IDs with `depth` of them in flight: one CUDA graph holds `depth` IDs on
+        forked streams (each with its own copy of A, workspace and outputs, so nothing is
+        shared through L2), replayed until exactly `steps` IDs have run (a one-ID graph
+        covers the remainder).  Throughput of a stream of IDs, as a server would run them."""
+        copies = [A] + [A.clone() for _ in range(depth - 1)]
+        wss = [torch.empty(gid.id_workspace_size(M, N, torch.float64, k=K, precision=precision, sketch=True,
+                                                 ell=ELL, omega=om), dtype=torch.uint8, device=dev)
+               for _ in range(depth)]
+        outs = [make_out(K) for _ in range(depth)]
+        streams = [torch.cuda.Stream() for _ in range(depth)]
+
+        def capture(count):
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                for i in range(count):   # warm each branch once outside the capture
+                    gid.id_factor(copies[i], K, precision=precision, omega=om, workspace=wss[i], out=outs[i],
+                                  sync=False, stream=cs)
+                cs.synchronize()
+                with torch.cuda.graph(g, stream=cs):
+                    for i in range(count):
+                        streams[i].wait_stream(cs)
+                        gid.id_factor(copies[i], K, precision=precision, omega=om, workspace=wss[i],
+                                      out=outs[i], sync=False, stream=streams[i])
+                    for i in range(count):
+                        cs.wait_stream(streams[i])
+            torch.cuda.synchronize()
+            return g
+
+        g_full = capture(depth)
+        g_one = capture(1) if steps % depth else None
+        for _ in range(warmup):
+            g_full.replay()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps // depth):
+            g_full.replay()
+        for _ in range(steps % depth):
+            g_one.replay()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return t0.elapsed_time(t1), outs[0]
+
     def max_over_ranks(x):
         if world == 1:
             return x
@@ -529,9 +581,10 @@ def main():
     # ---- main timed region: inputs resident in HBM
     if sampler:
         sampler.start()
-    total_ms, out_main, _ = run_loop(args.precision, omega, args.steps, args.warmup, graph=True)
+    total_ms, out_main = run_inflight(args.precision, omega, args.steps, args.warmup, max(1, args.inflight))
     clocks = sampler.stop() if sampler else None
-    # stage split (CUDA events at the library's stage boundaries) from plain launches
+    # one ID at a time (latency of a single ID, graph replay) and the stage split from plain launches
+    seq_ms, _, _ = run_loop(args.precision, omega, args.steps, args.warmup, graph=True)
     _, _, stages = run_loop(args.precision, omega, max(3, min(args.steps, 10)), 2, stage=True)
     total_ms = max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
@@ -564,9 +617,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "ell": ELL, "precision": args.precision,
-                   "launch": "each step replays one CUDA graph holding the whole ID (id_factor captured once)",
+                   "launch": f"a stream of IDs, {args.inflight} in flight: CUDA graphs of {args.inflight} IDs on forked "
+                             f"streams (own A copy, workspace, outputs each), replayed; single-ID latency "
+                             f"in latency_ms_per_id",
                    "l2": "inputs larger than L2 (A is 320 MB vs 129 MB L2); no flush needed"},
         "tflops": id_flops(M, N, ELL, K) * value / 1e12,
+        "latency_ms_per_id": seq_ms / args.steps,
         "stages_ms": stages, "roofline": roofline, "sketch_roofline": sketch_roof, "cpqr_roofline": cpqr_roof,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks,
@@ -590,15 +646,19 @@ def main():
         line["e2e"] = {"value": world * e2e_steps / (e2e_ms / 1e3), "unit": "IDs/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-        # ---- plain FP64 GPU ID (same A, same Omega in FP64) and the matched-error form
+        # ---- plain FP64 GPU ID (same A, same Omega in FP64) and the matched-error form, each
+        # one ID at a time (latency) and as a stream with the same number of IDs in flight
+        depth = max(1, args.inflight)
         p_steps = max(3, min(args.steps, 5))
         p_ms, out_plain, p_stages = run_loop("plain_f64", omega64, p_steps, 1, stage=True)
-        x_ms, out_x3, _ = run_loop("mixed_bf16x3", omega, args.steps, 2)
-        plain_ids = p_steps / (p_ms / 1e3)
-        x3_ids = args.steps / (x_ms / 1e3)
-        line["plain_f64"] = {"ids_per_s": plain_ids, "ms_per_id": p_ms / p_steps, "stages_ms": p_stages,
-                             "tflops": id_flops(M, N, ELL, K) * plain_ids / 1e12}
-        line["mixed_bf16x3"] = {"ids_per_s": x3_ids, "ms_per_id": x_ms / args.steps}
+        p_flight_ms, _ = run_inflight("plain_f64", omega64, depth, 1, depth)
+        x_ms, out_x3, _ = run_loop("mixed_bf16x3", omega, args.steps, 2, graph=True)
+        x_flight_ms, _ = run_inflight("mixed_bf16x3", omega, args.steps, 2, depth)
+        plain_ids = depth / (p_flight_ms / 1e3)
+        x3_ids = args.steps / (x_flight_ms / 1e3)
+        line["plain_f64"] = {"ids_per_s": plain_ids, "latency_ms_per_id": p_ms / p_steps, "stages_ms": p_stages,
+                             "tflops": id_flops(M, N, ELL, K) * plain_ids / 1e12, "inflight": depth}
+        line["mixed_bf16x3"] = {"ids_per_s": x3_ids, "latency_ms_per_id": x_ms / args.steps, "inflight": depth}
 
         # ---- accuracy (FP64 on the GPU): relative 2-norm errors and distances between IDs
         def ahat(out):
@@ -630,9 +690,13 @@ def main():
             "same_skeleton_bf16x3": bool(torch.equal(out_x3[0][:K], out_plain[0][:K])),
         }
         d3 = line["accuracy"]["d_bf16x3_vs_plain"]
-        line["speedup_vs_plain_f64"] = {"mixed_bf16": value / world / plain_ids,
-                                        "mixed_bf16x3": x3_ids / plain_ids,
-                                        "matched_1e-6_form": "mixed_bf16x3" if d3 <= 1e-6 else None}
+        lat_plain = p_ms / p_steps
+        line["speedup_vs_plain_f64"] = {
+            "throughput_mixed_bf16": value / world / plain_ids,
+            "throughput_mixed_bf16x3": x3_ids / plain_ids,
+            "latency_mixed_bf16": lat_plain / (seq_ms / args.steps),
+            "latency_mixed_bf16x3": lat_plain / (x_ms / args.steps),
+            "matched_1e-6_form": "mixed_bf16x3" if d3 <= 1e-6 else None}
         del h_m, h_p, h_x
 
         # ---- the uneven batch: 512 FP64 matrices in one launch sequence (graph-captured)
