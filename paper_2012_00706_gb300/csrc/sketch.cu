@@ -70,23 +70,44 @@ __device__ __forceinline__ float scaled_f32_from_f64(double x, int s) {
     return scaled_slow(x, s);
 }
 
-// Branch-free fast path of scaled_f32_from_f64 for the sketch's converter.
-// u holds the exponent's low 9 bits and the top 23 significand bits; adding
-// 2^30 - (s << 23) rebiases the exponent from 1023 to 127 and applies the
-// shift (exact modulo 2^32 whenever the result is a normal float), and `inc`
-// is the round-to-nearest-even increment from the 29 discarded bits.  Zeros
-// map to signed zeros.  Sets `slow` when the scaled value is not a normal
-// float; the caller then redoes the block with scaled_f32_from_f64.
-__device__ __forceinline__ float scaled_f32_from_f64_fast(double x, int s, uint32_t kbias, bool& slow) {
+// Per-block constants of the converter's FP64 fast path for a block shift s:
+// kb3 rebiases the exponent from 1023 to 127 and applies 2^-s (added to the high
+// word before it is shifted left by 3, hence the division by 8; the sum is exact
+// modulo 2^32 whenever the result is a normal float), thr is the smallest
+// (hi << 1) whose scaled value is a normal float, and a block with s < -872 is
+// redone exactly (its zero-exponent elements could scale to nonzero floats).
+struct F64CastBlock {
+    uint32_t kb3, thr;
+    bool slow;
+};
+
+__device__ __forceinline__ F64CastBlock f64_cast_block(int s) {
+    F64CastBlock b;
+    b.kb3 = (0x40000000u - (static_cast<uint32_t>(s) << 23)) >> 3;
+    b.thr = static_cast<uint32_t>(max(0, 897 + s)) << 21;
+    b.slow = s < -872;
+    return b;
+}
+
+// Branch-free fast path of scaled_f32_from_f64 for the sketch's converter, for an
+// element at or below its block's largest magnitude.  The round-to-nearest-even
+// increment is the carry out of lo + 0x0FFFFFFF + lsb (lsb = bit 29 of lo, the last
+// kept bit), which the same add chain carries into the rebiased high word; a funnel
+// shift then takes the exponent's low 9 bits and 23 significand bits.  An element
+// with a zero exponent (zero or subnormal double) maps to a signed zero; `slow` is
+// set when the scaled value of a nonzero-exponent element is below the normal range.
+// ha = hi << 1.
+__device__ __forceinline__ float scaled_f32_from_f64_fast(double x, uint32_t ha, const F64CastBlock& b,
+                                                          bool& slow) {
     const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
     const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
-    const uint32_t u = __funnelshift_l(lo, hi, 3);
-    const uint32_t inc = ((lo & 0x1FFFFFFFu) + 0x0FFFFFFFu + (u & 1u)) >> 29;
-    const uint32_t e = (hi >> 20) & 0x7FFu;
-    const bool zero = ((hi << 1) | lo) == 0u;
-    const uint32_t bits = zero ? 0u : (u + kbias + inc);
-    slow |= !zero && (static_cast<uint32_t>(static_cast<int>(e) - s - 897) > 252u);
-    return __uint_as_float(bits | (hi & 0x80000000u));
+    const uint32_t t = ((lo >> 29) & 1u) + 0x0FFFFFFFu;
+    uint32_t lo2, hi2;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;" : "=r"(lo2), "=r"(hi2) : "r"(lo), "r"(t), "r"(hi), "r"(b.kb3));
+    const uint32_t u = __funnelshift_l(lo2, hi2, 3);
+    const bool zero = ha < 0x00200000u;
+    slow |= !zero && ha < b.thr;
+    return __uint_as_float((zero ? 0u : u) | (hi & 0x80000000u));
 }
 
 // fl32(x 2^-s) for float x: exponent adjust when both ends are normal.
@@ -460,15 +481,21 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 }
                 // every converter has its values in registers before the stage is overwritten
                 if (P.aop_in_stage) asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
+                // high words without the sign (hi << 1), their maximum three at a time
+                uint32_t ha[16];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) mx = max(mx, static_cast<uint32_t>(__double2hiint(v[r])) & 0x7fffffffu);
+                for (int r = 0; r < 16; ++r) ha[r] = static_cast<uint32_t>(__double2hiint(v[r])) << 1;
+#pragma unroll
+                for (int r = 0; r < 16; r += 2) mx = __vimax3_u32(mx, ha[r], ha[r + 1]);
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+                mx >>= 1;
                 if (q == 0 && (mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
                 shift = shift_from_max_f64hi(mx, F16 ? 1 : 0);
-                const uint32_t kbias = 0x40000000u - (static_cast<uint32_t>(shift) << 23);
+                const F64CastBlock cb = f64_cast_block(shift);
+                slow = cb.slow;
 #pragma unroll
-                for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64_fast(v[r], shift, kbias, slow);
+                for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64_fast(v[r], ha[r], cb, slow);
                 if (__any_sync(0xffffffffu, slow) && slow) {
 #pragma unroll
                     for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64(v[r], shift);
@@ -921,11 +948,11 @@ __global__ void k_scale_cast(const void* __restrict__ A, int a_f64, int64_t m, i
             mx = max(mx, static_cast<uint32_t>(__double2hiint(col[r])) & 0x7fffffffu);
         if ((mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
         shift = shift_from_max_f64hi(mx, f16);
-        const uint32_t kbias = 0x40000000u - (static_cast<uint32_t>(shift) << 23);
+        const F64CastBlock cb = f64_cast_block(shift);
         // the converter's fast path, with the exact routine for out-of-range values
         auto conv = [&](double x) {
-            bool slow = false;
-            const float f = scaled_f32_from_f64_fast(x, shift, kbias, slow);
+            bool slow = cb.slow;
+            const float f = scaled_f32_from_f64_fast(x, static_cast<uint32_t>(__double2hiint(x)) << 1, cb, slow);
             return slow ? scaled_f32_from_f64(x, shift) : f;
         };
         for (int r = 0; r < rows; r += 2) {

@@ -74,6 +74,18 @@ def test_scale_cast_bit_exact(gid, dev, orc, precision, dtype):
                           -(1.5 + 2.0 ** -25), 0.75 - 2.0 ** -54, 1.9999999403953552, 1.0000000596046448])
         a[: len(edges), 9] = edges
         a[len(edges):2 * len(edges), 10] = -edges * 2.0 ** 40
+        # scaled values below the FP32 normal range (exact fallback), subnormal doubles
+        # in a block of ordinary values (signed zeros), a block near the bottom of the
+        # FP64 range (shift below -872: the whole block takes the exact route, and its
+        # subnormal double scales to a nonzero float), values near the FP64 maximum
+        a[:64, 11] = 1.0
+        a[1:9, 11] = [2.0 ** -140, -2.0 ** -130, 1.5 * 2.0 ** -126, 2.0 ** -149, 3.0 * 2.0 ** -151,
+                      5e-324, -5e-324, 2.0 ** -1022]
+        a[64:128, 12] = rng.standard_normal(64) * 1e-300
+        a[70, 12] = 1e-310
+        a[71, 12] = -0.0
+        a[128:192, 13] = rng.standard_normal(64) * 1e300
+        a[130:134, 13] = [1.0, -1e-20, 1e270, 2.0 ** -1074]
     a = np.asfortranarray(a.astype(dtype))
     fmt, nsplit = FMT[precision]
     pieces, shifts, info = gid.id_scale_cast(torch.from_numpy(a).to(dev), precision)
