@@ -401,7 +401,7 @@ def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0, world
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="mixed_bf16")
@@ -515,8 +515,9 @@ def main():
     def run_inflight(precision, om, steps, warmup, depth):
         """`steps` IDs with `depth` of them in flight: one CUDA graph holds `depth` IDs on
         forked streams (each with its own copy of A, workspace and outputs, so nothing is
-        shared through L2), replayed until exactly `steps` IDs have run (a one-ID graph
-        covers the remainder).  Throughput of a stream of IDs, as a server would run them."""
+        shared through L2), replayed until exactly `steps` IDs have run (a graph of the
+        remaining steps % depth IDs, also in flight together, covers the rest).  Throughput
+        of a stream of IDs, as a server would run them."""
         copies = [A] + [A.clone() for _ in range(depth - 1)]
         wss = [torch.empty(gid.id_workspace_size(M, N, torch.float64, k=K, precision=precision, sketch=True,
                                                  ell=ELL, omega=om), dtype=torch.uint8, device=dev)
@@ -544,7 +545,7 @@ def main():
             return g
 
         g_full = capture(depth)
-        g_one = capture(1) if steps % depth else None
+        g_rest = capture(steps % depth) if steps % depth else None
         for _ in range(warmup):
             g_full.replay()
         torch.cuda.synchronize()
@@ -555,8 +556,8 @@ def main():
         t0.record(stream)
         for _ in range(steps // depth):
             g_full.replay()
-        for _ in range(steps % depth):
-            g_one.replay()
+        if g_rest is not None:
+            g_rest.replay()
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()

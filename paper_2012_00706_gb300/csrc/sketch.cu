@@ -562,14 +562,27 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
             const float sc = ldexpf(1.0f, S.shifts[h * kTileCols + t]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh_free[h]);
-            for (int sl = 0; sl < nsl; ++sl) {
-                float acc[16], run[16];
-                tmem_ld16(lane_base + static_cast<uint32_t>(b * P.lpa + 16 * sl), acc);
-                if (i > 0) tmem_ld16(lane_base + run_col + 16u * sl, run);
+            // two 16-column slices per round trip: the tensor-memory load latency, not the
+            // arithmetic, sets the pace here
+            const uint32_t acc_col = static_cast<uint32_t>(b * P.lpa);
+            for (int sl = 0; sl < nsl; sl += 2) {
+                const bool two = sl + 1 < nsl;
+                float acc0[16], acc1[16], run0[16], run1[16];
+                tmem_ld16(lane_base + acc_col + 16u * sl, acc0);
+                if (two) tmem_ld16(lane_base + acc_col + 16u * (sl + 1), acc1);
+                if (i > 0) {
+                    tmem_ld16(lane_base + run_col + 16u * sl, run0);
+                    if (two) tmem_ld16(lane_base + run_col + 16u * (sl + 1), run1);
+                }
                 tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) run[j] = (i > 0) ? fmaf(acc[j], sc, run[j]) : acc[j] * sc;
-                tmem_st16(lane_base + run_col + 16u * sl, run);
+                for (int j = 0; j < 16; ++j) run0[j] = (i > 0) ? fmaf(acc0[j], sc, run0[j]) : acc0[j] * sc;
+                tmem_st16(lane_base + run_col + 16u * sl, run0);
+                if (two) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) run1[j] = (i > 0) ? fmaf(acc1[j], sc, run1[j]) : acc1[j] * sc;
+                    tmem_st16(lane_base + run_col + 16u * (sl + 1), run1);
+                }
             }
             tmem_st_wait();
             tc_fence_before();
@@ -661,7 +674,8 @@ bool sketch_pipeline_plan(int lp, int a_f64, int nsplit, SketchPlan* plan) {
     SketchPlan p = *plan;
     p.lp = lp;
     const int lpa = (lp + 31) / 32 * 32;
-    p.acc_bufs = (3 * lpa <= 512) ? 2 : 1;
+    // chunk accumulators in flight between the MMAs and the epilogue, next to the running sum
+    p.acc_bufs = (4 * lpa <= 512) ? 3 : (3 * lpa <= 512) ? 2 : 1;
     const uint32_t stage_bytes = static_cast<uint32_t>(kChunkRows * kTileCols * (a_f64 ? 8 : 4));
     const uint32_t omega_tile = (static_cast<uint32_t>(lp) * 128u + 1023u) & ~1023u;
     LowpParams P{};
@@ -675,16 +689,16 @@ bool sketch_pipeline_plan(int lp, int a_f64, int nsplit, SketchPlan* plan) {
         return lowp_carve(0, P, nullptr) <= budget;
     };
     // The MMA operand lives inside the consumed stage when the stage can hold its pieces,
-    // which frees room for more stages in flight.  Prefer two Omega buffers, then load
-    // depth (stages), then (separate operands only) a second operand buffer.
+    // which frees room for more stages in flight.  Prefer load depth (stages), then a
+    // second Omega buffer, then (separate operands only) a second operand buffer.
     P.aop_in_stage = stage_bytes >= static_cast<uint32_t>(nsplit) * kAopTileBytes ? 1 : 0;
     int st = 2, na = 1, no = 1;
     if (P.aop_in_stage) na = 2;
     auto fits2 = [&](int st_, int no_) { return fits(st_, P.aop_in_stage ? st_ : na, no_); };
     if (!fits2(st, no)) return false;
-    if (fits2(st, 2)) no = 2;
     const int max_st = a_f64 ? 3 : 6;
     while (st < max_st && fits2(st + 1, no)) ++st;
+    if (fits2(st, 2)) no = 2;
     if (P.aop_in_stage) na = st;
     else if (fits(st, 2, no)) na = 2;
     fits(st, na, no);
