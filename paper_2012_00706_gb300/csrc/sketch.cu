@@ -74,8 +74,10 @@ __device__ __forceinline__ float scaled_f32_from_f64(double x, int s) {
 // kb3 rebiases the exponent from 1023 to 127 and applies 2^-s (added to the high
 // word before it is shifted left by 3, hence the division by 8; the sum is exact
 // modulo 2^32 whenever the result is a normal float), thr is the smallest
-// (hi << 1) whose scaled value is a normal float, and a block with s < -872 is
-// redone exactly (its zero-exponent elements could scale to nonzero floats).
+// (hi << 1) whose scaled value is a normal float, less 2^21 (so that one unsigned
+// compare of (hi << 1) - 2^21 against it also passes the zero-exponent elements),
+// and a block with s < -872 is redone exactly (its zero-exponent elements could
+// scale to nonzero floats).
 struct F64CastBlock {
     uint32_t kb3, thr;
     bool slow;
@@ -84,7 +86,7 @@ struct F64CastBlock {
 __device__ __forceinline__ F64CastBlock f64_cast_block(int s) {
     F64CastBlock b;
     b.kb3 = (0x40000000u - (static_cast<uint32_t>(s) << 23)) >> 3;
-    b.thr = static_cast<uint32_t>(max(0, 897 + s)) << 21;
+    b.thr = static_cast<uint32_t>(max(1, 897 + s) - 1) << 21;
     b.slow = s < -872;
     return b;
 }
@@ -106,7 +108,7 @@ __device__ __forceinline__ float scaled_f32_from_f64_fast(double x, uint32_t ha,
     asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;" : "=r"(lo2), "=r"(hi2) : "r"(lo), "r"(t), "r"(hi), "r"(b.kb3));
     const uint32_t u = __funnelshift_l(lo2, hi2, 3);
     const bool zero = ha < 0x00200000u;
-    slow |= !zero && ha < b.thr;
+    slow |= ha - 0x00200000u < b.thr;
     return __uint_as_float((zero ? 0u : u) | (hi & 0x80000000u));
 }
 
@@ -269,6 +271,20 @@ __device__ __forceinline__ void store_pieces(uint8_t* aop_buf, int t, int g, flo
     }
 }
 
+// Slot and phase parity of a ring of n buffers, advanced once per chunk (the ring sizes
+// are runtime values, so this replaces a division per use).
+struct Ring {
+    int slot = 0, n;
+    uint32_t phase = 0;
+    __device__ explicit Ring(int n_) : n(n_) {}
+    __device__ void next() {
+        if (++slot == n) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
 // BATCH = false: one ID, CTA (x, y) computes 128-column tile x over row slab y of A.
 // BATCH = true: CTA b computes unit b of the batch table (a tile and row slab of one
 // matrix), reading that matrix through its own tensor map in global memory.
@@ -374,13 +390,14 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                         prefetch_tensor_2d(&tm_pf, static_cast<int32_t>((ch_begin + g) * kChunkRows),
                                            static_cast<int32_t>(col0));
             }
-            for (int i = 0; i < nloc; ++i) {
+            Ring rs(NS);
+            for (int i = 0; i < nloc; ++i, rs.next()) {
                 const int64_t c = ch_begin + i;
-                const int s = i % NS;
+                const int s = rs.slot;
                 if (P.prefetch && !P.direct && (i % kPrefetchGroup) == 0 && c + kPrefetchAhead < ch_end)
                     prefetch_tensor_2d(&tm_pf, static_cast<int32_t>((c + kPrefetchAhead) * kChunkRows),
                                        static_cast<int32_t>(col0));
-                if (!mbar_wait(&stage_free[s], ((i / NS) & 1) ^ 1, abort, P.limit_ns)) break;
+                if (!mbar_wait(&stage_free[s], rs.phase ^ 1u, abort, P.limit_ns)) break;
                 if (P.direct) {
                     mbar_arrive(&stage_full[s]);
                 } else {
@@ -397,10 +414,11 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
         // ---------------- Omega producer: one swizzled Omega tile per chunk
         if (lane == 0) {
             prefetch_tensormap(&tm_omega);
-            for (int i = 0; i < nloc; ++i) {
+            Ring ro(NO);
+            for (int i = 0; i < nloc; ++i, ro.next()) {
                 const int64_t c = ch_begin + i;
-                const int o = i % NO;
-                if (!mbar_wait(&omg_free[o], ((i / NO) & 1) ^ 1, abort, P.limit_ns)) break;
+                const int o = ro.slot;
+                if (!mbar_wait(&omg_free[o], ro.phase ^ 1u, abort, P.limit_ns)) break;
                 mbar_arrive_expect_tx(&omg_full[o], P.omega_tile_bytes);
                 tma_load_2d(S.omega + (size_t)o * P.omega_tile_bytes, &tm_omega,
                             static_cast<int32_t>(c * kChunkRows), 0, &omg_full[o]);
@@ -411,11 +429,12 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
         if (lane == 0) {
             const uint32_t idesc = umma_idesc_f16(F16 ? 0u : 1u, 128u, static_cast<uint32_t>(lp));
             int issued = 0;
-            for (int i = 0; i < nloc; ++i) {
-                const int a = i % NA, o = i % NO, b = i % NC;
-                if (!mbar_wait(&aop_full[a], (i / NA) & 1, abort, P.limit_ns)) break;
-                if (!mbar_wait(&omg_full[o], (i / NO) & 1, abort, P.limit_ns)) break;
-                if (!mbar_wait(&acc_empty[b], ((i / NC) & 1) ^ 1, abort, P.limit_ns)) break;
+            Ring ra(NA), ro(NO), rb(NC);
+            for (int i = 0; i < nloc; ++i, ra.next(), ro.next(), rb.next()) {
+                const int a = ra.slot, o = ro.slot, b = rb.slot;
+                if (!mbar_wait(&aop_full[a], ra.phase, abort, P.limit_ns)) break;
+                if (!mbar_wait(&omg_full[o], ro.phase, abort, P.limit_ns)) break;
+                if (!mbar_wait(&acc_empty[b], rb.phase ^ 1u, abort, P.limit_ns)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + static_cast<uint32_t>(b * P.lpa);
                 const uint32_t bbase = smem_addr(S.omega + (size_t)o * P.omega_tile_bytes);
@@ -448,12 +467,13 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
         const int t = cw * 8 + (lane & 7);
         const int64_t col = col0 + t;
         const bool valid = t < ncols_valid;
-        for (int i = 0; i < nloc; ++i) {
+        Ring rs(NS), ra(NA), rh(H);
+        for (int i = 0; i < nloc; ++i, rs.next(), ra.next(), rh.next()) {
             const int64_t c = ch_begin + i;
-            const int s = i % NS, a = P.aop_in_stage ? s : i % NA, h = i % H;
-            if (!mbar_wait(&stage_full[s], (i / NS) & 1, abort, P.limit_ns)) break;
-            if (!P.aop_in_stage && !mbar_wait(&aop_free[a], ((i / NA) & 1) ^ 1, abort, P.limit_ns)) break;
-            if (!mbar_wait(&sh_free[h], ((i / H) & 1) ^ 1, abort, P.limit_ns)) break;
+            const int s = rs.slot, a = P.aop_in_stage ? s : ra.slot, h = rh.slot;
+            if (!mbar_wait(&stage_full[s], rs.phase, abort, P.limit_ns)) break;
+            if (!P.aop_in_stage && !mbar_wait(&aop_free[a], ra.phase ^ 1u, abort, P.limit_ns)) break;
+            if (!mbar_wait(&sh_free[h], rh.phase ^ 1u, abort, P.limit_ns)) break;
             const int64_t row0 = c * kChunkRows;
             const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), P.m - row0));
             const uint8_t* stg = S.stage + (size_t)s * P.stage_bytes;
@@ -554,10 +574,11 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
         const uint32_t run_col = static_cast<uint32_t>(NC * P.lpa);
         const int nsl = lp / 16;
         bool ok = true;
-        for (int i = 0; i < nloc; ++i) {
-            const int b = i % NC, h = i % H;
-            if (!mbar_wait(&acc_full[b], (i / NC) & 1, abort, P.limit_ns)) { ok = false; break; }
-            if (!mbar_wait(&sh_full[h], (i / H) & 1, abort, P.limit_ns)) { ok = false; break; }
+        Ring rb(NC), rh(H);
+        for (int i = 0; i < nloc; ++i, rb.next(), rh.next()) {
+            const int b = rb.slot, h = rh.slot;
+            if (!mbar_wait(&acc_full[b], rb.phase, abort, P.limit_ns)) { ok = false; break; }
+            if (!mbar_wait(&sh_full[h], rh.phase, abort, P.limit_ns)) { ok = false; break; }
             tc_fence_after();
             const float sc = ldexpf(1.0f, S.shifts[h * kTileCols + t]);
             __syncwarp();
