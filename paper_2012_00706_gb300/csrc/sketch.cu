@@ -633,16 +633,26 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
     if (warp == 2) tmem_dealloc(tmem, 512);
 }
 
-// Y(l, j) = sum over split-K slabs of the partial sums (fixed slab order).
-__global__ void k_reduce_partials_f32(const float* __restrict__ partial, int kslabs, int64_t n,
-                                      int lp, int ell, float* __restrict__ Y, int64_t ldy) {
-    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= n * ell) return;
-    const int64_t j = idx / ell;
-    const int l = static_cast<int>(idx - j * ell);
-    float s = 0.f;
-    for (int k = 0; k < kslabs; ++k) s += partial[(static_cast<int64_t>(k) * n + j) * lp + l];
-    Y[j * ldy + l] = s;
+// Y(l, j) = sum over split-K slabs of the partial sums [kslabs][n][lp] (fixed slab
+// order).  Warp w of a block reduces column j = 4 blockIdx.x + w, its lanes striding
+// over the sketch rows l; info (FP64 sums only) flags a non-finite sum.
+constexpr int kReduceCols = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kReduceCols * 32)
+k_reduce_partials(const T* __restrict__ partial, int kslabs, int64_t n, int lp, int ell, T* __restrict__ Y,
+                  int64_t ldy, int32_t* info) {
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * kReduceCols + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const int64_t slab = n * lp;
+    const T* src = partial + j * lp;
+    for (int l = threadIdx.x & 31; l < ell; l += 32) {
+        T s = T(0);
+#pragma unroll 4
+        for (int k = 0; k < kslabs; ++k) s += src[k * slab + l];
+        if (info && !isfinite(s)) set_info(info, kInfoNonFinite);
+        Y[j * ldy + l] = s;
+    }
 }
 
 // ------------------------------------------------------------- host plans
@@ -809,9 +819,8 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
     if (e != cudaSuccess) return e;
     if (after_main) cudaEventRecord(after_main, s);
     if (!Y) return cudaSuccess;   // the consumer adds the partial sums itself
-    const int64_t total = n * ell;
-    k_reduce_partials_f32<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
-        partial, plan.kslabs, n, plan.lp, ell, Y, ldy);
+    k_reduce_partials<float><<<static_cast<unsigned>((n + kReduceCols - 1) / kReduceCols), kReduceCols * 32, 0, s>>>(
+        partial, plan.kslabs, n, plan.lp, ell, Y, ldy, nullptr);
     return cudaGetLastError();
 }
 
@@ -924,18 +933,6 @@ k_sketch_f64(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
     }
 }
 
-__global__ void k_reduce_partials_f64(const double* __restrict__ partial, int kslabs, int64_t n, int lp,
-                                      int ell, double* __restrict__ Y, int64_t ldy, int32_t* info) {
-    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= n * ell) return;
-    const int64_t j = idx / ell;
-    const int l = static_cast<int>(idx - j * ell);
-    double s = 0.0;
-    for (int k = 0; k < kslabs; ++k) s += partial[(static_cast<int64_t>(k) * n + j) * lp + l];
-    if (!isfinite(s)) set_info(info, kInfoNonFinite);
-    Y[j * ldy + l] = s;
-}
-
 void sketch_plan_f64(int64_t m, int64_t n, int ell, SketchF64Plan* plan) {
     const DeviceInfo& dev = device_info();
     const int64_t tiles = ((n + kF64Tile - 1) / kF64Tile) * ((ell + kF64Tile - 1) / kF64Tile);
@@ -956,8 +953,7 @@ cudaError_t launch_sketch_f64(const double* A, int64_t m, int64_t n, int64_t lda
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (after_main) cudaEventRecord(after_main, s);
-    const int64_t total = n * ell;
-    k_reduce_partials_f64<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+    k_reduce_partials<double><<<static_cast<unsigned>((n + kReduceCols - 1) / kReduceCols), kReduceCols * 32, 0, s>>>(
         partial, plan.kslabs, n, plan.lp, ell, Y, ldy, info);
     return cudaGetLastError();
 }
