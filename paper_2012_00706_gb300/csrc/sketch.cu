@@ -634,9 +634,13 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
 }
 
 // Y(l, j) = sum over split-K slabs of the partial sums [kslabs][n][lp] (fixed slab
-// order).  Warp w of a block reduces column j = 4 blockIdx.x + w, its lanes striding
-// over the sketch rows l; info (FP64 sums only) flags a non-finite sum.
+// order).  Warp w of a block reduces column j = 4 blockIdx.x + w: lane i sums rows
+// i, i + 32, i + 64, i + 96 of each group of 128, with the loads of eight slabs for
+// all four rows issued before their sums (the partial sums are in L2; the time is
+// load latency); info (FP64 sums only) flags a non-finite sum.
 constexpr int kReduceCols = 4;
+constexpr int kReduceRows = 4;
+constexpr int kReduceSlabs = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(kReduceCols * 32)
@@ -644,14 +648,36 @@ k_reduce_partials(const T* __restrict__ partial, int kslabs, int64_t n, int lp, 
                   int64_t ldy, int32_t* info) {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * kReduceCols + (threadIdx.x >> 5);
     if (j >= n) return;
+    const int lane = threadIdx.x & 31;
     const int64_t slab = n * lp;
     const T* src = partial + j * lp;
-    for (int l = threadIdx.x & 31; l < ell; l += 32) {
-        T s = T(0);
-#pragma unroll 4
-        for (int k = 0; k < kslabs; ++k) s += src[k * slab + l];
-        if (info && !isfinite(s)) set_info(info, kInfoNonFinite);
-        Y[j * ldy + l] = s;
+    for (int l0 = 0; l0 < ell; l0 += 32 * kReduceRows) {
+        T s[kReduceRows];
+#pragma unroll
+        for (int r = 0; r < kReduceRows; ++r) s[r] = T(0);
+        for (int k0 = 0; k0 < kslabs; k0 += kReduceSlabs) {
+            T v[kReduceSlabs][kReduceRows];
+#pragma unroll
+            for (int kk = 0; kk < kReduceSlabs; ++kk)
+#pragma unroll
+                for (int r = 0; r < kReduceRows; ++r) {
+                    const int l = l0 + 32 * r + lane;
+                    v[kk][r] = (k0 + kk < kslabs && l < ell) ? src[(k0 + kk) * slab + l] : T(0);
+                }
+#pragma unroll
+            for (int kk = 0; kk < kReduceSlabs; ++kk)
+#pragma unroll
+                for (int r = 0; r < kReduceRows; ++r)
+                    if (k0 + kk < kslabs) s[r] += v[kk][r];
+        }
+#pragma unroll
+        for (int r = 0; r < kReduceRows; ++r) {
+            const int l = l0 + 32 * r + lane;
+            if (l < ell) {
+                if (info && !isfinite(s[r])) set_info(info, kInfoNonFinite);
+                Y[j * ldy + l] = s[r];
+            }
+        }
     }
 }
 
