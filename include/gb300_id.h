@@ -142,7 +142,9 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
  * A is scaled per (ID_SCALE_BLOCK_ROWS rows, column) by a power of two,
  * rounded to nearest-even in the low format (1-3 pieces), multiplied on the
  * tensor cores with FP32 accumulation, and Y is float.  info (device, nullable)
- * is set to -1 if A holds a non-finite value, else 0. */
+ * is set to -1 if A holds a non-finite value or an entry of Y is not finite
+ * (a column whose scaled blocks reach past the FP32 range overflows the FP32
+ * accumulation; its entries of Y are then inf or NaN), else 0. */
 id_status_t id_sketch(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
                       const void* omega, int64_t omega_ld, int32_t ell, int32_t precision,
                       void* Y, int64_t ldy, int32_t* info,

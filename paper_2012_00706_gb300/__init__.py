@@ -247,8 +247,11 @@ def set_stage_events(events) -> None:
     lib.id_set_stage_events(arr, len(events))
 
 
-def id_sketch(A: torch.Tensor, omega: torch.Tensor, precision: str = "mixed_bf16", stream=None) -> torch.Tensor:
-    """Y = Omega A (ell, n): float32 for the mixed precisions, float64 for plain_f64."""
+def id_sketch(A: torch.Tensor, omega: torch.Tensor, precision: str = "mixed_bf16", stream=None,
+              return_info: bool = False):
+    """Y = Omega A (ell, n): float32 for the mixed precisions, float64 for plain_f64.
+    With return_info, (Y, info): info a one-element device int32 tensor, -1 when A holds
+    a non-finite value or an entry of Y is not finite, else 0."""
     _require_cuda(A, omega)
     a, lda = _colmajor(A)
     m, n = a.shape
@@ -264,7 +267,7 @@ def id_sketch(A: torch.Tensor, omega: torch.Tensor, precision: str = "mixed_bf16
     _check(lib.id_sketch(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, omega.data_ptr(), _omega_ld(omega), ell,
                          PRECISIONS[precision], Y.data_ptr(), ell, info.data_ptr(), work.data_ptr(), work.numel(),
                          _stream_ptr(stream)), "id_sketch")
-    return Y
+    return (Y, info) if return_info else Y
 
 
 def id_scale_cast(A: torch.Tensor, precision: str = "mixed_bf16", stream=None):

@@ -166,6 +166,10 @@ int precision_is_f16(int precision) { return precision == ID_MIXED_F16 ? 1 : 0; 
 // Warp roles: 0 producer (TMA), 1 MMA issuer, 2 TMEM allocator, 3 idle,
 // 4..19 converters (four threads per column), 20..23 epilogue.
 constexpr int kConvWarps = 16;
+// Elements of a converter thread's 16 (rows 16q .. 16q + 3 of the chunk) cast on the FP64
+// pipe, the rest in integer arithmetic: four balances the two pipes on GB300 (measured
+// against two to eight).
+constexpr int kF2F = 4;
 constexpr int kFirstConvWarp = 4;
 constexpr int kFirstEpiWarp = kFirstConvWarp + kConvWarps;
 constexpr int kSketchThreads = (kFirstEpiWarp + 4) * 32;
@@ -514,8 +518,23 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 shift = shift_from_max_f64hi(mx, F16 ? 1 : 0);
                 const F64CastBlock cb = f64_cast_block(shift);
                 slow = cb.slow;
+                // the first kF2F elements through the FP64 pipe's conversion (idle otherwise) and
+                // an exact FP32 power-of-two scale: fl32(x) 2^-s = fl32(x 2^-s) while both are
+                // normal floats, i.e. for a nonzero exponent e >= max(897, 897 + s) (one compare
+                // like the integer path's); zero exponents give signed zeros both ways, a shift
+                // outside [-126, 127] sends the block to the exact routine below
+                if (kF2F > 0) slow |= shift < -126 || shift > 127;
+                const float sc = __uint_as_float(static_cast<uint32_t>(127 - shift) << 23);
+                const uint32_t thr_f2f = max(cb.thr, 896u << 21);
 #pragma unroll
-                for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64_fast(v[r], ha[r], cb, slow);
+                for (int r = 0; r < 16; ++r) {
+                    if (r < kF2F) {
+                        f[r] = __double2float_rn(v[r]) * sc;
+                        slow |= ha[r] - 0x00200000u < thr_f2f;
+                    } else {
+                        f[r] = scaled_f32_from_f64_fast(v[r], ha[r], cb, slow);
+                    }
+                }
                 if (__any_sync(0xffffffffu, slow) && slow) {
 #pragma unroll
                     for (int r = 0; r < 16; ++r) f[r] = scaled_f32_from_f64(v[r], shift);
@@ -637,7 +656,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
 // order).  Warp w of a block reduces column j = 4 blockIdx.x + w: lane i sums rows
 // i, i + 32, i + 64, i + 96 of each group of 128, with the loads of eight slabs for
 // all four rows issued before their sums (the partial sums are in L2; the time is
-// load latency); info (FP64 sums only) flags a non-finite sum.
+// load latency); info flags a non-finite sum (an FP32 sketch that overflowed).
 constexpr int kReduceCols = 4;
 constexpr int kReduceRows = 4;
 constexpr int kReduceSlabs = 8;
@@ -846,7 +865,7 @@ cudaError_t launch_sketch_lowp(const void* A, int a_f64, int64_t m, int64_t n, i
     if (after_main) cudaEventRecord(after_main, s);
     if (!Y) return cudaSuccess;   // the consumer adds the partial sums itself
     k_reduce_partials<float><<<static_cast<unsigned>((n + kReduceCols - 1) / kReduceCols), kReduceCols * 32, 0, s>>>(
-        partial, plan.kslabs, n, plan.lp, ell, Y, ldy, nullptr);
+        partial, plan.kslabs, n, plan.lp, ell, Y, ldy, info);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,8 @@ Tolerances (written here, derived from the arithmetic):
   * plain FP64 sketch: 1e-12 relative to |Omega| |A|;
   * plain FP64 ID: pivots bit-exact on separated inputs, T within 1e-9 relative,
     relative reconstruction error within 1e-10 of the oracle's;
-  * mixed ID: e_M <= 1.1 e_D + 10 u_low (spec tolerance), e the relative
-    2-norm error of the reconstruction.
+  * mixed ID: e_M <= 1.1 e_D + 10 u_low (the matched-accuracy criterion), e the
+    relative 2-norm error of the reconstruction.
 """
 import numpy as np
 import pytest
@@ -54,11 +54,9 @@ def bits_as_f64(bits, fmt):
 
 # ------------------------------------------------------------------ scaled cast
 
-@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_f16", "mixed_bf16x2", "mixed_bf16x3"])
-@pytest.mark.parametrize("dtype", [np.float64, np.float32])
-def test_scale_cast_bit_exact(gid, dev, orc, precision, dtype):
-    """Shifts and piece bits equal the oracle's cast (ragged last block, zero column,
-    wide dynamic range, ties)."""
+def edge_matrix(dtype):
+    """200 x 37 test matrix for the scaled cast: ragged last block, zero column, wide
+    dynamic range, ties, FP64 -> FP32 rounding edges and range extremes (FP64 only)."""
     rng = np.random.default_rng(1)
     m, n = 200, 37
     a = rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-6, 6, (m, n))
@@ -86,7 +84,23 @@ def test_scale_cast_bit_exact(gid, dev, orc, precision, dtype):
         a[71, 12] = -0.0
         a[128:192, 13] = rng.standard_normal(64) * 1e300
         a[130:134, 13] = [1.0, -1e-20, 1e270, 2.0 ** -1074]
-    a = np.asfortranarray(a.astype(dtype))
+        # the FP32 normal-range boundary of the scaled values (block maximum 1, shift 1),
+        # on rows 16q .. 16q + 3 and on the other rows of each 16
+        a[:64, 14] = 1.0
+        for r0 in (0, 5, 16, 21, 32, 37, 48, 53):
+            a[r0 + 1: r0 + 4, 14] = [2.0 ** -125, -(2.0 ** -125) * (1 + 2.0 ** -30), 2.0 ** -126 * 1.25]
+        a[64:128, 15] = 2.0 ** -100       # a block near the bottom of the FP32 range (shift -99)
+        a[65:128:7, 15] = 2.0 ** -150 * 3.0
+        a[66:128:5, 15] = 2.0 ** -170
+    return np.asfortranarray(a.astype(dtype))
+
+
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_f16", "mixed_bf16x2", "mixed_bf16x3"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_scale_cast_bit_exact(gid, dev, orc, precision, dtype):
+    """Shifts and piece bits equal the oracle's cast (ragged last block, zero column,
+    wide dynamic range, ties, range edges)."""
+    a = edge_matrix(dtype)
     fmt, nsplit = FMT[precision]
     pieces, shifts, info = gid.id_scale_cast(torch.from_numpy(a).to(dev), precision)
     ref_p, ref_s, rc = orc.quantize(a, fmt, 64, nsplit)
@@ -96,6 +110,39 @@ def test_scale_cast_bit_exact(gid, dev, orc, precision, dtype):
     for p in range(nsplit):
         vals = bits_as_f64(np.ascontiguousarray(got[p]), fmt)
         assert np.array_equal(vals, ref_p[p]), f"piece {p} differs"
+
+
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_f16", "mixed_bf16x2", "mixed_bf16x3"])
+def test_sketch_identity_reproduces_cast(gid, dev, orc, precision):
+    """The sketch kernel's own converter (the one inside the tensor-core pipeline, with
+    its FP64-pipe and integer paths) against the oracle's cast, bit for bit: with Omega
+    the identity every entry of Y is one product 1 x (sum of the pieces) x 2^s, exact in
+    FP32.  Entries whose value is not a normal FP32 number (FP32 subnormals, whose
+    handling is the tensor core's) are left out, and so is the column with values near the
+    FP64 maximum: its scaled blocks reach past the FP32 range, so its FP32 sketch is not
+    finite, which info reports."""
+    a = edge_matrix(np.float64)
+    m, n = a.shape
+    fmt, nsplit = FMT[precision]
+    ident = np.eye(m, dtype=np.float32)
+    bits = wl.to_bf16_bits(ident) if fmt == "bf16" else wl.to_f16_bits(ident)
+    y, info = gid.id_sketch(torch.from_numpy(a).to(dev), omega_dev(bits, dev, fmt), precision, return_info=True)
+    y = y.cpu().numpy()
+    assert int(info.item()) == -1
+    ref_p, ref_s, rc = orc.quantize(a, fmt, 64, nsplit)
+    assert rc == 0
+    scale = np.repeat(2.0 ** ref_s, 64, axis=0)[:m]
+    exact = ref_p.sum(axis=0) * scale
+    with np.errstate(over="ignore"):
+        ref32 = exact.astype(np.float32)
+    mag = np.abs(exact)
+    overflow_col = (mag >= 2.0 ** 127).any(axis=0)
+    assert overflow_col.tolist() == [j == 13 for j in range(n)]
+    normal = ((mag == 0) | ((mag >= 2.0 ** -126) & (mag < 2.0 ** 127))) & ~overflow_col[None, :]
+    assert normal.sum() > 0.9 * normal.size
+    # equal as numbers (a zero's sign is the sum's: -0 + 0 products is +0)
+    bad = np.nonzero(y[normal] != ref32[normal])[0]
+    assert bad.size == 0, (int(bad.size), np.argwhere(normal)[bad[:5]].tolist())
 
 
 def test_scale_cast_nonfinite(gid, dev):
@@ -136,7 +183,9 @@ def test_sketch_lowp_vs_oracle(gid, dev, orc, precision, m, n, ell, dtype, pad):
     bits_pad = np.zeros((ell, ldo), dtype=np.uint16)
     bits_pad[:, :m] = bits
     omt = omega_dev(bits_pad, dev, fmt)[:, :m]
-    y = gid.id_sketch(at, omt, precision).cpu().numpy().astype(np.float64)
+    y, info = gid.id_sketch(at, omt, precision, return_info=True)
+    assert int(info.item()) == 0
+    y = y.cpu().numpy().astype(np.float64)
     ref, rc = orc.sketch_lowp(om, np.asfortranarray(a), fmt, nsplit, 64)
     pieces, shifts, _ = orc.quantize(np.asfortranarray(a), fmt, 64, nsplit)
     bound = lowp_bound(om, pieces, shifts)
