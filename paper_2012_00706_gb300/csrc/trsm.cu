@@ -77,22 +77,22 @@ size_t solve_T_scratch_doubles(int kcap, int64_t n) { return static_cast<size_t>
 // R12 - R11 T formed in FP64 (mixed-precision iterative refinement).
 constexpr int kWarpSolveWarps = 8;
 
+// The steps a run by 32-row block qa (a compile-time register index), bottom block
+// first: rows of the blocks above are all updated, rows of block qa only above a, and
+// the blocks below, already final, are not touched.
 template <typename TS, int KQ>
 __device__ __forceinline__ void warp_backsub(TS (&t)[KQ], const TS* __restrict__ r11, const TS* __restrict__ rinv,
                                              int k, int lane) {
-    for (int a = k - 1; a >= 0; --a) {
-        const int qa = a >> 5, owner = a & 31;
-        TS ta = t[0];
 #pragma unroll
-        for (int q = 1; q < KQ; ++q) ta = (qa == q) ? t[q] : ta;
-        ta = ta * rinv[a];
-        ta = __shfl_sync(0xffffffffu, ta, owner);
-        const TS* col = r11 + static_cast<int64_t>(a) * k;
+    for (int qa = KQ - 1; qa >= 0; --qa) {
+        for (int a = min(32 * qa + 31, k - 1); a >= 32 * qa; --a) {
+            const int i = a - 32 * qa;
+            const TS ta = __shfl_sync(0xffffffffu, t[qa] * rinv[a], i);
+            const TS* col = r11 + static_cast<int64_t>(a) * k + lane;
 #pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            const int b = lane + 32 * q;
-            if (b < a) t[q] = fma(-col[b], ta, t[q]);
-            else if (b == a) t[q] = ta;
+            for (int q = 0; q < qa; ++q) t[q] = fma(-col[32 * q], ta, t[q]);
+            if (lane < i) t[qa] = fma(-col[32 * qa], ta, t[qa]);
+            else if (lane == i) t[qa] = ta;
         }
     }
 }
@@ -113,36 +113,57 @@ __device__ __forceinline__ void residual_pairs(const double (&rhs)[KQ], const fl
         sh[q] = static_cast<float>(rhs[q]);
         sl[q] = 0.f;
     }
-    for (int a = 0; a < k; ++a) {
-        const int qa = a >> 5, owner = a & 31;
-        float ah = th[0], al = tl[0];
+    // a runs by 32-row block qa (compile-time register index): rows of the blocks above
+    // take every step, rows of block qa those with b <= a
+    auto update = [&](float& h, float& l, float rv, float ah, float al) {
+        // explicit round-to-nearest operations: no contraction into FMAs
+        const float p = __fmul_rn(rv, ah);
+        const float e = fmaf(rv, ah, -p);
+        const float s = __fadd_rn(h, p);                     // TwoSum(h, p)
+        const float bp = __fsub_rn(s, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+        h = s;
+        l = __fadd_rn(l, __fadd_rn(err, e));
+        if (use_lo) l = fmaf(rv, al, l);                     // R t_lo is below the pair's resolution
+    };
 #pragma unroll
-        for (int q = 1; q < KQ; ++q) {
-            ah = (qa == q) ? th[q] : ah;
-            al = (qa == q) ? tl[q] : al;
-        }
-        ah = __shfl_sync(0xffffffffu, ah, owner);
-        if (use_lo) al = __shfl_sync(0xffffffffu, al, owner);
-        const float* col = r11s + static_cast<int64_t>(a) * k;
+    for (int qa = 0; qa < KQ; ++qa) {
+        const int a_end = min(32 * qa + 32, k);
+        for (int a = 32 * qa; a < a_end; ++a) {
+            const int i = a - 32 * qa;
+            const float ah = __shfl_sync(0xffffffffu, th[qa], i);
+            const float al = use_lo ? __shfl_sync(0xffffffffu, tl[qa], i) : 0.f;
+            const float* col = r11s + static_cast<int64_t>(a) * k + lane;
 #pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            const int b = lane + 32 * q;
-            if (b <= a) {
-                // explicit round-to-nearest operations: no contraction into FMAs
-                const float rv = -col[b];
-                const float p = __fmul_rn(rv, ah);
-                const float e = fmaf(rv, ah, -p);
-                const float s = __fadd_rn(sh[q], p);             // TwoSum(sh, p)
-                const float bp = __fsub_rn(s, sh[q]);
-                const float err = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(s, bp)), __fsub_rn(p, bp));
-                sh[q] = s;
-                sl[q] = __fadd_rn(sl[q], __fadd_rn(err, e));
-                if (use_lo) sl[q] = fmaf(rv, al, sl[q]);       // R t_lo is below the pair's resolution
-            }
+            for (int q = 0; q < qa; ++q) update(sh[q], sl[q], -col[32 * q], ah, al);
+            if (lane <= i) update(sh[qa], sl[qa], -col[32 * qa], ah, al);
         }
     }
 #pragma unroll
     for (int q = 0; q < KQ; ++q) res[q] = static_cast<double>(sh[q]) + static_cast<double>(sl[q]);
+}
+
+// Stage R11 = R(0:k, J[0:k]) (k x k, column-major, upper triangle: the solves never read
+// below the diagonal) and the reciprocals of its diagonal.  Warp w takes columns
+// a = w, w + nw, ...: its lanes first load those columns' pivot indices together, then
+// each column's rows go to consecutive lanes, so the R loads are coalesced and none
+// waits on another.
+template <typename TS>
+__device__ __forceinline__ void stage_r11(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+                                          int k, TS* r11s, TS* rinv) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int a0 = warp; a0 < k; a0 += 32 * nw) {
+        const int ncol = min(32, (k - a0 + nw - 1) / nw);
+        const int jl = lane < ncol ? __ldg(J + a0 + nw * lane) : 0;
+#pragma unroll 4
+        for (int c = 0; c < ncol; ++c) {
+            const int a = a0 + nw * c;
+            const double* col = R + static_cast<int64_t>(__shfl_sync(0xffffffffu, jl, c)) * ldr;
+            TS* dst = r11s + static_cast<int64_t>(a) * k;
+            for (int b = lane; b <= a; b += 32) dst[b] = static_cast<TS>(col[b]);
+            if (lane == 0) rinv[a] = static_cast<TS>(1.0) / static_cast<TS>(col[a]);
+        }
+    }
 }
 
 template <typename TS, int KQ>
@@ -158,13 +179,7 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
     double* r11d = reinterpret_cast<double*>(sm);
     TS* r11s = reinterpret_cast<TS*>(sm);
     TS* rinv = r11s + static_cast<int64_t>(k) * k;
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-        const int b = idx % k, a = idx / k;                               // row b, column a
-        const double v = (b <= a) ? R[static_cast<int64_t>(J[a]) * ldr + b] : 0.0;
-        r11s[idx] = static_cast<TS>(v);
-    }
-    for (int a = threadIdx.x; a < k; a += blockDim.x)
-        rinv[a] = static_cast<TS>(1.0) / static_cast<TS>(R[static_cast<int64_t>(J[a]) * ldr + a]);
+    stage_r11<TS>(R, ldr, J, k, r11s, rinv);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
@@ -198,17 +213,16 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
                 // residual R12 - R11 T in FP64 (row-oriented: lane b sums over a >= b)
 #pragma unroll
                 for (int q = 0; q < KQ; ++q) res[q] = rhs[q];
-                for (int a = 0; a < k; ++a) {
-                    const int qa = a >> 5, owner = a & 31;
-                    double ta = tt[0];
 #pragma unroll
-                    for (int q = 1; q < KQ; ++q) ta = (qa == q) ? tt[q] : ta;
-                    ta = __shfl_sync(0xffffffffu, ta, owner);
-                    const double* col = r11d + static_cast<int64_t>(a) * k;
+                for (int qa = 0; qa < KQ; ++qa) {
+                    const int a_end = min(32 * qa + 32, k);
+                    for (int a = 32 * qa; a < a_end; ++a) {
+                        const int i = a - 32 * qa;
+                        const double ta = __shfl_sync(0xffffffffu, tt[qa], i);
+                        const double* col = r11d + static_cast<int64_t>(a) * k + lane;
 #pragma unroll
-                    for (int q = 0; q < KQ; ++q) {
-                        const int b = lane + 32 * q;
-                        if (b <= a) res[q] = fma(-col[b], ta, res[q]);
+                        for (int q = 0; q < qa; ++q) res[q] = fma(-col[32 * q], ta, res[q]);
+                        if (lane <= i) res[qa] = fma(-col[32 * qa], ta, res[qa]);
                     }
                 }
             }
@@ -285,12 +299,7 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
     }
     float* r11s = reinterpret_cast<float*>(sm);                         // k x k, column-major
     float* rinv = r11s + static_cast<int64_t>(k) * k;
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-        const int b = idx % k, a = idx / k;
-        r11s[idx] = (b <= a) ? static_cast<float>(R[static_cast<int64_t>(J[a]) * ldr + b]) : 0.f;
-    }
-    for (int a = threadIdx.x; a < k; a += blockDim.x)
-        rinv[a] = 1.0f / static_cast<float>(R[static_cast<int64_t>(J[a]) * ldr + a]);
+    stage_r11<float>(R, ldr, J, k, r11s, rinv);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     double* T = T_base + bt.t_off;
