@@ -8,7 +8,8 @@ Mixed precision by default: power-of-two scaled bfloat16 sketch on the
 tensor cores with FP32 accumulation, FP32 pivoted QR of Y, FP64 T solve with
 one refinement step.  Inputs stay resident in HBM for the timed loop (A is
 320 MB, larger than the 129 MB L2, so no flush is needed); `e2e` repeats the
-measurement with A and Omega copied from pinned host memory each step and the
+measurement with A and Omega copied from pinned host memory each step (double-buffered:
+the copy of the next ID overlaps the current one's compute) and the
 result read back.
 
 Also reported: the plain FP64 GPU ID on the same matrix and Omega (FP64
@@ -40,6 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "IDs/sec and effective TFLOP/s, mixed vs plain FP64 GPU ID at rel.err ≤1e-6"
 M, N, K, P = 20000, 2000, 100, 10
 INFLIGHT = 8        # IDs in flight in the timed stream of IDs
+INFLIGHT_GROUPS = 2  # graphs the in-flight IDs are issued as, replayed in turn on their own streams
 ELL = K + P
 WORKLOAD = ("randomized column ID, A 20000x2000 FP64 (sigma_i = i^-2, seeded orthonormal factors), "
             "Gaussian Omega 110x20000, rank k=100")
@@ -512,12 +514,67 @@ def main():
             stages = {nm: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j, nm in enumerate(names)}
         return total_ms, out, stages
 
+    def run_e2e(precision, host, steps, warmup):
+        """End to end through the public API, as a streaming caller runs it: every step copies
+        its A and Omega from pinned host memory into one of two device buffers on a copy
+        stream, runs id_factor on the compute stream once its copy has landed, and copies J,
+        T and (k, info) back to pinned host memory.  The copy of step i + 1 overlaps the
+        compute of step i (the host-to-device link, about 0.2 TB/s, is the bound)."""
+        ws = torch.empty(gid.id_workspace_size(M, N, torch.float64, k=K, precision=precision, sketch=True,
+                                               ell=ELL, omega=omega), dtype=torch.uint8, device=dev)
+        out = make_out(K)
+        a_buf = [torch.empty_like(A) for _ in range(2)]
+        o_buf = [torch.empty_like(omega) for _ in range(2)]
+        copy_s = torch.cuda.Stream()
+        comp_s = torch.cuda.Stream()
+        landed = [torch.cuda.Event() for _ in range(2)]
+        used = [torch.cuda.Event() for _ in range(2)]
+        for e in used:
+            e.record(comp_s)
+
+        def step(i):
+            b = i % 2
+            copy_s.wait_event(used[b])
+            with torch.cuda.stream(copy_s):
+                a_buf[b].copy_(host["A"], non_blocking=True)
+                o_buf[b].copy_(host["omega"], non_blocking=True)
+                landed[b].record(copy_s)
+            comp_s.wait_event(landed[b])
+            gid.id_factor(a_buf[b], K, precision=precision, omega=o_buf[b], workspace=ws, out=out, sync=False,
+                          stream=comp_s)
+            with torch.cuda.stream(comp_s):
+                host["J"].copy_(out[0], non_blocking=True)
+                host["T"].copy_(out[1][:, : N - K], non_blocking=True)
+                host["small"].copy_(out[2], non_blocking=True)
+                used[b].record(comp_s)
+
+        for i in range(warmup):
+            step(i)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(cur)
+        copy_s.wait_stream(cur)
+        comp_s.wait_stream(cur)
+        for i in range(steps):
+            step(i)
+        cur.wait_stream(comp_s)
+        t1.record(cur)
+        torch.cuda.synchronize()
+        barrier()
+        return t0.elapsed_time(t1)
+
     def run_inflight(precision, om, steps, warmup, depth):
-        """`steps` IDs with `depth` of them in flight: one CUDA graph holds `depth` IDs on
-        forked streams (each with its own copy of A, workspace and outputs, so nothing is
-        shared through L2), replayed until exactly `steps` IDs have run (a graph of the
-        remaining steps % depth IDs, also in flight together, covers the rest).  Throughput
-        of a stream of IDs, as a server would run them."""
+        """`steps` IDs with `depth` of them in flight, issued as INFLIGHT_GROUPS CUDA graphs of
+        depth / INFLIGHT_GROUPS IDs each, replayed in turn on their own streams: a graph holds
+        its IDs on forked streams (each with its own copy of A, workspace and outputs, so
+        nothing is shared through L2), and while one group's pivoted QRs run on 16-SM
+        clusters the next group's sketches fill the other SMs.  A graph of the remaining
+        steps % depth IDs covers the rest.  Throughput of a stream of IDs, as a server would
+        run them."""
         copies = [A] + [A.clone() for _ in range(depth - 1)]
         wss = [torch.empty(gid.id_workspace_size(M, N, torch.float64, k=K, precision=precision, sketch=True,
                                                  ell=ELL, omega=om), dtype=torch.uint8, device=dev)
@@ -525,40 +582,57 @@ def main():
         outs = [make_out(K) for _ in range(depth)]
         streams = [torch.cuda.Stream() for _ in range(depth)]
 
-        def capture(count):
+        def capture(ids):
             g = torch.cuda.CUDAGraph()
             cs = torch.cuda.Stream()
             cs.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(cs):
-                for i in range(count):   # warm each branch once outside the capture
+                for i in ids:   # warm each branch once outside the capture
                     gid.id_factor(copies[i], K, precision=precision, omega=om, workspace=wss[i], out=outs[i],
                                   sync=False, stream=cs)
                 cs.synchronize()
                 with torch.cuda.graph(g, stream=cs):
-                    for i in range(count):
+                    for i in ids:
                         streams[i].wait_stream(cs)
                         gid.id_factor(copies[i], K, precision=precision, omega=om, workspace=wss[i],
                                       out=outs[i], sync=False, stream=streams[i])
-                    for i in range(count):
+                    for i in ids:
                         cs.wait_stream(streams[i])
             torch.cuda.synchronize()
             return g
 
-        g_full = capture(depth)
-        g_rest = capture(steps % depth) if steps % depth else None
+        ngroups = max(1, min(INFLIGHT_GROUPS, depth))
+        per = depth // ngroups
+        bounds = [(gi * per, depth if gi == ngroups - 1 else (gi + 1) * per) for gi in range(ngroups)]
+        groups = [capture(range(lo, hi)) for lo, hi in bounds]
+        gstreams = [torch.cuda.Stream() for _ in groups]
+        rest = steps % depth
+        g_rest = capture(range(rest)) if rest else None
+
+        def round_():
+            for g, s_ in zip(groups, gstreams):
+                with torch.cuda.stream(s_):
+                    g.replay()
+
         for _ in range(warmup):
-            g_full.replay()
+            round_()
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
+        t0.record(cur)
+        for s_ in gstreams:
+            s_.wait_stream(cur)
         for _ in range(steps // depth):
-            g_full.replay()
+            round_()
         if g_rest is not None:
-            g_rest.replay()
-        t1.record(stream)
+            with torch.cuda.stream(gstreams[0]):
+                g_rest.replay()
+        for s_ in gstreams:
+            cur.wait_stream(s_)
+        t1.record(cur)
         torch.cuda.synchronize()
         barrier()
         return t0.elapsed_time(t1), outs[0]
@@ -618,9 +692,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "ell": ELL, "precision": args.precision,
-                   "launch": f"a stream of IDs, {args.inflight} in flight: CUDA graphs of {args.inflight} IDs on forked "
-                             f"streams (own A copy, workspace, outputs each), replayed; single-ID latency "
-                             f"in latency_ms_per_id",
+                   "launch": f"a stream of IDs, {args.inflight} in flight: {min(INFLIGHT_GROUPS, args.inflight)} "
+                             f"CUDA graphs of {args.inflight // min(INFLIGHT_GROUPS, args.inflight)} IDs on forked "
+                             f"streams (own A copy, workspace, outputs each), replayed in turn on their own "
+                             f"streams; single-ID latency in latency_ms_per_id; e2e double-buffers A",
                    "l2": "inputs larger than L2 (A is 320 MB vs 129 MB L2); no flush needed"},
         "tflops": id_flops(M, N, ELL, K) * value / 1e12,
         "latency_ms_per_id": seq_ms / args.steps,
@@ -634,13 +709,12 @@ def main():
         host = {"A": torch.from_numpy(a_np).pin_memory(),
                 "omega": omega.cpu().pin_memory(),
                 "J": torch.empty(N, dtype=torch.int32).pin_memory(),
-                "T": torch.empty((K, N - K), dtype=torch.float64).pin_memory(),
+                # T's device layout (column-major K x (N - K)), pinned: a device-to-host copy
+                # into pageable memory would block the host and serialise the steps
+                "T": torch.empty((N - K, K), dtype=torch.float64).pin_memory().t(),
                 "small": torch.empty(2, dtype=torch.int32).pin_memory()}
-        host["T"] = host["T"].t().contiguous().t()
-        A_e2e = torch.empty_like(A)
-        om_e2e = torch.empty_like(omega)
         e2e_steps = max(3, min(args.steps, 10))
-        e2e_ms, _, _ = run_loop(args.precision, om_e2e, e2e_steps, 2, a_src=A_e2e, host=host)
+        e2e_ms = run_e2e(args.precision, host, e2e_steps, 2)
         e2e_ms = max_over_ranks(e2e_ms)
         h2d = 8 * M * N + 2 * ELL * M
         d2h = 4 * N + 8 * K * (N - K) + 8
