@@ -503,8 +503,10 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
 #pragma unroll
                     for (int r = 0; r < 16; ++r) v[r] = (valid && 16 * q + r < rows) ? __ldg(g + 16 * q + r) : 0.0;
                 }
-                // every converter has its values in registers before the stage is overwritten
-                if (P.aop_in_stage) asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
+                // in-place pieces: piece p of column t lands on line t of box p of the stage,
+                // which only the four threads of column t (one warp) read, so the warp's reads
+                // must be done before its writes, and no other warp's
+                if (P.aop_in_stage) __syncwarp();
                 // high words without the sign (hi << 1), their maximum three at a time
                 uint32_t ha[16];
 #pragma unroll
@@ -555,7 +557,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
 #pragma unroll
                     for (int r = 0; r < 16; ++r) v[r] = (valid && 16 * q + r < rows) ? __ldg(g + 16 * q + r) : 0.f;
                 }
-                if (P.aop_in_stage) asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
+                if (P.aop_in_stage) __syncwarp();     // as above: rows 0-31 are box 0, rows 32-63 box 1
 #pragma unroll
                 for (int r = 0; r < 16; ++r) mx = max(mx, __float_as_uint(v[r]) & 0x7fffffffu);
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
