@@ -157,7 +157,6 @@ cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, con
                            int kcap, int64_t n, double* T, int64_t ldt, double* scratch,
                            int refine_steps, int low_solve, cudaStream_t s);
 size_t solve_T_scratch_doubles(int kcap, int64_t n);
-size_t solve_smem_bytes(int kcap, size_t ts_bytes);
 // Batched mixed-precision solve (FP32 solves, FP64 residual): one CTA of `warps` warps
 // per unit; kmax bounds the ranks of the listed tasks (<= 128).
 cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* units, int nunits, int kmax,

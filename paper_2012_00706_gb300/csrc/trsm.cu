@@ -342,10 +342,6 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
     }
 }
 
-size_t solve_smem_bytes(int kcap, size_t ts_bytes) {
-    return static_cast<size_t>(kcap) * kcap * (sizeof(double) + ts_bytes) + kcap * ts_bytes + 16;
-}
-
 template <int KQ>
 static cudaError_t launch_batched_solve(const BatchTask* tasks, const SolveUnit* units, int nunits, int kmax,
                                         int warps, const double* R_base, const int32_t* J_base,
