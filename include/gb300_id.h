@@ -189,8 +189,8 @@ id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t 
                           int32_t precision, uint16_t* pieces, int32_t* shifts,
                           int32_t* info, void* stream);
 
-/* Adjoint of the column ID with the pivot set J held fixed (north-star
- * differentiation; the paper does not differentiate the ID), FP32.
+/* Adjoint of the column ID with the pivot set J held fixed (the
+ * differentiable form; the paper does not differentiate the ID), FP32.
  * The map is the fixed-pivot least-squares ID: X = A(:,J[0:k]),
  * C = A(:,J[k:n]), T = X^+ C (what a column-pivoted QR of A gives as
  * R11^-1 R12, Sec. 1.1), A_hat = A(:,J[0:k]) P (Algorithm 1).
@@ -222,7 +222,7 @@ id_status_t id_reconstruct(int64_t batch, const float* A, int64_t m, int64_t n, 
 
 /* ------------------------------------------------------------ batched IDs
  * Many independent mixed-precision IDs of uneven sizes in one stream-ordered
- * launch sequence (spec batching; the paper factors one matrix at a
+ * launch sequence (the batched form; the paper factors one matrix at a
  * time).  Matrix i is m[i] x n[i] (column-major, lda[i]) with target rank
  * k[i]; it is sketched with the leading ell_i = min(k[i] + oversample, m[i])
  * rows and m[i] columns of one shared low-precision Gaussian Omega, then

@@ -226,7 +226,7 @@ def test_sketch_lowp_nonfinite_flag(orc):
 
 @pytest.mark.parametrize("m,n,k", [(60, 40, 7), (33, 33, 11), (200, 50, 1)])
 def test_exact_rank_reconstruction(orc, m, n, k):
-    """North-star pin: exact rank k => relative error <= 1e-12 (2-norm and Frobenius)."""
+    """Exact rank k => relative reconstruction error <= 1e-12 (2-norm and Frobenius)."""
     a = rand_lowrank(m, n, k, seed=m + n + k)
     out = orc.interp_decomp(a, k=k)
     assert out["k"] == k and out["info"] == 0
@@ -341,7 +341,7 @@ def test_brute_force_tiny(orc):
 
 
 def test_cpqr_bound_config1_shape(orc):
-    """Spec bound ||A - A(:,J)T||_2 <= sqrt(1+k(n-k)) 2^k sigma_{k+1} at a
+    """The pivoted-QR ID bound ||A - A(:,J)T||_2 <= sqrt(1+k(n-k)) 2^k sigma_{k+1} at a
     config-1-like decay (smaller size)."""
     m, n, k = 300, 150, 20
     sigma = 10.0 ** (-np.arange(1, n + 1) / 25.0)
