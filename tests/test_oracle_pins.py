@@ -88,6 +88,31 @@ def test_sec3_lemma1_bound_fast_k51(orc):
     assert abs(orc.lemma1_bound(51, 1000, sig[51]) - val) > tol * val
 
 
+# ------------------------------------------------------------- 2-norm
+
+@pytest.mark.parametrize("m,n", [(4001, 1000), (1000, 4001), (2001, 2001)])
+def test_two_norm_large_branch_matches_lapack(orc, m, n):
+    """Just past the size where oracle.two_norm leaves LAPACK's SVD for the Gram
+    matrix's largest eigenvalue: both branches agree with numpy's SVD-based 2-norm,
+    for tall, wide and square inputs (a transposed Gram product or a wrong
+    eigenvalue index would fail)."""
+    rng = np.random.default_rng(m + 7 * n)
+    x = rng.standard_normal((m, n)) * np.linspace(1.0, 3.0, n)[None, :]
+    assert min(x.shape) > 2000 or x.size > 4_000_000
+    ref = float(np.linalg.norm(x, 2))
+    assert abs(orc.two_norm(x) - ref) <= 1e-12 * ref
+
+
+def test_two_norm_known_singular_values(orc):
+    """A = U diag(sigma) V^T with sigma_1 = 3, sigma_2 = 2.9999 (a close runner-up,
+    which slows a power iteration): the 2-norm is sigma_1 in both branches."""
+    sig = np.array([3.0, 2.9999] + [1.0 / i for i in range(3, 60)])
+    for m, n in [(300, 200), (5000, 900)]:
+        a = wl.lowrank(m, n, sig, 17)
+        assert abs(orc.two_norm(a) - 3.0) <= 1e-12 * 3.0
+        assert abs(orc.two_norm(np.asfortranarray(a.T)) - 3.0) <= 1e-12 * 3.0
+
+
 # ------------------------------------------------------------ sketch, cast
 
 def test_sketch_f64_matches_blas(orc):
