@@ -4,19 +4,23 @@
 Workload (one step = one full ID: sketch -> pivoted QR -> coefficient solve):
 A = U diag(sigma) V^T, 20000 x 2000 FP64, sigma_i = i^-2 (seeded orthonormal
 U, V); Gaussian Omega of 110 x 20000 rounded to bfloat16; rank k = 100.
-Mixed precision by default: power-of-two scaled bfloat16 sketch on the
-tensor cores with FP32 accumulation, FP32 pivoted QR of Y, FP64 T solve with
-one refinement step.  Inputs stay resident in HBM for the timed loop (A is
-320 MB, larger than the 129 MB L2, so no flush is needed); `e2e` repeats the
-measurement with A and Omega copied from pinned host memory each step (double-buffered:
-the copy of the next ID overlaps the current one's compute) and the
-result read back.
+The headline form is the matched-error one (d = ||A_hat_M - A_hat_D||_2 /
+||A||_2 <= 1e-6 against the plain FP64 GPU ID): A scaled by powers of two and
+split into three bfloat16 pieces, sketched on the tensor cores with FP32
+accumulation, FP32 pivoted QR of Y, FP64 T solve with one refinement step.
+Inputs stay resident in HBM for the timed loop (A is 320 MB, larger than the
+129 MB L2, so no flush is needed); `e2e` repeats the measurement with A and
+Omega copied from pinned host memory each step (double-buffered: the copy of
+the next ID overlaps the current one's compute) and the result read back.
 
 Also reported: the plain FP64 GPU ID on the same matrix and Omega (FP64
-sketch by DFMA), the 3-piece bfloat16 sketch (the matched-error form), their
-errors, the roofline of the dominant kernel, sampled SM clocks, and the FP64
-CPU oracle timed on the host (`cpu_baseline`).  `--impl reference` times the
-oracle alone as the reference arm.
+sketch by DFMA), the single-piece bfloat16 sketch (faster, not at matched
+error), their errors, the roofline of the dominant kernel against peaks
+measured in the same run, sampled SM clocks, the other workloads (plain FP64
+ID of a 1000 x 500 matrix, the 65536 x 1000 snapshot matrix at tolerance
+1e-6, the 512-matrix uneven batch, the differentiable 64 x 2048 x 512 batch)
+and the FP64 CPU oracle timed on the host (`cpu_baseline`).  `--impl
+reference` times the oracle alone as the reference arm.
 
 Under torchrun (N > 1) every rank runs its own IDs (independent problems, no
 collective on the data path); value = all ranks' IDs / the slowest rank's time.
@@ -101,11 +105,12 @@ def ncu_traffic(profile="sketch_lowp_20000x2000.md", files=("sketch.cu", "common
         return None
 
 
-# FP32 and FP64 ALU peaks derived from the unit counts and the maximum SM clock:
-# 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz, and the FP64 rate of 1.2 TFLOP/s
-# measured on this GPU with a DFMA loop (the nominal figure is 1.25).
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.2
+def alu_peaks(gid):
+    """FP32 (FFMA) and FP64 (DFMA) rates of this GPU in TFLOP/s, measured now by the
+    library's probe (independent FMA chains on every SM)."""
+    return {"fp32_tflops": gid.probe_fma_peak("fp32"), "fp64_tflops": gid.probe_fma_peak("fp64"),
+            "source": "measured in this run: id_probe_fma_peak (8 independent FMA chains per thread, "
+                      "2 x 1024-thread CTAs per SM, CUDA-event time of one ~30 ms launch)"}
 
 
 def cpqr_flops(r, n, k):
@@ -400,15 +405,177 @@ def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0, world
     return out
 
 
+def _time_id(gid, dev, A, k, reps, **kw):
+    """Median time of one id_factor call (ms) over `reps` CUDA-graph replays, the stage split
+    of one plain launch (stage events), and the result of the last call."""
+    import torch
+    om = kw.get("omega")
+    ws = torch.empty(gid.id_workspace_size(A.shape[0], A.shape[1], A.dtype, k=k, sketch=om is not None,
+                                           ell=om.shape[0] if om is not None else 0, **kw),
+                     dtype=torch.uint8, device=dev)
+    kcap = kw.get("k_max") or k
+    n = A.shape[1]
+    out = (torch.empty(n, dtype=torch.int32, device=dev),
+           torch.empty((max(n - 1, 1), kcap), dtype=torch.float64, device=dev).t(),
+           torch.zeros(2, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.float64, device=dev))
+    kk = None if kw.get("tol") else k
+
+    def one(stream=None):
+        gid.id_factor(A, kk, workspace=ws, out=out, sync=False, stream=stream, **kw)
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(gs):
+        with torch.cuda.graph(g, stream=gs):
+            one(gs)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    cur = torch.cuda.current_stream()
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        g.replay()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    gid.set_stage_events(evs)
+    one()
+    gid.set_stage_events(None)
+    torch.cuda.synchronize()
+    names = ["sketch_kernel", "sketch_reduce", "cpqr", "solve_T", "tail"]
+    stages = {nm: evs[j].elapsed_time(evs[j + 1]) for j, nm in enumerate(names)}
+    return statistics.median(ts), stages, out
+
+
+def config1_leg(gid, wl, dev, peaks, reps=20):
+    """Plain FP64 ID of a 1000 x 500 matrix (sigma_i = 10^(-i/25), k = 50, no sketch), and
+    the FP32 pivoted QR of the same matrix (the mixed-single ID of Algorithm 2), one ID at
+    a time (CUDA-graph replay)."""
+    import torch
+    c = wl.config1()
+    m, n, k = c["m"], c["n"], c["k"]
+    A = torch.from_numpy(c["A"]).to(dev)
+    flops = id_flops(m, n, 0, k, sketch=False)
+    out = {"workload": "A 1000x500 FP64, sigma_i = 10^(-i/25), k = 50, no sketch; seed 1", "flops_per_id": flops}
+    for prec, peak in (("plain_f64", peaks["fp64_tflops"]), ("plain_f32", peaks["fp32_tflops"])):
+        ms, stages, res = _time_id(gid, dev, A, k, reps, precision=prec)
+        kout = int(res[2][0].item())
+        cq_flops = cpqr_flops(m, n, k)
+        ach = cq_flops / (stages["cpqr"] / 1e3) / 1e12
+        err = gid.id_factor(A, k, precision=prec, estimate_error=True).err
+        out[prec] = {"ms_per_id": ms, "ids_per_s": 1e3 / ms, "tflops": flops / (ms / 1e3) / 1e12,
+                     "stages_ms": stages, "k": kout, "err_fro": err,
+                     "cpqr_roofline": {"kernel": "k_cpqr_grid", "bound": "alu", "achieved": ach, "peak": peak,
+                                       "unit": "TFLOP/s", "frac": ach / peak,
+                                       "algorithmic_flops": cq_flops}}
+    return out
+
+
+def config3_leg(gid, wl, dev, peaks, reps=3):
+    """The 65536 x 1000 FP32 snapshot matrix (travelling sinusoids plus 1e-6 noise) at
+    tolerance 1e-6: the plain FP64 ID of A itself against sketched mixed IDs (half sketch,
+    three-piece bfloat16 sketch) with ell = k_max + 10."""
+    import torch
+    c = wl.config3()
+    m, n, tol = c["m"], c["n"], c["tol"]
+    A = torch.from_numpy(c["A"]).to(dev)
+    kmax = 150
+    ell = kmax + 10
+    out = {"workload": "snapshot matrix 65536x1000 FP32 (40 travelling sinusoids, amplitudes 0.8^j, "
+                       "1e-6 noise; seed 3), relative Frobenius tolerance 1e-6, k_max 150",
+           "a_bytes": 4 * m * n}
+    ms, stages, res = _time_id(gid, dev, A, None, reps, tol=tol, k_max=200, precision="plain_f64")
+    k = int(res[2][0].item())
+    err = gid.id_factor(A, tol=tol, k_max=200, precision="plain_f64", estimate_error=True).err
+    cq = cpqr_flops(m, n, k)
+    ach = cq / (stages["cpqr"] / 1e3) / 1e12
+    out["plain_f64"] = {"ms_per_id": ms, "ids_per_s": 1e3 / ms, "k": k, "err_fro": err,
+                        "tflops": id_flops(m, n, 0, k, sketch=False) / (ms / 1e3) / 1e12, "stages_ms": stages,
+                        "cpqr_roofline": {"kernel": "k_cpqr_grid", "bound": "alu", "achieved": ach,
+                                          "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                                          "frac": ach / peaks["fp64_tflops"], "algorithmic_flops": cq,
+                                          "hbm_bytes_per_step_min": 16 * m * n}}
+    for prec, fmt in (("mixed_f16", "f16"), ("mixed_bf16x3", "bf16")):
+        _, bits = wl.gaussian_omega(ell, m, 3003, fmt)
+        om = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16 if fmt == "bf16" else torch.float16)
+        ms, stages, res = _time_id(gid, dev, A, None, max(reps, 10), tol=tol, k_max=kmax, precision=prec, omega=om)
+        k = int(res[2][0].item())
+        err = gid.id_factor(A, tol=tol, k_max=kmax, precision=prec, omega=om, estimate_error=True).err
+        sk_bytes = sketch_bytes(m, n, ell, a_bytes=4)
+        out[prec] = {"ms_per_id": ms, "ids_per_s": 1e3 / ms, "k": k, "err_fro": err, "ell": ell,
+                     "tflops": id_flops(m, n, ell, k) / (ms / 1e3) / 1e12, "stages_ms": stages,
+                     "sketch_hbm_frac": sk_bytes / (stages["sketch_kernel"] / 1e3) / 1e9 / measured_peaks()[0],
+                     "speedup_vs_plain_f64": out["plain_f64"]["ms_per_id"] / ms}
+    return out
+
+
+def config5_leg(gid, wl, dev, peaks, reps=5):
+    """Differentiable IDs: 64 FP32 matrices 2048 x 512 of rank 32 (sigma_i = 10^(-i/16)),
+    k = 32, loss ||A_hat - B||_F^2 with Gaussian B; forward (pivoted QR, T, reconstruction)
+    and backward (the fixed-pivot adjoint) timed separately with CUDA events."""
+    import torch
+    c = wl.config5()
+    k, m, n = c["k"], c["m"], c["n"]
+    batch = c["A"].shape[0]
+    A = torch.from_numpy(np.ascontiguousarray(c["A"].transpose(0, 2, 1))).to(dev).transpose(1, 2)
+    B = torch.from_numpy(c["B"]).to(dev)
+    A.requires_grad_(True)
+
+    def fwd():
+        Ahat, T, J = gid.IDFunction.apply(A, k)
+        return ((Ahat - B) ** 2).sum()
+
+    for _ in range(2):
+        loss = fwd()
+        loss.backward()
+        A.grad = None
+    torch.cuda.synchronize()
+    tf, tb = [], []
+    cur = torch.cuda.current_stream()
+    for _ in range(reps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(cur)
+        loss = fwd()
+        e1.record(cur)
+        loss.backward()
+        e2.record(cur)
+        torch.cuda.synchronize()
+        tf.append(e0.elapsed_time(e1))
+        tb.append(e1.elapsed_time(e2))
+        A.grad = None
+    f_fwd = batch * (id_flops(m, n, 0, k, sketch=False) + 2.0 * m * k * (n - k))
+    f_bwd = batch * 8.0 * m * n * k
+    fms, bms = statistics.median(tf), statistics.median(tb)
+    return {"workload": "64 x (2048x512 FP32), exact rank 32, sigma_i = 10^(-i/16), k = 32, loss ||A_hat - B||_F^2; "
+                        "seed 5",
+            "forward_ms": fms, "backward_ms": bms, "ids_per_s_forward": batch / (fms / 1e3),
+            "forward_tflops": f_fwd / (fms / 1e3) / 1e12, "backward_tflops": f_bwd / (bms / 1e3) / 1e12,
+            "backward_flops_model": "8 m n k per matrix (thin QR of the skeleton, the projections of the "
+                                    "cotangent and their products)",
+            "backward_frac_of_fp32": f_bwd / (bms / 1e3) / 1e12 / peaks["fp32_tflops"],
+            "note": "forward includes the host read of the 64 ranks (one synchronisation per batch)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="mixed_bf16")
+    ap.add_argument("--precision", default="mixed_bf16x3",
+                    help="form of the headline stream (mixed_bf16x3 meets d <= 1e-6 against plain FP64)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/matched/e2e/cpu legs")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 1000x500 plain, 65536x1000 snapshot and differentiable-batch legs")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched leg (a profiling case) and print its JSON")
     ap.add_argument("--batch-count", type=int, default=512, help="matrices in the batched leg")
@@ -437,6 +604,7 @@ def main():
             dist.barrier()
 
     gid.load()
+    peaks = alu_peaks(gid)
     if args.batched_only:
         line = {"batched": batched_leg(gid, wl, dev, torch.cuda.current_stream(), count=args.batch_count,
                                        loops=False, lean_steps=args.steps)}
@@ -678,11 +846,12 @@ def main():
     cq_ms = stages["cpqr"]
     cq_flops = cpqr_flops(ELL, N, K)
     cq_ach = cq_flops / (cq_ms / 1e3) / 1e12
-    cpqr_roof = {"kernel": "k_cpqr_cluster", "bound": "alu", "achieved": cq_ach, "peak": FP32_PEAK_TFLOPS,
-                 "unit": "TFLOP/s", "frac": cq_ach / FP32_PEAK_TFLOPS,
+    fp32_peak = peaks["fp32_tflops"]
+    cpqr_roof = {"kernel": "k_cpqr_cluster", "bound": "alu", "achieved": cq_ach, "peak": fp32_peak,
+                 "unit": "TFLOP/s", "frac": cq_ach / fp32_peak,
                  "traffic": ncu_traffic("cpqr_solve_110x2000.md", ("cpqr_cluster.cu", "common.cuh")),
                  "algorithmic_flops": cq_flops, "kernel_ms": cq_ms,
-                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                 "peak_source": "FP32 FFMA rate " + peaks["source"],
                  "note": "latency-bound: k sequential cluster-wide pivot steps"}
     # the roofline object describes the stage that takes the longest
     roofline = cpqr_roof if cq_ms >= sk_ms else sketch_roof
@@ -700,6 +869,7 @@ def main():
         "tflops": id_flops(M, N, ELL, K) * value / 1e12,
         "latency_ms_per_id": seq_ms / args.steps,
         "stages_ms": stages, "roofline": roofline, "sketch_roofline": sketch_roof, "cpqr_roofline": cpqr_roof,
+        "alu_peaks": peaks,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks,
     }
@@ -721,19 +891,23 @@ def main():
         line["e2e"] = {"value": world * e2e_steps / (e2e_ms / 1e3), "unit": "IDs/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-        # ---- plain FP64 GPU ID (same A, same Omega in FP64) and the matched-error form, each
-        # one ID at a time (latency) and as a stream with the same number of IDs in flight
+        # ---- plain FP64 GPU ID (same A, same Omega in FP64) and the other mixed form (a single
+        # bfloat16 piece: faster, not at matched error), each one ID at a time (latency) and as a
+        # stream with the same number of IDs in flight
+        other = "mixed_bf16" if args.precision != "mixed_bf16" else "mixed_bf16x3"
         depth = max(1, args.inflight)
         p_steps = max(3, min(args.steps, 5))
         p_ms, out_plain, p_stages = run_loop("plain_f64", omega64, p_steps, 1, stage=True)
         p_flight_ms, _ = run_inflight("plain_f64", omega64, depth, 1, depth)
-        x_ms, out_x3, _ = run_loop("mixed_bf16x3", omega, args.steps, 2, graph=True)
-        x_flight_ms, _ = run_inflight("mixed_bf16x3", omega, args.steps, 2, depth)
+        o_ms, out_other, _ = run_loop(other, omega, args.steps, 2, graph=True)
+        o_flight_ms, _ = run_inflight(other, omega, args.steps, 2, depth)
         plain_ids = depth / (p_flight_ms / 1e3)
-        x3_ids = args.steps / (x_flight_ms / 1e3)
+        other_ids = args.steps / (o_flight_ms / 1e3)
         line["plain_f64"] = {"ids_per_s": plain_ids, "latency_ms_per_id": p_ms / p_steps, "stages_ms": p_stages,
-                             "tflops": id_flops(M, N, ELL, K) * plain_ids / 1e12, "inflight": depth}
-        line["mixed_bf16x3"] = {"ids_per_s": x3_ids, "latency_ms_per_id": x_ms / args.steps, "inflight": depth}
+                             "tflops": id_flops(M, N, ELL, K) * plain_ids / 1e12, "inflight": depth,
+                             "sketch_fp64_frac": 2.0 * ELL * M * N / (p_stages["sketch_kernel"] / 1e3) / 1e12
+                             / peaks["fp64_tflops"]}
+        line[other] = {"ids_per_s": other_ids, "latency_ms_per_id": o_ms / args.steps, "inflight": depth}
 
         # ---- accuracy (FP64 on the GPU): relative 2-norm errors and distances between IDs
         def ahat(out):
@@ -758,21 +932,30 @@ def main():
             return s
 
         na = norm2(A)
-        h_m, h_p, h_x = ahat(out_main), ahat(out_plain), ahat(out_x3)
+        h_m, h_p, h_o = ahat(out_main), ahat(out_plain), ahat(out_other)
+        d_main = norm2(h_m - h_p) / na
         line["accuracy"] = {
-            "e_mixed": norm2(A - h_m) / na, "e_plain_f64": norm2(A - h_p) / na, "e_bf16x3": norm2(A - h_x) / na,
-            "d_mixed_vs_plain": norm2(h_m - h_p) / na, "d_bf16x3_vs_plain": norm2(h_x - h_p) / na,
-            "same_skeleton_bf16x3": bool(torch.equal(out_x3[0][:K], out_plain[0][:K])),
+            "form": args.precision, "e": norm2(A - h_m) / na, "e_plain_f64": norm2(A - h_p) / na,
+            f"e_{other}": norm2(A - h_o) / na, "d_vs_plain": d_main, f"d_{other}_vs_plain": norm2(h_o - h_p) / na,
+            "same_skeleton_as_plain": bool(torch.equal(out_main[0][:K], out_plain[0][:K])),
+            "matched_1e-6": d_main <= 1e-6,
+            "how": "2-norms by 60 power iterations in FP64 on the GPU; d = ||A_hat - A_hat_plain||_2 / ||A||_2",
         }
-        d3 = line["accuracy"]["d_bf16x3_vs_plain"]
         lat_plain = p_ms / p_steps
         line["speedup_vs_plain_f64"] = {
-            "throughput_mixed_bf16": value / world / plain_ids,
-            "throughput_mixed_bf16x3": x3_ids / plain_ids,
-            "latency_mixed_bf16": lat_plain / (seq_ms / args.steps),
-            "latency_mixed_bf16x3": lat_plain / (x_ms / args.steps),
-            "matched_1e-6_form": "mixed_bf16x3" if d3 <= 1e-6 else None}
-        del h_m, h_p, h_x
+            f"throughput_{args.precision}": value / world / plain_ids,
+            f"throughput_{other}": other_ids / plain_ids,
+            f"latency_{args.precision}": lat_plain / (seq_ms / args.steps),
+            f"latency_{other}": lat_plain / (o_ms / args.steps),
+            "matched_1e-6_form": args.precision if d_main <= 1e-6 else None}
+        del h_m, h_p, h_o
+
+        # ---- the other workloads: plain FP64 ID of a 1000 x 500 matrix, the 65536 x 1000
+        # snapshot matrix at tolerance 1e-6, the differentiable 64 x 2048 x 512 batch
+        if not args.no_configs:
+            line["plain_1000x500"] = config1_leg(gid, wl, dev, peaks)
+            line["snapshot_65536x1000"] = config3_leg(gid, wl, dev, peaks)
+            line["differentiable_64x2048x512"] = config5_leg(gid, wl, dev, peaks)
 
         # ---- the uneven batch: 512 FP64 matrices in one launch sequence (graph-captured)
         if not args.no_batched:

@@ -60,7 +60,8 @@ typedef enum {
 
 /* Arithmetic of the factorisation.
  *   PLAIN_F64     everything in FP64 (Algorithm 1).  With a sketch, Omega is FP64.
- *   PLAIN_F32     pivoted QR in FP32 of the given matrix (no sketch), T in FP64.
+ *   PLAIN_F32     pivoted QR in FP32 of the given matrix (no sketch; FP64 input is
+ *                 rounded to FP32 as it is loaded), T in FP64.
  *   MIXED_BF16    Algorithm 2 re-cast for GB300: A is scaled by powers of two per
  *                 (64-row block, column), rounded to bfloat16, sketched on the
  *                 tensor cores with FP32 accumulation; pivoted QR of Y in FP32;
@@ -130,7 +131,9 @@ id_status_t id_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n,
  * Errors: ID_ERR_ARG for m, n < 1, lda < m, k outside [1, min(rows, n)],
  * ell outside [k, min(m, ID_MAX_ELL)], null outputs, precision / dtype
  * combinations not listed above (mixed precisions require sketch = 1;
- * PLAIN_F32 requires a_dtype = ID_F32 and sketch = 0). */
+ * PLAIN_F32 requires sketch = 0 and takes A as ID_F32, or as ID_F64 whose
+ * values are rounded to FP32 (nearest even) when the pivoted QR loads them;
+ * PLAIN_F64 with a sketch requires ID_F64). */
 id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
                       const id_opts_t* opts,
                       int32_t* J, double* T, int64_t ldt, int32_t* k_out, int32_t* info,
@@ -159,8 +162,10 @@ id_status_t id_sketch(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
  * ID_NOALLOC_SCRATCH_BYTES bytes that every GPU loading this library holds
  * until the process exits.
  *   - Returns ID_ERR_WORKSPACE, without launching anything, when the problem's
- *     scratch would exceed ID_NOALLOC_SCRATCH_BYTES (id_sketch_workspace_size
- *     gives the figure); other errors as id_sketch.
+ *     split-K scratch exceeds ID_NOALLOC_SCRATCH_BYTES; that scratch is
+ *     id_sketch_workspace_size minus the 512 bytes of alignment slack it adds
+ *     for a caller's buffer (the static array is already aligned).  Other
+ *     errors as id_sketch.
  *   - The array is shared by all calls on a device and keeps the last call's
  *     contents.  Calls that overlap on the GPU race on it: serialise them
  *     (one stream, or explicit ordering between streams and host threads).
@@ -344,6 +349,14 @@ id_status_t id_batch_shard(int32_t batch, const int64_t* m, const int64_t* n, co
  * Stages a call does not run record at the same point as the previous one.
  * count <= 0 or events == NULL switches recording off.  Always ID_OK. */
 id_status_t id_set_stage_events(void* const* events, int32_t count);
+
+/* Profiling aid (not part of the computation): the FP32 (which = 0, FFMA) or FP64
+ * (which = 1, DFMA) multiply-add rate of the current GPU in TFLOP/s (host output),
+ * measured as eight independent FMA chains per thread on a grid filling every SM,
+ * flops over the CUDA-event time of one launch after a warm-up launch (about 30 ms).
+ * These are the peaks the ALU-bound kernels' rooflines are reported against.
+ * Synchronises the stream.  Errors: ID_ERR_ARG, ID_ERR_CUDA. */
+id_status_t id_probe_fma_peak(int32_t which, double* tflops, void* stream);
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char* id_status_string(id_status_t status);

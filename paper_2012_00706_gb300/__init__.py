@@ -20,7 +20,7 @@ import torch
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
     "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
-    "BatchPlan", "shard_batch",
+    "BatchPlan", "shard_batch", "probe_fma_peak",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -106,6 +106,8 @@ def load():
         lib.id_batch_autotune.argtypes = [p, p, i64, p, p, p, p, p, sz, p, i32, ctypes.c_char_p,
                                           ctypes.POINTER(ctypes.c_double)]
         lib.id_batch_shard.argtypes = [i32, p, p, p, i32, i32, p, p]
+        lib.id_probe_fma_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), p]
+        lib.id_probe_fma_peak.restype = ctypes.c_int
         for name in ("id_batch_plan_create", "id_batch_plan_query", "id_batch_workspace_size", "id_batch_bind",
                      "id_factor_batched", "id_batch_autotune", "id_batch_shard"):
             getattr(lib, name).restype = ctypes.c_int
@@ -234,6 +236,15 @@ def id_factor(A: torch.Tensor, k: int | None = None, *, tol: float | None = None
     return IDResult(J, T[:kk, : n - kk], kk, info, float(err.item()) if estimate_error else None)
 
 
+def probe_fma_peak(which: str = "fp32", stream=None) -> float:
+    """Measured FFMA ("fp32") or DFMA ("fp64") rate of the current GPU in TFLOP/s
+    (a profiling aid: the peak the ALU-bound kernels' rooflines use).  Synchronises."""
+    t = ctypes.c_double(0.0)
+    _check(load().id_probe_fma_peak({"fp32": 0, "fp64": 1}[which], ctypes.byref(t), _stream_ptr(stream)),
+           "id_probe_fma_peak")
+    return t.value
+
+
 def set_stage_events(events) -> None:
     """Record these torch.cuda.Event objects at id_factor's stage boundaries (None: stop)."""
     lib = load()
@@ -360,15 +371,23 @@ class IDFunction(torch.autograd.Function):
         squeeze = A.dim() == 2
         a = A.unsqueeze(0) if squeeze else A
         batch, m, n = a.shape
-        Js, Ts = [], []
+        dev = a.device
+        # every matrix is factored into preallocated outputs with one shared workspace,
+        # stream-ordered, and the ranks are read back once for the whole batch
+        ws = torch.empty(id_workspace_size(m, n, a.dtype, k=k, precision="plain_f32"), dtype=torch.uint8,
+                         device=dev)
+        Jt = torch.empty((batch, n), dtype=torch.int32, device=dev)
+        Tall = torch.empty((batch, max(n - k, 1), k), dtype=torch.float64, device=dev)
+        small = torch.zeros((batch, 2), dtype=torch.int32, device=dev)
+        err = torch.zeros(1, dtype=torch.float64, device=dev)
         for b in range(batch):
-            res = id_factor(a[b], k, precision="plain_f32")
-            if res.k != k:
-                raise IDError(f"matrix {b}: rank {res.k} < k = {k} (info {res.info})")
-            Js.append(res.J)
-            Ts.append(res.T)
-        Jt = torch.stack(Js)
-        Tt = torch.stack([t.t().contiguous().t() for t in Ts])
+            id_factor(a[b], k, precision="plain_f32", workspace=ws, out=(Jt[b], Tall[b], small[b], err), sync=False)
+        kinfo = small.cpu()
+        bad = (kinfo[:, 0] != k).nonzero()
+        if bad.numel():
+            b = int(bad[0, 0])
+            raise IDError(f"matrix {b}: rank {int(kinfo[b, 0])} < k = {k} (info {int(kinfo[b, 1])})")
+        Tt = Tall[:, : n - k, :].transpose(1, 2)          # (batch, k, n - k), column-major per matrix
         Ahat = id_reconstruct(a, Jt, Tt, k)
         ctx.save_for_backward(a, Jt, Tt)
         ctx.k = k

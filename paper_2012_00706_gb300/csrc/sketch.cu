@@ -289,6 +289,16 @@ struct Ring {
     }
 };
 
+// After a watchdog abort: wait (bounded) until the last loads a producer issued into a ring
+// of n buffers have landed, so that no bulk copy still writes into this CTA's shared memory
+// when it leaves.  Load i went to slot i % n and completes phase (i / n) & 1 of its barrier;
+// loads older than the last n were consumed before their slot was reused.
+__device__ __forceinline__ void drain_issued(uint64_t* full, int n, int issued, uint64_t limit_ns) {
+    volatile int keep_waiting = 0;
+    for (int i = max(0, issued - n); i < issued; ++i)
+        mbar_wait(&full[i % n], static_cast<uint32_t>((i / n) & 1), &keep_waiting, limit_ns);
+}
+
 // BATCH = false: one ID, CTA (x, y) computes 128-column tile x over row slab y of A.
 // BATCH = true: CTA b computes unit b of the batch table (a tile and row slab of one
 // matrix), reading that matrix through its own tensor map in global memory.
@@ -395,6 +405,7 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                                            static_cast<int32_t>(col0));
             }
             Ring rs(NS);
+            int issued = 0;
             for (int i = 0; i < nloc; ++i, rs.next()) {
                 const int64_t c = ch_begin + i;
                 const int s = rs.slot;
@@ -411,14 +422,17 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                         tma_load_2d(dst + (size_t)sl * kSlabBytes, amap,
                                     static_cast<int32_t>(c * kChunkRows + sl * slab_rows),
                                     static_cast<int32_t>(col0), &stage_full[s]);
+                    issued = i + 1;
                 }
             }
+            if (*abort) drain_issued(stage_full, NS, issued, P.limit_ns);
         }
     } else if (warp == 3) {
         // ---------------- Omega producer: one swizzled Omega tile per chunk
         if (lane == 0) {
             prefetch_tensormap(&tm_omega);
             Ring ro(NO);
+            int issued = 0;
             for (int i = 0; i < nloc; ++i, ro.next()) {
                 const int64_t c = ch_begin + i;
                 const int o = ro.slot;
@@ -426,7 +440,9 @@ k_sketch_lowp(const __grid_constant__ CUtensorMap tm_omega, const __grid_constan
                 mbar_arrive_expect_tx(&omg_full[o], P.omega_tile_bytes);
                 tma_load_2d(S.omega + (size_t)o * P.omega_tile_bytes, &tm_omega,
                             static_cast<int32_t>(c * kChunkRows), 0, &omg_full[o]);
+                issued = i + 1;
             }
+            if (*abort) drain_issued(omg_full, NO, issued, P.limit_ns);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (one thread)

@@ -10,6 +10,12 @@
 //
 // k <= 128: one warp per column of T, the column in registers (lane l holds
 // rows l, l+32, ...), R11 in shared memory; otherwise one thread per column.
+//
+// An FP32 solve refined once cuts the error by about kappa(R11) u32 per step, so
+// the mixed path estimates kappa(R11) from the ratio of R11's largest and smallest
+// diagonal magnitudes (a lower bound of the condition number) and, when
+// kappa u32 exceeds 1e-2, solves and refines in FP64 instead (one ID), or takes
+// more refinement steps (batched IDs).
 #include "common.cuh"
 #include "internal.h"
 
@@ -166,22 +172,44 @@ __device__ __forceinline__ void stage_r11(const double* __restrict__ R, int64_t 
     }
 }
 
-template <typename TS, int KQ>
-__global__ void __launch_bounds__(kWarpSolveWarps * 32)
-k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
-               const int32_t* __restrict__ k_ptr, int64_t n, double* __restrict__ T, int64_t ldt,
-               int refine_steps) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    const int k = *k_ptr;
-    if (k <= 0) return;
-    // R11 (k x k, column-major) in the solve precision TS: FP64 for the plain path; FP32
-    // for the mixed path, whose R is FP32 (its refinement residual works on float pairs)
-    double* r11d = reinterpret_cast<double*>(sm);
-    TS* r11s = reinterpret_cast<TS*>(sm);
-    TS* rinv = r11s + static_cast<int64_t>(k) * k;
-    stage_r11<TS>(R, ldr, J, k, r11s, rinv);
+// kappa u32 > 1e-2, i.e. max |R_jj| > kIllRatio min |R_jj| over the diagonal of R11.
+constexpr double kIllRatio = 1e-2 * 16777216.0;
+// Refinement steps of the batched FP32 solve when R11 is that ill-conditioned.
+constexpr int kIllRefineSteps = 6;
+
+// max |R(a, J[a])| > kIllRatio min |R(a, J[a])| over a < k, the same answer in every
+// thread of the block (and in every block: all read the same R).
+__device__ __forceinline__ bool r11_ill_conditioned(const double* __restrict__ R, int64_t ldr,
+                                                    const int32_t* __restrict__ J, int k) {
+    __shared__ double s_mx[32], s_mn[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double mx = 0.0, mn = INFINITY;
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+        const double d = fabs(__ldg(R + static_cast<int64_t>(__ldg(J + a)) * ldr + a));
+        mx = fmax(mx, d);
+        mn = fmin(mn, d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
     __syncthreads();
+    if (lane == 0) { s_mx[warp] = mx; s_mn[warp] = mn; }
+    __syncthreads();
+    mx = 0.0;
+    mn = INFINITY;
+    for (int w = 0; w < nw; ++w) { mx = fmax(mx, s_mx[w]); mn = fmin(mn, s_mn[w]); }
+    return mx > kIllRatio * mn;
+}
+
+// The columns of T this warp owns, with R11 staged in shared memory in precision TS.
+template <typename TS, int KQ>
+__device__ __forceinline__ void solve_columns(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+                                              int k, int64_t n, double* __restrict__ T, int64_t ldt, int refine_steps,
+                                              const TS* r11s, const TS* rinv) {
     const int lane = threadIdx.x & 31;
+    const double* r11d = reinterpret_cast<const double*>(r11s);
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     for (int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n - k;
          c += nwarps) {
@@ -242,10 +270,40 @@ k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
     }
 }
 
+// TS = double: the plain path.  TS = float: the mixed path, whose R is FP32 (R11 in FP32,
+// float-pair refinement residual), unless R11 is ill-conditioned (r11_ill_conditioned):
+// then the FP64 solve and residual, on the same FP64-stored R.  Shared memory is sized
+// for an FP64 copy of R11 in both cases.
+template <typename TS, int KQ>
+__global__ void __launch_bounds__(kWarpSolveWarps * 32)
+k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+               const int32_t* __restrict__ k_ptr, int64_t n, double* __restrict__ T, int64_t ldt,
+               int refine_steps) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int k = *k_ptr;
+    if (k <= 0) return;
+    if constexpr (std::is_same<TS, float>::value) {
+        if (r11_ill_conditioned(R, ldr, J, k)) {
+            double* r11s = reinterpret_cast<double*>(sm);
+            double* rinv = r11s + static_cast<int64_t>(k) * k;
+            stage_r11<double>(R, ldr, J, k, r11s, rinv);
+            __syncthreads();
+            solve_columns<double, KQ>(R, ldr, J, k, n, T, ldt, refine_steps, r11s, rinv);
+            return;
+        }
+    }
+    TS* r11s = reinterpret_cast<TS*>(sm);
+    TS* rinv = r11s + static_cast<int64_t>(k) * k;
+    stage_r11<TS>(R, ldr, J, k, r11s, rinv);
+    __syncthreads();
+    solve_columns<TS, KQ>(R, ldr, J, k, n, T, ldt, refine_steps, r11s, rinv);
+}
+
 template <typename TS, int KQ>
 static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
                                      int64_t n, double* T, int64_t ldt, int refine_steps, cudaStream_t s) {
-    const size_t smem = static_cast<size_t>(kcap) * kcap * sizeof(TS) + kcap * sizeof(TS) + 16;
+    // room for an FP64 copy of R11 (the mixed path switches to it for an ill-conditioned R11)
+    const size_t smem = static_cast<size_t>(kcap) * kcap * sizeof(double) + kcap * sizeof(double) + 16;
     auto kern = k_solve_T_warp<TS, KQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -297,6 +355,9 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
         if (threadIdx.x == 0) set_info(infos + su.task, kInfoBadTable);
         return;
     }
+    // an ill-conditioned R11 takes more refinement steps (each cuts the error by kappa u32)
+    const int steps = (refine_steps > 0 && r11_ill_conditioned(R, ldr, J, k))
+                          ? max(refine_steps, kIllRefineSteps) : refine_steps;
     float* r11s = reinterpret_cast<float*>(sm);                         // k x k, column-major
     float* rinv = r11s + static_cast<int64_t>(k) * k;
     stage_r11<float>(R, ldr, J, k, r11s, rinv);
@@ -317,7 +378,7 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
         double tt[KQ];
 #pragma unroll
         for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
-        for (int it = 0; it < refine_steps; ++it) {
+        for (int it = 0; it < steps; ++it) {
             double res[KQ];
             float th[KQ], tl[KQ];
 #pragma unroll

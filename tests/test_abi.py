@@ -73,6 +73,12 @@ def test_workspace_size_and_argument_checks(lib):
                omega_ld=20004)[0] == 1   # TMA needs a row stride that is a multiple of 8
     assert _ws(lib, 0, 1000, 500, rel_tol=1e-6, k_max=50)[0] == 0
     assert _ws(lib, 0, 1000, 500, rel_tol=1e-6, k_max=0)[0] == 1
+    # PLAIN_F32 pivots A itself: FP32 or FP64 storage (rounded to FP32 on load), no sketch
+    assert _ws(lib, 1, 1000, 500, k=50, precision=1)[0] == 0
+    assert _ws(lib, 0, 1000, 500, k=50, precision=1)[0] == 0
+    assert _ws(lib, 1, 20000, 2000, k=100, sketch=1, ell=110, precision=1, omega=fake_omega)[0] == 1
+    # the plain FP64 sketch takes FP64 data only
+    assert _ws(lib, 1, 20000, 2000, k=100, sketch=1, ell=110, precision=0, omega=fake_omega)[0] == 1
 
 
 def test_factor_rejects_null_outputs(lib):

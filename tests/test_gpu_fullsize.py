@@ -1,0 +1,135 @@
+"""GPU path against the FP64 oracle at the sizes the benchmark runs, through the C ABI.
+
+* Randomized ID of the benchmark matrix (A 20000 x 2000 FP64, sigma_i = i^-2,
+  k = 100, ell = 110, the benchmark's bfloat16 Omega): BF16 meets
+  e_M <= 1.1 e_D + 10 u_bf16 (E1); BF16x3 (the matched-error form the benchmark
+  headlines) has the oracle's pivots up to its first step whose two leading norms
+  are within 1e-3 of each other, e_M <= 1.1 e_D + 10 u32, and
+  d = ||A_hat_M - A_hat_D||_2 / ||A||_2 <= 1e-6 (E2, the Sec. 3.1 comparison).
+* Plain FP64 ID of the 65536 x 1000 snapshot matrix at tolerance 1e-6 (no sketch):
+  rank within one step of the oracle's, pivots equal up to the oracle's first step
+  whose two leading norms are within 1e-8, relative Frobenius residual at the
+  tolerance.
+* 64 matrices of the uneven 512-matrix batch (every 8th), factored as one batch:
+  each against the oracle's sketched ID with the same Omega.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+U_BF16 = 2.0 ** -8
+
+
+@pytest.fixture(scope="module")
+def gid():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2012_00706_gb300 as g
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return wl.config2()
+
+
+@pytest.fixture(scope="module")
+def cfg2_oracle(orc, cfg2):
+    return orc.interp_decomp(cfg2["A"], k=cfg2["k"], omega=cfg2["omega"])
+
+
+def first_close_step(gaps, thr, k):
+    close = gaps < thr
+    return int(np.argmax(close)) if np.any(close) else k
+
+
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_bf16x3"])
+def test_benchmark_matrix_mixed_vs_oracle(gid, dev, orc, cfg2, cfg2_oracle, precision):
+    a, k = cfg2["A"], cfg2["k"]
+    omega = torch.from_numpy(cfg2["omega_bits"].view(np.int16)).to(dev).view(torch.bfloat16)
+    res = gid.id_factor(torch.from_numpy(a).to(dev), k, precision=precision, omega=omega)
+    assert res.info == 0 and res.k == k
+    J, T = res.J.cpu().numpy(), res.T.cpu().numpy()
+    assert sorted(J.tolist()) == list(range(a.shape[1]))
+    ref = cfg2_oracle
+    e_m = orc.rel_err(a, J, T, k)
+    e_d = orc.rel_err(a, ref["J"], ref["T"], k)
+    if precision == "mixed_bf16":
+        assert e_m <= 1.1 * e_d + 10 * U_BF16, (e_m, e_d)
+        return
+    first = first_close_step(ref["gaps"], 1e-3, k)
+    assert first > 10
+    assert np.array_equal(J[:first], ref["J"][:first])
+    assert e_m <= 1.1 * e_d + 10 * U32, (e_m, e_d)
+    d = orc.id_distance(a, J, T, k, ref["J"], ref["T"], k)
+    assert d <= 1e-6, d
+
+
+def test_snapshot_plain_f64_full_size_vs_oracle(gid, dev, orc):
+    c = wl.config3()
+    a = c["A"]
+    a64 = a.astype(np.float64)
+    tol, kmax = 1e-6, 200
+    ref = orc.interp_decomp(a64, tol=tol, k_max=kmax, norm_mode="downdate")
+    res = gid.id_factor(torch.from_numpy(a).to(dev), tol=tol, k_max=kmax, precision="plain_f64",
+                        estimate_error=True)
+    assert res.info == 0 and ref["info"] == 0
+    assert ref["k"] < kmax
+    assert abs(res.k - ref["k"]) <= 1, (res.k, ref["k"])
+    J = res.J.cpu().numpy()
+    first = min(first_close_step(ref["gaps"], 1e-8, ref["k"]), res.k)
+    assert first > 10
+    assert np.array_equal(J[:first], ref["J"][:first])
+    T = res.T.cpu().numpy()
+    e = orc.rel_err(a64, J, T, res.k, "fro")
+    assert e <= 1.05 * tol, e
+    assert abs(res.err - e) <= 1e-10 * e
+
+
+def test_uneven_batch_sample_vs_oracle(gid, dev, orc):
+    shapes_all = wl.config4_shapes(512, 4)
+    pick = list(range(0, 512, 8))
+    shapes = [shapes_all[i] for i in pick]
+    mats = []
+    for i, (m, n, r) in zip(pick, shapes):
+        sigma = 10.0 ** (-np.arange(1, r + 1) / r)
+        mats.append(wl.lowrank(m, n, sigma, 4 * 100003 + i))
+    ranks = [r for _, _, r in shapes]
+    ldas = [(m + 1) // 2 * 2 for m, _, _ in shapes]
+    plan = gid.BatchPlan([(m, n) for m, n, _ in shapes], ranks, precision="mixed_bf16x3", lda=ldas)
+    om, bits = wl.gaussian_omega(plan.ell_max, (plan.m_max + 7) // 8 * 8, 4004, "bf16")
+    omega = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
+    bufs = []
+    for a, lda in zip(mats, ldas):
+        m, n = a.shape
+        buf = torch.zeros((n, lda), dtype=torch.float64, device=dev)
+        buf[:, :m] = torch.from_numpy(np.ascontiguousarray(a.T)).to(dev)
+        bufs.append(buf)
+    plan.bind([b.t()[: a.shape[0]] for b, a in zip(bufs, mats)])
+    plan.run(omega)
+    torch.cuda.synchronize()
+    for i, (a, r, res) in enumerate(zip(mats, ranks, plan.results())):
+        m, n = a.shape
+        ell = min(r + 10, m)
+        ref = orc.interp_decomp(a, k=r, omega=om[:ell, :m])
+        assert res.info == 0 and res.k == r, (i, res.info, res.k)
+        J = res.J.cpu().numpy()
+        assert sorted(J.tolist()) == list(range(n)), i
+        T = res.T.cpu().numpy()
+        e_m = orc.rel_err(a, J, T, r)
+        e_d = orc.rel_err(a, ref["J"], ref["T"], r)
+        # E1 with the unit round-off of the bfloat16 pieces (exact rank: e_D is at FP64 level)
+        assert e_m <= 1.1 * e_d + 10 * U_BF16, (i, e_m, e_d)
+        first = first_close_step(ref["gaps"], 1e-2, r)
+        assert np.array_equal(J[:first], ref["J"][:first]), i

@@ -103,6 +103,7 @@ def test_snapshot_f16_sketch(gid, dev, orc, snap):
                        omega=omega_dev(bits3, dev, "bf16"))
     assert r16.info == 0 and r3.info == 0
     assert 0 < r16.k <= kmax
+    assert r16.k <= r3.k + 1, (r16.k, r3.k)
 
 
 def test_snapshot_plain_f64_tolerance(gid, dev, orc, snap):

@@ -314,6 +314,20 @@ def test_pivots_and_diag_match_lapack(orc):
         assert np.allclose(np.abs(rp), np.abs(r[:k]), rtol=1e-9, atol=1e-12 * np.abs(r).max())
 
 
+def test_householder_exact_on_power_of_two_triangle(orc):
+    """Greedy Householder CPQR of a triangular matrix with power-of-two diagonal and
+    separated norms: pivots in triangular order, R = -W exactly (beta = -sign(alpha)
+    ||x|| flips each row), and T = W11^-1 W12 to FP64 accuracy (numpy's solve)."""
+    w, perm = wl.exact_triangular_id_matrix(k=12, n=60, rows=20)
+    w64 = w.astype(np.float64)
+    out = orc.cpqr(w64, k=12)
+    assert np.array_equal(out["J"][:12], perm[:12])
+    assert np.array_equal(out["R"], -w64[:12])
+    T = orc.solve_T(out["R"], out["J"], 12)
+    ref = np.linalg.solve(w64[:12, out["J"][:12]], w64[:12, out["J"][12:]])
+    assert np.max(np.abs(T - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
 def test_mgs_crosscheck(orc):
     """The paper's MGS column selection gives the same pivots and |R| as Householder."""
     for seed in range(3):

@@ -72,3 +72,29 @@ def test_noalloc_rejects_problems_beyond_its_scratch(lib):
     omega = torch.zeros((ell, m), dtype=torch.bfloat16, device=dev)
     code, _, _ = _noalloc(lib, a, omega, "mixed_bf16", torch.float32)
     assert code == ID_ERR_WORKSPACE
+
+
+def test_noalloc_limit_is_the_workspace_size_less_its_slack(lib):
+    """The static array holds exactly ID_NOALLOC_SCRATCH_BYTES of split-K partial sums: a
+    64-row FP32 matrix with ell = 16 has one row slab, so n columns need 64 n bytes.
+    n = 2^18 fills the array to the byte and runs (and matches id_sketch); one more column
+    is refused.  id_sketch_workspace_size reports the same figure plus 512 bytes of slack."""
+    import paper_2012_00706_gb300 as gid
+    dev = torch.device("cuda:0")
+    m, ell, limit = 64, 16, 16 * 1024 * 1024
+    n = limit // (ell * 4)
+    nb = ctypes.c_size_t(0)
+    assert lib.id_sketch_workspace_size(1, m, n, ell, gid.PRECISIONS["mixed_bf16"], ctypes.byref(nb)) == ID_OK
+    assert nb.value - 512 == limit
+    rng = np.random.default_rng(8)
+    big = torch.from_numpy(rng.standard_normal((n + 1, m)).astype(np.float32)).to(dev)
+    _, bits = wl.gaussian_omega(ell, m, 9, "bf16")
+    omega = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
+    a = big[:n].t()
+    code, y, info = _noalloc(lib, a, omega, "mixed_bf16", torch.float32)
+    torch.cuda.synchronize()
+    assert code == ID_OK and int(info.item()) == 0
+    ref = gid.id_sketch(a, omega, "mixed_bf16")
+    assert float((y - ref).abs().max()) <= 2.0 * (64 + 1 + 16) * 2.0 ** -24 * float(ref.abs().max())
+    code, _, _ = _noalloc(lib, big.t(), omega, "mixed_bf16", torch.float32)
+    assert code == ID_ERR_WORKSPACE

@@ -26,7 +26,8 @@ import numpy as np
 __all__ = [
     "orthonormal", "lowrank", "paper_sigma", "paper_dataset", "gaussian_omega",
     "config1", "config2", "config3", "config4", "config5", "BatchItem",
-    "separated_matrix", "to_bf16_bits", "to_f16_bits", "lowrank_device", "config4_device",
+    "separated_matrix", "exact_triangular_id_matrix", "to_bf16_bits", "to_f16_bits", "lowrank_device",
+    "config4_device",
 ]
 
 
@@ -240,3 +241,24 @@ def probe_vectors(n: int, s: int, seed: int) -> np.ndarray:
 def sinusoid_rank(modes: int) -> int:
     """Exact rank of the noiseless snapshot matrix: two per travelling mode."""
     return 2 * modes
+
+
+def exact_triangular_id_matrix(k: int = 24, n: int = 224, rows: int = 40, c: float = 0.5, seed: int = 0):
+    """FP32 matrix whose column-pivoted Householder QR is exact in FP32 and FP64.
+
+    Columns perm[0..k-1] hold an upper-triangular W11 (rows 0..k-1) with diagonal
+    2^0, 2^-1, ..., 2^-(k-1) and off-diagonal entries c 2^-i u in column i (u uniform
+    in [-1, 1], rounded to FP32); the other n - k columns hold c 2^-r u in row r < k;
+    rows k..rows-1 are zero.  Greedy pivoting then takes the triangular columns in
+    order (each step's leading residual norm is at least twice the runner-up's), every
+    reflector maps a multiple of a unit vector (v = e_j, tau = 2), and R equals -W
+    exactly.  The condition number of W11 is at least 2^(k-1).  Returns (W, perm)."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros((rows, n), dtype=np.float64)
+    d = 2.0 ** -np.arange(k)
+    tri = np.triu(c * rng.uniform(-1.0, 1.0, (k, k)) * d[None, :], 1) + np.diag(d)
+    rest = c * rng.uniform(-1.0, 1.0, (k, n - k)) * d[:, None]
+    perm = rng.permutation(n)
+    w[:k, perm[:k]] = tri
+    w[:k, perm[k:]] = rest
+    return np.asfortranarray(w.astype(np.float32)), perm
