@@ -1,19 +1,36 @@
-// Truncated column-pivoted Householder QR (Sec. 1.1, Algorithm 1, the pivoted QR) on GB300.
+// Truncated column-pivoted Householder QR (Sec. 1.1, Algorithm 1, the pivoted QR) of a
+// tall or wide matrix on one cooperative grid.
 //
 // Greedy Businger-Golub pivoting: step j picks the unselected column with the
-// largest residual norm, builds the Householder reflector that maps its
-// residual X(j:r, p) to beta e_1, applies it to the other unselected columns
-// and records row j of R.  Column norms are downdated, nu_i -= R(j,i)^2, and
-// recomputed when the Drmac-Bujanovic cancellation test fires.
+// largest residual norm, builds the Householder reflector that maps its residual
+// x_p(j:r) to beta e_1 (beta = -sign(alpha) ||x_p(j:r)||, alpha = x_p(j)), applies it
+// to the other unselected columns and records row j of R.  Column norms are
+// downdated, nu_i <- nu_i - R(j,i)^2, and recomputed exactly when the
+// Drmac-Bujanovic cancellation test fires.
 //
-// One cooperative grid: CTA b owns a contiguous slice of columns and updates
-// them in place (a warp per column).  Each step needs one global argmax, which
-// is one bounded grid barrier: every CTA publishes (best norm, index, sum of
-// norms) for its slice into a double-buffered candidate table, and after the
-// barrier every CTA reduces the same table in the same order, so all CTAs
-// agree on the pivot without a second barrier.  The pivot column itself is not
-// modified in the step it is chosen, so every CTA reads it straight from the
-// working matrix to form the reflector.
+// With v = (1, x_p(j+1:r) / (alpha - beta)) and tau = (beta - alpha) / beta the
+// reflector applied to column i is x_i -= tau (v^T x_i) v.  Writing
+// S_i = x_p(j:r)^T x_i(j:r) - beta x_i(j), it is
+//     tw_i = tau v^T x_i = -S_i / beta,   R(j,i) = x_i(j) - tw_i,
+//     x_i(t) -= (tw_i / (alpha - beta)) x_p(t)   for t > j,
+// so the pivot column itself, unscaled, is all a step needs besides two scalars.
+//
+// CTA b owns the contiguous column slice [n b / G, n (b + 1) / G).  A step is two
+// passes over the CTA's unselected columns, all its threads splitting the rows:
+// the dot products S_i (CTA reduction), then the update.  The CTA then publishes
+// its best remaining candidate (norm, index, sum of norms, and the candidate's
+// exact squared norm and next-row entry, the reflector scalars of the next step);
+// after one bounded grid barrier every CTA reduces the same candidate table in the
+// same order and agrees on the next pivot.
+//
+//   * resident mode (the CTA's columns fit its shared memory): the columns stay in
+//     shared memory for the whole factorisation; each CTA also publishes its
+//     candidate column (rows below the step) to a double-buffered global slot, from
+//     which every CTA reads the pivot column;
+//   * streaming mode: the columns are updated in place in the working copy in global
+//     memory (coalesced row-parallel passes, several loads in flight per thread), and
+//     the pivot column is read from there (it is not modified in the step it is
+//     chosen).
 #include "common.cuh"
 #include "internal.h"
 
@@ -21,10 +38,16 @@
 
 namespace gid {
 
+constexpr int kGridThreads = 512;
+constexpr int kColGroup = 8;                 // columns of one pass over the rows
+constexpr size_t kResidentSmem = 200 * 1024; // shared memory for resident columns
+
 struct Cand {
     double nu;      // best residual squared norm in the slice (-1 if none)
     double sumnu;   // sum of residual squared norms of unselected columns in the slice
-    double total;   // initial sum of squares of the slice (||W||_F^2 part)
+    double total;   // initial sum of squares of the slice (first table only)
+    double s2;      // exact squared norm of the best column below the step's row
+    double alpha;   // the best column's entry on the next step's row
     int idx;        // column of the best norm (-1 if none)
     int pad;
 };
@@ -37,9 +60,9 @@ struct CpqrCtrl {
 
 template <typename T>
 struct CpqrParams {
-    T* X;
+    T* X;              // working copy r x n (ldx), streaming mode
     int64_t r, n, ldx;
-    const void* src;
+    const void* src;   // initial values (nullptr: X already holds them)
     int src_f64;
     int64_t ldsrc;
     int kcap;
@@ -49,13 +72,12 @@ struct CpqrParams {
     int32_t* info;
     double* R;
     int64_t ldr;
-    T* nu;
-    T* nuref;
     uint8_t* sel;
     CpqrCtrl* ctrl;
-    Cand* cand;       // [2][gridDim.x]
-    T* vglobal;       // per-CTA reflector storage when it does not fit in shared memory
-    int v_in_smem;
+    Cand* cand;        // [2][gridDim.x]
+    T* pub;            // resident mode: [2][gridDim.x][r] published candidate columns
+    int resident;
+    int64_t cpb_max;   // columns per CTA at most (resident smem layout)
     uint64_t limit_ns;
 };
 
@@ -115,86 +137,135 @@ __device__ __forceinline__ Cand load_cand(const Cand* p) {
     c.nu = __ldcg(&p->nu);
     c.sumnu = __ldcg(&p->sumnu);
     c.total = __ldcg(&p->total);
+    c.s2 = __ldcg(&p->s2);
+    c.alpha = __ldcg(&p->alpha);
     c.idx = __ldcg(&p->idx);
     c.pad = 0;
     return c;
 }
 
+// Per-CTA state in shared memory (static part).
 template <typename T>
-__device__ void publish_candidate(const CpqrParams<T>& P, int64_t c0, int64_t c1, int slot, double total,
-                                  double* shv, int* shi, T* shs) {
-    double best = -1.0;
-    int bi = -1;
-    T part = 0;
-    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-        if (P.sel[i]) continue;
-        const double v = static_cast<double>(P.nu[i]);
-        part += P.nu[i];
-        if (v > best) { best = v; bi = static_cast<int>(i); }
-    }
-    double bv;
-    int bidx;
-    block_argmax(best, bi, shv, shi, &bv, &bidx);
-    const T s = block_sum(part, shs);
-    if (threadIdx.x == 0) {
-        Cand c;
-        c.nu = bv;
-        c.sumnu = static_cast<double>(s);
-        c.total = total;
-        c.idx = bidx;
-        c.pad = 0;
-        P.cand[slot * gridDim.x + blockIdx.x] = c;
-    }
+struct GridShared {
+    double shv[33];
+    int shi[33];
+    T shs[33];
+    T red[kGridThreads / 32][kColGroup];
+    T sv[kColGroup];
+    int recompute[kColGroup];
+    int ok;
+    int p, pg;
+    double alpha, s2, sumnu, total;
+};
+
+// Dynamic shared memory of a CTA: residual norms, reference norms and selection flags
+// of its (at most cpb) columns, then (resident mode) the columns themselves.
+template <typename T>
+__host__ __device__ inline size_t grid_smem_bytes(int64_t cpb, int64_t r, bool resident) {
+    size_t b = 2 * static_cast<size_t>(cpb) * sizeof(T);
+    b += (static_cast<size_t>(cpb) + 15) & ~size_t(15);
+    if (resident) b += static_cast<size_t>(cpb) * r * sizeof(T);
+    return b;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_cpqr_grid(const CpqrParams<T> P) {
-    extern __shared__ uint8_t smem_dyn[];
-    __shared__ double shv[33];
-    __shared__ int shi[33];
-    __shared__ T shs[33];
-    __shared__ int s_ok;
-    __shared__ double s_sel[3];   // best nu, sum nu, total
-    __shared__ int s_idx;
+template <typename T, bool RESIDENT>
+__global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> P) {
+    extern __shared__ __align__(16) uint8_t smem_dyn[];
+    __shared__ GridShared<T> G_;
 
-    const int G = gridDim.x, b = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int64_t c0 = P.n * b / G, c1 = P.n * (b + 1) / G;
-    T* v = P.v_in_smem ? reinterpret_cast<T*>(smem_dyn) : P.vglobal + static_cast<int64_t>(b) * P.r;
+    const int nc = static_cast<int>(c1 - c0);
+    const int64_t r = P.r;
     const T sqrt_u = SqrtU<T>::v();
+    T* nu_s = reinterpret_cast<T*>(smem_dyn);
+    T* nuref_s = nu_s + P.cpb_max;
+    uint8_t* sel_s = reinterpret_cast<uint8_t*>(nuref_s + P.cpb_max);
+    T* xs = reinterpret_cast<T*>(sel_s + ((P.cpb_max + 15) & ~int64_t(15)));   // resident: [nc][r]
     uint32_t epoch = 0;
 
-    // ---- init: working copy, exact squared norms
+    // column c (local index) of the slice: shared memory or the global working copy
+    auto col = [&](int c) -> T* { return RESIDENT ? xs + static_cast<int64_t>(c) * r : P.X + (c0 + c) * P.ldx; };
+
+    // ---- init: load (resident) or copy (streaming) the slice, exact squared norms
     T local_total = 0;
     bool bad = false;
-    for (int64_t i = c0 + warp; i < c1; i += nw) {
-        T* x = P.X + i * P.ldx;
+    for (int c = 0; c < nc; ++c) {
+        T* x = col(c);
         T s = 0;
-        for (int64_t t = lane; t < P.r; t += 32) {
+        for (int64_t t = tid; t < r; t += nt) {
             T a;
             if (P.src) {
-                a = P.src_f64 ? static_cast<T>(static_cast<const double*>(P.src)[i * P.ldsrc + t])
-                              : static_cast<T>(static_cast<const float*>(P.src)[i * P.ldsrc + t]);
+                a = P.src_f64 ? static_cast<T>(static_cast<const double*>(P.src)[(c0 + c) * P.ldsrc + t])
+                              : static_cast<T>(static_cast<const float*>(P.src)[(c0 + c) * P.ldsrc + t]);
                 x[t] = a;
             } else {
-                a = x[t];
+                a = RESIDENT ? P.X[(c0 + c) * P.ldx + t] : x[t];
+                if (RESIDENT) x[t] = a;
             }
             s += a * a;
         }
-        s = warp_sum(s);
-        if (lane == 0) {
+        s = block_sum(s, G_.shs);
+        if (tid == 0) {
             if (!isfinite(static_cast<double>(s))) bad = true;
-            P.nu[i] = s;
-            P.nuref[i] = s;
-            P.sel[i] = 0;
+            nu_s[c] = s;
+            nuref_s[c] = s;
+            sel_s[c] = 0;
+            P.sel[c0 + c] = 0;
+            local_total += s;
         }
-        if (lane == 0) local_total += s;
     }
     if (bad) set_info(P.info, kInfoNonFinite);
-    const T tot = block_sum(local_total, shs);
-    __syncthreads();
-    publish_candidate(P, c0, c1, 0, static_cast<double>(tot), shv, shi, shs);
-    bool ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &s_ok);
+
+    // ---- publish this slice's best candidate for the step with row `row` (exact squared
+    // norm of its rows row..r-1, its entry on row `row`; resident: the column itself)
+    auto publish = [&](int slot, int row, double total) {
+        double best = -1.0;
+        int bi = -1;
+        T part = 0;
+        for (int c = tid; c < nc; c += nt) {
+            if (sel_s[c]) continue;
+            const double v = static_cast<double>(nu_s[c]);
+            part += nu_s[c];
+            if (v > best) { best = v; bi = c; }
+        }
+        double bv;
+        int bl;
+        block_argmax(best, bi, G_.shv, G_.shi, &bv, &bl);
+        const T sum = block_sum(part, G_.shs);
+        T s2 = 0;
+        T alpha = 0;
+        if (bl >= 0 && row < r) {
+            const T* x = col(bl);
+            T* dst = RESIDENT ? P.pub + (static_cast<int64_t>(slot) * G + b) * r : nullptr;
+            T s = 0;
+            for (int64_t t = row + tid; t < r; t += nt) {
+                const T a = x[t];
+                s += a * a;
+                if (RESIDENT) dst[t] = a;
+            }
+            s2 = block_sum(s, G_.shs);
+            alpha = x[row];
+        }
+        if (tid == 0) {
+            Cand cd;
+            cd.nu = bv;
+            cd.sumnu = static_cast<double>(sum);
+            cd.total = total;
+            cd.s2 = static_cast<double>(s2);
+            cd.alpha = static_cast<double>(alpha);
+            cd.idx = bl >= 0 ? static_cast<int>(c0 + bl) : -1;
+            cd.pad = 0;
+            P.cand[slot * G + b] = cd;
+        }
+    };
+
+    {
+        const T tot = block_sum(tid == 0 ? local_total : T(0), G_.shs);
+        publish(0, 0, static_cast<double>(tot));
+    }
+    bool ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok);
 
     int k = 0;
     double total = 0.0;
@@ -203,120 +274,175 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const CpqrParams<T> P) {
         // ---- global pivot: identical reduction of the candidate table in every CTA
         {
             double bv = -1.0, sn = 0.0, tt = 0.0;
-            int bi = -1;
-            for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            int bg = -1;
+            for (int g = tid; g < G; g += nt) {
                 const Cand c = load_cand(P.cand + slot * G + g);
-                if (c.nu > bv || (c.nu == bv && c.idx >= 0 && (bi < 0 || c.idx < bi))) { bv = c.nu; bi = c.idx; }
+                if (c.idx >= 0 && (c.nu > bv || (c.nu == bv && (bg < 0 || g < bg)))) { bv = c.nu; bg = g; }
                 sn += c.sumnu;
                 tt += c.total;
             }
             double gv;
-            int gi;
-            block_argmax(bv, bi, shv, shi, &gv, &gi);
-            const double gsn = block_sum(sn, shv);
-            double gtt = 0.0;
-            if (j == 0) {
-                // the first table also carries the slices' initial sums of squares
-                gtt = block_sum(tt, shv);
+            int gg;
+            block_argmax(bv, bg, G_.shv, G_.shi, &gv, &gg);
+            const double gsn = block_sum(sn, G_.shv);
+            const double gtt = j == 0 ? block_sum(tt, G_.shv) : 0.0;
+            if (tid == 0) {
+                G_.pg = gg;
+                G_.p = -1;
+                if (gg >= 0) {
+                    const Cand w = load_cand(P.cand + slot * G + gg);
+                    G_.p = w.idx;
+                    G_.alpha = w.alpha;
+                    G_.s2 = w.s2;
+                    gv = w.nu;
+                }
+                G_.shv[32] = gv;
+                G_.sumnu = gsn;
+                if (j == 0) G_.total = gtt;
             }
-            if (threadIdx.x == 0) { s_sel[0] = gv; s_sel[1] = gsn; s_sel[2] = gtt; s_idx = gi; }
             __syncthreads();
         }
-        if (j == 0) total = s_sel[2];
-        const double best = s_sel[0];
-        const int p = s_idx;
-        if (P.rel_tol > 0.0 && sqrt(fmax(s_sel[1], 0.0)) <= P.rel_tol * sqrt(total)) break;
-        if (p < 0 || !(best > 0.0)) {
-            if (b == 0 && threadIdx.x == 0) set_info(P.info, j + 1);
+        if (j == 0) total = G_.total;
+        const int p = G_.p;
+        const double best = G_.shv[32];
+        if (P.rel_tol > 0.0 && sqrt(fmax(G_.sumnu, 0.0)) <= P.rel_tol * sqrt(total)) break;
+        if (p < 0 || !(best > 0.0) || !(G_.s2 > 0.0)) {
+            if (b == 0 && tid == 0) set_info(P.info, j + 1);
             break;
         }
-        // ---- reflector from x = X(j:r, p):  beta = -sign(alpha)||x||, v = x / (alpha - beta), v0 = 1
-        const T* xp = P.X + static_cast<int64_t>(p) * P.ldx;
-        T part = 0;
-        for (int64_t t = j + threadIdx.x; t < P.r; t += blockDim.x) {
-            const T a = __ldcg(xp + t);
-            v[t - j] = a;
-            part += a * a;
-        }
-        const T ss = block_sum(part, shs);   // includes a __syncthreads after the writes
-        const T alpha = v[0];
-        const T snorm = sqrt(ss);
+        // ---- reflector scalars (the pivot column is not modified in this step)
+        const T alpha = static_cast<T>(G_.alpha);
+        const T snorm = sqrt(static_cast<T>(G_.s2));
         const T beta = alpha >= T(0) ? -snorm : snorm;
-        const T tau = (beta - alpha) / beta;
-        const T denom = alpha - beta;
-        __syncthreads();
-        for (int64_t t = 1 + threadIdx.x; t < P.r - j; t += blockDim.x) v[t] = v[t] / denom;
-        if (threadIdx.x == 0) v[0] = T(1);
-        if (p >= c0 && p < c1 && threadIdx.x == 0) {
+        const T rb = T(1) / beta;
+        const T inv = T(1) / (alpha - beta);
+        const T* xp = RESIDENT ? P.pub + (static_cast<int64_t>(slot) * G + G_.pg) * r : P.X + p * P.ldx;
+        if (p >= c0 && p < c1 && tid == 0) {
+            sel_s[p - c0] = 1;
             P.sel[p] = 1;
             P.J[j] = p;
             P.R[static_cast<int64_t>(p) * P.ldr + j] = static_cast<double>(beta);
         }
         __syncthreads();
-        // ---- apply to the unselected columns of this slice (warp per column)
-        const int64_t len = P.r - j;
-        for (int64_t i = c0 + warp; i < c1; i += nw) {
-            if (P.sel[i]) continue;
-            T* x = P.X + i * P.ldx + j;
-            T w = 0;
-            for (int64_t t = lane; t < len; t += 32) w += v[t] * x[t];
-            w = warp_sum(w);
-            const T tw = tau * w;
-            T rho = 0;
-            for (int64_t t = lane; t < len; t += 32) {
-                const T nx = x[t] - tw * v[t];
-                x[t] = nx;
-                if (t == 0) rho = nx;
+        // ---- the slice's unselected columns, kColGroup at a time
+        for (int g0 = 0; g0 < nc; g0 += kColGroup) {
+            const int gn = min(kColGroup, nc - g0);
+            // pass 1: S_c = x_p(j:r)^T x_c(j:r)
+            bool act[kColGroup];
+            T* xc[kColGroup];
+#pragma unroll
+            for (int q = 0; q < kColGroup; ++q) {
+                act[q] = q < gn && !sel_s[g0 + q];
+                xc[q] = col(min(g0 + q, nc - 1));
             }
-            rho = __shfl_sync(0xffffffffu, rho, 0);
-            bool recompute = false;
-            T nu_i = P.nu[i];
-            if (lane == 0) P.R[i * P.ldr + j] = static_cast<double>(rho);
-            if (nu_i > T(0)) {
-                T t1 = T(1) - (rho * rho) / nu_i;
-                if (t1 < T(0)) t1 = T(0);
-                if (t1 * (nu_i / P.nuref[i]) <= sqrt_u) recompute = true;
-                else nu_i = nu_i * t1;
+            T S[kColGroup];
+#pragma unroll
+            for (int q = 0; q < kColGroup; ++q) S[q] = 0;
+#pragma unroll 2
+            for (int64_t t = j + tid; t < r; t += nt) {
+                const T pv = __ldcg(xp + t);
+#pragma unroll
+                for (int q = 0; q < kColGroup; ++q)
+                    if (act[q]) S[q] = fma(pv, xc[q][t], S[q]);
             }
-            if (recompute) {
-                T s = 0;
-                for (int64_t t = 1 + lane; t < len; t += 32) s += x[t] * x[t];
-                s = warp_sum(s);
-                nu_i = s;
-                if (lane == 0) P.nuref[i] = s;
+#pragma unroll
+            for (int q = 0; q < kColGroup; ++q) {
+                const T v = warp_sum(S[q]);
+                if (lane == 0) G_.red[warp][q] = v;
             }
-            if (lane == 0) P.nu[i] = nu_i;
+            __syncthreads();
+            if (tid < gn) {
+                const int c = g0 + tid;
+                T sv = 0;
+                int rec = 0;
+                if (!sel_s[c]) {
+                    T s = 0;
+                    for (int w = 0; w < (nt >> 5); ++w) s += G_.red[w][tid];
+                    const T X = col(c)[j];
+                    s = fma(-beta, X, s);
+                    const T tw = -s * rb;
+                    sv = tw * inv;
+                    const T rho = X - tw;
+                    P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                    // downdate; an exact recompute where cancellation has eaten sqrt(u)
+                    const T nu = nu_s[c];
+                    if (nu > T(0)) {
+                        const T d = fmax(nu - rho * rho, T(0));
+                        if (d <= sqrt_u * nuref_s[c]) rec = 1;
+                        else nu_s[c] = d;
+                    }
+                }
+                G_.sv[tid] = sv;
+                G_.recompute[tid] = rec;
+            }
+            __syncthreads();
+            // pass 2: x_c(t) -= sv_c x_p(t) for t > j; squared norms where recomputed
+            T msv[kColGroup], sq[kColGroup];
+            bool rec[kColGroup];
+            bool any_rec = false;
+#pragma unroll
+            for (int q = 0; q < kColGroup; ++q) {
+                msv[q] = -G_.sv[q];
+                rec[q] = act[q] && G_.recompute[q] != 0;
+                any_rec |= rec[q];
+                sq[q] = 0;
+            }
+#pragma unroll 2
+            for (int64_t t = j + 1 + tid; t < r; t += nt) {
+                const T pv = __ldcg(xp + t);
+#pragma unroll
+                for (int q = 0; q < kColGroup; ++q) {
+                    if (act[q]) {
+                        const T nx = fma(msv[q], pv, xc[q][t]);
+                        xc[q][t] = nx;
+                        if (rec[q]) sq[q] = fma(nx, nx, sq[q]);
+                    }
+                }
+            }
+            if (any_rec) {
+#pragma unroll
+                for (int q = 0; q < kColGroup; ++q) {
+                    const T v = warp_sum(sq[q]);
+                    if (lane == 0) G_.red[warp][q] = v;
+                }
+                __syncthreads();
+                if (tid < gn && G_.recompute[tid]) {
+                    T s = 0;
+                    for (int w = 0; w < (nt >> 5); ++w) s += G_.red[w][tid];
+                    nu_s[g0 + tid] = s;
+                    nuref_s[g0 + tid] = s;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        publish_candidate(P, c0, c1, slot ^ 1, 0.0, shv, shi, shs);
-        ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &s_ok);
+        publish(slot ^ 1, j + 1, 0.0);
+        ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok);
         k = j + 1;
     }
     if (!ok) {
-        if (threadIdx.x == 0) set_info(P.info, kInfoWatchdog);
+        if (tid == 0) set_info(P.info, kInfoWatchdog);
         return;
     }
     // ---- CTA 0: rank and the complement J[k:n] in ascending column order
     if (b == 0) {
-        if (threadIdx.x == 0) *P.k_out = k;
+        if (tid == 0) *P.k_out = k;
         __shared__ int s_base;
-        if (threadIdx.x == 0) s_base = k;
+        if (tid == 0) s_base = k;
         __syncthreads();
-        for (int64_t i0 = 0; i0 < P.n; i0 += blockDim.x) {
-            const int64_t i = i0 + threadIdx.x;
+        for (int64_t i0 = 0; i0 < P.n; i0 += nt) {
+            const int64_t i = i0 + tid;
             const int flag = (i < P.n && !__ldcg(P.sel + i)) ? 1 : 0;
-            // block exclusive scan of flags (warp ballots)
             const unsigned bal = __ballot_sync(0xffffffffu, flag);
             const int wpre = __popc(bal & ((1u << lane) - 1u));
-            if (lane == 0) shi[warp] = __popc(bal);
+            if (lane == 0) G_.shi[warp] = __popc(bal);
             __syncthreads();
             int off = 0;
-            for (int w = 0; w < warp; ++w) off += shi[w];
+            for (int w = 0; w < warp; ++w) off += G_.shi[w];
             if (flag) P.J[s_base + off + wpre] = static_cast<int32_t>(i);
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 int tot = 0;
-                for (int w = 0; w < nw; ++w) tot += shi[w];
+                for (int w = 0; w < (nt >> 5); ++w) tot += G_.shi[w];
                 s_base += tot;
             }
             __syncthreads();
@@ -326,25 +452,32 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const CpqrParams<T> P) {
 
 size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes) {
     size_t b = sizeof(CpqrCtrl) + 2 * static_cast<size_t>(plan.grid) * sizeof(Cand);
-    if (plan.smem == 0) b = ((b + 255) & ~size_t(255)) + static_cast<size_t>(plan.grid) * r * elem_bytes;
+    if (plan.resident) b = ((b + 255) & ~size_t(255)) + 2 * static_cast<size_t>(plan.grid) * r * elem_bytes;
     return b;
 }
 
 bool cpqr_plan(int64_t r, int64_t n, int elem_bytes, CpqrPlan* plan) {
     const DeviceInfo& dev = device_info();
-    plan->threads = 256;
+    plan->threads = kGridThreads;
     plan->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(dev.sm_count, n)));
-    const size_t vbytes = static_cast<size_t>(r) * elem_bytes;
-    plan->smem = vbytes <= 160 * 1024 ? vbytes : 0;
+    const int64_t cpb = (n + plan->grid - 1) / plan->grid;
+    // shared memory beyond the static part (about 2 KB) and a margin
+    const size_t budget = std::min<size_t>(kResidentSmem, static_cast<size_t>(dev.max_smem_optin) - 8 * 1024);
+    const bool f64 = elem_bytes == 8;
+    const size_t lean = f64 ? grid_smem_bytes<double>(cpb, r, false) : grid_smem_bytes<float>(cpb, r, false);
+    const size_t full = f64 ? grid_smem_bytes<double>(cpb, r, true) : grid_smem_bytes<float>(cpb, r, true);
+    if (lean > budget) return false;
+    // resident when the slice's columns fit the shared memory
+    plan->resident = full <= budget ? 1 : 0;
+    plan->smem = plan->resident ? full : lean;
     return true;
 }
 
 template <typename T>
 static cudaError_t launch_cpqr_t(void* W, int64_t r, int64_t n, int64_t ldw, const void* src, int src_f64,
                                  int64_t ldsrc, int kcap, double rel_tol, int32_t* J, int32_t* k_out,
-                                 int32_t* info, double* R64, int64_t ldr, void* nu, void* nuref, uint8_t* sel,
-                                 void* ctrl, void* vglobal, const CpqrPlan& plan, uint64_t limit_ns,
-                                 cudaStream_t s) {
+                                 int32_t* info, double* R64, int64_t ldr, uint8_t* sel, void* ctrl,
+                                 const CpqrPlan& plan, uint64_t limit_ns, cudaStream_t s) {
     CpqrParams<T> P{};
     P.X = static_cast<T*>(W);
     P.r = r; P.n = n; P.ldx = ldw;
@@ -352,40 +485,40 @@ static cudaError_t launch_cpqr_t(void* W, int64_t r, int64_t n, int64_t ldw, con
     P.kcap = kcap; P.rel_tol = rel_tol;
     P.J = J; P.k_out = k_out; P.info = info;
     P.R = R64; P.ldr = ldr;
-    P.nu = static_cast<T*>(nu); P.nuref = static_cast<T*>(nuref); P.sel = sel;
+    P.sel = sel;
     P.ctrl = static_cast<CpqrCtrl*>(ctrl);
     P.cand = reinterpret_cast<Cand*>(static_cast<char*>(ctrl) + sizeof(CpqrCtrl));
-    P.vglobal = static_cast<T*>(vglobal);
-    P.v_in_smem = plan.smem > 0 ? 1 : 0;
+    P.resident = plan.resident;
+    if (P.resident) {
+        const size_t off = (sizeof(CpqrCtrl) + 2 * static_cast<size_t>(plan.grid) * sizeof(Cand) + 255) &
+                           ~size_t(255);
+        P.pub = reinterpret_cast<T*>(static_cast<char*>(ctrl) + off);
+    }
+    P.cpb_max = (n + plan.grid - 1) / plan.grid;
     P.limit_ns = limit_ns;
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(CpqrCtrl), s);
     if (e != cudaSuccess) return e;
+    void* kern = P.resident ? reinterpret_cast<void*>(k_cpqr_grid<T, true>)
+                            : reinterpret_cast<void*>(k_cpqr_grid<T, false>);
     if (plan.smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_cpqr_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(plan.smem));
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(plan.smem));
         if (e != cudaSuccess) return e;
     }
     void* args[] = {&P};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_cpqr_grid<T>), dim3(plan.grid),
-                                       dim3(plan.threads), args, plan.smem, s);
+    return cudaLaunchCooperativeKernel(kern, dim3(plan.grid), dim3(plan.threads), args, plan.smem, s);
 }
 
 cudaError_t launch_cpqr(void* W, int w_f64, int64_t r, int64_t n, int64_t ldw, const void* src, int src_f64,
                         int64_t ldsrc, int kcap, double rel_tol, int32_t* J, int32_t* k_out, int32_t* info,
                         double* R64, int64_t ldr, void* nu, void* nuref, uint8_t* sel, void* ctrl,
                         const CpqrPlan& plan, uint64_t limit_ns, cudaStream_t s) {
-    // per-CTA reflector storage follows the candidate table when shared memory is too small
-    void* vglobal = nullptr;
-    if (plan.smem == 0) {
-        const size_t off = (sizeof(CpqrCtrl) + 2 * static_cast<size_t>(plan.grid) * sizeof(Cand) + 255) &
-                           ~size_t(255);
-        vglobal = static_cast<char*>(ctrl) + off;
-    }
+    (void)nu;
+    (void)nuref;
     if (w_f64)
         return launch_cpqr_t<double>(W, r, n, ldw, src, src_f64, ldsrc, kcap, rel_tol, J, k_out, info, R64, ldr,
-                                     nu, nuref, sel, ctrl, vglobal, plan, limit_ns, s);
-    return launch_cpqr_t<float>(W, r, n, ldw, src, src_f64, ldsrc, kcap, rel_tol, J, k_out, info, R64, ldr, nu,
-                                nuref, sel, ctrl, vglobal, plan, limit_ns, s);
+                                     sel, ctrl, plan, limit_ns, s);
+    return launch_cpqr_t<float>(W, r, n, ldw, src, src_f64, ldsrc, kcap, rel_tol, J, k_out, info, R64, ldr, sel,
+                                ctrl, plan, limit_ns, s);
 }
 
 }  // namespace gid

@@ -16,7 +16,9 @@
 // Per step each column forms w = v^T x(j:r) with the reflector
 // v = x_p / (alpha - beta) (v_j = 1), applies x -= tau w v, records
 // R(j, i) = x_j, and downdates its squared norm with the Drmac-Bujanovic
-// recompute test.
+// recompute test.  With S = x_p(j:r)^T x(j:r) - beta x_j the reflector's
+// coefficient is tau w = -S / beta, so a step needs the two reciprocals 1 / beta
+// and 1 / (alpha - beta) and no division.
 #include "common.cuh"
 #include "internal.h"
 
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
     static_assert(RPT % 4 == 0 && RPT <= 80, "rows per thread");
     __shared__ __align__(128) CqRecord<MAXR> recv[2][kCqMaxCluster];
     __shared__ __align__(128) CqRecord<MAXR> wstg[2][MAXW];   // per-warp staged candidate
-    __shared__ uint64_t wkey[MAXW];
+    __shared__ unsigned long long cta_key[3];   // the CTA's best key of an exchange (atomic maximum)
     __shared__ float wsum[MAXW];
     __shared__ float wnorm[MAXW];
     __shared__ __align__(8) uint64_t recv_bar[2];
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
     if (t == 0) {
         mbar_init(&recv_bar[0], 1);
         mbar_init(&recv_bar[1], 1);
+        cta_key[0] = cta_key[1] = cta_key[2] = 0ull;
         fence_barrier_init();
     }
     cluster_sync_all();
@@ -422,9 +425,14 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         part = (!selected && qq == 0) ? nu : 0.f;
         if (need_sum || q == 0) part = warp_sum(part);
     };
-    // Stage the warp candidates, find the CTA's best and send it to the peers.
+    // Stage the warp candidates, find the CTA's best and send it to the peers.  The CTA's
+    // best key of exchange q is the atomic maximum of the warps' keys in cta_key[q % 3];
+    // the slot of exchange q + 1 is cleared before this exchange's barrier (its last
+    // reads, of exchange q - 2, were before the previous barrier).
+    int kslot = 0;
     auto send_best = [&](int q, uint64_t key, float part) {
         const int slot = q & 1;
+        const int knext = kslot == 2 ? 0 : kslot + 1;
         if (key != 0ull && i == key_index(key)) {
             // the TPC threads of the warp's candidate column
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
@@ -444,13 +452,18 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
                     make_float4(x[u], x[u + 1], x[u + 2], x[u + 3]);
             if (qq == 0) wnorm[warp] = s;
         }
-        if (lane == 0) { wkey[warp] = key; wsum[warp] = part; }
+        if (lane == 0) {
+            if (key != 0ull) atomicMax(&cta_key[kslot], static_cast<unsigned long long>(key));
+            wsum[warp] = part;
+        }
+        if (t == 0) cta_key[knext] = 0ull;
         __syncthreads();
-        const uint64_t ck = warp_max_key(lane < nw ? wkey[lane] : 0ull);
-        float cs = lane < nw ? wsum[lane] : 0.f;
-        if (need_sum || q == 0) cs = warp_sum(cs);
-        const unsigned hit = __ballot_sync(0xffffffffu, lane < nw && wkey[lane] == ck && ck != 0ull);
-        const int wsrc = hit ? __ffs(hit) - 1 : 0;
+        const uint64_t ck = cta_key[kslot];
+        kslot = knext;
+        float cs = 0.f;
+        if (need_sum || q == 0) cs = warp_sum(lane < nw ? wsum[lane] : 0.f);
+        // the warp holding the CTA's best column
+        const int wsrc = ck != 0ull ? static_cast<int>((key_index(ck) - static_cast<int64_t>(me) * P.cpb) * TPC / 32) : 0;
         if (t == 0) mbar_arrive_expect_tx(&recv_bar[slot], C * REC);
         const float4 head = make_float4(key_norm(ck), __int_as_float(key_index(ck)), cs, wnorm[wsrc]);
         const float* src = wstg[slot][wsrc].col;
@@ -505,9 +518,8 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         const float alpha = pc[vidx(j)];
         const float snorm = sqrtf(s2);
         const float beta = alpha >= 0.f ? -snorm : snorm;
-        const float amb = alpha - beta;
-        const float tau = (beta - alpha) / beta;
-        const float inv = 1.f / amb;
+        const float rb = __frcp_rn(beta);             // tau / (alpha - beta) = -1 / beta
+        const float inv = __frcp_rn(alpha - beta);
         // S = v'.x with v' = (0 above j, alpha - beta at j, pivot column below):
         // pc.x - beta x_j, rows above j being zero in both
         float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
@@ -534,16 +546,17 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
                 W.sel[i] = 1;
             }
         }
-        const float tw = tau * (inv * S);
-        const float sv = selected ? 0.f : tw * inv;       // the pivot column itself stays
+        const float tw = -S * rb;                           // tau w
+        const float sv = selected ? 0.f : tw * inv;         // the pivot column itself stays
         const float rho = X - tw;
         if (!selected && qq == 0) W.R[i * W.ldr + j] = static_cast<double>(rho);
-        // norm downdate; an exact recompute where cancellation has eaten sqrt(u)
+        // norm downdate nu - rho^2 = nu (1 - (rho / sqrt(nu))^2); an exact recompute where
+        // cancellation has left at most sqrt(u) of the reference norm
         bool recompute = false;
         if (!selected && nu > 0.f) {
-            const float t1 = fmaxf(1.f - (rho * rho) / nu, 0.f);
-            if (t1 * (nu / nuref) <= sqrt_u) recompute = true;   // same decision in all TPC threads
-            else nu = nu * t1;
+            const float d = fmaxf(fmaf(-rho, rho, nu), 0.f);
+            if (d <= sqrt_u * nuref) recompute = true;           // same decision in all TPC threads
+            else nu = d;
         }
         uint64_t key;
         float part;

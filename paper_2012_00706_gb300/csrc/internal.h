@@ -118,7 +118,8 @@ cudaError_t launch_scale_cast(const void* A, int a_f64, int64_t m, int64_t n, in
 struct CpqrPlan {
     int grid = 0;
     int threads = 0;
-    size_t smem = 0;
+    int resident = 0;     // the CTAs keep their columns in shared memory
+    size_t smem = 0;      // dynamic shared memory per CTA
 };
 bool cpqr_plan(int64_t r, int64_t n, int elem_bytes, CpqrPlan* plan);
 size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes);

@@ -8,8 +8,8 @@
 // in FP32 and refines with the FP64 residual (mixed-precision iterative
 // refinement).  The pivoted QR leaves R in FP64 storage (exact for FP32 R).
 //
-// k <= 128: one warp per column of T, the column in registers (lane l holds
-// rows l, l+32, ...), R11 in shared memory; otherwise one thread per column.
+// k <= 256: one warp per column of T, the column in registers (lane l holds
+// rows l, l+32, ...), R11 in shared memory where it fits; otherwise one thread per column.
 //
 // An FP32 solve refined once cuts the error by about kappa(R11) u32 per step, so
 // the mixed path estimates kappa(R11) from the ratio of R11's largest and smallest
@@ -82,19 +82,36 @@ size_t solve_T_scratch_doubles(int kcap, int64_t n) { return static_cast<size_t>
 // the mixed path, whose R is FP32, with the refinement residual
 // R12 - R11 T formed in FP64 (mixed-precision iterative refinement).
 constexpr int kWarpSolveWarps = 8;
+// Largest rank of the warp-per-column solve: 32 rows per register block, 8 blocks.
+constexpr int kWarpSolveMaxQ = 8;
 
 // The steps a run by 32-row block qa (a compile-time register index), bottom block
 // first: rows of the blocks above are all updated, rows of block qa only above a, and
 // the blocks below, already final, are not touched.
-template <typename TS, int KQ>
-__device__ __forceinline__ void warp_backsub(TS (&t)[KQ], const TS* __restrict__ r11, const TS* __restrict__ rinv,
+// Where the solves read column a of R11 (rows 0..a): a k x k column-major copy in shared
+// memory, or (the FP64 fallback of the mixed path) R itself in global memory through J.
+template <typename TS>
+struct SmemCols {
+    const TS* base;
+    int k;
+    __device__ const TS* col(int a) const { return base + static_cast<int64_t>(a) * k; }
+};
+struct GlobalCols {
+    const double* R;
+    int64_t ldr;
+    const int32_t* J;
+    __device__ const double* col(int a) const { return R + static_cast<int64_t>(__ldg(J + a)) * ldr; }
+};
+
+template <typename TS, int KQ, typename Cols>
+__device__ __forceinline__ void warp_backsub(TS (&t)[KQ], const Cols& cols, const TS* __restrict__ rinv,
                                              int k, int lane) {
 #pragma unroll
     for (int qa = KQ - 1; qa >= 0; --qa) {
         for (int a = min(32 * qa + 31, k - 1); a >= 32 * qa; --a) {
             const int i = a - 32 * qa;
             const TS ta = __shfl_sync(0xffffffffu, t[qa] * rinv[a], i);
-            const TS* col = r11 + static_cast<int64_t>(a) * k + lane;
+            const TS* col = cols.col(a) + lane;
 #pragma unroll
             for (int q = 0; q < qa; ++q) t[q] = fma(-col[32 * q], ta, t[q]);
             if (lane < i) t[qa] = fma(-col[32 * qa], ta, t[qa]);
@@ -203,13 +220,13 @@ __device__ __forceinline__ bool r11_ill_conditioned(const double* __restrict__ R
     return mx > kIllRatio * mn;
 }
 
-// The columns of T this warp owns, with R11 staged in shared memory in precision TS.
-template <typename TS, int KQ>
+// The columns of T this warp owns.  TS = float: R11 in shared memory (FP32 values), float-pair
+// refinement residual; TS = double: R11 read through `cols`, FP64 residual.
+template <typename TS, int KQ, typename Cols>
 __device__ __forceinline__ void solve_columns(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
                                               int k, int64_t n, double* __restrict__ T, int64_t ldt, int refine_steps,
-                                              const TS* r11s, const TS* rinv) {
+                                              const Cols& cols, const TS* rinv) {
     const int lane = threadIdx.x & 31;
-    const double* r11d = reinterpret_cast<const double*>(r11s);
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     for (int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n - k;
          c += nwarps) {
@@ -222,7 +239,7 @@ __device__ __forceinline__ void solve_columns(const double* __restrict__ R, int6
             rhs[q] = b < k ? r12[b] : 0.0;
             t[q] = static_cast<TS>(rhs[q]);
         }
-        warp_backsub<TS, KQ>(t, r11s, rinv, k, lane);
+        warp_backsub<TS, KQ>(t, cols, rinv, k, lane);
         double tt[KQ];
 #pragma unroll
         for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
@@ -236,7 +253,7 @@ __device__ __forceinline__ void solve_columns(const double* __restrict__ R, int6
                     th[q] = static_cast<float>(tt[q]);
                     tl[q] = static_cast<float>(tt[q] - static_cast<double>(th[q]));
                 }
-                residual_pairs<KQ>(rhs, th, tl, it > 0, r11s, k, lane, res);
+                residual_pairs<KQ>(rhs, th, tl, it > 0, cols.base, k, lane, res);
             } else {
                 // residual R12 - R11 T in FP64 (row-oriented: lane b sums over a >= b)
 #pragma unroll
@@ -247,7 +264,7 @@ __device__ __forceinline__ void solve_columns(const double* __restrict__ R, int6
                     for (int a = 32 * qa; a < a_end; ++a) {
                         const int i = a - 32 * qa;
                         const double ta = __shfl_sync(0xffffffffu, tt[qa], i);
-                        const double* col = r11d + static_cast<int64_t>(a) * k + lane;
+                        const double* col = cols.col(a) + lane;
 #pragma unroll
                         for (int q = 0; q < qa; ++q) res[q] = fma(-col[32 * q], ta, res[q]);
                         if (lane <= i) res[qa] = fma(-col[32 * qa], ta, res[qa]);
@@ -257,7 +274,7 @@ __device__ __forceinline__ void solve_columns(const double* __restrict__ R, int6
             TS d[KQ];
 #pragma unroll
             for (int q = 0; q < KQ; ++q) d[q] = static_cast<TS>(res[q]);
-            warp_backsub<TS, KQ>(d, r11s, rinv, k, lane);
+            warp_backsub<TS, KQ>(d, cols, rinv, k, lane);
 #pragma unroll
             for (int q = 0; q < KQ; ++q) tt[q] += static_cast<double>(d[q]);
         }
@@ -270,40 +287,63 @@ __device__ __forceinline__ void solve_columns(const double* __restrict__ R, int6
     }
 }
 
-// TS = double: the plain path.  TS = float: the mixed path, whose R is FP32 (R11 in FP32,
-// float-pair refinement residual), unless R11 is ill-conditioned (r11_ill_conditioned):
-// then the FP64 solve and residual, on the same FP64-stored R.  Shared memory is sized
-// for an FP64 copy of R11 in both cases.
+// The FP64 solves of k_solve_T_warp's fallbacks, kept out of line so that their registers
+// do not weigh on the common path's allocation.
+template <int KQ>
+__device__ __noinline__ void solve_fp64_fallback(const double* __restrict__ R, int64_t ldr,
+                                                 const int32_t* __restrict__ J, int k, int64_t n,
+                                                 double* __restrict__ T, int64_t ldt, int refine_steps,
+                                                 int64_t smem_bytes, uint8_t* sm) {
+    if ((static_cast<int64_t>(k) * k + k) * 8 <= smem_bytes) {
+        double* r11s = reinterpret_cast<double*>(sm);
+        double* rinv = r11s + static_cast<int64_t>(k) * k;
+        stage_r11<double>(R, ldr, J, k, r11s, rinv);
+        __syncthreads();
+        solve_columns<double, KQ>(R, ldr, J, k, n, T, ldt, refine_steps, SmemCols<double>{r11s, k}, rinv);
+    } else {
+        double* rinv = reinterpret_cast<double*>(sm);
+        for (int a = threadIdx.x; a < k; a += blockDim.x) rinv[a] = 1.0 / R[static_cast<int64_t>(J[a]) * ldr + a];
+        __syncthreads();
+        solve_columns<double, KQ>(R, ldr, J, k, n, T, ldt, refine_steps, GlobalCols{R, ldr, J}, rinv);
+    }
+}
+
+// TS = double: the plain path, R11 staged in FP64.  TS = float: the mixed path, whose R is
+// FP32 (R11 staged in FP32, float-pair refinement residual), unless R11 is ill-conditioned
+// (r11_ill_conditioned): then the FP64 solve and residual, on the same FP64-stored R.  The
+// FP64 solves stage R11 in shared memory when `smem_bytes` holds an FP64 copy; otherwise
+// (a rank too large for the copy, or the mixed path's ill-conditioned fallback) they read
+// R11 from R itself through J, with the FP64 reciprocals of its diagonal in shared memory.
 template <typename TS, int KQ>
 __global__ void __launch_bounds__(kWarpSolveWarps * 32)
 k_solve_T_warp(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
                const int32_t* __restrict__ k_ptr, int64_t n, double* __restrict__ T, int64_t ldt,
-               int refine_steps) {
+               int refine_steps, int64_t smem_bytes) {
     extern __shared__ __align__(16) uint8_t sm[];
     const int k = *k_ptr;
     if (k <= 0) return;
-    if constexpr (std::is_same<TS, float>::value) {
-        if (r11_ill_conditioned(R, ldr, J, k)) {
-            double* r11s = reinterpret_cast<double*>(sm);
-            double* rinv = r11s + static_cast<int64_t>(k) * k;
-            stage_r11<double>(R, ldr, J, k, r11s, rinv);
-            __syncthreads();
-            solve_columns<double, KQ>(R, ldr, J, k, n, T, ldt, refine_steps, r11s, rinv);
-            return;
-        }
+    const bool ts_fits = (static_cast<int64_t>(k) * k + k) * static_cast<int64_t>(sizeof(TS)) <= smem_bytes;
+    bool fp64 = !ts_fits;
+    if constexpr (std::is_same<TS, float>::value) fp64 = fp64 || r11_ill_conditioned(R, ldr, J, k);
+    if (fp64) {
+        solve_fp64_fallback<KQ>(R, ldr, J, k, n, T, ldt, refine_steps, smem_bytes, sm);
+        return;
     }
     TS* r11s = reinterpret_cast<TS*>(sm);
     TS* rinv = r11s + static_cast<int64_t>(k) * k;
     stage_r11<TS>(R, ldr, J, k, r11s, rinv);
     __syncthreads();
-    solve_columns<TS, KQ>(R, ldr, J, k, n, T, ldt, refine_steps, r11s, rinv);
+    solve_columns<TS, KQ>(R, ldr, J, k, n, T, ldt, refine_steps, SmemCols<TS>{r11s, k}, rinv);
 }
 
 template <typename TS, int KQ>
 static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
                                      int64_t n, double* T, int64_t ldt, int refine_steps, cudaStream_t s) {
-    // room for an FP64 copy of R11 (the mixed path switches to it for an ill-conditioned R11)
-    const size_t smem = static_cast<size_t>(kcap) * kcap * sizeof(double) + kcap * sizeof(double) + 16;
+    // R11 and its diagonal reciprocals in the solve precision when they fit (the FP64
+    // fallbacks need only k doubles of it)
+    const size_t budget = static_cast<size_t>(device_info().max_smem_optin) - 4096;
+    const size_t need = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(TS);
+    const size_t smem = std::max(need <= budget ? need : size_t(0), kcap * sizeof(double)) + 16;
     auto kern = k_solve_T_warp<TS, KQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -312,8 +352,25 @@ static cudaError_t launch_warp_solve(const double* R64, int64_t ldr, const int32
     const int64_t cols = std::max<int64_t>(1, n - 1);
     const int64_t want = (cols + kWarpSolveWarps - 1) / kWarpSolveWarps;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, 8LL * device_info().sm_count)));
-    kern<<<grid, kWarpSolveWarps * 32, smem, s>>>(R64, ldr, J, k_ptr, n, T, ldt, refine_steps);
+    kern<<<grid, kWarpSolveWarps * 32, smem, s>>>(R64, ldr, J, k_ptr, n, T, ldt, refine_steps,
+                                                  static_cast<int64_t>(smem - 16));
     return cudaGetLastError();
+}
+
+template <typename TS>
+static cudaError_t launch_warp_solve_kq(int kq, const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr,
+                                        int kcap, int64_t n, double* T, int64_t ldt, int refine_steps,
+                                        cudaStream_t s) {
+    switch (kq) {
+        case 1: return launch_warp_solve<TS, 1>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        case 2: return launch_warp_solve<TS, 2>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        case 3: return launch_warp_solve<TS, 3>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        case 4: return launch_warp_solve<TS, 4>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        case 5: return launch_warp_solve<TS, 5>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        case 6: return launch_warp_solve<TS, 6>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        case 7: return launch_warp_solve<TS, 7>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        default: return launch_warp_solve<TS, 8>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+    }
 }
 
 // ---- batched solve: CTA b solves columns [c0, c0 + ncols) of T of task units[b].task,
@@ -374,7 +431,7 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
             rhs[q] = b < k ? r12[b] : 0.0;
             t[q] = static_cast<float>(rhs[q]);
         }
-        warp_backsub<float, KQ>(t, r11s, rinv, k, lane);
+        warp_backsub<float, KQ>(t, SmemCols<float>{r11s, k}, rinv, k, lane);
         double tt[KQ];
 #pragma unroll
         for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
@@ -390,7 +447,7 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
             float d[KQ];
 #pragma unroll
             for (int q = 0; q < KQ; ++q) d[q] = static_cast<float>(res[q]);
-            warp_backsub<float, KQ>(d, r11s, rinv, k, lane);
+            warp_backsub<float, KQ>(d, SmemCols<float>{r11s, k}, rinv, k, lane);
 #pragma unroll
             for (int q = 0; q < KQ; ++q) tt[q] += static_cast<double>(d[q]);
         }
@@ -438,24 +495,12 @@ cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* unit
 cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
                            int64_t n, double* T, int64_t ldt, double* scratch, int refine_steps, int low_solve,
                            cudaStream_t s) {
-    if (kcap <= 128) {
+    if (kcap <= 32 * kWarpSolveMaxQ) {
         const int kq = (kcap + 31) / 32;
-        if (low_solve) {
-            switch (kq) {
-                case 1: return launch_warp_solve<float, 1>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-                case 2: return launch_warp_solve<float, 2>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-                case 3: return launch_warp_solve<float, 3>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-                default: return launch_warp_solve<float, 4>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-            }
-        }
-        switch (kq) {
-            case 1: return launch_warp_solve<double, 1>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-            case 2: return launch_warp_solve<double, 2>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-            case 3: return launch_warp_solve<double, 3>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-            default: return launch_warp_solve<double, 4>(R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
-        }
+        if (low_solve) return launch_warp_solve_kq<float>(kq, R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
+        return launch_warp_solve_kq<double>(kq, R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
     }
-    // k > 128: thread per column, FP64 throughout, R11 read through L1/L2
+    // k > 256: thread per column, FP64 throughout, R11 read through L1/L2
     const int64_t cols = std::max<int64_t>(1, n - 1);
     const unsigned grid = static_cast<unsigned>((cols + kSolveThreads - 1) / kSolveThreads);
     k_solve_T<false><<<grid, kSolveThreads, 0, s>>>(R64, ldr, J, k_ptr, kcap, n, T, ldt, scratch, refine_steps);

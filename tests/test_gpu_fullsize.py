@@ -9,7 +9,9 @@
 * Plain FP64 ID of the 65536 x 1000 snapshot matrix at tolerance 1e-6 (no sketch):
   rank within one step of the oracle's, pivots equal up to the oracle's first step
   whose two leading norms are within 1e-8, relative Frobenius residual at the
-  tolerance.
+  tolerance.  (Every snapshot column has nearly the same norm, the modes being
+  orthogonal over the periodic domain, so already the first step is that close;
+  the rank and residual gates apply whatever the pivots.)
 * 64 matrices of the uneven 512-matrix batch (every 8th), factored as one batch:
   each against the oracle's sketched ID with the same Omega.
 """
@@ -89,7 +91,6 @@ def test_snapshot_plain_f64_full_size_vs_oracle(gid, dev, orc):
     assert abs(res.k - ref["k"]) <= 1, (res.k, ref["k"])
     J = res.J.cpu().numpy()
     first = min(first_close_step(ref["gaps"], 1e-8, ref["k"]), res.k)
-    assert first > 10
     assert np.array_equal(J[:first], ref["J"][:first])
     T = res.T.cpu().numpy()
     e = orc.rel_err(a64, J, T, res.k, "fro")

@@ -81,9 +81,11 @@ def test_snapshot_error_estimate_full_size(gid, dev, orc):
 
 
 def test_snapshot_f16_sketch(gid, dev, orc, snap):
-    """FP16 sketch of the FP32 snapshots: E1 at a fixed rank; at tolerance 1e-6 it
-    cannot resolve modes below its rounding floor (~1.8e-5 of ||A||), so its rank
-    stops at or below the FP32-accurate one."""
+    """FP16 sketch of the FP32 snapshots: E1 at a fixed rank.  At tolerance 1e-6 the
+    half-precision cast's rounding noise (about 1.8e-5 of ||A||, well above the
+    tolerance) stays in the sketch's remaining norm, so the stopping test never fires
+    and the rank runs to k_max, while the FP32-accurate three-piece sketch stops
+    below it."""
     a = snap
     a64 = a.astype(np.float64)
     k = 60
@@ -102,8 +104,8 @@ def test_snapshot_f16_sketch(gid, dev, orc, snap):
     r3 = gid.id_factor(torch.from_numpy(a).to(dev), tol=1e-6, k_max=kmax, precision="mixed_bf16x3",
                        omega=omega_dev(bits3, dev, "bf16"))
     assert r16.info == 0 and r3.info == 0
-    assert 0 < r16.k <= kmax
-    assert r16.k <= r3.k + 1, (r16.k, r3.k)
+    assert r16.k == kmax, r16.k
+    assert 0 < r3.k < kmax, r3.k
 
 
 def test_snapshot_plain_f64_tolerance(gid, dev, orc, snap):
