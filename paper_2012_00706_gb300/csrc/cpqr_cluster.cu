@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         const float alpha = pc[vidx(j)];
         const float snorm = sqrtf(s2);
         const float beta = alpha >= 0.f ? -snorm : snorm;
-        const float rb = __frcp_rn(beta);             // tau / (alpha - beta) = -1 / beta
+        const float rbeta = __frcp_rn(beta);          // tau / (alpha - beta) = -1 / beta
         const float inv = __frcp_rn(alpha - beta);
         // S = v'.x with v' = (0 above j, alpha - beta at j, pivot column below):
         // pc.x - beta x_j, rows above j being zero in both
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
                 W.sel[i] = 1;
             }
         }
-        const float tw = -S * rb;                           // tau w
+        const float tw = -S * rbeta;                        // tau w
         const float sv = selected ? 0.f : tw * inv;         // the pivot column itself stays
         const float rho = X - tw;
         if (!selected && qq == 0) W.R[i * W.ldr + j] = static_cast<double>(rho);
