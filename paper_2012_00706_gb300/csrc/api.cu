@@ -142,7 +142,7 @@ id_status_t plan_factor(id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, c
             sketch_plan_f64(m, n, o->ell, &p.sp64);
         }
     }
-    cpqr_plan(p.rows, n, p.w_f64 ? 8 : 4, &p.cp);
+    if (!cpqr_plan(p.rows, n, p.w_f64 ? 8 : 4, &p.cp)) return ID_ERR_UNSUPPORTED;
     // the cluster kernel reads A directly when it is a short float matrix (PLAIN_F32, no sketch)
     const bool short_f32 = !p.w_f64 && (p.sketch || a_dtype == ID_F32);
     p.use_cluster = short_f32 && cpqr_cluster_plan(p.rows, n, &p.ccp) ? 1 : 0;

@@ -15,24 +15,17 @@
 //     x_i(t) -= (tw_i / (alpha - beta)) x_p(t)   for t > j,
 // so the pivot column itself, unscaled, is all a step needs besides two scalars.
 //
-// CTA b owns the contiguous column slice [n b / G, n (b + 1) / G).  A step is two
-// passes over the CTA's unselected columns, all its threads splitting the rows:
-// the dot products S_i (CTA reduction), then the update.  The CTA then publishes
-// its best remaining candidate (norm, index, sum of norms, and the candidate's
-// exact squared norm and next-row entry, the reflector scalars of the next step);
-// after one bounded grid barrier every CTA reduces the same candidate table in the
-// same order and agrees on the next pivot.
-//
-//   * resident mode (the CTA's columns fit its shared memory): the columns stay in
-//     shared memory for the whole factorisation; each CTA also publishes its
-//     candidate column (rows below the step) to a double-buffered global slot, from
-//     which every CTA reads the pivot column;
-//   * streaming mode: the columns are updated in place in the working copy in global
-//     memory (coalesced row-parallel passes, several loads in flight per thread), and
-//     the pivot column is read from there (it is not modified in the step it is
-//     chosen).
-#include "common.cuh"
-#include "internal.h"
+// CTA b owns the contiguous column slice [n b / G, n (b + 1) / G) of the working copy
+// in global memory and updates it in place.  A step is two coalesced row-parallel passes
+// over the CTA's unselected columns, all its threads splitting the rows (several loads in
+// flight per thread): the dot products S_i (CTA reduction), then the update.  The pivot
+// column is read straight from the working copy (it is not modified in the step it is
+// chosen).  The CTA then publishes its best remaining candidate (norm, index, sum of
+// norms, and the candidate's exact squared norm and next-row entry, the reflector scalars
+// of the next step); after one bounded grid barrier every CTA reduces the same candidate
+// table in the same order and agrees on the next pivot.  Matrices whose columns fit the
+// grid's shared memory go to the resident kernel instead (cpqr_resident.cu).
+#include "cpqr_grid.cuh"
 
 #include <algorithm>
 
@@ -41,45 +34,6 @@ namespace gid {
 constexpr int kGridThreads = 512;
 constexpr int kColGroup = 8;                 // columns of one pass over the rows
 constexpr size_t kResidentSmem = 200 * 1024; // shared memory for resident columns
-
-struct Cand {
-    double nu;      // best residual squared norm in the slice (-1 if none)
-    double sumnu;   // sum of residual squared norms of unselected columns in the slice
-    double total;   // initial sum of squares of the slice (first table only)
-    double s2;      // exact squared norm of the best column below the step's row
-    double alpha;   // the best column's entry on the next step's row
-    int idx;        // column of the best norm (-1 if none)
-    int pad;
-};
-
-struct CpqrCtrl {
-    uint32_t counter;
-    int abort;
-    uint32_t pad[62];
-};
-
-template <typename T>
-struct CpqrParams {
-    T* X;              // working copy r x n (ldx), streaming mode
-    int64_t r, n, ldx;
-    const void* src;   // initial values (nullptr: X already holds them)
-    int src_f64;
-    int64_t ldsrc;
-    int kcap;
-    double rel_tol;
-    int32_t* J;
-    int32_t* k_out;
-    int32_t* info;
-    double* R;
-    int64_t ldr;
-    uint8_t* sel;
-    CpqrCtrl* ctrl;
-    Cand* cand;        // [2][gridDim.x]
-    T* pub;            // resident mode: [2][gridDim.x][r] published candidate columns
-    int resident;
-    int64_t cpb_max;   // columns per CTA at most (resident smem layout)
-    uint64_t limit_ns;
-};
 
 template <typename T> struct SqrtU;
 template <> struct SqrtU<double> { static __device__ double v() { return 1.0536712127723509e-08; } };  // 2^-26.5
@@ -131,19 +85,6 @@ __device__ void block_argmax(double v, int idx, double* shv, int* shi, double* o
     *outi = shi[32];
 }
 
-// Candidate entries written by other CTAs are read from L2 (never from a stale L1 line).
-__device__ __forceinline__ Cand load_cand(const Cand* p) {
-    Cand c;
-    c.nu = __ldcg(&p->nu);
-    c.sumnu = __ldcg(&p->sumnu);
-    c.total = __ldcg(&p->total);
-    c.s2 = __ldcg(&p->s2);
-    c.alpha = __ldcg(&p->alpha);
-    c.idx = __ldcg(&p->idx);
-    c.pad = 0;
-    return c;
-}
-
 // Per-CTA state in shared memory (static part).
 template <typename T>
 struct GridShared {
@@ -159,16 +100,13 @@ struct GridShared {
 };
 
 // Dynamic shared memory of a CTA: residual norms, reference norms and selection flags
-// of its (at most cpb) columns, then (resident mode) the columns themselves.
+// of its (at most cpb) columns.
 template <typename T>
-__host__ __device__ inline size_t grid_smem_bytes(int64_t cpb, int64_t r, bool resident) {
-    size_t b = 2 * static_cast<size_t>(cpb) * sizeof(T);
-    b += (static_cast<size_t>(cpb) + 15) & ~size_t(15);
-    if (resident) b += static_cast<size_t>(cpb) * r * sizeof(T);
-    return b;
+__host__ __device__ inline size_t grid_smem_bytes(int64_t cpb) {
+    return 2 * static_cast<size_t>(cpb) * sizeof(T) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
 }
 
-template <typename T, bool RESIDENT>
+template <typename T>
 __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> P) {
     extern __shared__ __align__(16) uint8_t smem_dyn[];
     __shared__ GridShared<T> G_;
@@ -182,13 +120,12 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
     T* nu_s = reinterpret_cast<T*>(smem_dyn);
     T* nuref_s = nu_s + P.cpb_max;
     uint8_t* sel_s = reinterpret_cast<uint8_t*>(nuref_s + P.cpb_max);
-    T* xs = reinterpret_cast<T*>(sel_s + ((P.cpb_max + 15) & ~int64_t(15)));   // resident: [nc][r]
     uint32_t epoch = 0;
 
-    // column c (local index) of the slice: shared memory or the global working copy
-    auto col = [&](int c) -> T* { return RESIDENT ? xs + static_cast<int64_t>(c) * r : P.X + (c0 + c) * P.ldx; };
+    // column c (local index) of the slice in the global working copy
+    auto col = [&](int c) -> T* { return P.X + (c0 + c) * P.ldx; };
 
-    // ---- init: load (resident) or copy (streaming) the slice, exact squared norms
+    // ---- init: copy the slice into the working copy (or take it there), exact squared norms
     T local_total = 0;
     bool bad = false;
     for (int c = 0; c < nc; ++c) {
@@ -201,8 +138,7 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
                               : static_cast<T>(static_cast<const float*>(P.src)[(c0 + c) * P.ldsrc + t]);
                 x[t] = a;
             } else {
-                a = RESIDENT ? P.X[(c0 + c) * P.ldx + t] : x[t];
-                if (RESIDENT) x[t] = a;
+                a = x[t];
             }
             s += a * a;
         }
@@ -219,7 +155,7 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
     if (bad) set_info(P.info, kInfoNonFinite);
 
     // ---- publish this slice's best candidate for the step with row `row` (exact squared
-    // norm of its rows row..r-1, its entry on row `row`; resident: the column itself)
+    // norm of its rows row..r-1, its entry on row `row`)
     auto publish = [&](int slot, int row, double total) {
         double best = -1.0;
         int bi = -1;
@@ -238,12 +174,10 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
         T alpha = 0;
         if (bl >= 0 && row < r) {
             const T* x = col(bl);
-            T* dst = RESIDENT ? P.pub + (static_cast<int64_t>(slot) * G + b) * r : nullptr;
             T s = 0;
             for (int64_t t = row + tid; t < r; t += nt) {
                 const T a = x[t];
                 s += a * a;
-                if (RESIDENT) dst[t] = a;
             }
             s2 = block_sum(s, G_.shs);
             alpha = x[row];
@@ -316,7 +250,7 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
         const T beta = alpha >= T(0) ? -snorm : snorm;
         const T rb = T(1) / beta;
         const T inv = T(1) / (alpha - beta);
-        const T* xp = RESIDENT ? P.pub + (static_cast<int64_t>(slot) * G + G_.pg) * r : P.X + p * P.ldx;
+        const T* xp = P.X + p * P.ldx;
         if (p >= c0 && p < c1 && tid == 0) {
             sel_s[p - c0] = 1;
             P.sel[p] = 1;
@@ -423,31 +357,7 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
         if (tid == 0) set_info(P.info, kInfoWatchdog);
         return;
     }
-    // ---- CTA 0: rank and the complement J[k:n] in ascending column order
-    if (b == 0) {
-        if (tid == 0) *P.k_out = k;
-        __shared__ int s_base;
-        if (tid == 0) s_base = k;
-        __syncthreads();
-        for (int64_t i0 = 0; i0 < P.n; i0 += nt) {
-            const int64_t i = i0 + tid;
-            const int flag = (i < P.n && !__ldcg(P.sel + i)) ? 1 : 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, flag);
-            const int wpre = __popc(bal & ((1u << lane) - 1u));
-            if (lane == 0) G_.shi[warp] = __popc(bal);
-            __syncthreads();
-            int off = 0;
-            for (int w = 0; w < warp; ++w) off += G_.shi[w];
-            if (flag) P.J[s_base + off + wpre] = static_cast<int32_t>(i);
-            __syncthreads();
-            if (tid == 0) {
-                int tot = 0;
-                for (int w = 0; w < (nt >> 5); ++w) tot += G_.shi[w];
-                s_base += tot;
-            }
-            __syncthreads();
-        }
-    }
+    if (b == 0) list_complement(P.J, P.sel, P.n, k, P.k_out, G_.shi);
 }
 
 size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes) {
@@ -464,11 +374,12 @@ bool cpqr_plan(int64_t r, int64_t n, int elem_bytes, CpqrPlan* plan) {
     // shared memory beyond the static part (about 2 KB) and a margin
     const size_t budget = std::min<size_t>(kResidentSmem, static_cast<size_t>(dev.max_smem_optin) - 8 * 1024);
     const bool f64 = elem_bytes == 8;
-    const size_t lean = f64 ? grid_smem_bytes<double>(cpb, r, false) : grid_smem_bytes<float>(cpb, r, false);
-    const size_t full = f64 ? grid_smem_bytes<double>(cpb, r, true) : grid_smem_bytes<float>(cpb, r, true);
-    if (lean > budget) return false;
-    // resident when the slice's columns fit the shared memory
+    const size_t lean = f64 ? grid_smem_bytes<double>(cpb) : grid_smem_bytes<float>(cpb);
+    const size_t full = f64 ? resident_smem_bytes<double>(cpb, r) : resident_smem_bytes<float>(cpb, r);
+    // resident (warp per column, cpqr_resident.cu) when the slice's columns fit the shared
+    // memory, streamed through the working copy otherwise
     plan->resident = full <= budget ? 1 : 0;
+    if (!plan->resident && lean > budget) return false;
     plan->smem = plan->resident ? full : lean;
     return true;
 }
@@ -498,8 +409,8 @@ static cudaError_t launch_cpqr_t(void* W, int64_t r, int64_t n, int64_t ldw, con
     P.limit_ns = limit_ns;
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(CpqrCtrl), s);
     if (e != cudaSuccess) return e;
-    void* kern = P.resident ? reinterpret_cast<void*>(k_cpqr_grid<T, true>)
-                            : reinterpret_cast<void*>(k_cpqr_grid<T, false>);
+    if (P.resident) return launch_cpqr_resident<T>(P, plan.grid, plan.smem, s);
+    void* kern = reinterpret_cast<void*>(k_cpqr_grid<T>);
     if (plan.smem > 48 * 1024) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(plan.smem));
         if (e != cudaSuccess) return e;

@@ -1,0 +1,101 @@
+// State shared by the two cooperative-grid pivoted-QR kernels (cpqr.cu: columns streamed
+// through the working copy in global memory; cpqr_resident.cu: columns resident in shared
+// memory): the per-CTA candidate record, the grid-barrier control word, the parameters,
+// and the final listing of the unselected columns.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gid {
+
+// One CTA's best remaining candidate for the next step.
+struct Cand {
+    double nu;      // best residual squared norm in the slice (-1 if none)
+    double sumnu;   // sum of residual squared norms of unselected columns in the slice
+    double total;   // initial sum of squares of the slice (first table only)
+    double s2;      // exact squared norm of the best column below the next step's row
+    double alpha;   // the best column's entry on the next step's row
+    int idx;        // column of the best norm (-1 if none)
+    int pad;
+};
+
+struct CpqrCtrl {
+    uint32_t counter;
+    int abort;
+    uint32_t pad[62];
+};
+
+template <typename T>
+struct CpqrParams {
+    T* X;              // working copy r x n (ldx): streamed columns, or the resident kernel's input
+    int64_t r, n, ldx;
+    const void* src;   // initial values (nullptr: X already holds them)
+    int src_f64;
+    int64_t ldsrc;
+    int kcap;
+    double rel_tol;
+    int32_t* J;
+    int32_t* k_out;
+    int32_t* info;
+    double* R;
+    int64_t ldr;
+    uint8_t* sel;
+    CpqrCtrl* ctrl;
+    Cand* cand;        // [2][gridDim.x]
+    T* pub;            // resident kernel: [2][gridDim.x][r] published candidate columns
+    int resident;
+    int64_t cpb_max;   // columns per CTA at most (shared-memory layout)
+    uint64_t limit_ns;
+};
+
+// Candidate entries written by other CTAs are read from L2 (never from a stale L1 line).
+__device__ __forceinline__ Cand load_cand(const Cand* p) {
+    Cand c;
+    c.nu = __ldcg(&p->nu);
+    c.sumnu = __ldcg(&p->sumnu);
+    c.total = __ldcg(&p->total);
+    c.s2 = __ldcg(&p->s2);
+    c.alpha = __ldcg(&p->alpha);
+    c.idx = __ldcg(&p->idx);
+    c.pad = 0;
+    return c;
+}
+
+// CTA 0 after the last step: the rank and the complement J[k:n] in ascending column order
+// (a block-wide exclusive scan of the unselected flags).  cnt: shared scratch of one int
+// per warp.
+__device__ __forceinline__ void list_complement(int32_t* J, const uint8_t* sel, int64_t n, int k, int32_t* k_out,
+                                                int* cnt) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    if (tid == 0) *k_out = k;
+    int base = k;
+    for (int64_t i0 = 0; i0 < n; i0 += nt) {
+        const int64_t i = i0 + tid;
+        const int flag = (i < n && !__ldcg(sel + i)) ? 1 : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+        const int wpre = __popc(bal & ((1u << lane) - 1u));
+        __syncthreads();
+        if (lane == 0) cnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) off += cnt[w];
+            tot += cnt[w];
+        }
+        if (flag) J[base + off + wpre] = static_cast<int32_t>(i);
+        base += tot;
+    }
+}
+
+// Shared-memory bytes of the resident kernel for a CTA of at most cpb columns of r rows.
+template <typename T>
+__host__ __device__ inline size_t resident_smem_bytes(int64_t cpb, int64_t r) {
+    return static_cast<size_t>(cpb) * sizeof(T) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15)) +
+           static_cast<size_t>(cpb) * r * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_cpqr_resident(const CpqrParams<T>& P, int grid, size_t smem, cudaStream_t s);
+
+}  // namespace gid

@@ -225,6 +225,24 @@ def test_plain_f64_id_matches_oracle(gid, dev, orc, m, n, k):
     assert abs(res.err - e_ref) <= 1e-10
 
 
+@pytest.mark.parametrize("m,n,k,dtype", [(30000, 300, 30, np.float64), (60000, 160, 24, np.float32)])
+def test_plain_tall_streamed_matches_oracle(gid, dev, orc, m, n, k, dtype):
+    """Tall matrices whose column slices do not fit the grid's shared memory take the
+    streamed pivoted QR (the working copy updated in place in global memory): pivots equal
+    the oracle's on separated inputs, T to the solve's accuracy."""
+    a = wl.separated_matrix(m, n, seed=m + n, decay=0.9)
+    ref = orc.interp_decomp(a, k=k)
+    assert np.min(ref["gaps"]) >= 1e-3
+    prec = "plain_f64" if dtype == np.float64 else "plain_f32"
+    res = gid.id_factor(torch.from_numpy(a.astype(dtype)).to(dev), k, precision=prec)
+    assert res.info == 0 and res.k == k
+    J = res.J.cpu().numpy()
+    assert np.array_equal(J, ref["J"])
+    T = res.T.cpu().numpy()
+    tol = 1e-9 if dtype == np.float64 else 1e-3
+    assert np.max(np.abs(T - ref["T"])) <= tol * max(1.0, np.max(np.abs(ref["T"])))
+
+
 def test_plain_f64_config1_full(gid, dev, orc):
     """Config 1 (1000 x 500, sigma_i = 10^(-i/25), k = 50): pivots equal the oracle's up
     to its first step whose two leading norms are within 1e-8 (none on this matrix),
