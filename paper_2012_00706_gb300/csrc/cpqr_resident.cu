@@ -21,7 +21,10 @@ namespace gid {
 
 constexpr int kResWarps = 8;
 
-// (value, index) warp argmax, ties to the smaller index; every lane gets the result.
+// (value, index) warp argmax, ties to the smaller index; lane 0's result goes to every
+// lane.  Values must be ordered (no NaN: callers map non-finite norms to -1), so that
+// every lane and every warp reducing the same entries takes the same decision: the
+// warps of a CTA branch on it independently, and must meet at the same barriers.
 __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -29,7 +32,13 @@ __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
         const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         if (oi >= 0 && (idx < 0 || ov > v || (ov == v && oi < idx))) { v = ov; idx = oi; }
     }
+    v = __shfl_sync(0xffffffffu, v, 0);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
 }
+
+// A residual norm as a pivot key: non-finite values (a non-finite input, reported in
+// info) order below every real norm.
+__device__ __forceinline__ double norm_key(double nu) { return isfinite(nu) ? nu : -1.0; }
 
 template <typename T>
 __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrParams<T> P) {
@@ -86,7 +95,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         int ci = -1;
         for (int c = warp; c < nc; c += kResWarps) {
             if (sel_s[c]) continue;
-            const double nu = static_cast<double>(nu_s[c]);
+            const double nu = norm_key(static_cast<double>(nu_s[c]));
             part += nu;
             if (ci < 0 || nu > v) { v = nu; ci = c; }     // c ascends: ties keep the smaller
         }
@@ -131,13 +140,14 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         int bg = -1;
         for (int g = lane; g < G; g += 32) {
             const Cand c = load_cand(P.cand + slot * G + g);
-            if (c.idx >= 0 && (bg < 0 || c.nu > bv)) { bv = c.nu; bg = g; }   // g ascends per lane
+            const double nu = norm_key(c.nu);
+            if (c.idx >= 0 && (bg < 0 || nu > bv)) { bv = nu; bg = g; }   // g ascends per lane
             sn += c.sumnu;
             tt += c.total;
         }
         warp_argmax(bv, bg);
-        sn = warp_sum(sn);
-        if (j == 0) total = warp_sum(tt);
+        sn = __shfl_sync(0xffffffffu, warp_sum(sn), 0);
+        if (j == 0) total = __shfl_sync(0xffffffffu, warp_sum(tt), 0);
         double alpha_d = 0.0, s2 = 0.0;
         int p = -1;
         if (bg >= 0) {
