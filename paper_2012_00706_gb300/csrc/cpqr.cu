@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
             cd.s2 = static_cast<double>(s2);
             cd.alpha = static_cast<double>(alpha);
             cd.idx = bl >= 0 ? static_cast<int>(c0 + bl) : -1;
-            cd.pad = 0;
+            cd.stamp = 0;
             P.cand[slot * G + b] = cd;
         }
     };
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
             T S[kColGroup];
 #pragma unroll
             for (int q = 0; q < kColGroup; ++q) S[q] = 0;
-#pragma unroll 2
+#pragma unroll 4
             for (int64_t t = j + tid; t < r; t += nt) {
                 const T pv = __ldcg(xp + t);
 #pragma unroll
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
                 any_rec |= rec[q];
                 sq[q] = 0;
             }
-#pragma unroll 2
+#pragma unroll 4
             for (int64_t t = j + 1 + tid; t < r; t += nt) {
                 const T pv = __ldcg(xp + t);
 #pragma unroll

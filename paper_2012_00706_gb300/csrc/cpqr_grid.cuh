@@ -17,7 +17,7 @@ struct Cand {
     double s2;      // exact squared norm of the best column below the next step's row
     double alpha;   // the best column's entry on the next step's row
     int idx;        // column of the best norm (-1 if none)
-    int pad;
+    int stamp;      // resident kernel: step + 1 the record is for, stored last (release)
 };
 
 struct CpqrCtrl {
@@ -58,7 +58,7 @@ __device__ __forceinline__ Cand load_cand(const Cand* p) {
     c.s2 = __ldcg(&p->s2);
     c.alpha = __ldcg(&p->alpha);
     c.idx = __ldcg(&p->idx);
-    c.pad = 0;
+    c.stamp = 0;
     return c;
 }
 
@@ -88,11 +88,12 @@ __device__ __forceinline__ void list_complement(int32_t* J, const uint8_t* sel, 
     }
 }
 
-// Shared-memory bytes of the resident kernel for a CTA of at most cpb columns of r rows.
+// Shared-memory bytes of the resident kernel for a CTA of at most cpb columns of r rows:
+// norms, selection flags, the columns, and a copy of the step's pivot column.
 template <typename T>
 __host__ __device__ inline size_t resident_smem_bytes(int64_t cpb, int64_t r) {
     return static_cast<size_t>(cpb) * sizeof(T) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15)) +
-           static_cast<size_t>(cpb) * r * sizeof(T);
+           static_cast<size_t>(cpb + 1) * r * sizeof(T);
 }
 
 template <typename T>

@@ -9,10 +9,17 @@
 //     R(j,i) = x_i(j) - tw_i,   x_i(t) -= (tw_i / (alpha - beta)) x_p(t)  (t > j),
 // tw_i = -S_i / beta.  A column's dot product, update and new squared norm (rows below
 // the step, accumulated as the update writes them, so every pivot choice uses exact
-// norms) are the work of its warp alone: no CTA-wide reduction.  Per step a warp reduces
-// the grid's candidate table itself (no barrier), the CTA takes one barrier to find its
-// best remaining column, publishes that column and its norm to a double-buffered global
-// slot, and one bounded grid barrier ends the step.
+// norms) are the work of its warp alone: no CTA-wide reduction.
+//
+// The grid synchronises through its candidate table alone.  Each CTA publishes its best
+// remaining column (the column into a double-buffered global slot, then a record with its
+// norm, next-row entry and the slice's sum of norms) and stamps the record with the step
+// number last, after a fence (release).  Warp 0 of every CTA polls the stamps of the whole
+// table with acquire loads until every record of the step has arrived (bounded by the
+// watchdog), reduces it in a fixed order, stages the winner's column in shared memory,
+// and one CTA barrier hands the step to the other warps.  No counter barrier: the wait
+// for the table is the step's only grid-wide wait.  The table is cleared before the
+// launch, so a replayed launch never sees an earlier call's stamps.
 #include "cpqr_grid.cuh"
 
 #include <algorithm>
@@ -20,6 +27,17 @@
 namespace gid {
 
 constexpr int kResWarps = 8;
+// Candidate-table entries per lane of the polling warp (a grid of up to 32 x 5 = 160 CTAs).
+constexpr int kTableLanes = 5;
+
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // (value, index) warp argmax, ties to the smaller index; lane 0's result goes to every
 // lane.  Values must be ordered (no NaN: callers map non-finite norms to -1), so that
@@ -45,8 +63,10 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
     extern __shared__ __align__(16) uint8_t smem_dyn[];
     __shared__ double w_nu[kResWarps], w_sum[kResWarps];
     __shared__ int w_idx[kResWarps];
-    __shared__ int s_ok;
     __shared__ int cnt[kResWarps];
+    // the step's decision, written by warp 0 before the CTA barrier
+    __shared__ double s_alpha, s_s2;
+    __shared__ int s_p, s_go;   // s_go: 1 carry on, 0 stop (rank reached or tolerance met), -1 watchdog
 
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -56,7 +76,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
     T* nu_s = reinterpret_cast<T*>(smem_dyn);                                       // [cpb]
     uint8_t* sel_s = reinterpret_cast<uint8_t*>(nu_s + P.cpb_max);                 // [cpb]
     T* xs = reinterpret_cast<T*>(sel_s + ((P.cpb_max + 15) & ~int64_t(15)));       // [nc][r]
-    uint32_t epoch = 0;
+    T* xps = xs + P.cpb_max * r;                                                    // [r] pivot column
 
     // ---- init: this warp's columns into shared memory, their exact squared norms
     bool bad = false;
@@ -85,12 +105,13 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
     }
     if (bad) set_info(P.info, kInfoNonFinite);
 
-    // ---- the CTA's best remaining column for the step on row `row`: each warp's best and
-    // sum, one barrier, then warp 0 picks the CTA's best (ties to the smaller column) and
-    // publishes it: its rows row..r-1 to pub[slot][b], and the record (exact squared norm
-    // of those rows, the entry on `row`, the slice's sum of norms; before the first step
-    // that sum is also the slice's total sum of squares)
-    auto publish = [&](int slot, int64_t row, bool first) {
+    // ---- the CTA's best remaining column for step `step` (row `step`): each warp's best
+    // and sum, one barrier, then warp 0 picks the CTA's best (ties to the smaller column),
+    // writes its rows step..r-1 to pub[step & 1][b] and the record (exact squared norm of
+    // those rows, the entry on row `step`, the slice's sum of norms; for step 0 that sum is
+    // also the slice's total), and stamps the record with step + 1 after a fence
+    auto publish = [&](int step) {
+        const int slot = step & 1;
         double v = -1.0, part = 0.0;
         int ci = -1;
         for (int c = warp; c < nc; c += kResWarps) {
@@ -108,66 +129,134 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
             warp_argmax(bv, bi);
             sum = warp_sum(sum);
             T alpha = 0;
-            if (bi >= 0 && row < r) {
+            if (bi >= 0 && step < r) {
                 const T* x = xs + static_cast<int64_t>(bi) * r;
                 T* dst = P.pub + (static_cast<int64_t>(slot) * G + b) * r;
-                for (int64_t t = row + lane; t < r; t += 32) dst[t] = x[t];
-                alpha = x[row];
+                for (int64_t t = step + lane; t < r; t += 32) dst[t] = x[t];
+                alpha = x[step];
             }
+            Cand* rec = P.cand + slot * G + b;
             if (lane == 0) {
-                Cand cd;
-                cd.nu = bv;
-                cd.sumnu = sum;
-                cd.total = first ? sum : 0.0;
-                cd.s2 = bi >= 0 && row < r ? bv : 0.0;    // nu is the exact norm of rows row..r-1
-                cd.alpha = static_cast<double>(alpha);
-                cd.idx = bi >= 0 ? static_cast<int>(c0 + bi) : -1;
-                cd.pad = 0;
-                P.cand[slot * G + b] = cd;
+                rec->nu = bv;
+                rec->sumnu = sum;
+                rec->total = step == 0 ? sum : 0.0;
+                rec->s2 = bi >= 0 && step < r ? bv : 0.0;   // nu is the exact norm of rows step..r-1
+                rec->alpha = static_cast<double>(alpha);
+                rec->idx = bi >= 0 ? static_cast<int>(c0 + bi) : -1;
             }
+            // every lane's stores (column and record) before the stamp
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release_s32(&rec->stamp, step + 1);
         }
     };
 
-    publish(0, 0, true);
-    bool ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &s_ok);
-
-    int k = 0;
-    double total = 0.0;
-    for (int j = 0; ok && j < P.kcap; ++j) {
-        const int slot = j & 1;
-        // ---- the pivot: every warp reduces the candidate table in the same order
-        double bv = -1.0, sn = 0.0, tt = 0.0;
-        int bg = -1;
-        for (int g = lane; g < G; g += 32) {
-            const Cand c = load_cand(P.cand + slot * G + g);
-            const double nu = norm_key(c.nu);
-            if (c.idx >= 0 && (bg < 0 || nu > bv)) { bv = nu; bg = g; }   // g ascends per lane
-            sn += c.sumnu;
-            tt += c.total;
+    // ---- warp 0: wait (bounded) until every record of step `step` carries its stamp,
+    // reduce the table in a fixed order (ties to the smaller CTA, hence column) and, unless
+    // `final`, decide the step and stage the winner's rows step..r-1 in shared memory.
+    // s_go: 1 carry on, 0 stop (tolerance met, or zero residual: info = step + 1), -1 watchdog
+    double total = 0.0;   // warp 0: ||W||_F^2, from the first table
+    auto decide = [&](int step, bool final_wait) {
+        const int slot = step & 1;
+        // a lane's stamps are read together (relaxed loads, one round trip per poll); once all
+        // have arrived, a fence orders the reads of the records and columns after them
+        bool ok = true;
+        const uint64_t t0 = globaltimer_ns();
+        uint32_t it = 0;
+        while (true) {
+            bool ready = true;
+#pragma unroll
+            for (int q = 0; q < kTableLanes; ++q) {
+                const int g = 32 * q + lane;
+                if (g < G) ready &= ld_relaxed_s32(&P.cand[slot * G + g].stamp) == step + 1;
+            }
+            if (__all_sync(0xffffffffu, ready)) break;
+            if ((++it & 15u) == 0) {
+                bool stop = false;
+                if (lane == 0) {
+                    if (ld_volatile_i32(&P.ctrl->abort)) {
+                        stop = true;
+                    } else if (globaltimer_ns() - t0 > P.limit_ns) {
+                        atomicExch(&P.ctrl->abort, 1);
+                        stop = true;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, stop, 0)) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (!ok) {
+            if (lane == 0) s_go = -1;
+            return;
+        }
+        if (final_wait) {
+            if (lane == 0) s_go = 0;
+            return;
+        }
+        double bv = -1.0, sn = 0.0, tt = 0.0, wa = 0.0, ws = 0.0;
+        int bg = -1, wi = -1;
+        Cand e[kTableLanes];
+#pragma unroll
+        for (int q = 0; q < kTableLanes; ++q) {
+            const int g = 32 * q + lane;
+            if (g < G) e[q] = load_cand(P.cand + slot * G + g);
+            else e[q].idx = -1;
+        }
+#pragma unroll
+        for (int q = 0; q < kTableLanes; ++q) {
+            const int g = 32 * q + lane;
+            if (g >= G) continue;
+            const double nu = norm_key(e[q].nu);
+            if (e[q].idx >= 0 && (bg < 0 || nu > bv)) {   // g ascends per lane
+                bv = nu; bg = g; wa = e[q].alpha; ws = e[q].s2; wi = e[q].idx;
+            }
+            sn += e[q].sumnu;
+            tt += e[q].total;
         }
         warp_argmax(bv, bg);
         sn = __shfl_sync(0xffffffffu, warp_sum(sn), 0);
-        if (j == 0) total = __shfl_sync(0xffffffffu, warp_sum(tt), 0);
-        double alpha_d = 0.0, s2 = 0.0;
-        int p = -1;
-        if (bg >= 0) {
-            const Cand w = load_cand(P.cand + slot * G + bg);
-            p = w.idx;
-            alpha_d = w.alpha;
-            s2 = w.s2;
+        if (step == 0) total = __shfl_sync(0xffffffffu, warp_sum(tt), 0);
+        const int src_lane = bg >= 0 ? (bg & 31) : 0;
+        const double alpha = __shfl_sync(0xffffffffu, wa, src_lane);
+        const double s2 = __shfl_sync(0xffffffffu, ws, src_lane);
+        const int p = bg >= 0 ? __shfl_sync(0xffffffffu, wi, src_lane) : -1;
+        int go = 1;
+        if (P.rel_tol > 0.0 && sqrt(fmax(sn, 0.0)) <= P.rel_tol * sqrt(total)) {
+            go = 0;
+        } else if (p < 0 || !(bv > 0.0) || !(s2 > 0.0)) {
+            go = 0;
+            if (b == 0 && lane == 0) set_info(P.info, step + 1);
+        } else {
+            const T* src = P.pub + (static_cast<int64_t>(slot) * G + bg) * r;
+            for (int64_t t = step + lane; t < r; t += 32) xps[t] = __ldcg(src + t);
         }
-        if (P.rel_tol > 0.0 && sqrt(fmax(sn, 0.0)) <= P.rel_tol * sqrt(total)) break;
-        if (p < 0 || !(bv > 0.0) || !(s2 > 0.0)) {
-            if (b == 0 && tid == 0) set_info(P.info, j + 1);
-            break;
+        if (lane == 0) {
+            s_go = go;
+            s_p = p;
+            s_alpha = alpha;
+            s_s2 = s2;
         }
-        // ---- reflector scalars; the pivot column as published (not modified in this step)
-        const T alpha = static_cast<T>(alpha_d);
-        const T snorm = sqrt(static_cast<T>(s2));
+    };
+
+    publish(0);
+    int k = 0, go = 1;
+    for (int j = 0; j < P.kcap; ++j) {
+        if (warp == 0) decide(j, false);
+        __syncthreads();
+        go = s_go;
+        if (go <= 0) break;
+        // ---- reflector scalars; the pivot column staged in xps (not modified in this step)
+        const int p = s_p;
+        const T alpha = static_cast<T>(s_alpha);
+        const T snorm = sqrt(static_cast<T>(s_s2));
         const T beta = alpha >= T(0) ? -snorm : snorm;
         const T rbeta = T(1) / beta;
         const T inv = T(1) / (alpha - beta);
-        const T* xp = P.pub + (static_cast<int64_t>(slot) * G + bg) * r;
+        const T* xp = xps;
         const int cp = (p >= c0 && p < c1) ? static_cast<int>(p - c0) : -1;
         if (cp >= 0 && (cp % kResWarps) == warp && lane == 0) {
             sel_s[cp] = 1;
@@ -182,10 +271,10 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
             T s0 = 0, s1 = 0;
             int64_t t = j + lane;
             for (; t + 32 < r; t += 64) {
-                s0 = fma(__ldcg(xp + t), x[t], s0);
-                s1 = fma(__ldcg(xp + t + 32), x[t + 32], s1);
+                s0 = fma(xp[t], x[t], s0);
+                s1 = fma(xp[t + 32], x[t + 32], s1);
             }
-            if (t < r) s0 = fma(__ldcg(xp + t), x[t], s0);
+            if (t < r) s0 = fma(xp[t], x[t], s0);
             T S = warp_sum(s0 + s1);
             const T X = x[j];
             S = fma(-beta, X, S);
@@ -195,15 +284,15 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
             T q0 = 0, q1 = 0;
             t = j + 1 + lane;
             for (; t + 32 < r; t += 64) {
-                const T a0 = fma(-sv, __ldcg(xp + t), x[t]);
-                const T a1 = fma(-sv, __ldcg(xp + t + 32), x[t + 32]);
+                const T a0 = fma(-sv, xp[t], x[t]);
+                const T a1 = fma(-sv, xp[t + 32], x[t + 32]);
                 x[t] = a0;
                 x[t + 32] = a1;
                 q0 = fma(a0, a0, q0);
                 q1 = fma(a1, a1, q1);
             }
             if (t < r) {
-                const T a0 = fma(-sv, __ldcg(xp + t), x[t]);
+                const T a0 = fma(-sv, xp[t], x[t]);
                 x[t] = a0;
                 q0 = fma(a0, a0, q0);
             }
@@ -211,25 +300,40 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
             if (lane == 0) nu_s[c] = nu;
         }
         __syncwarp();
-        publish(slot ^ 1, j + 1, false);
-        ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &s_ok);
+        publish(j + 1);
         k = j + 1;
     }
-    if (!ok) {
+    if (go < 0) {
         if (tid == 0) set_info(P.info, kInfoWatchdog);
         return;
     }
-    if (b == 0) list_complement(P.J, P.sel, P.n, k, P.k_out, cnt);
+    if (b == 0) {
+        // after the last step, CTA 0 waits for the final table too: every pivot's flag
+        // (written before its owner's next record) is then visible to the listing
+        if (go == 1) {
+            if (warp == 0) decide(k, true);
+            __syncthreads();
+            if (s_go < 0) {
+                if (tid == 0) set_info(P.info, kInfoWatchdog);
+                return;
+            }
+        }
+        list_complement(P.J, P.sel, P.n, k, P.k_out, cnt);
+    }
 }
 
 template <typename T>
 cudaError_t launch_cpqr_resident(const CpqrParams<T>& P, int grid, size_t smem, cudaStream_t s) {
+    if (grid > 32 * kTableLanes) return cudaErrorInvalidValue;
     auto kern = k_cpqr_resident<T>;
     if (smem > 48 * 1024) {
         const cudaError_t e =
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
+    // clear the stamps of both table slots: a record of this launch is recognised by them
+    cudaError_t e = cudaMemsetAsync(P.cand, 0, 2 * static_cast<size_t>(grid) * sizeof(Cand), s);
+    if (e != cudaSuccess) return e;
     CpqrParams<T> Pc = P;
     void* args[] = {&Pc};
     return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), dim3(grid), dim3(kResWarps * 32), args, smem,
