@@ -479,6 +479,47 @@ def config1_leg(gid, wl, dev, peaks, reps=20):
     return out
 
 
+def low_id_leg(gid, wl, dev, peaks, reps=20):
+    """Algorithm 2 as the paper states it, on its own test matrices (Slow, Fast: 1000 x 1000,
+    sigma_i = i^-1, i^-4, k = 20): the whole matrix cast to half / bfloat16 (scaled per
+    64-row block and column), FP32 pivoted QR of A_L, FP64 T; against the plain FP64 ID of
+    the same matrix.  Errors of both approximations (A_hat_M from A, A_hat_L from A_L)
+    against A, relative 2-norms by 60 FP64 power iterations on the GPU."""
+    import torch
+
+    def norm2(X, iters=60):
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        v = torch.randn(X.shape[1], dtype=torch.float64, device=dev, generator=g)
+        v /= v.norm()
+        s_ = 0.0
+        for _ in range(iters):
+            w = X.T @ (X @ v)
+            s_ = float(w.norm().sqrt())
+            v = w / w.norm()
+        return s_
+
+    out = {"workload": "paper Slow / Fast matrices 1000x1000 (sigma_i = i^-1, i^-4; seed 21), k = 20, no sketch"}
+    k = 20
+    for kind in ("slow", "fast"):
+        A = torch.from_numpy(wl.paper_dataset(kind, seed=21)).to(dev)
+        na = norm2(A)
+        row = {}
+        for prec in ("plain_f64", "low_bf16", "low_f16"):
+            ms, stages, res = _time_id(gid, dev, A, k, reps, precision=prec)
+            J, T = res[0], res[1][:k, : A.shape[1] - k]
+            hm = gid.reconstruct(A, J, T, k)
+            item = {"ms_per_id": ms, "ids_per_s": 1e3 / ms, "stages_ms": stages, "e_M": norm2(A - hm) / na}
+            if prec != "plain_f64":
+                AL = gid.low_cast(A, prec)
+                hl = gid.reconstruct(AL, J, T, k).double()
+                item["e_L"] = norm2(A - hl) / na
+                item["speedup_vs_plain_f64"] = row["plain_f64"]["ms_per_id"] / ms
+            row[prec] = item
+        out[kind] = row
+    return out
+
+
 def config3_leg(gid, wl, dev, peaks, reps=3):
     """The 65536 x 1000 FP32 snapshot matrix (travelling sinusoids plus 1e-6 noise) at
     tolerance 1e-6: the plain FP64 ID of A itself against sketched mixed IDs (half sketch,
@@ -954,6 +995,7 @@ def main():
         # snapshot matrix at tolerance 1e-6, the differentiable 64 x 2048 x 512 batch
         if not args.no_configs:
             line["plain_1000x500"] = config1_leg(gid, wl, dev, peaks)
+            line["low_id_1000x1000"] = low_id_leg(gid, wl, dev, peaks)
             line["snapshot_65536x1000"] = config3_leg(gid, wl, dev, peaks)
             line["differentiable_64x2048x512"] = config5_leg(gid, wl, dev, peaks)
 

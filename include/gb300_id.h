@@ -70,14 +70,24 @@ typedef enum {
  *   MIXED_F16     as MIXED_BF16 with IEEE half (Omega is half).
  *   MIXED_BF16X2  A split into 2 bfloat16 pieces (hi + lo), both sketched.
  *   MIXED_BF16X3  A split into 3 bfloat16 pieces: an FP32-accurate sketch at the
- *                 same HBM traffic.                                              */
+ *                 same HBM traffic.
+ *   LOW_BF16      Algorithm 2 as the paper states it (no sketch): the whole of A is
+ *   LOW_F16       cast to the low-precision matrix A_L (bfloat16 / half, scaled by
+ *                 powers of two per (64-row block, column) like the mixed sketch's
+ *                 cast), and the pivoted QR of A_L runs in FP32 arithmetic on those
+ *                 values (low-precision data, single-precision accumulation); T in FP64
+ *                 with refinement.  The ID's columns can then be taken from A (the
+ *                 mixed ID A_hat_M = A(:,J) P) or from A_L (the low ID
+ *                 A_hat_L = A_L(:,J) P, A_L from id_low_cast). */
 typedef enum {
     ID_PLAIN_F64 = 0,
     ID_PLAIN_F32 = 1,
     ID_MIXED_BF16 = 2,
     ID_MIXED_F16 = 3,
     ID_MIXED_BF16X2 = 4,
-    ID_MIXED_BF16X3 = 5
+    ID_MIXED_BF16X3 = 5,
+    ID_LOW_BF16 = 6,
+    ID_LOW_F16 = 7
 } id_precision_t;
 
 /* Rows per power-of-two scaling block of the low-precision cast (a block of
@@ -133,7 +143,7 @@ id_status_t id_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n,
  * combinations not listed above (mixed precisions require sketch = 1;
  * PLAIN_F32 requires sketch = 0 and takes A as ID_F32, or as ID_F64 whose
  * values are rounded to FP32 (nearest even) when the pivoted QR loads them;
- * PLAIN_F64 with a sketch requires ID_F64). */
+ * LOW_* require sketch = 0; PLAIN_F64 with a sketch requires ID_F64). */
 id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
                       const id_opts_t* opts,
                       int32_t* J, double* T, int64_t ldt, int32_t* k_out, int32_t* info,
@@ -193,6 +203,26 @@ id_status_t id_sketch_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, i
 id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
                           int32_t precision, uint16_t* pieces, int32_t* shifts,
                           int32_t* info, void* stream);
+
+/* The low-precision matrix A_L of Algorithm 2 (A_L = fl(A)), as FP32 values: for every
+ * block of ID_SCALE_BLOCK_ROWS rows of a column, the shift s of id_scale_cast and
+ * A_L(i,j) = 2^s fl_low(x 2^-s), fl_low the first piece of that cast (bfloat16 for
+ * LOW_BF16 / MIXED_BF16*, half for LOW_F16 / MIXED_F16), x = A(i,j) taken at FP32
+ * precision.  This is the matrix the LOW_* precisions of id_factor pivot.  AL: m x n
+ * floats, column-major, ldal >= m.  info (nullable) -1 if A holds a non-finite value.
+ * A_L entries below the FP32 normal range (data spanning more than the FP32 range)
+ * round to FP32 subnormals or zero.  Errors: ID_ERR_ARG, ID_ERR_CUDA. */
+id_status_t id_low_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t precision,
+                        float* AL, int64_t ldal, int32_t* info, void* stream);
+
+/* A_hat = A(:,J[0:k]) P of one matrix (Sec. 1.1; Algorithm 2's last line with A = A_D
+ * for the mixed ID, A = A_L for the low ID): A m x n of a_dtype (column-major, lda),
+ * J as id_factor returns it, T k x (n-k) doubles (ldt >= k).  Ahat: m x n of a_dtype
+ * (ldh >= m), columns J[0:k] copied from A, columns J[k:n] accumulated in FP64.
+ * Ahat must not alias A.  Errors: ID_ERR_ARG, ID_ERR_CUDA. */
+id_status_t id_reconstruct_one(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                               const int32_t* J, int32_t k, const double* T, int64_t ldt, void* Ahat, int64_t ldh,
+                               void* stream);
 
 /* Adjoint of the column ID with the pivot set J held fixed (the
  * differentiable form; the paper does not differentiate the ID), FP32.

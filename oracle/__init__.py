@@ -220,6 +220,27 @@ def interp_decomp(a: np.ndarray, k: int | None = None, tol: float | None = None,
             "gaps": gaps[:kk]}
 
 
+# ------------------------------------------------------ Algorithm 2 (low ID)
+
+def low_cast(a: np.ndarray, fmt: str, block_rows: int = 64) -> np.ndarray:
+    """A_L = fl(A) of Algorithm 2 with power-of-two scaling per (row block, column):
+    the first piece of ``quantize`` times 2^shift (FP64 values)."""
+    pieces, shifts, _ = quantize(a, fmt, block_rows, 1)
+    m = pieces.shape[1]
+    scale = np.repeat(2.0 ** shifts.astype(np.float64), block_rows, axis=0)[:m]
+    return np.asfortranarray(pieces[0] * scale)
+
+
+def low_id(a: np.ndarray, fmt: str, k: int, block_rows: int = 64):
+    """Algorithm 2 without a sketch: the ID of A_L = low_cast(A).  Returns the ID of A_L
+    (dict as interp_decomp) with A_L added under "AL"; the mixed approximation is
+    reconstruct(A, J, T, k), the low one reconstruct(AL, J, T, k) (Sec. 2)."""
+    al = low_cast(a, fmt, block_rows)
+    out = interp_decomp(al, k=k)
+    out["AL"] = al
+    return out
+
+
 # ------------------------------------------------------------ reconstruction
 
 def coefficient_matrix(J: np.ndarray, T: np.ndarray, k: int, n: int) -> np.ndarray:

@@ -20,7 +20,7 @@ import torch
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
     "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
-    "BatchPlan", "shard_batch", "probe_fma_peak",
+    "BatchPlan", "shard_batch", "probe_fma_peak", "low_cast", "reconstruct",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -30,6 +30,7 @@ _lock = threading.Lock()
 
 PRECISIONS = {
     "plain_f64": 0, "plain_f32": 1, "mixed_bf16": 2, "mixed_f16": 3, "mixed_bf16x2": 4, "mixed_bf16x3": 5,
+    "low_bf16": 6, "low_f16": 7,
 }
 _DTYPE = {torch.float64: 0, torch.float32: 1}
 ID_SCALE_BLOCK_ROWS = 64
@@ -108,6 +109,10 @@ def load():
         lib.id_batch_shard.argtypes = [i32, p, p, p, i32, i32, p, p]
         lib.id_probe_fma_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), p]
         lib.id_probe_fma_peak.restype = ctypes.c_int
+        lib.id_low_cast.argtypes = [p, ctypes.c_int, i64, i64, i64, i32, p, i64, p, p]
+        lib.id_low_cast.restype = ctypes.c_int
+        lib.id_reconstruct_one.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i32, p, i64, p, i64, p]
+        lib.id_reconstruct_one.restype = ctypes.c_int
         for name in ("id_batch_plan_create", "id_batch_plan_query", "id_batch_workspace_size", "id_batch_bind",
                      "id_factor_batched", "id_batch_autotune", "id_batch_shard"):
             getattr(lib, name).restype = ctypes.c_int
@@ -197,8 +202,9 @@ def id_factor(A: torch.Tensor, k: int | None = None, *, tol: float | None = None
               out=None, sync: bool = True) -> IDResult:
     """Column ID of the CUDA matrix A (m, n); sketched when ``omega`` (ell, m) is given.
 
-    ``precision``: plain_f64 | plain_f32 | mixed_bf16 | mixed_f16 | mixed_bf16x2 | mixed_bf16x3
-    (mixed precisions need ``omega`` in bfloat16/half; plain_f64 sketches with a float64 omega).
+    ``precision``: plain_f64 | plain_f32 | mixed_bf16 | mixed_f16 | mixed_bf16x2 | mixed_bf16x3 |
+    low_bf16 | low_f16 (mixed precisions need ``omega`` in bfloat16/half; plain_f64 sketches with
+    a float64 omega; low_* pivot the cast A_L of the whole matrix, no omega).
     With ``sync=False`` the result tensors are returned without waiting; k and info are then -1.
     """
     _require_cuda(A, omega)
@@ -295,6 +301,41 @@ def id_scale_cast(A: torch.Tensor, precision: str = "mixed_bf16", stream=None):
                                 pieces.data_ptr(), shifts.data_ptr(), info.data_ptr(), _stream_ptr(stream)),
            "id_scale_cast")
     return pieces.transpose(1, 2), shifts.t(), info
+
+
+def low_cast(A: torch.Tensor, precision: str = "low_f16", stream=None, return_info: bool = False):
+    """A_L of Algorithm 2 as a float32 (m, n) tensor: 2^s fl_low(x 2^-s) per (64-row block,
+    column), the matrix the low_* precisions pivot (low_bf16 / mixed_bf16*: bfloat16,
+    low_f16 / mixed_f16: half)."""
+    _require_cuda(A)
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    out = torch.empty((n, m), dtype=torch.float32, device=a.device).t()
+    info = torch.zeros(1, dtype=torch.int32, device=a.device)
+    _check(load().id_low_cast(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, PRECISIONS[precision], out.data_ptr(), m,
+                              info.data_ptr(), _stream_ptr(stream)), "id_low_cast")
+    return (out, info) if return_info else out
+
+
+def reconstruct(A: torch.Tensor, J: torch.Tensor, T: torch.Tensor, k: int, stream=None) -> torch.Tensor:
+    """A_hat = A(:, J[:k]) P of one (m, n) float64 or float32 matrix (FP64 accumulation):
+    with A = A_D the ID's approximation (the mixed ID for low/mixed precisions), with
+    A = low_cast(A_D) the low ID of Algorithm 2."""
+    _require_cuda(A, J, T)
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    j = J.reshape(n).to(torch.int32).contiguous()
+    out = torch.empty((n, m), dtype=A.dtype, device=a.device).t()
+    if k < n:
+        t = T[:k, : n - k]
+        if not (t.stride(0) == 1 and t.stride(1) >= k):
+            t = t.t().contiguous().t()
+        tptr, ldt = t.data_ptr(), max(t.stride(1), k)
+    else:
+        tptr, ldt = None, k
+    _check(load().id_reconstruct_one(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, j.data_ptr(), k, tptr, ldt,
+                                     out.data_ptr(), m, _stream_ptr(stream)), "id_reconstruct_one")
+    return out
 
 
 # ------------------------------------------------------------------ fixed-pivot adjoint

@@ -53,12 +53,15 @@ bool is_mixed(int p) {
     return p == ID_MIXED_BF16 || p == ID_MIXED_F16 || p == ID_MIXED_BF16X2 || p == ID_MIXED_BF16X3;
 }
 
+bool is_low(int p) { return p == ID_LOW_BF16 || p == ID_LOW_F16; }
+
 // Everything id_factor derives from its arguments before touching the GPU.
 struct FactorPlan {
     int64_t rows = 0;       // rows of the matrix being pivoted (ell or m)
     int kcap = 0;           // rank capacity (k or k_max)
     int w_f64 = 1;          // working precision of the pivoted QR
     int mixed = 0, sketch = 0;
+    int low = 0;            // Algorithm 2 on the whole matrix: pivot the cast A_L
     int64_t omega_ld = 0;
     SketchPlan sp;
     SketchF64Plan sp64;
@@ -107,11 +110,12 @@ id_status_t plan_factor(id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, c
     if (n > (int64_t(1) << 31) - 1) return ID_ERR_UNSUPPORTED;
     FactorPlan p;
     const int prec = o->precision;
-    if (prec < ID_PLAIN_F64 || prec > ID_MIXED_BF16X3) return ID_ERR_ARG;
+    if (prec < ID_PLAIN_F64 || prec > ID_LOW_F16) return ID_ERR_ARG;
     p.mixed = is_mixed(prec);
+    p.low = is_low(prec);
     p.sketch = o->sketch ? 1 : 0;
     if (p.mixed && !p.sketch) return ID_ERR_ARG;
-    if (prec == ID_PLAIN_F32 && p.sketch) return ID_ERR_ARG;
+    if ((prec == ID_PLAIN_F32 || p.low) && p.sketch) return ID_ERR_ARG;
     p.w_f64 = (prec == ID_PLAIN_F64) ? 1 : 0;
     if (p.sketch) {
         if (o->ell < 1 || o->ell > m || !o->omega) return ID_ERR_ARG;
@@ -143,8 +147,9 @@ id_status_t plan_factor(id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, c
         }
     }
     if (!cpqr_plan(p.rows, n, p.w_f64 ? 8 : 4, &p.cp)) return ID_ERR_UNSUPPORTED;
-    // the cluster kernel reads A directly when it is a short float matrix (PLAIN_F32, no sketch)
-    const bool short_f32 = !p.w_f64 && (p.sketch || a_dtype == ID_F32);
+    // the cluster kernel reads A directly when it is a short float matrix (PLAIN_F32, no
+    // sketch), or the sketch Y, or the cast A_L
+    const bool short_f32 = !p.w_f64 && (p.sketch || p.low || a_dtype == ID_F32);
     p.use_cluster = short_f32 && cpqr_cluster_plan(p.rows, n, &p.ccp) ? 1 : 0;
     p.bytes = carve_factor(nullptr, n, p, nullptr);
     *plan = p;
@@ -241,6 +246,11 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
                                   static_cast<double*>(f.partial), static_cast<double*>(f.W), opts->ell, info, s,
                                   stage_event(1));
         }
+    } else if (e == cudaSuccess && p.low) {
+        // Algorithm 2's A_L: the scaled low-precision cast of A, as FP32 values, in W
+        e = launch_low_cast(A, a_f64, m, n, lda, opts->precision == ID_LOW_F16 ? 1 : 0, static_cast<float*>(f.W),
+                            m, info, s);
+        record_stage(1, s);
     } else if (e == cudaSuccess) {
         record_stage(1, s);
         cpqr_src = A;
@@ -253,7 +263,7 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
             // short FP32 matrix: the sketch Y (or a short A) goes straight to the cluster kernel
             const float* Wf = static_cast<const float*>(f.W);
             int64_t ldw = p.rows;
-            if (!p.sketch) {
+            if (!p.sketch && !p.low) {
                 Wf = static_cast<const float*>(A);
                 ldw = lda;
             }
@@ -331,6 +341,30 @@ id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t 
     cudaError_t e = cudaSuccess;
     if (info) e = cudaMemsetAsync(info, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = launch_scale_cast(A, a_dtype == ID_F64, m, n, lda, precision, pieces, shifts, info, s);
+    return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
+}
+
+id_status_t id_low_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t precision,
+                        float* AL, int64_t ldal, int32_t* info, void* stream) {
+    if (!A || !AL || m < 1 || n < 1 || lda < m || ldal < m) return ID_ERR_ARG;
+    if (a_dtype != ID_F64 && a_dtype != ID_F32) return ID_ERR_ARG;
+    if (!is_low(precision) && !is_mixed(precision)) return ID_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (info) e = cudaMemsetAsync(info, 0, sizeof(int32_t), s);
+    const int f16 = (precision == ID_LOW_F16 || precision == ID_MIXED_F16) ? 1 : 0;
+    if (e == cudaSuccess) e = launch_low_cast(A, a_dtype == ID_F64, m, n, lda, f16, AL, ldal, info, s);
+    return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
+}
+
+id_status_t id_reconstruct_one(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                               const int32_t* J, int32_t k, const double* T, int64_t ldt, void* Ahat, int64_t ldh,
+                               void* stream) {
+    if (!A || !J || !Ahat || m < 1 || n < 1 || lda < m || ldh < m || k < 1 || k > n) return ID_ERR_ARG;
+    if (a_dtype != ID_F64 && a_dtype != ID_F32) return ID_ERR_ARG;
+    if (k < n && (!T || ldt < k)) return ID_ERR_ARG;
+    const cudaError_t e = launch_reconstruct_one(A, a_dtype == ID_F64, m, n, lda, J, k, T, ldt, Ahat, ldh,
+                                                 static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
 }
 

@@ -113,6 +113,9 @@ cudaError_t launch_sketch_f64(const double* A, int64_t m, int64_t n, int64_t lda
 cudaError_t launch_scale_cast(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                               int precision, uint16_t* pieces, int32_t* shifts, int32_t* info,
                               cudaStream_t s);
+// A_L of Algorithm 2 as FP32 values (2^s fl_low(x 2^-s) per 64-row block and column), out: m x n, ldo.
+cudaError_t launch_low_cast(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, int f16, float* out,
+                            int64_t ldo, int32_t* info, cudaStream_t s);
 
 // ---- pivoted QR (cpqr.cu)
 struct CpqrPlan {
@@ -164,6 +167,8 @@ cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* unit
                                    int warps, const double* R_base, const int32_t* J_base,
                                    const int32_t* k_out, int32_t* infos, double* T_base,
                                    const BatchTotals& tot, int refine_steps, cudaStream_t s);
+cudaError_t launch_reconstruct_one(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, const int32_t* J,
+                                   int k, const double* T, int64_t ldt, void* Ahat, int64_t ldh, cudaStream_t s);
 cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                                 const int32_t* J, const int32_t* k_ptr, const double* T,
                                 int64_t ldt, double* acc2, double* err_out, cudaStream_t s);

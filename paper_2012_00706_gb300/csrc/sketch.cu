@@ -1092,4 +1092,73 @@ cudaError_t launch_scale_cast(const void* A, int a_f64, int64_t m, int64_t n, in
     return cudaGetLastError();
 }
 
+// ------------------------------------------------- the low-precision matrix A_L
+
+// A_L of Algorithm 2 as FP32 values: every entry of every (64-row block, column) becomes
+// 2^s fl_low(x 2^-s), the first piece of the scaled cast above times the block's power of
+// two (exact in FP32 while the result is a normal float).  One thread per (block, column).
+__global__ void k_low_cast(const void* __restrict__ A, int a_f64, int64_t m, int64_t n, int64_t lda, int f16,
+                           float* __restrict__ out, int64_t ldo, int32_t* info) {
+    const int64_t nb = (m + kChunkRows - 1) / kChunkRows;
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= nb * n) return;
+    const int64_t j = idx / nb, b = idx - j * nb;
+    const int64_t r0 = b * kChunkRows;
+    const int rows = static_cast<int>(min(static_cast<int64_t>(kChunkRows), m - r0));
+    float* dst = out + j * ldo + r0;
+    if (a_f64) {
+        const double* col = static_cast<const double*>(A) + j * lda + r0;
+        uint32_t mx = 0;
+        for (int r = 0; r < rows; ++r) mx = max(mx, static_cast<uint32_t>(__double2hiint(col[r])) & 0x7fffffffu);
+        if ((mx >> 20) == 0x7FFu) set_info(info, kInfoNonFinite);
+        const int shift = shift_from_max_f64hi(mx, f16);
+        const F64CastBlock cb = f64_cast_block(shift);
+        for (int r = 0; r < rows; r += 2) {
+            auto conv = [&](double x) {
+                bool slow = cb.slow;
+                const float f = scaled_f32_from_f64_fast(x, static_cast<uint32_t>(__double2hiint(x)) << 1, cb, slow);
+                return slow ? scaled_f32_from_f64(x, shift) : f;
+            };
+            float v0 = conv(col[r]);
+            float v1 = r + 1 < rows ? conv(col[r + 1]) : 0.f;
+            const uint32_t w = take_piece2(v0, v1, f16);
+            const float p0 = f16 ? __half2float(__ushort_as_half(static_cast<unsigned short>(w & 0xFFFFu)))
+                                 : __uint_as_float(w << 16);
+            const float p1 = f16 ? __half2float(__ushort_as_half(static_cast<unsigned short>(w >> 16)))
+                                 : __uint_as_float(w & 0xFFFF0000u);
+            dst[r] = ldexpf(p0, shift);
+            if (r + 1 < rows) dst[r + 1] = ldexpf(p1, shift);
+        }
+    } else {
+        const float* col = static_cast<const float*>(A) + j * lda + r0;
+        uint32_t mx = 0;
+        for (int r = 0; r < rows; ++r) mx = max(mx, __float_as_uint(col[r]) & 0x7fffffffu);
+        if ((mx >> 23) == 0xFFu) set_info(info, kInfoNonFinite);
+        const int shift = shift_from_max_f32(mx, f16);
+        for (int r = 0; r < rows; r += 2) {
+            auto conv = [&](float x) {
+                bool slow = false;
+                const float f = scaled_f32_from_f32_fast(x, shift, slow);
+                return slow ? scaled_f32_from_f32(x, shift) : f;
+            };
+            float v0 = conv(col[r]);
+            float v1 = r + 1 < rows ? conv(col[r + 1]) : 0.f;
+            const uint32_t w = take_piece2(v0, v1, f16);
+            const float p0 = f16 ? __half2float(__ushort_as_half(static_cast<unsigned short>(w & 0xFFFFu)))
+                                 : __uint_as_float(w << 16);
+            const float p1 = f16 ? __half2float(__ushort_as_half(static_cast<unsigned short>(w >> 16)))
+                                 : __uint_as_float(w & 0xFFFF0000u);
+            dst[r] = ldexpf(p0, shift);
+            if (r + 1 < rows) dst[r + 1] = ldexpf(p1, shift);
+        }
+    }
+}
+
+cudaError_t launch_low_cast(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, int f16, float* out,
+                            int64_t ldo, int32_t* info, cudaStream_t s) {
+    const int64_t total = ((m + kChunkRows - 1) / kChunkRows) * n;
+    k_low_cast<<<static_cast<unsigned>((total + 127) / 128), 128, 0, s>>>(A, a_f64, m, n, lda, f16, out, ldo, info);
+    return cudaGetLastError();
+}
+
 }  // namespace gid

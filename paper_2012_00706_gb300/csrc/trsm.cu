@@ -560,4 +560,90 @@ cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ reconstruction
+
+// Ahat(:, J[k + c]) = A(:, J[0:k]) T(:, c): a 64 x 64 output tile per CTA (256 threads,
+// 4 x 4 outputs each), k in chunks of 16 staged in shared memory, FP64 accumulation.
+constexpr int kRecTile = 64;
+constexpr int kRecK = 16;
+
+template <typename TA>
+__global__ void __launch_bounds__(256)
+k_reconstruct_one(const TA* __restrict__ A, int64_t m, int64_t lda, const int32_t* __restrict__ J, int k,
+                  const double* __restrict__ T, int64_t ldt, int64_t nc, TA* __restrict__ Ahat, int64_t ldh) {
+    __shared__ double As[kRecK][kRecTile + 1];
+    __shared__ double Ts[kRecK][kRecTile + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kRecTile;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.y) * kRecTile;
+    double acc[4][4] = {};
+    for (int b0 = 0; b0 < k; b0 += kRecK) {
+        for (int idx = threadIdx.x; idx < kRecK * kRecTile; idx += 256) {
+            const int bb = idx / kRecTile, i = idx % kRecTile;
+            const int b = b0 + bb;
+            const int64_t row = r0 + i, c = q0 + i;
+            As[bb][i] = (b < k && row < m) ? static_cast<double>(A[static_cast<int64_t>(J[b]) * lda + row]) : 0.0;
+            Ts[bb][i] = (b < k && c < nc) ? T[c * ldt + b] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int bb = 0; bb < kRecK; ++bb) {
+            double a[4], t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[bb][ty * 4 + u]; t[u] = Ts[bb][tx * 4 + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], t[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int64_t c = q0 + tx * 4 + v;
+        if (c >= nc) continue;
+        TA* dst = Ahat + static_cast<int64_t>(J[k + c]) * ldh;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t row = r0 + ty * 4 + u;
+            if (row < m) dst[row] = static_cast<TA>(acc[u][v]);
+        }
+    }
+}
+
+// Ahat(:, J[b]) = A(:, J[b]) for the skeleton columns b < k.
+template <typename TA>
+__global__ void k_copy_skeleton(const TA* __restrict__ A, int64_t m, int64_t lda, const int32_t* __restrict__ J,
+                                int k, TA* __restrict__ Ahat, int64_t ldh) {
+    for (int b = blockIdx.y; b < k; b += gridDim.y) {
+        const int64_t col = J[b];
+        for (int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; row < m;
+             row += static_cast<int64_t>(gridDim.x) * blockDim.x)
+            Ahat[col * ldh + row] = A[col * lda + row];
+    }
+}
+
+cudaError_t launch_reconstruct_one(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, const int32_t* J,
+                                   int k, const double* T, int64_t ldt, void* Ahat, int64_t ldh, cudaStream_t s) {
+    const int64_t nc = n - k;
+    const dim3 gs(static_cast<unsigned>(std::min<int64_t>((m + 255) / 256, 64)),
+                  static_cast<unsigned>(std::min(k, 65535)));
+    if (a_f64)
+        k_copy_skeleton<double><<<gs, 256, 0, s>>>(static_cast<const double*>(A), m, lda, J, k,
+                                                   static_cast<double*>(Ahat), ldh);
+    else
+        k_copy_skeleton<float><<<gs, 256, 0, s>>>(static_cast<const float*>(A), m, lda, J, k,
+                                                  static_cast<float*>(Ahat), ldh);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nc <= 0) return e;
+    const dim3 g(static_cast<unsigned>((m + kRecTile - 1) / kRecTile), static_cast<unsigned>((nc + kRecTile - 1) / kRecTile));
+    if (a_f64)
+        k_reconstruct_one<double><<<g, 256, 0, s>>>(static_cast<const double*>(A), m, lda, J, k, T, ldt, nc,
+                                                    static_cast<double*>(Ahat), ldh);
+    else
+        k_reconstruct_one<float><<<g, 256, 0, s>>>(static_cast<const float*>(A), m, lda, J, k, T, ldt, nc,
+                                                   static_cast<float*>(Ahat), ldh);
+    return cudaGetLastError();
+}
+
 }  // namespace gid

@@ -62,7 +62,7 @@ def test_workspace_size_and_argument_checks(lib):
     assert _ws(lib, 0, 1000, 500, k=501)[0] == 1          # k > min(m, n)
     assert _ws(lib, 0, 0, 5, k=1)[0] == 1                 # empty
     assert _ws(lib, 0, 1000, 500, k=50, precision=2)[0] == 1   # mixed without sketch
-    assert _ws(lib, 0, 1000, 500, k=50, precision=7)[0] == 1   # unknown precision
+    assert _ws(lib, 0, 1000, 500, k=50, precision=9)[0] == 1   # unknown precision
     fake_omega = 0x1000
     ok, nb = _ws(lib, 0, 20000, 2000, k=100, sketch=1, ell=110, precision=2, omega=fake_omega)
     assert ok == 0 and nb > 110 * 2000 * 4
@@ -77,6 +77,11 @@ def test_workspace_size_and_argument_checks(lib):
     assert _ws(lib, 1, 1000, 500, k=50, precision=1)[0] == 0
     assert _ws(lib, 0, 1000, 500, k=50, precision=1)[0] == 0
     assert _ws(lib, 1, 20000, 2000, k=100, sketch=1, ell=110, precision=1, omega=fake_omega)[0] == 1
+    # Algorithm 2 on the whole matrix: no sketch
+    assert _ws(lib, 0, 1000, 500, k=50, precision=6)[0] == 0
+    assert _ws(lib, 1, 1000, 500, k=50, precision=7)[0] == 0
+    assert _ws(lib, 0, 20000, 2000, k=100, sketch=1, ell=110, precision=7, omega=fake_omega)[0] == 1
+    assert _ws(lib, 0, 1000, 500, k=50, precision=8)[0] == 1
     # the plain FP64 sketch takes FP64 data only
     assert _ws(lib, 1, 20000, 2000, k=100, sketch=1, ell=110, precision=0, omega=fake_omega)[0] == 1
 

@@ -328,6 +328,31 @@ def test_householder_exact_on_power_of_two_triangle(orc):
     assert np.max(np.abs(T - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
+def test_low_cast_unit_blocks_is_the_library_cast(orc):
+    """Blocks whose largest magnitude already sits in the format's target binade get shift 0,
+    so A_L is the plain round-to-nearest cast: torch's bfloat16 and numpy's float16."""
+    import torch
+    rng = np.random.default_rng(3)
+    a = rng.uniform(-0.999, 0.999, (200, 7)).astype(np.float32)
+    a[0::64, :] = 0.999                                  # each 64-row block's maximum in [0.5, 1)
+    ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(orc.low_cast(a, "bf16"), ref)
+    h = (a * 2.0 ** 14 * 0.999).astype(np.float32)        # maxima in [2^13, 2^14)
+    h[0::64, :] = 2.0 ** 14 * 0.999
+    assert np.array_equal(orc.low_cast(h, "f16"), h.astype(np.float16).astype(np.float64))
+
+
+def test_low_id_of_representable_data_is_the_plain_id(orc):
+    """Integers of at most 8 significant bits are bfloat16 values at any power-of-two
+    scale: A_L = A, and Algorithm 2's low ID equals Algorithm 1's ID."""
+    rng = np.random.default_rng(4)
+    a = np.asfortranarray(rng.integers(-120, 121, (90, 40)).astype(np.float64) * 2.0 ** rng.integers(-5, 6, (1, 40)))
+    out = orc.low_id(a, "bf16", 10)
+    assert np.array_equal(out["AL"], a)
+    ref = orc.interp_decomp(a, k=10)
+    assert np.array_equal(out["J"], ref["J"]) and np.array_equal(out["T"], ref["T"])
+
+
 def test_mgs_crosscheck(orc):
     """The paper's MGS column selection gives the same pivots and |R| as Householder."""
     for seed in range(3):
