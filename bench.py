@@ -605,6 +605,63 @@ def config5_leg(gid, wl, dev, peaks, reps=5):
             "note": "forward includes the host read of the 64 ranks (one synchronisation per batch)"}
 
 
+def figures(gid, wl, dev, ks=tuple(range(1, 52, 5)), ns=(50, 100, 200, 300, 500, 700, 1000)):
+    """The sweeps of the paper's Figs. 1-6 (Sec. 3): the paper's Slow / Medium / Fast
+    matrices (1000 x 1000, sigma_i = i^-1, i^-2, i^-4), target rank k over `ks` with all
+    1000 columns, and column count n over `ns` (first n columns) with k = 20.  For each low
+    format (FP32: the plain FP32 ID of A; bfloat16 and half: Algorithm 2, low_bf16 /
+    low_f16) both approximations, A_hat_M = A(:,J) P and A_hat_L = A_L(:,J) P, against
+    the double ID A_hat_D of the same matrix (d_X = ||A_hat_X - A_hat_D||_2 / ||A||_2,
+    Figs. 1-4) and against A itself (e_X = ||A - A_hat_X||_2 / ||A||_2, Figs. 5-6).  The
+    half column `f16_unscaled` casts A to half without the power-of-two scaling (torch's
+    float16 cast) and pivots it in FP32: the configuration of the paper's half precision
+    runs, whose breakdown on Fast beyond k = 21 it reports.  2-norms: 80 FP64 power
+    iterations on the GPU."""
+    import torch
+
+    def norm2(X, iters=80):
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        v = torch.randn(X.shape[1], dtype=torch.float64, device=dev, generator=g)
+        v /= v.norm()
+        s_ = 0.0
+        for _ in range(iters):
+            w = X.T @ (X @ v)
+            nw = float(w.norm())
+            if nw == 0.0:
+                return 0.0
+            s_ = nw ** 0.5
+            v = w / nw
+        return s_
+
+    def one(A, k):
+        na = norm2(A)
+        d = gid.id_factor(A, k, precision="plain_f64")
+        hd = gid.reconstruct(A, d.J, d.T, d.k)
+        row = {"e_D": norm2(A - hd) / na, "k_D": d.k}
+        forms = [("f32", A, "plain_f32", A.float()), ("bf16", A, "low_bf16", None), ("f16", A, "low_f16", None)]
+        a16 = A.to(torch.float16).float()                      # unscaled half cast of A
+        forms.append(("f16_unscaled", a16, "plain_f32", a16))
+        for name, src, prec, al in forms:
+            res = gid.id_factor(src, k, precision=prec)
+            if res.info != 0 or res.k < 1:
+                row[name] = {"info": res.info, "k": res.k}
+                continue
+            al = al if al is not None else gid.low_cast(A, prec)
+            hm = gid.reconstruct(A, res.J, res.T, res.k)
+            hl = gid.reconstruct(al, res.J, res.T, res.k).double()
+            row[name] = {"k": res.k, "info": res.info, "d_M": norm2(hm - hd) / na, "d_L": norm2(hl - hd) / na,
+                         "e_M": norm2(A - hm) / na, "e_L": norm2(A - hl) / na}
+        return row
+
+    out = {"workload": "paper Slow / Medium / Fast matrices, 1000 x 1000 (seed 21)", "k_sweep": {}, "n_sweep": {}}
+    for kind in ("slow", "medium", "fast"):
+        A = torch.from_numpy(wl.paper_dataset(kind, seed=21)).to(dev)
+        out["k_sweep"][kind] = {str(k): one(A, k) for k in ks}
+        out["n_sweep"][kind] = {str(n): one(A[:, :n].contiguous().t().contiguous().t(), 20) for n in ns}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -621,6 +678,8 @@ def main():
                     help="run only the batched leg (a profiling case) and print its JSON")
     ap.add_argument("--batch-count", type=int, default=512, help="matrices in the batched leg")
     ap.add_argument("--inflight", type=int, default=INFLIGHT, help="IDs in flight in the timed stream")
+    ap.add_argument("--figures", action="store_true",
+                    help="print the k and n sweeps of the paper's Figs. 1-6 as one JSON object and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -645,6 +704,10 @@ def main():
             dist.barrier()
 
     gid.load()
+    if args.figures:
+        if rank == 0:
+            print(json.dumps(figures(gid, wl, dev)), flush=True)
+        return 0
     peaks = alu_peaks(gid)
     if args.batched_only:
         line = {"batched": batched_leg(gid, wl, dev, torch.cuda.current_stream(), count=args.batch_count,
