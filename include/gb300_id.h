@@ -149,6 +149,27 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
                       int32_t* J, double* T, int64_t ldt, int32_t* k_out, int32_t* info,
                       double* err_out, void* work, size_t work_bytes, void* stream);
 
+/* Rank-adaptive randomized ID: the sketching the paper names as a next step (Sec. 5),
+ * grown by blocks of Omega's rows until the ID meets a tolerance on A itself.  For
+ * ell = block, 2 block, ... up to opts->ell:
+ *   Y(ell - b : ell, :) = Omega(ell - b : ell, :) A     (only the new rows are sketched),
+ *   rank k = min(opts->k_max, ell - oversample, n): pivoted QR of Y(0:ell, :), T,
+ *   e = ||A - A(:,J) P||_F / ||A||_F in FP64 (as estimate_error),
+ * and it stops at the first ell with e <= opts->rel_tol (or after the last block).  The
+ * rank therefore grows with the sketch and is the smallest multiple-of-block step that
+ * meets the tolerance.  opts: rel_tol > 0 the target, k_max the rank cap (<= ell -
+ * oversample), sketch = 1, ell = rows of omega available, precision PLAIN_F64 or MIXED_*,
+ * omega / omega_ld as for id_factor.  Outputs as id_factor (T with ldt >= k_max), err_out
+ * (device, required) the final e, *ell_out (host, nullable) the sketch rows used.
+ * Synchronises the stream once per block (the stopping test reads e on the host).
+ * Errors: ID_ERR_ARG, ID_ERR_WORKSPACE, ID_ERR_UNSUPPORTED, ID_ERR_CUDA, ID_ERR_TIMEOUT. */
+id_status_t id_adaptive_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts,
+                                       int32_t block, int32_t oversample, size_t* bytes);
+id_status_t id_factor_adaptive(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                               const id_opts_t* opts, int32_t block, int32_t oversample, int32_t* J, double* T,
+                               int64_t ldt, int32_t* k_out, int32_t* info, double* err_out, int32_t* ell_out,
+                               void* work, size_t work_bytes, void* stream);
+
 /* The sketch step alone (the sketching of Sec. 5; Algorithm 2 for
  * the cast): Y = Omega A (ell x n, column-major, ldy >= ell).
  * PLAIN_F64: Omega and Y are double.  MIXED_*: Omega is bfloat16/half bits,

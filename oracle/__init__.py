@@ -220,6 +220,34 @@ def interp_decomp(a: np.ndarray, k: int | None = None, tol: float | None = None,
             "gaps": gaps[:kk]}
 
 
+# ------------------------------------------------- rank-adaptive sketched ID
+
+def adaptive_id(a: np.ndarray, omega: np.ndarray, tol: float, block: int, k_max: int,
+                oversample: int = 10):
+    """Rank-adaptive randomized ID (the sketching the paper names as future work in Sec. 5,
+    grown by blocks): for ell = block, 2 block, ... (at most omega's rows), Y = Omega(0:ell) A,
+    the truncated CPQR of Y with k = min(k_max, ell - oversample) steps (fewer if a
+    residual norm reaches zero), T = R11^-1 R12, and the exact relative Frobenius residual
+    e = ||A - A(:,J) P||_F / ||A||_F; stop at the first ell whose e <= tol, or at the last
+    block.  The rank grows with the sketch, so it is the smallest multiple-of-block step
+    that meets the tolerance.  Returns the ID of the final round with "ell" and "err"."""
+    a = _f64(a)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    ell_max = om.shape[0]
+    na2 = float(np.sum(a * a))
+    out = None
+    ell = 0
+    while ell < ell_max:
+        ell = min(ell + block, ell_max)
+        k = max(1, min(k_max, ell - oversample, a.shape[1]))
+        out = interp_decomp(a, k=k, omega=om[:ell])
+        err = np.sqrt(residual_fro2(a, out["J"], out["T"], out["k"]) / na2) if na2 > 0 else 0.0
+        out["ell"], out["err"] = ell, float(err)
+        if err <= tol:
+            break
+    return out
+
+
 # ------------------------------------------------------ Algorithm 2 (low ID)
 
 def low_cast(a: np.ndarray, fmt: str, block_rows: int = 64) -> np.ndarray:

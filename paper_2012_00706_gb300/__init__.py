@@ -20,7 +20,7 @@ import torch
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
     "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
-    "BatchPlan", "shard_batch", "probe_fma_peak", "low_cast", "reconstruct",
+    "BatchPlan", "shard_batch", "probe_fma_peak", "low_cast", "reconstruct", "id_factor_adaptive",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -109,6 +109,12 @@ def load():
         lib.id_batch_shard.argtypes = [i32, p, p, p, i32, i32, p, p]
         lib.id_probe_fma_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), p]
         lib.id_probe_fma_peak.restype = ctypes.c_int
+        lib.id_adaptive_workspace_size.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(IDOpts), i32, i32,
+                                                   ctypes.POINTER(sz)]
+        lib.id_adaptive_workspace_size.restype = ctypes.c_int
+        lib.id_factor_adaptive.argtypes = [p, ctypes.c_int, i64, i64, i64, ctypes.POINTER(IDOpts), i32, i32, p, p,
+                                           i64, p, p, p, ctypes.POINTER(i32), p, sz, p]
+        lib.id_factor_adaptive.restype = ctypes.c_int
         lib.id_low_cast.argtypes = [p, ctypes.c_int, i64, i64, i64, i32, p, i64, p, p]
         lib.id_low_cast.restype = ctypes.c_int
         lib.id_reconstruct_one.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i32, p, i64, p, i64, p]
@@ -249,6 +255,37 @@ def probe_fma_peak(which: str = "fp32", stream=None) -> float:
     _check(load().id_probe_fma_peak({"fp32": 0, "fp64": 1}[which], ctypes.byref(t), _stream_ptr(stream)),
            "id_probe_fma_peak")
     return t.value
+
+
+def id_factor_adaptive(A: torch.Tensor, tol: float, k_max: int, omega: torch.Tensor, *, block: int = 16,
+                       oversample: int = 10, precision: str = "mixed_bf16x3", refine_steps: int = 1,
+                       watchdog_ms: int = 0, stream=None, workspace=None):
+    """Rank-adaptive randomized ID: the sketch grows by ``block`` rows of ``omega`` (ell_max x m)
+    and the rank with it (k = ell - oversample, at most k_max) until the FP64 relative
+    Frobenius residual on A is <= tol.  Returns (IDResult with err, ell used).  Synchronises."""
+    _require_cuda(A, omega)
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    o = _opts(None, tol, k_max, precision, True, omega.shape[0], omega, _omega_ld(omega), refine_steps, True,
+              watchdog_ms)
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.id_adaptive_workspace_size(_DTYPE[A.dtype], m, n, ctypes.byref(o), block, oversample,
+                                          ctypes.byref(nb)), "id_adaptive_workspace_size")
+    dev = a.device
+    if workspace is None or workspace.numel() < nb.value:
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    J = torch.empty(n, dtype=torch.int32, device=dev)
+    T = torch.empty((max(n - 1, 1), k_max), dtype=torch.float64, device=dev).t()
+    small = torch.zeros(2, dtype=torch.int32, device=dev)
+    err = torch.zeros(1, dtype=torch.float64, device=dev)
+    ell = ctypes.c_int32(0)
+    _check(lib.id_factor_adaptive(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, ctypes.byref(o), block, oversample,
+                                  J.data_ptr(), T.data_ptr(), k_max, small.data_ptr(), small.data_ptr() + 4,
+                                  err.data_ptr(), ctypes.byref(ell), workspace.data_ptr(), workspace.numel(),
+                                  _stream_ptr(stream)), "id_factor_adaptive")
+    kk, info = (int(v) for v in small.cpu())
+    return IDResult(J, T[:kk, : n - kk], kk, info, float(err.item())), ell.value
 
 
 def set_stage_events(events) -> None:

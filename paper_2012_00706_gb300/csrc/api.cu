@@ -344,6 +344,134 @@ id_status_t id_scale_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t 
     return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
 }
 
+// ---------------------------------------------------------- rank-adaptive ID
+
+namespace {
+struct AdaptivePlan {
+    FactorPlan f;
+    size_t y_off = 0, partial_off = 0, bytes = 0;
+};
+
+// Split-K partial sums of one round's sketch of b rows.
+size_t adaptive_partial_bytes(id_dtype_t a_dtype, int64_t m, int64_t n, int b, int precision) {
+    if (precision == ID_PLAIN_F64) {
+        SketchF64Plan sp;
+        sketch_plan_f64(m, n, b, &sp);
+        return static_cast<size_t>(sp.kslabs) * n * sp.lp * sizeof(double);
+    }
+    SketchPlan sp;
+    if (!sketch_plan_lowp(m, n, b, a_dtype == ID_F64, precision_nsplit(precision), &sp)) return 0;
+    return sketch_partial_bytes_lowp(sp, n);
+}
+
+id_status_t plan_adaptive(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* o, int32_t block,
+                          int32_t oversample, AdaptivePlan* ap) {
+    if (!o || block < 1 || oversample < 0 || !(o->rel_tol > 0.0) || !o->sketch) return ID_ERR_ARG;
+    if (o->precision != ID_PLAIN_F64 && !is_mixed(o->precision)) return ID_ERR_ARG;
+    if (o->k_max < 1 || o->k_max > o->ell - oversample || o->k_max > n) return ID_ERR_ARG;
+    id_opts_t fo = *o;
+    fo.rel_tol = 0.0;
+    fo.k = o->k_max;
+    AdaptivePlan p;
+    const id_status_t st = plan_factor(a_dtype, m, n, m, &fo, &p.f);
+    if (st != ID_OK) return st;
+    const size_t elem = p.f.w_f64 ? 8 : 4;
+    // the rounds sketch `block` rows, the last one the remainder
+    const int rem = static_cast<int>(o->ell % block);
+    size_t part = adaptive_partial_bytes(a_dtype, m, n, std::min<int>(block, o->ell), o->precision);
+    if (rem > 0) part = std::max(part, adaptive_partial_bytes(a_dtype, m, n, rem, o->precision));
+    if (part == 0) return ID_ERR_UNSUPPORTED;
+    p.y_off = (p.f.bytes + 255) & ~size_t(255);
+    p.partial_off = (p.y_off + static_cast<size_t>(o->ell) * n * elem + 255) & ~size_t(255);
+    p.bytes = p.partial_off + part + 256;
+    *ap = p;
+    return ID_OK;
+}
+}  // namespace
+
+id_status_t id_adaptive_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts,
+                                       int32_t block, int32_t oversample, size_t* bytes) {
+    if (!bytes) return ID_ERR_ARG;
+    AdaptivePlan ap;
+    const id_status_t st = plan_adaptive(a_dtype, m, n, opts, block, oversample, &ap);
+    if (st == ID_OK) *bytes = ap.bytes;
+    return st;
+}
+
+id_status_t id_factor_adaptive(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                               const id_opts_t* opts, int32_t block, int32_t oversample, int32_t* J, double* T,
+                               int64_t ldt, int32_t* k_out, int32_t* info, double* err_out, int32_t* ell_out,
+                               void* work, size_t work_bytes, void* stream) {
+    if (!A || !J || !T || !k_out || !info || !err_out || !work || lda < m) return ID_ERR_ARG;
+    AdaptivePlan ap;
+    id_status_t st = plan_adaptive(a_dtype, m, n, opts, block, oversample, &ap);
+    if (st != ID_OK) return st;
+    const FactorPlan& p = ap.f;
+    if (ldt < opts->k_max) return ID_ERR_ARG;
+    if (work_bytes < ap.bytes) return ID_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
+    FactorPtrs f;
+    carve_factor(aligned, n, p, &f);
+    void* Y = aligned + ap.y_off;
+    void* partial = aligned + ap.partial_off;
+    const int64_t ell_max = opts->ell, ldo = p.omega_ld, ldy = ell_max;
+    const uint64_t lim = limit_ns_of(*opts);
+    const int a_f64 = a_dtype == ID_F64;
+    const int elem = p.w_f64 ? 8 : 4;
+    int64_t ell = 0;
+    int32_t h_info = 0;
+    while (ell < ell_max) {
+        const int64_t e0 = ell;
+        ell = std::min<int64_t>(ell + block, ell_max);
+        const int b = static_cast<int>(ell - e0);
+        const int k = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({opts->k_max, ell - oversample, n})));
+        cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int32_t), s);
+        // the block's rows of the sketch: Y(e0:ell, :) = Omega(e0:ell, :) A
+        if (e == cudaSuccess) {
+            if (p.mixed) {
+                SketchPlan sp;
+                if (!sketch_plan_lowp(m, n, b, a_f64, precision_nsplit(opts->precision), &sp)) return ID_ERR_UNSUPPORTED;
+                e = launch_sketch_lowp(A, a_f64, m, n, lda, static_cast<const uint16_t*>(opts->omega) + e0 * ldo, ldo,
+                                       b, opts->precision, sp, static_cast<float*>(partial),
+                                       static_cast<float*>(Y) + e0, ldy, info, lim, s);
+            } else {
+                SketchF64Plan sp;
+                sketch_plan_f64(m, n, b, &sp);
+                e = launch_sketch_f64(static_cast<const double*>(A), m, n, lda,
+                                      static_cast<const double*>(opts->omega) + e0 * ldo, ldo, b, sp,
+                                      static_cast<double*>(partial), static_cast<double*>(Y) + e0, ldy, info, s);
+            }
+        }
+        // rank-k pivoted QR of Y(0:ell, :) (the kernels read Y and leave it as it is)
+        if (e == cudaSuccess) {
+            ClusterCpqrPlan ccp;
+            if (p.mixed && cpqr_cluster_plan(ell, n, &ccp)) {
+                e = launch_cpqr_cluster(static_cast<const float*>(Y), ell, n, ldy, 1, 0, k, 0.0, J, k_out, info,
+                                        f.R64, opts->k_max, f.sel, ccp, lim, s);
+            } else {
+                CpqrPlan cp;
+                if (!cpqr_plan(ell, n, elem, &cp)) return ID_ERR_UNSUPPORTED;
+                e = launch_cpqr(f.W, p.w_f64, ell, n, ell, Y, p.w_f64, ldy, k, 0.0, J, k_out, info, f.R64,
+                                opts->k_max, f.nu, f.nuref, f.sel, f.ctrl, cp, lim, s);
+            }
+        }
+        if (e == cudaSuccess)
+            e = launch_solve_T(f.R64, opts->k_max, J, k_out, k, n, T, ldt, f.tscr, opts->refine_steps,
+                               p.w_f64 ? 0 : 1, s);
+        if (e == cudaSuccess) e = launch_residual_fro(A, a_f64, m, n, lda, J, k_out, T, ldt, f.acc, err_out, s);
+        double h_err = 0.0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err_out, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_info, info, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return ID_ERR_CUDA;
+        if (h_info < 0) break;                      // non-finite data or a watchdog: report, stop
+        if (h_err <= opts->rel_tol) break;
+    }
+    if (ell_out) *ell_out = static_cast<int32_t>(ell);
+    return h_info == kInfoWatchdog ? ID_ERR_TIMEOUT : ID_OK;
+}
+
 id_status_t id_low_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t precision,
                         float* AL, int64_t ldal, int32_t* info, void* stream) {
     if (!A || !AL || m < 1 || n < 1 || lda < m || ldal < m) return ID_ERR_ARG;

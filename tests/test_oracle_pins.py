@@ -353,6 +353,31 @@ def test_low_id_of_representable_data_is_the_plain_id(orc):
     assert np.array_equal(out["J"], ref["J"]) and np.array_equal(out["T"], ref["T"])
 
 
+def test_adaptive_id_exact_rank_and_invariants(orc):
+    """Exact rank r: the adaptive ID stops at the first block with ell - oversample >= r
+    (ell = 48 for r = 23, blocks of 16), where its rank ell - oversample covers r and the
+    reconstruction is exact (the later pivots pick up rounding only); on a decaying
+    spectrum the stopped error is within the tolerance and one block fewer would not have
+    met it."""
+    rng = np.random.default_rng(6)
+    r = 23
+    a = rand_lowrank(900, 300, r, 6, decay=0.8)
+    om = rng.standard_normal((200, 900))
+    out = orc.adaptive_id(a, om, 1e-10, 16, 150)
+    assert out["ell"] == 48 and out["k"] == 38 and out["err"] <= 1e-12
+    short = orc.interp_decomp(a, k=22, omega=om[:32])
+    assert np.sqrt(orc.residual_fro2(a, short["J"], short["T"], 22) / np.sum(a * a)) > 1e-3
+    sig = 10.0 ** (-np.arange(1, 301) / 20.0)
+    b = wl.lowrank(900, 300, sig, 7)
+    out = orc.adaptive_id(b, om, 1e-4, 16, 150)
+    assert out["err"] <= 1e-4 and out["k"] == out["ell"] - 10
+    # the exact Frobenius tail of the spectrum bounds any rank-k approximation from below
+    assert np.sqrt(np.sum(sig[out["k"]:] ** 2) / np.sum(sig ** 2)) <= 1e-4
+    prev = orc.interp_decomp(b, k=out["k"] - 16, omega=om[: out["ell"] - 16])
+    e_prev = np.sqrt(orc.residual_fro2(b, prev["J"], prev["T"], prev["k"]) / np.sum(b * b))
+    assert e_prev > 1e-4
+
+
 def test_mgs_crosscheck(orc):
     """The paper's MGS column selection gives the same pivots and |R| as Householder."""
     for seed in range(3):
