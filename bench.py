@@ -555,22 +555,24 @@ def config3_leg(gid, wl, dev, peaks, reps=3):
                      "tflops": id_flops(m, n, ell, k) / (ms / 1e3) / 1e12, "stages_ms": stages,
                      "sketch_hbm_frac": sk_bytes / (stages["sketch_kernel"] / 1e3) / 1e9 / measured_peaks()[0],
                      "speedup_vs_plain_f64": out["plain_f64"]["ms_per_id"] / ms}
-    # rank-adaptive: sketch rows (and the rank) grow by blocks of 16 until the FP64 residual
-    # on A itself meets the tolerance (one host synchronisation per block, inside the time)
-    _, bits = wl.gaussian_omega(ell, m, 3003, "bf16")
+    # rank-adaptive: sketch rows (and the rank) grow by blocks of 32, up to 256 rows, until
+    # the FP64 residual on A itself meets the tolerance (one host synchronisation per block,
+    # inside the time)
+    ell_a, kmax_a, blk = 256, 240, 32
+    _, bits = wl.gaussian_omega(ell_a, m, 3004, "bf16")
     om = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
-    res, used = gid.id_factor_adaptive(A, tol, kmax, om, block=16)      # warm-up
+    res, used = gid.id_factor_adaptive(A, tol, kmax_a, om, block=blk)      # warm-up
     ts = []
     for _ in range(max(reps, 5)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        res, used = gid.id_factor_adaptive(A, tol, kmax, om, block=16)
+        res, used = gid.id_factor_adaptive(A, tol, kmax_a, om, block=blk)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = statistics.median(ts)
     out["mixed_bf16x3_adaptive"] = {"ms_per_id": ms, "ids_per_s": 1e3 / ms, "k": res.k, "err_fro": res.err,
-                                    "ell_used": used, "block": 16, "meets_tol": res.err <= tol,
+                                    "ell_used": used, "ell_max": ell_a, "block": blk, "meets_tol": res.err <= tol,
                                     "speedup_vs_plain_f64": out["plain_f64"]["ms_per_id"] / ms}
     return out
 

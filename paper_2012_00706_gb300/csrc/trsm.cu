@@ -509,35 +509,89 @@ cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, con
 
 // ------------------------------------------------------------ error estimate
 
-// acc2[0] += sum over complement columns c of ||A(:,Jc[c]) - A(:,J[0:k]) T(:,c)||^2,
-// acc2[1] += ||A||_F^2.  One warp per column, FP64.
+// acc2[0] += sum over complement columns c of ||A(:,J[k+c]) - A(:,J[0:k]) T(:,c)||^2 by
+// 64 x 64 residual tiles (256 threads, 4 x 4 entries each, k in chunks of 16 staged in
+// shared memory, FP64): A(:,J[0:k]) is read once per 64 complement columns.  The grid
+// covers n - 1 complement columns; k is read on the device, tiles past n - k leave.
+constexpr int kResTile = 64;
+constexpr int kResK = 16;
+
 template <typename TA>
-__global__ void k_residual_fro(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda,
-                               const int32_t* __restrict__ J, const int32_t* __restrict__ k_ptr,
-                               const double* __restrict__ T, int64_t ldt, double* acc2) {
+__global__ void __launch_bounds__(256)
+k_residual_tiles(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda, const int32_t* __restrict__ J,
+                 const int32_t* __restrict__ k_ptr, const double* __restrict__ T, int64_t ldt, double* acc2) {
+    __shared__ double As[kResK][kResTile + 1];
+    __shared__ double Ts[kResK][kResTile + 1];
+    __shared__ double red[8];
     const int k = *k_ptr;
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    if (w >= n) return;
-    double res = 0.0, tot = 0.0;
-    const int64_t col = J[w];
-    const TA* a = A + col * lda;
-    for (int64_t i = lane; i < m; i += 32) {
-        const double x = static_cast<double>(a[i]);
-        tot += x * x;
-        if (w >= k) {
-            const double* t = T + (w - k) * ldt;
-            double r = x;
-            for (int b = 0; b < k; ++b) r = fma(-static_cast<double>(A[static_cast<int64_t>(J[b]) * lda + i]), t[b], r);
-            res += r * r;
+    const int64_t nc = n - k;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kResTile;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.y) * kResTile;
+    if (k <= 0 || q0 >= nc) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int64_t c = q0 + tx * 4 + v;
+        const TA* col = c < nc ? A + static_cast<int64_t>(J[k + c]) * lda : nullptr;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t row = r0 + ty * 4 + u;
+            acc[u][v] = (col && row < m) ? static_cast<double>(col[row]) : 0.0;
         }
     }
-    res = warp_sum(res);
-    tot = warp_sum(tot);
-    if (lane == 0) {
-        atomicAdd(acc2, res);
-        atomicAdd(acc2 + 1, tot);
+    for (int b0 = 0; b0 < k; b0 += kResK) {
+        for (int idx = threadIdx.x; idx < kResK * kResTile; idx += 256) {
+            const int bb = idx / kResTile, i = idx % kResTile;
+            const int b = b0 + bb;
+            const int64_t row = r0 + i, c = q0 + i;
+            As[bb][i] = (b < k && row < m) ? static_cast<double>(A[static_cast<int64_t>(J[b]) * lda + row]) : 0.0;
+            Ts[bb][i] = (b < k && c < nc) ? T[c * ldt + b] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int bb = 0; bb < kResK; ++bb) {
+            double a[4], t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[bb][ty * 4 + u]; t[u] = Ts[bb][tx * 4 + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(-a[u], t[v], acc[u][v]);
+        }
+        __syncthreads();
     }
+    double sq = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sq = fma(acc[u][v], acc[u][v], sq);
+    sq = warp_sum(sq);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        atomicAdd(acc2, tot);
+    }
+}
+
+// acc2[1] += ||A||_F^2 (grid-stride over the columns, warp per column).
+template <typename TA>
+__global__ void k_sumsq(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda, double* acc2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    double s = 0.0;
+    for (int64_t j = w0; j < n; j += nw) {
+        const TA* col = A + j * lda;
+        for (int64_t i = lane; i < m; i += 32) {
+            const double x = static_cast<double>(col[i]);
+            s = fma(x, x, s);
+        }
+    }
+    s = warp_sum(s);
+    if (lane == 0) atomicAdd(acc2 + 1, s);
 }
 
 __global__ void k_residual_finish(const double* acc2, double* err_out) {
@@ -549,11 +603,17 @@ cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, 
                                 double* err_out, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(acc2, 0, 2 * sizeof(double), s);
     if (e != cudaSuccess) return e;
-    const unsigned grid = static_cast<unsigned>((n * 32 + 255) / 256);
-    if (a_f64)
-        k_residual_fro<double><<<grid, 256, 0, s>>>(static_cast<const double*>(A), m, n, lda, J, k_ptr, T, ldt, acc2);
-    else
-        k_residual_fro<float><<<grid, 256, 0, s>>>(static_cast<const float*>(A), m, n, lda, J, k_ptr, T, ldt, acc2);
+    const int64_t ncmax = std::max<int64_t>(1, n - 1);
+    const dim3 g(static_cast<unsigned>((m + kResTile - 1) / kResTile),
+                 static_cast<unsigned>((ncmax + kResTile - 1) / kResTile));
+    const unsigned gs = static_cast<unsigned>(std::min<int64_t>((n * 32 + 255) / 256, 8LL * device_info().sm_count));
+    if (a_f64) {
+        k_residual_tiles<double><<<g, 256, 0, s>>>(static_cast<const double*>(A), m, n, lda, J, k_ptr, T, ldt, acc2);
+        k_sumsq<double><<<gs, 256, 0, s>>>(static_cast<const double*>(A), m, n, lda, acc2);
+    } else {
+        k_residual_tiles<float><<<g, 256, 0, s>>>(static_cast<const float*>(A), m, n, lda, J, k_ptr, T, ldt, acc2);
+        k_sumsq<float><<<gs, 256, 0, s>>>(static_cast<const float*>(A), m, n, lda, acc2);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_residual_finish<<<1, 1, 0, s>>>(acc2, err_out);
