@@ -170,6 +170,32 @@ id_status_t id_factor_adaptive(const void* A, id_dtype_t a_dtype, int64_t m, int
                                int64_t ldt, int32_t* k_out, int32_t* info, double* err_out, int32_t* ell_out,
                                void* work, size_t work_bytes, void* stream);
 
+/* Row ID (the standard companion of the column ID of Sec. 1.1; the paper has only the
+ * column form): A ~= X A(I[0:k], :) with X(I[0:k], :) = I_k and X(I[k:m], :) = T^T, i.e.
+ * row I[k+c] of A ~= sum_b T(b, c) row I[b].  It is the column ID of A^T: A is
+ * transposed into the workspace (tiled copy) and id_factor runs on it with the same
+ * options (a sketch then uses Omega of ell x n, sketching A^T's columns).  Outputs as
+ * id_factor with the roles of m and n exchanged: I [m], T k_cap x (m - k) (ldt >= k_cap),
+ * k_out, info, err_out (the same relative Frobenius residual).  Workspace from
+ * id_rows_workspace_size.  Errors as id_factor. */
+id_status_t id_rows_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts, size_t* bytes);
+id_status_t id_factor_rows(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, const id_opts_t* opts,
+                           int32_t* I, double* T, int64_t ldt, int32_t* k_out, int32_t* info, double* err_out,
+                           void* work, size_t work_bytes, void* stream);
+
+/* Two-sided ID A ~= X A(I[0:k], J[0:k]) P at a fixed rank k (opts->rel_tol = 0): the
+ * column ID of A with opts (J, Tc as id_factor), then the rank-k row ID of the column
+ * skeleton C = A(:, J[0:k]) in plain precision (FP64 for ID_F64 data, FP32 for ID_F32)
+ * giving I [m] and Tr k x (m - k) (ldtr >= k); X is the row ID's interpolation matrix.
+ * k_out[2], info[2] (device): [0] the column stage, [1] the row stage.  Workspace from
+ * id_two_sided_workspace_size.  Errors as id_factor; ID_ERR_ARG for a tolerance. */
+id_status_t id_two_sided_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts,
+                                        size_t* bytes);
+id_status_t id_factor_two_sided(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                                const id_opts_t* opts, int32_t* J, double* Tc, int64_t ldtc, int32_t* I, double* Tr,
+                                int64_t ldtr, int32_t* k_out, int32_t* info, void* work, size_t work_bytes,
+                                void* stream);
+
 /* The sketch step alone (the sketching of Sec. 5; Algorithm 2 for
  * the cast): Y = Omega A (ell x n, column-major, ldy >= ell).
  * PLAIN_F64: Omega and Y are double.  MIXED_*: Omega is bfloat16/half bits,

@@ -248,6 +248,32 @@ def adaptive_id(a: np.ndarray, omega: np.ndarray, tol: float, block: int, k_max:
     return out
 
 
+# ------------------------------------------------------- row and two-sided IDs
+
+def row_id(a: np.ndarray, k: int, omega: np.ndarray | None = None):
+    """Row ID A ~= X A(I[0:k], :): the column ID of A^T (Omega, if given, is ell x n).
+    Returns interp_decomp's dict for A^T: J are the row indices I, T gives X(I[k:], :) = T^T."""
+    return interp_decomp(np.asarray(a, dtype=np.float64).T, k=k, omega=omega)
+
+
+def two_sided_id(a: np.ndarray, k: int, omega: np.ndarray | None = None):
+    """Two-sided ID A ~= X A(I[0:k], J[0:k]) P: the column ID (J, T) of A, then the rank-k
+    row ID (I, Tr) of the skeleton A(:, J[0:k]).  Returns (col, row) dicts."""
+    a = np.asarray(a, dtype=np.float64)
+    col = interp_decomp(a, k=k, omega=omega)
+    row = row_id(a[:, col["J"][:k]], k)
+    return col, row
+
+
+def two_sided_reconstruct(a: np.ndarray, col, row, k: int) -> np.ndarray:
+    """X A(I[0:k], J[0:k]) P with X(I[0:k], :) = I_k, X(I[k:], :) = Tr^T."""
+    a = np.asarray(a, dtype=np.float64)
+    m, n = a.shape
+    X = coefficient_matrix(row["J"], row["T"], k, m).T
+    P = coefficient_matrix(col["J"], col["T"], k, n)
+    return X @ a[np.ix_(row["J"][:k], col["J"][:k])] @ P
+
+
 # ------------------------------------------------------ Algorithm 2 (low ID)
 
 def low_cast(a: np.ndarray, fmt: str, block_rows: int = 64) -> np.ndarray:

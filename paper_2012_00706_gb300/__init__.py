@@ -21,6 +21,7 @@ __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
     "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
     "BatchPlan", "shard_batch", "probe_fma_peak", "low_cast", "reconstruct", "id_factor_adaptive",
+    "id_factor_rows", "id_factor_two_sided",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -115,6 +116,16 @@ def load():
         lib.id_factor_adaptive.argtypes = [p, ctypes.c_int, i64, i64, i64, ctypes.POINTER(IDOpts), i32, i32, p, p,
                                            i64, p, p, p, ctypes.POINTER(i32), p, sz, p]
         lib.id_factor_adaptive.restype = ctypes.c_int
+        lib.id_rows_workspace_size.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(IDOpts), ctypes.POINTER(sz)]
+        lib.id_factor_rows.argtypes = [p, ctypes.c_int, i64, i64, i64, ctypes.POINTER(IDOpts), p, p, i64, p, p, p,
+                                       p, sz, p]
+        lib.id_two_sided_workspace_size.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(IDOpts),
+                                                    ctypes.POINTER(sz)]
+        lib.id_factor_two_sided.argtypes = [p, ctypes.c_int, i64, i64, i64, ctypes.POINTER(IDOpts), p, p, i64, p, p,
+                                            i64, p, p, p, sz, p]
+        for name in ("id_rows_workspace_size", "id_factor_rows", "id_two_sided_workspace_size",
+                     "id_factor_two_sided"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.id_low_cast.argtypes = [p, ctypes.c_int, i64, i64, i64, i32, p, i64, p, p]
         lib.id_low_cast.restype = ctypes.c_int
         lib.id_reconstruct_one.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i32, p, i64, p, i64, p]
@@ -286,6 +297,63 @@ def id_factor_adaptive(A: torch.Tensor, tol: float, k_max: int, omega: torch.Ten
                                   _stream_ptr(stream)), "id_factor_adaptive")
     kk, info = (int(v) for v in small.cpu())
     return IDResult(J, T[:kk, : n - kk], kk, info, float(err.item())), ell.value
+
+
+def id_factor_rows(A: torch.Tensor, k: int, *, precision: str = "plain_f64", omega: torch.Tensor | None = None,
+                   refine_steps: int = 1, estimate_error: bool = False, stream=None) -> IDResult:
+    """Row ID A ~= X A(I[:k], :) of the CUDA matrix A (m, n): the column ID of A^T (``omega``,
+    if given, is (ell, n)).  Returns IDResult with J = I (m row indices) and T (k, m - k):
+    row I[k + c] of A ~= sum_b T[b, c] row I[b].  Synchronises."""
+    _require_cuda(A, omega)
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    sketch = omega is not None
+    o = _opts(k, None, None, precision, sketch, omega.shape[0] if sketch else 0, omega, _omega_ld(omega),
+              refine_steps, estimate_error, 0)
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.id_rows_workspace_size(_DTYPE[A.dtype], m, n, ctypes.byref(o), ctypes.byref(nb)),
+           "id_rows_workspace_size")
+    dev = a.device
+    work = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    I = torch.empty(m, dtype=torch.int32, device=dev)
+    T = torch.empty((max(m - 1, 1), k), dtype=torch.float64, device=dev).t()
+    small = torch.zeros(2, dtype=torch.int32, device=dev)
+    err = torch.zeros(1, dtype=torch.float64, device=dev)
+    _check(lib.id_factor_rows(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, ctypes.byref(o), I.data_ptr(), T.data_ptr(),
+                              k, small.data_ptr(), small.data_ptr() + 4, err.data_ptr() if estimate_error else None,
+                              work.data_ptr(), work.numel(), _stream_ptr(stream)), "id_factor_rows")
+    kk, info = (int(v) for v in small.cpu())
+    return IDResult(I, T[:kk, : m - kk], kk, info, float(err.item()) if estimate_error else None)
+
+
+def id_factor_two_sided(A: torch.Tensor, k: int, *, precision: str = "plain_f64", omega: torch.Tensor | None = None,
+                        refine_steps: int = 1, stream=None):
+    """Two-sided ID A ~= X A(I[:k], J[:k]) P at rank k: the column ID (J, Tc) of A, then the
+    rank-k row ID (I, Tr) of A(:, J[:k]).  Returns (col IDResult, row IDResult).  Synchronises."""
+    _require_cuda(A, omega)
+    a, lda = _colmajor(A)
+    m, n = a.shape
+    sketch = omega is not None
+    o = _opts(k, None, None, precision, sketch, omega.shape[0] if sketch else 0, omega, _omega_ld(omega),
+              refine_steps, False, 0)
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.id_two_sided_workspace_size(_DTYPE[A.dtype], m, n, ctypes.byref(o), ctypes.byref(nb)),
+           "id_two_sided_workspace_size")
+    dev = a.device
+    work = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    J = torch.empty(n, dtype=torch.int32, device=dev)
+    Tc = torch.empty((max(n - 1, 1), k), dtype=torch.float64, device=dev).t()
+    I = torch.empty(m, dtype=torch.int32, device=dev)
+    Tr = torch.empty((max(m - 1, 1), k), dtype=torch.float64, device=dev).t()
+    ks = torch.zeros(2, dtype=torch.int32, device=dev)
+    infos = torch.zeros(2, dtype=torch.int32, device=dev)
+    _check(lib.id_factor_two_sided(a.data_ptr(), _DTYPE[A.dtype], m, n, lda, ctypes.byref(o), J.data_ptr(),
+                                   Tc.data_ptr(), k, I.data_ptr(), Tr.data_ptr(), k, ks.data_ptr(), infos.data_ptr(),
+                                   work.data_ptr(), work.numel(), _stream_ptr(stream)), "id_factor_two_sided")
+    (kc, kr), (ic, ir) = ks.cpu().tolist(), infos.cpu().tolist()
+    return (IDResult(J, Tc[:kc, : n - kc], kc, ic, None), IDResult(I, Tr[:kr, : m - kr], kr, ir, None))
 
 
 def set_stage_events(events) -> None:

@@ -472,6 +472,97 @@ id_status_t id_factor_adaptive(const void* A, id_dtype_t a_dtype, int64_t m, int
     return h_info == kInfoWatchdog ? ID_ERR_TIMEOUT : ID_OK;
 }
 
+// ------------------------------------------------------- row and two-sided IDs
+
+namespace {
+int64_t round_up8(int64_t x) { return (x + 7) / 8 * 8; }
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+}  // namespace
+
+id_status_t id_rows_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts, size_t* bytes) {
+    if (!bytes || (a_dtype != ID_F64 && a_dtype != ID_F32)) return ID_ERR_ARG;
+    size_t fb = 0;
+    const id_status_t st = id_workspace_size(a_dtype, n, m, opts, &fb);   // the column ID of A^T (n x m)
+    if (st != ID_OK) return st;
+    const size_t elem = a_dtype == ID_F64 ? 8 : 4;
+    *bytes = align256(static_cast<size_t>(round_up8(n)) * m * elem) + fb + 512;
+    return ID_OK;
+}
+
+id_status_t id_factor_rows(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, const id_opts_t* opts,
+                           int32_t* I, double* T, int64_t ldt, int32_t* k_out, int32_t* info, double* err_out,
+                           void* work, size_t work_bytes, void* stream) {
+    if (!A || !work || m < 1 || n < 1 || lda < m) return ID_ERR_ARG;
+    size_t need = 0;
+    id_status_t st = id_rows_workspace_size(a_dtype, m, n, opts, &need);
+    if (st != ID_OK) return st;
+    if (work_bytes < need) return ID_ERR_WORKSPACE;
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
+    const size_t elem = a_dtype == ID_F64 ? 8 : 4;
+    const int64_t ldb = round_up8(n);
+    const size_t tb = align256(static_cast<size_t>(ldb) * m * elem);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (launch_transpose(A, a_dtype == ID_F64, m, n, lda, base, ldb, s) != cudaSuccess) return ID_ERR_CUDA;
+    return id_factor(base, a_dtype, n, m, ldb, opts, I, T, ldt, k_out, info, err_out, base + tb,
+                     work_bytes - tb - static_cast<size_t>(base - static_cast<char*>(work)), stream);
+}
+
+namespace {
+// The row stage of the two-sided ID: the rank-k row ID of the m x k skeleton, plain precision.
+id_opts_t two_sided_row_opts(id_dtype_t a_dtype, int32_t k) {
+    id_opts_t o;
+    id_opts_default(&o);
+    o.k = k;
+    o.precision = a_dtype == ID_F64 ? ID_PLAIN_F64 : ID_PLAIN_F32;
+    return o;
+}
+}  // namespace
+
+id_status_t id_two_sided_workspace_size(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opts_t* opts,
+                                        size_t* bytes) {
+    if (!bytes || !opts || opts->rel_tol != 0.0) return ID_ERR_ARG;
+    size_t cb = 0, rb = 0;
+    id_status_t st = id_workspace_size(a_dtype, m, n, opts, &cb);
+    if (st != ID_OK) return st;
+    const int32_t k = opts->k;
+    if (k > m) return ID_ERR_ARG;
+    const id_opts_t ro = two_sided_row_opts(a_dtype, k);
+    st = id_rows_workspace_size(a_dtype, m, k, &ro, &rb);
+    if (st != ID_OK) return st;
+    const size_t elem = a_dtype == ID_F64 ? 8 : 4;
+    *bytes = align256(cb) + align256(static_cast<size_t>(round_up8(m)) * k * elem) + rb + 512;
+    return ID_OK;
+}
+
+id_status_t id_factor_two_sided(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda,
+                                const id_opts_t* opts, int32_t* J, double* Tc, int64_t ldtc, int32_t* I, double* Tr,
+                                int64_t ldtr, int32_t* k_out, int32_t* info, void* work, size_t work_bytes,
+                                void* stream) {
+    if (!A || !J || !Tc || !I || !Tr || !k_out || !info || !work || lda < m) return ID_ERR_ARG;
+    size_t need = 0;
+    id_status_t st = id_two_sided_workspace_size(a_dtype, m, n, opts, &need);
+    if (st != ID_OK) return st;
+    if (work_bytes < need) return ID_ERR_WORKSPACE;
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
+    const size_t avail = work_bytes - static_cast<size_t>(base - static_cast<char*>(work));
+    size_t cb = 0;
+    id_workspace_size(a_dtype, m, n, opts, &cb);
+    const size_t elem = a_dtype == ID_F64 ? 8 : 4;
+    const int32_t k = opts->k;
+    const int64_t ldc = round_up8(m);
+    const size_t c_off = align256(cb), r_off = c_off + align256(static_cast<size_t>(ldc) * k * elem);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // column stage: A ~= A(:,J[0:k]) Pc
+    st = id_factor(A, a_dtype, m, n, lda, opts, J, Tc, ldtc, k_out, info, nullptr, base, cb, stream);
+    if (st != ID_OK) return st;
+    // row stage: the skeleton C = A(:,J[0:k]) ~= X C(I[0:k], :), a rank-k row ID
+    if (launch_gather_cols(A, a_dtype == ID_F64, m, lda, J, k, base + c_off, ldc, s) != cudaSuccess)
+        return ID_ERR_CUDA;
+    const id_opts_t ro = two_sided_row_opts(a_dtype, k);
+    return id_factor_rows(base + c_off, a_dtype, m, k, ldc, &ro, I, Tr, ldtr, k_out + 1, info + 1, nullptr,
+                          base + r_off, avail - r_off, stream);
+}
+
 id_status_t id_low_cast(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, int32_t precision,
                         float* AL, int64_t ldal, int32_t* info, void* stream) {
     if (!A || !AL || m < 1 || n < 1 || lda < m || ldal < m) return ID_ERR_ARG;

@@ -173,6 +173,12 @@ cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, 
                                 const int32_t* J, const int32_t* k_ptr, const double* T,
                                 int64_t ldt, double* acc2, double* err_out, cudaStream_t s);
 
+// ---- transpose and column gather (transform.cu)
+cudaError_t launch_transpose(const void* A, int f64, int64_t m, int64_t n, int64_t lda, void* B, int64_t ldb,
+                             cudaStream_t s);
+cudaError_t launch_gather_cols(const void* A, int f64, int64_t m, int64_t lda, const int32_t* J, int k, void* C,
+                               int64_t ldc, cudaStream_t s);
+
 // ---- adjoint and reconstruction (backward.cu)
 size_t backward_workspace_bytes(int64_t batch, int64_t m, int64_t n, int k);
 size_t reconstruct_workspace_bytes(int64_t batch, int64_t n, int k);

@@ -378,6 +378,27 @@ def test_adaptive_id_exact_rank_and_invariants(orc):
     assert e_prev > 1e-4
 
 
+def test_row_id_of_symmetric_is_column_id(orc):
+    """For a symmetric matrix the row ID is the column ID."""
+    b = rand_lowrank(60, 60, 60, 8, decay=0.9)
+    a = np.asfortranarray((b + b.T) / 2)
+    r, c = orc.row_id(a, 12), orc.interp_decomp(a, k=12)
+    assert np.array_equal(r["J"], c["J"]) and np.allclose(r["T"], c["T"], rtol=0, atol=1e-12)
+
+
+def test_two_sided_error_is_the_column_error(orc):
+    """The rank-k row ID of the rank-k skeleton A(:,J) is exact, so the two-sided ID's
+    residual equals the column ID's (to rounding), and exact rank gives an exact result."""
+    a = wl.lowrank(300, 200, 10.0 ** (-np.arange(1, 201) / 30.0), 9)
+    col, row = orc.two_sided_id(a, 25)
+    e2 = np.linalg.norm(a - orc.two_sided_reconstruct(a, col, row, 25))
+    e1 = np.linalg.norm(a - orc.reconstruct(a, col["J"], col["T"], 25))
+    assert abs(e2 - e1) <= 1e-10 * np.linalg.norm(a)
+    x = rand_lowrank(200, 150, 12, 10, decay=0.8)
+    col, row = orc.two_sided_id(x, 12)
+    assert np.linalg.norm(x - orc.two_sided_reconstruct(x, col, row, 12)) <= 1e-12 * np.linalg.norm(x)
+
+
 def test_mgs_crosscheck(orc):
     """The paper's MGS column selection gives the same pivots and |R| as Householder."""
     for seed in range(3):
