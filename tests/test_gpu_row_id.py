@@ -51,7 +51,10 @@ def test_row_id_sketched_bf16x3(gid, dev, orc):
     m, n, k, ell = 2000, 1500, 40, 50
     a = wl.lowrank(m, n, np.arange(1, min(m, n) + 1, dtype=np.float64) ** -2.0, 51)
     om, bits = wl.gaussian_omega(ell, n, 52, "bf16")
-    omega = torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
+    ldo = (n + 7) // 8 * 8                    # the tensor-core sketch reads Omega rows by TMA
+    padded = np.zeros((ell, ldo), dtype=np.uint16)
+    padded[:, :n] = bits
+    omega = torch.from_numpy(padded.view(np.int16)).to(dev).view(torch.bfloat16)[:, :n]
     res = gid.id_factor_rows(torch.from_numpy(a).to(dev), k, precision="mixed_bf16x3", omega=omega)
     assert res.info == 0 and res.k == k
     ref = orc.row_id(a, k, omega=om)
