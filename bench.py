@@ -234,8 +234,9 @@ def run_reference(args):
 def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0, world=1, rank=0):
     """512 uneven FP64 IDs (exact rank r, sigma_i = 10^(-i/r), m in [256, 4096],
     n in [64, 1024], k = r): the batched mixed path (default and autotuned unit
-    shapes, plain launches and a replayed CUDA graph) against one id_factor call
-    per matrix, mixed and plain FP64, with the errors of a sample of matrices."""
+    shapes, plain launches and a replayed CUDA graph) against the batched FP64
+    twin (same call, precision plain_f64) and one id_factor call per matrix,
+    mixed and plain FP64, with the errors of a sample of matrices."""
     import tempfile
     import torch
     t_gen = time.perf_counter()
@@ -322,6 +323,27 @@ def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0, world
         else:
             del plan
 
+    # ---- the FP64 twin through the same batched call: each matrix's sketched FP64 ID
+    plan = gid.BatchPlan([(m, n) for m, n, _ in shapes], ranks, precision="plain_f64", lda=ldas)
+    plan.bind(views)
+    ms_plain = time_calls(lambda: plan.run(omega64), 3, warm=1)
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        plan.run(omega64, stream=gs)
+        gs.synchronize()
+        with torch.cuda.graph(graph, stream=gs):
+            plan.run(omega64, stream=gs)
+    torch.cuda.synchronize()
+    ms_plain_graph = time_calls(graph.replay, 3, warm=1)
+    best_plain = min(ms_plain, ms_plain_graph)
+    best_x3 = min(out["mixed_bf16x3"]["ms_tuned"], out["mixed_bf16x3"]["ms_graph_tuned"])
+    out["plain_f64"] = {"ms": ms_plain, "ms_graph": ms_plain_graph, "ids_per_s": count / (best_plain / 1e3),
+                        "tflops": flops / (best_plain / 1e3) / 1e12,
+                        "info_nonzero": int((plan.info != 0).sum().item())}
+    out["batched_bf16x3_vs_batched_plain_f64"] = best_plain / best_x3
+    del graph, plan
     if not loops:
         return out
 
@@ -350,7 +372,6 @@ def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0, world
     out["per_matrix_loop"] = {"mixed_bf16x3_ms": ms_loop_mixed, "plain_f64_ms": ms_loop_plain,
                               "plain_f64_ids_per_s": count / (ms_loop_plain / 1e3),
                               "plain_f64_tflops": flops / (ms_loop_plain / 1e3) / 1e12}
-    best_x3 = min(out["mixed_bf16x3"]["ms_tuned"], out["mixed_bf16x3"]["ms_graph_tuned"])
     out["speedup"] = {"batched_bf16x3_vs_plain_f64_loop": ms_loop_plain / best_x3,
                       "batched_bf16x3_vs_mixed_loop": ms_loop_mixed / best_x3,
                       "tuned_vs_default_bf16x3": out["mixed_bf16x3"]["ms_default_shapes"] /

@@ -353,7 +353,13 @@ id_batch_opts_t id_batch_opts_default(void);
 /* m, n, lda, k: HOST arrays of length batch.  Requirements per matrix:
  * 1 <= k[i] <= min(m[i], n[i], 128), lda[i] >= m[i], ell_i <= 160,
  * n[i] <= 2048.  Errors: ID_ERR_ARG, ID_ERR_UNSUPPORTED (a shape the kernels
- * do not cover). */
+ * do not cover).
+ * precision = ID_PLAIN_F64 (FP64 matrices, fixed ranks only) makes the plan of
+ * the FP64 twin: matrix i's sketched FP64 ID exactly as id_factor computes it
+ * (sketch = 1, ell_i, PLAIN_F64, the shared FP64 Omega), the matrices one after
+ * the other on the caller's stream, each in its own slice of the workspace.
+ * It takes any shape id_factor takes (no limits on k, ell or n), ignores the
+ * tuning fields, and id_batch_autotune rejects it (ID_ERR_ARG). */
 id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_t* m, const int64_t* n,
                                  const int64_t* lda, const int32_t* k, const id_batch_opts_t* opts,
                                  id_batch_plan_t** plan);
@@ -376,14 +382,15 @@ int64_t id_batch_plan_describe(const id_batch_plan_t* plan, char* buf, int64_t l
 id_status_t id_batch_workspace_size(const id_batch_plan_t* plan, size_t* bytes);
 
 /* A: HOST array of batch DEVICE pointers to the matrices (a_dtype of the plan).
- * Every matrix must be addressable by TMA: its address and lda[i] * element
- * size multiples of 16 bytes (ID_ERR_ARG otherwise).  work: 256-byte aligned,
+ * Every matrix of a mixed plan must be addressable by TMA: its address and
+ * lda[i] * element size multiples of 16 bytes (ID_ERR_ARG otherwise).  work: 256-byte aligned,
  * at least work_bytes; it holds the tables from now on. */
 id_status_t id_batch_bind(id_batch_plan_t* plan, const void* const* A, void* work, size_t work_bytes,
                           void* stream);
 
 /* omega: bfloat16/half bits (per the precision), row-major with omega_ld >=
- * m_max, omega_ld a multiple of 8, 16-byte aligned, >= ell_max rows.
+ * m_max, omega_ld a multiple of 8, 16-byte aligned, >= ell_max rows; for a
+ * PLAIN_F64 plan, doubles, row-major with omega_ld >= m_max and >= ell_max rows.
  * J (packed int32), T (packed double), k_out[batch], info[batch]: outputs as
  * laid out by id_batch_plan_query; info per matrix as for id_factor, plus -3
  * when a table entry does not fit its matrix (never expected; nothing of that

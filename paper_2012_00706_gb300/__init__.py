@@ -556,14 +556,16 @@ class IDFunction(torch.autograd.Function):
 # ------------------------------------------------------------------ batched IDs
 
 class BatchPlan:
-    """Many mixed-precision IDs of fixed uneven shapes in one launch sequence.
+    """Many IDs of fixed uneven shapes in one launch sequence: mixed precision
+    (``precision="mixed_*"``), or the FP64 twin (``"plain_f64"``: each matrix's
+    sketched FP64 ID as ``id_factor`` computes it, FP64 Omega).
 
     ``shapes``: list of (m, n); ``ranks``: list of k.  Matrices are column-major
     with leading dimensions ``lda`` (default m; lda * element size must be a
     multiple of 16 bytes).  The plan owns the workspace and the packed outputs.
     ``bind(mats)`` fixes the matrices (CUDA tensors, column-major views such as
-    ``buf.t()[:m]``); ``run(omega)`` factors them with the shared low-precision
-    Omega (at least ell_max x m_max, row-major).
+    ``buf.t()[:m]``); ``run(omega)`` factors them with the shared Omega (at least
+    ell_max x m_max, row-major; low precision bits, or float64 for plain_f64).
     """
 
     def __init__(self, shapes, ranks, *, dtype=torch.float64, precision="mixed_bf16", oversample=10,

@@ -42,6 +42,14 @@ void record_stage(int i, cudaStream_t s) {
 
 cudaEvent_t stage_event(int i) { return i < t_stage_count ? t_stage_events[i] : nullptr; }
 
+int pause_stages() {
+    const int c = t_stage_count;
+    t_stage_count = 0;
+    return c;
+}
+
+void resume_stages(int count) { t_stage_count = count; }
+
 namespace {
 
 uint64_t limit_ns_of(const id_opts_t& o) {

@@ -97,6 +97,10 @@ struct id_batch_plan {
     size_t table_bytes = 0;
     std::vector<uint8_t> tables;    // host image of the table region
     void* bound_work = nullptr;
+    // PLAIN_F64 plans: one FP64 id_factor per matrix in its own slice of the workspace
+    bool plain = false;
+    std::vector<size_t> woff, wbytes;
+    std::vector<const void*> mats;
     // fork/join of the pivoted-QR groups
     cudaStream_t aux[kMaxAuxStreams] = {};
     cudaEvent_t fork = nullptr;
@@ -495,11 +499,54 @@ id_status_t enqueue(const id_batch_plan* p, const void* omega, int64_t omega_ld,
     return ID_OK;
 }
 
+// The options of matrix i's FP64 ID in a PLAIN_F64 plan.
+id_opts_t plain_opts(const id_batch_plan* p, int32_t i, const void* omega, int64_t omega_ld) {
+    id_opts_t o;
+    id_opts_default(&o);
+    o.k = p->k[i];
+    o.sketch = 1;
+    o.ell = static_cast<int32_t>(std::min<int64_t>(p->k[i] + p->opts.oversample, p->m[i]));
+    o.precision = ID_PLAIN_F64;
+    o.omega = omega;
+    o.omega_ld = omega_ld;
+    o.refine_steps = p->opts.refine_steps;
+    o.watchdog_ms = p->opts.watchdog_ms;
+    return o;
+}
+
+// PLAIN_F64: the matrices' FP64 IDs (FP64 sketch by DFMA, FP64 pivoted QR and solve) in
+// order on the caller's stream, each in its own workspace slice.  One stream because the
+// FP64 pivoted QR is a cooperative grid launch, and two of those running side by side on
+// other streams are not guaranteed to be co-resident.
+id_status_t enqueue_plain(const id_batch_plan* p, const void* omega, int64_t omega_ld, int32_t* J, double* T,
+                          int32_t* k_out, int32_t* info, void* work, cudaStream_t s) {
+    uint8_t* w = static_cast<uint8_t*>(work);
+    record_stage(0, s);
+    const int stages = pause_stages();
+    id_status_t st = ID_OK;
+    for (int32_t i = 0; i < p->batch && st == ID_OK; ++i) {
+        const id_opts_t o = plain_opts(p, i, omega, omega_ld);
+        st = id_factor(p->mats[i], ID_F64, p->m[i], p->n[i], p->lda[i], &o, J + p->j_offsets[i], T + p->t_offsets[i],
+                       p->k[i], k_out + i, info + i, nullptr, w + p->woff[i], p->wbytes[i], s);
+    }
+    resume_stages(stages);
+    if (st != ID_OK) return st;
+    for (int i = 1; i < 6; ++i) record_stage(i, s);
+    return ID_OK;
+}
+
 id_status_t check_call(const id_batch_plan* p, const void* omega, int64_t omega_ld, const int32_t* J,
                        const double* T, const int32_t* k_out, const int32_t* info, const void* work,
                        size_t work_bytes) {
     if (!p || !omega || !J || !T || !k_out || !info || !work) return ID_ERR_ARG;
     if (work_bytes < p->work_bytes) return ID_ERR_WORKSPACE;
+    if (p->plain) {
+        if (work != p->bound_work || p->mats.size() != static_cast<size_t>(p->batch) || omega_ld < p->m_max)
+            return ID_ERR_ARG;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return ID_ERR_ARG;
+        return ID_OK;
+    }
     if (work != p->bound_work || p->maps.size() != static_cast<size_t>(p->batch)) return ID_ERR_ARG;
     if (omega_ld < p->m_max || (omega_ld % 8) != 0 || (reinterpret_cast<uintptr_t>(omega) & 15u) != 0)
         return ID_ERR_ARG;
@@ -539,11 +586,14 @@ id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_
     if (batch < 1 || !m || !n || !lda || !k) return ID_ERR_ARG;
     if (a_dtype != ID_F64 && a_dtype != ID_F32) return ID_ERR_ARG;
     id_batch_opts_t o = opts ? *opts : id_batch_opts_default();
-    if (!is_mixed(o.precision) || o.oversample < 0 || o.refine_steps < 0 || o.rel_tol < 0.0 ||
+    const bool plain = o.precision == ID_PLAIN_F64;
+    if ((!is_mixed(o.precision) && !plain) || o.oversample < 0 || o.refine_steps < 0 || o.rel_tol < 0.0 ||
         !std::isfinite(o.rel_tol))
         return ID_ERR_ARG;
+    if (plain && (a_dtype != ID_F64 || o.rel_tol > 0.0)) return ID_ERR_ARG;
     for (int32_t i = 0; i < batch; ++i) {
         if (m[i] < 1 || n[i] < 1 || lda[i] < m[i] || k[i] < 1 || k[i] > m[i] || k[i] > n[i]) return ID_ERR_ARG;
+        if (plain) continue;   // the single-matrix FP64 path takes any shape
         if (k[i] > 128 || n[i] > kMaxClusterBatch * 128 || m[i] > (int64_t(1) << 31) / 2) return ID_ERR_UNSUPPORTED;
         if (std::min<int64_t>(k[i] + o.oversample, m[i]) > 160) return ID_ERR_UNSUPPORTED;
     }
@@ -568,6 +618,33 @@ id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_
     if (!valid_tuning(p->tune)) {
         delete p;
         return ID_ERR_ARG;
+    }
+    if (plain) {
+        // per-matrix FP64 IDs: workspace slices, the packed J / T offsets and Omega's extent
+        p->plain = true;
+        p->j_offsets.assign(batch + 1, 0);
+        p->t_offsets.assign(batch + 1, 0);
+        size_t off = 0;
+        for (int32_t i = 0; i < batch; ++i) {
+            const double fake = 0.0;
+            const id_opts_t oi = plain_opts(p, i, &fake, p->m[i]);
+            size_t b = 0;
+            const id_status_t st = id_workspace_size(ID_F64, p->m[i], p->n[i], &oi, &b);
+            if (st != ID_OK) {
+                delete p;
+                return st;
+            }
+            p->woff.push_back(off);
+            p->wbytes.push_back(b);
+            off = align256(off + b);
+            p->j_offsets[i + 1] = p->j_offsets[i] + p->n[i];
+            p->t_offsets[i + 1] = p->t_offsets[i] + static_cast<int64_t>(p->k[i]) * (p->n[i] - p->k[i]);
+            p->ell_max = std::max(p->ell_max, oi.ell);
+            p->m_max = std::max(p->m_max, p->m[i]);
+        }
+        p->work_bytes = off;
+        *plan = p;
+        return ID_OK;
     }
     if (o.tune_cache) read_cache(p, o.tune_cache);
     if (!build_plan(p)) {
@@ -604,7 +681,11 @@ id_status_t id_batch_plan_query(const id_batch_plan_t* p, size_t* work_bytes, in
 int64_t id_batch_plan_describe(const id_batch_plan_t* p, char* buf, int64_t len) {
     if (!p) return 0;
     std::ostringstream os;
-    os << "{" << tuning_json(p, 0.0).substr(0, tuning_json(p, 0.0).rfind(", \"ms\""))
+    if (p->plain)
+        os << "{\"precision\": \"plain_f64\", \"ids\": " << p->batch << ", \"work_bytes\": " << p->work_bytes
+           << "}";
+    else
+        os << "{" << tuning_json(p, 0.0).substr(0, tuning_json(p, 0.0).rfind(", \"ms\""))
        << ", \"sketch_units\": " << p->sunits.size()
        << ", \"sketch_stages\": " << p->spipe.stages << ", \"cpqr_groups\": " << p->cq_groups.size()
        << ", \"solve_units\": " << p->solve_units.size() << ", \"work_bytes\": " << p->work_bytes << "}";
@@ -627,6 +708,13 @@ id_status_t id_batch_bind(id_batch_plan_t* p, const void* const* A, void* work, 
     if (!p || !A || !work) return ID_ERR_ARG;
     if (work_bytes < p->work_bytes) return ID_ERR_WORKSPACE;
     if ((reinterpret_cast<uintptr_t>(work) & 255u) != 0) return ID_ERR_ARG;
+    if (p->plain) {
+        for (int32_t i = 0; i < p->batch; ++i)
+            if (!A[i]) return ID_ERR_ARG;
+        p->mats.assign(A, A + p->batch);
+        p->bound_work = work;
+        return ID_OK;
+    }
     std::vector<CUtensorMap> maps(p->batch);
     for (int32_t i = 0; i < p->batch; ++i)
         if (!A[i] || !encode_a_map(A[i], p->a_f64, p->m[i], p->n[i], p->lda[i], &maps[i])) return ID_ERR_ARG;
@@ -639,6 +727,7 @@ id_status_t id_factor_batched(const id_batch_plan_t* p, const void* omega, int64
                               int32_t* k_out, int32_t* info, void* work, size_t work_bytes, void* stream) {
     const id_status_t st = check_call(p, omega, omega_ld, J, T, k_out, info, work, work_bytes);
     if (st != ID_OK) return st;
+    if (p->plain) return enqueue_plain(p, omega, omega_ld, J, T, k_out, info, work, static_cast<cudaStream_t>(stream));
     if (!ensure_streams(const_cast<id_batch_plan*>(p))) return ID_ERR_CUDA;
     return enqueue(p, omega, omega_ld, J, T, k_out, info, work, static_cast<cudaStream_t>(stream));
 }
@@ -677,6 +766,7 @@ id_status_t id_batch_autotune(id_batch_plan_t* p, const void* omega, int64_t ome
                               const char* cache_path, double* best_ms) {
     id_status_t st = check_call(p, omega, omega_ld, J, T, k_out, info, work, work_bytes);
     if (st != ID_OK) return st;
+    if (p->plain) return ID_ERR_ARG;      // nothing to tune: the FP64 IDs run with their own shapes
     if (!ensure_streams(p)) return ID_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (reps < 1) reps = 5;

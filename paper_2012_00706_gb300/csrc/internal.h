@@ -25,6 +25,10 @@ const DeviceInfo& device_info();   // current device, cached
 // Stage-boundary events set with id_set_stage_events (this host thread): record event i.
 void record_stage(int i, cudaStream_t s);
 cudaEvent_t stage_event(int i);
+// Stop recording stage events (returns how many were set) and start again; a call made of
+// several id_factor calls keeps its own boundaries this way.
+int pause_stages();
+void resume_stages(int count);
 
 // Bump allocator over the caller's workspace (256-byte alignment).
 struct Carver {

@@ -15,7 +15,7 @@ def gid():
     return g
 
 
-def plan_status(gid, m, n, k, lda=None, **opts):
+def plan_status(gid, m, n, k, lda=None, dtype=0, **opts):
     lib = gid.load()
     b = len(m)
     o = lib.id_batch_opts_default()
@@ -23,7 +23,7 @@ def plan_status(gid, m, n, k, lda=None, **opts):
         setattr(o, key, v)
     i64a = ctypes.c_int64 * b
     h = ctypes.c_void_p(0)
-    code = lib.id_batch_plan_create(b, 0, i64a(*m), i64a(*n), i64a(*(lda or m)), (ctypes.c_int32 * b)(*k),
+    code = lib.id_batch_plan_create(b, dtype, i64a(*m), i64a(*n), i64a(*(lda or m)), (ctypes.c_int32 * b)(*k),
                                     ctypes.byref(o), ctypes.byref(h))
     if h.value:
         lib.id_batch_plan_destroy(h)
@@ -89,7 +89,7 @@ def test_plan_argument_errors(gid):
     assert plan_status(gid, [1000], [500], [129]) == 5        # k > 128
     assert plan_status(gid, [1000], [3000], [50]) == 5        # n > 2048
     assert plan_status(gid, [1000], [500], [128], oversample=40) == 5   # ell > 160
-    assert plan_status(gid, [100], [50], [5], precision=0) == 1         # plain FP64 is not batched
+    assert plan_status(gid, [100], [50], [5], precision=1) == 1         # single-matrix PLAIN_F32 only
     assert plan_status(gid, [100], [50], [5], slab_chunks=7) == 1       # not a tuner candidate
     assert plan_status(gid, [100], [50], [5], cpqr_tpc=3) == 1
 
@@ -104,3 +104,31 @@ def test_plan_reads_tune_cache(gid, tmp_path):
     cache.write_text('{"key": "other|sm1|f64|p2|os10|tol0|b2|0", "slab_chunks": 64}\n')
     p = gid.BatchPlan(shapes, ranks, tune_cache=str(cache), device="cpu")
     assert p.describe()["slab_chunks"] == base.describe()["slab_chunks"]
+
+
+def test_plan_plain_f64(gid):
+    """The FP64 twin: any shape id_factor takes, the packed offsets of a mixed plan, and
+    one workspace slice per matrix; FP32 input and rank by tolerance are refused."""
+    shapes = [(300, 40), (1000, 700), (64, 64), (5000, 3000)]
+    ranks = [10, 200, 64, 1]
+    p = gid.BatchPlan(shapes, ranks, precision="plain_f64", device="cpu")
+    assert p.j_off == [0, 40, 740, 804, 3804]
+    assert p.t_off == [0, 300, 300 + 200 * 500, 100300, 100300 + 2999]
+    assert p.ell_max == 210 and p.m_max == 5000
+    d = p.describe()
+    assert d["precision"] == "plain_f64" and d["ids"] == 4 and d["work_bytes"] == p.work_bytes
+    lib = gid.load()
+    total = 0
+    for (m, n), k in zip(shapes, ranks):
+        o = gid.IDOpts()
+        lib.id_opts_default(ctypes.byref(o))
+        o.k, o.sketch, o.ell, o.precision = k, 1, min(k + 10, m), 0
+        o.omega, o.omega_ld = 256, m        # sizing reads neither; it only has to be set
+        nb = ctypes.c_size_t(0)
+        assert lib.id_workspace_size(0, m, n, ctypes.byref(o), ctypes.byref(nb)) == 0
+        total = (total + nb.value + 255) // 256 * 256
+    assert p.work_bytes == total
+    assert plan_status(gid, [100], [50], [5], precision=0) == 0
+    assert plan_status(gid, [1000], [3000], [129], precision=0) == 0     # beyond the mixed kernels' limits
+    assert plan_status(gid, [100], [50], [5], precision=0, dtype=1) == 1  # FP32 input
+    assert plan_status(gid, [100], [50], [5], precision=0, rel_tol=1e-6) == 1

@@ -8,7 +8,9 @@ oracle's.  Also: ragged and degenerate shapes (k = n, m < 64, n not a multiple
 of 128, padded leading dimensions, float input), rejection of matrices TMA
 cannot address,
 rank by tolerance, equality with one id_factor call per matrix, replay of a
-captured CUDA graph on new data, and the autotuner's cache round trip.
+captured CUDA graph on new data, and the autotuner's cache round trip.  The FP64
+twin (precision plain_f64) equals the oracle's FP64 ID of every matrix and one
+id_factor call per matrix, also when replayed from a captured graph.
 """
 import json
 import os
@@ -248,3 +250,41 @@ def test_batched_argument_errors(gid, dev):
     buf = torch.zeros((50, 101), dtype=torch.float64, device=dev)
     with pytest.raises(gid.IDError):
         odd.bind([buf.t()])
+
+
+def test_batched_plain_f64(gid, dev, orc):
+    """The FP64 twin: each matrix's pivots equal the oracle's sketched FP64 ID with the
+    same Omega block (separated columns: every gap well above FP64 rounding), T within
+    1e-9, and J / T equal one id_factor(plain_f64) call bit for bit, also from a graph."""
+    shapes, mats = small_batch(12, 61)
+    ranks = [r for _, _, r in shapes]
+    plan = gid.BatchPlan([a.shape for a in mats], ranks, precision="plain_f64")
+    om, _ = wl.gaussian_omega(plan.ell_max, plan.m_max, 4343, "bf16")
+    omd = torch.from_numpy(om).to(dev)
+    bufs = [to_dev(a, dev) for a in mats]
+    plan.bind([v for _, v in bufs])
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        plan.run(omd, stream=s)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            plan.run(omd, stream=s)
+    torch.cuda.synchronize()
+    plan.J.zero_()
+    plan.T.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for i, (a, r, res) in enumerate(zip(mats, ranks, plan.results())):
+        m, n = a.shape
+        ell = min(r + 10, m)
+        ref = orc.interp_decomp(a, k=r, omega=om[:ell, :m])
+        assert np.min(ref["gaps"]) >= 1e-8, i
+        assert res.info == 0 and res.k == r, (i, res.info, res.k)
+        J, T = res.J.cpu().numpy(), res.T.cpu().numpy()
+        assert np.array_equal(J, ref["J"]), i
+        assert np.max(np.abs(T - ref["T"])) <= 1e-9 * max(1.0, np.max(np.abs(ref["T"]))), i
+        one = gid.id_factor(bufs[i][1], r, precision="plain_f64", omega=omd[:ell, :m])
+        assert np.array_equal(one.J.cpu().numpy(), J), i
+        assert np.array_equal(one.T.cpu().numpy(), T), i
