@@ -668,7 +668,10 @@ def config5_leg(gid, wl, dev, peaks, reps=5):
             "backward_flops_model": "8 m n k per matrix (thin QR of the skeleton, the projections of the "
                                     "cotangent and their products)",
             "backward_frac_of_fp32": f_bwd / (bms / 1e3) / 1e12 / peaks["fp32_tflops"],
-            "note": "forward includes the host read of the 64 ranks (one synchronisation per batch)"}
+            "forward_path": gid.BatchPlan([(m, n)] * batch, [k] * batch, dtype=torch.float32, precision="plain_f32",
+                                          device=dev).describe(),
+            "note": "forward: one PLAIN_F32 batch plan per call (grouped pivoted QRs in waves, one batched "
+                    "solve), the reconstruction, and the host read of the 64 ranks (one synchronisation)"}
 
 
 def figures(gid, wl, dev, ks=tuple(range(1, 52, 5)), ns=(50, 100, 200, 300, 500, 700, 1000)):

@@ -359,7 +359,14 @@ id_batch_opts_t id_batch_opts_default(void);
  * (sketch = 1, ell_i, PLAIN_F64, the shared FP64 Omega), the matrices one after
  * the other on the caller's stream, each in its own slice of the workspace.
  * It takes any shape id_factor takes (no limits on k, ell or n), ignores the
- * tuning fields, and id_batch_autotune rejects it (ID_ERR_ARG). */
+ * tuning fields, and id_batch_autotune rejects it (ID_ERR_ARG).
+ * precision = ID_PLAIN_F32 (FP64 or FP32 matrices, fixed ranks or a tolerance,
+ * k[i] <= 128, any m and n) pivots every matrix itself, without a sketch, in
+ * FP32 (Algorithm 1 on A in single precision, as id_factor's PLAIN_F32): the
+ * matrices go in waves whose FP32 working copies fit half of L2, each wave one
+ * cooperative launch in which a group of CTAs factors each matrix, and then one
+ * batched T solve (FP32 solves, one refinement step) for all of them.  Omega
+ * is not read (NULL allowed); id_batch_autotune rejects it (ID_ERR_ARG). */
 id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_t* m, const int64_t* n,
                                  const int64_t* lda, const int32_t* k, const id_batch_opts_t* opts,
                                  id_batch_plan_t** plan);
@@ -390,7 +397,8 @@ id_status_t id_batch_bind(id_batch_plan_t* plan, const void* const* A, void* wor
 
 /* omega: bfloat16/half bits (per the precision), row-major with omega_ld >=
  * m_max, omega_ld a multiple of 8, 16-byte aligned, >= ell_max rows; for a
- * PLAIN_F64 plan, doubles, row-major with omega_ld >= m_max and >= ell_max rows.
+ * PLAIN_F64 plan, doubles, row-major with omega_ld >= m_max and >= ell_max rows;
+ * for a PLAIN_F32 plan not read (NULL allowed).
  * J (packed int32), T (packed double), k_out[batch], info[batch]: outputs as
  * laid out by id_batch_plan_query; info per matrix as for id_factor, plus -3
  * when a table entry does not fit its matrix (never expected; nothing of that

@@ -518,22 +518,31 @@ class IDFunction(torch.autograd.Function):
         a = A.unsqueeze(0) if squeeze else A
         batch, m, n = a.shape
         dev = a.device
-        # every matrix is factored into preallocated outputs with one shared workspace,
-        # stream-ordered, and the ranks are read back once for the whole batch
-        ws = torch.empty(id_workspace_size(m, n, a.dtype, k=k, precision="plain_f32"), dtype=torch.uint8,
-                         device=dev)
-        Jt = torch.empty((batch, n), dtype=torch.int32, device=dev)
-        Tall = torch.empty((batch, max(n - k, 1), k), dtype=torch.float64, device=dev)
-        small = torch.zeros((batch, 2), dtype=torch.int32, device=dev)
-        err = torch.zeros(1, dtype=torch.float64, device=dev)
-        for b in range(batch):
-            id_factor(a[b], k, precision="plain_f32", workspace=ws, out=(Jt[b], Tall[b], small[b], err), sync=False)
-        kinfo = small.cpu()
+        if batch > 1:
+            # the whole batch in one launch sequence: grouped pivoted QRs in waves, then
+            # one batched solve; the ranks are read back once
+            ac, lda, _ = _batched_colmajor(a, m)
+            plan = BatchPlan([(m, n)] * batch, [k] * batch, dtype=a.dtype, precision="plain_f32",
+                             lda=[lda] * batch, device=dev)
+            plan.bind([ac[b] for b in range(batch)])
+            plan.run()
+            kinfo = torch.stack([plan.k_out, plan.info], dim=1).cpu()
+            Jt = plan.J[: batch * n].view(batch, n)
+            Tt = plan.T[: batch * k * (n - k)].view(batch, n - k, k).transpose(1, 2)
+        else:
+            ws = torch.empty(id_workspace_size(m, n, a.dtype, k=k, precision="plain_f32"), dtype=torch.uint8,
+                             device=dev)
+            Jt = torch.empty((batch, n), dtype=torch.int32, device=dev)
+            Tall = torch.empty((batch, max(n - k, 1), k), dtype=torch.float64, device=dev)
+            small = torch.zeros((batch, 2), dtype=torch.int32, device=dev)
+            err = torch.zeros(1, dtype=torch.float64, device=dev)
+            id_factor(a[0], k, precision="plain_f32", workspace=ws, out=(Jt[0], Tall[0], small[0], err), sync=False)
+            kinfo = small.cpu()
+            Tt = Tall[:, : n - k, :].transpose(1, 2)          # (batch, k, n - k), column-major per matrix
         bad = (kinfo[:, 0] != k).nonzero()
         if bad.numel():
             b = int(bad[0, 0])
             raise IDError(f"matrix {b}: rank {int(kinfo[b, 0])} < k = {k} (info {int(kinfo[b, 1])})")
-        Tt = Tall[:, : n - k, :].transpose(1, 2)          # (batch, k, n - k), column-major per matrix
         Ahat = id_reconstruct(a, Jt, Tt, k)
         ctx.save_for_backward(a, Jt, Tt)
         ctx.k = k
@@ -557,8 +566,9 @@ class IDFunction(torch.autograd.Function):
 
 class BatchPlan:
     """Many IDs of fixed uneven shapes in one launch sequence: mixed precision
-    (``precision="mixed_*"``), or the FP64 twin (``"plain_f64"``: each matrix's
-    sketched FP64 ID as ``id_factor`` computes it, FP64 Omega).
+    (``precision="mixed_*"``), the FP64 twin (``"plain_f64"``: each matrix's
+    sketched FP64 ID as ``id_factor`` computes it, FP64 Omega), or the unsketched
+    FP32 pivoted QR of every matrix (``"plain_f32"``, no Omega).
 
     ``shapes``: list of (m, n); ``ranks``: list of k.  Matrices are column-major
     with leading dimensions ``lda`` (default m; lda * element size must be a
@@ -639,10 +649,11 @@ class BatchPlan:
         self._lib.id_batch_plan_describe(self._h, buf, need)
         return json.loads(buf.value.decode())
 
-    def run(self, omega: torch.Tensor, stream=None):
+    def run(self, omega: torch.Tensor | None = None, stream=None):
         """Enqueue the batch (no synchronisation); outputs land in self.J/T/k_out/info."""
-        ld = _omega_ld(omega)
-        _check(self._lib.id_factor_batched(self._h, omega.data_ptr(), ld, self.J.data_ptr(), self.T.data_ptr(),
+        ld = _omega_ld(omega) if omega is not None else 0
+        optr = omega.data_ptr() if omega is not None else None
+        _check(self._lib.id_factor_batched(self._h, optr, ld, self.J.data_ptr(), self.T.data_ptr(),
                                            self.k_out.data_ptr(), self.info.data_ptr(), self.work.data_ptr(),
                                            self.work.numel(), _stream_ptr(stream)), "id_factor_batched")
 

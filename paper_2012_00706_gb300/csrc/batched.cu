@@ -13,7 +13,13 @@
 //   3. the coefficient solve, one CTA per block of T columns.
 // Everything the launches need is in the tables the plan writes into the
 // caller's workspace once (id_batch_bind), so a call enqueues kernels only.
+//
+// Two plain twins share the call: PLAIN_F64 issues each matrix's FP64 ID as id_factor
+// computes it, and PLAIN_F32 pivots the matrices themselves (no sketch) in waves, each
+// wave one cooperative launch whose CTA groups factor one matrix each, followed by the
+// batched solve of stage 3.
 #include "common.cuh"
+#include "cpqr_grid.cuh"
 #include "internal.h"
 
 #include <algorithm>
@@ -36,6 +42,7 @@ constexpr int kMinSlabChunks = 16;
 constexpr int kMaxAuxStreams = 32;
 constexpr int kMaxClusterBatch = 16;    // CTAs of one matrix's pivoted QR (non-portable cluster size)
 constexpr int kRowClasses[] = {32, 64, 96, 128, 160};
+constexpr size_t kWaveBytes = size_t(64) << 20;   // PLAIN_F32 working copies of one wave (half of L2)
 constexpr int kNumRowClasses = 5;
 
 int row_class(int ell) {
@@ -65,6 +72,14 @@ struct CqGroup {
 struct SolveClass {
     int kmax = 0;
     int32_t first = 0, count = 0;
+};
+
+// PLAIN_F32: matrices wave_order[first, first + count) in one grouped launch of gsize
+// CTAs per matrix.
+struct Wave {
+    int32_t first = 0, count = 0, gsize = 1;
+    size_t smem = 0;
+    size_t x_bytes = 0, ctrl_stride = 0;
 };
 
 }  // namespace
@@ -101,6 +116,11 @@ struct id_batch_plan {
     bool plain = false;
     std::vector<size_t> woff, wbytes;
     std::vector<const void*> mats;
+    // PLAIN_F32 plans: waves of grouped pivoted QRs, then the batched solve
+    bool plain32 = false;
+    std::vector<int32_t> wave_order;
+    std::vector<Wave> waves;
+    size_t off_params = 0, off_x = 0, off_ctrl = 0;
     // fork/join of the pivoted-QR groups
     cudaStream_t aux[kMaxAuxStreams] = {};
     cudaEvent_t fork = nullptr;
@@ -307,6 +327,141 @@ bool build_plan(id_batch_plan* p) {
     memcpy(p->tables.data() + p->off_cq, p->cq_order.data(), p->cq_order.size() * sizeof(int32_t));
     memcpy(p->tables.data() + p->off_solve, p->solve_units.data(), p->solve_units.size() * sizeof(SolveUnit));
     return true;
+}
+
+// PLAIN_F32: tasks and offsets as for a mixed plan (no sketch), the solve units, and the
+// waves.  Matrices are taken in decreasing order of pivoting work (m n k); a wave holds as
+// many as keep their FP32 working copies within kWaveBytes (and at most one per SM), and
+// shares the SMs evenly between them (gsize CTAs each, at most n of the narrowest).
+bool build_plan_plain32(id_batch_plan* p) {
+    const int sms = device_info().sm_count;
+    p->tasks.assign(p->batch, BatchTask{});
+    p->j_offsets.assign(p->batch + 1, 0);
+    p->t_offsets.assign(p->batch + 1, 0);
+    int64_t rr = 0, sel = 0;
+    p->ell_max = 0;
+    p->m_max = 0;
+    for (int32_t i = 0; i < p->batch; ++i) {
+        BatchTask& t = p->tasks[i];
+        t.m = p->m[i];
+        t.n = p->n[i];
+        t.lda = p->lda[i];
+        t.kcap = p->k[i];
+        t.r_off = rr;
+        rr += static_cast<int64_t>(t.kcap) * t.n;
+        t.sel_off = sel;
+        sel += (t.n + 15) / 16 * 16;
+        t.j_off = p->j_offsets[i];
+        p->j_offsets[i + 1] = p->j_offsets[i] + t.n;
+        t.tcols = p->opts.rel_tol > 0.0 ? t.n - 1 : t.n - t.kcap;
+        t.t_off = p->t_offsets[i];
+        p->t_offsets[i + 1] = p->t_offsets[i] + static_cast<int64_t>(t.kcap) * t.tcols;
+        t.rel_tol = p->opts.rel_tol;
+        p->m_max = std::max(p->m_max, t.m);
+    }
+    build_solve_units(p);
+
+    std::vector<int32_t> order(p->batch);
+    for (int32_t i = 0; i < p->batch; ++i) order[i] = i;
+    auto work = [&](int32_t i) { return static_cast<double>(p->m[i]) * p->n[i] * p->k[i]; };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work(a) > work(b); });
+    p->wave_order = order;
+    p->waves.clear();
+    size_t x_max = 0, ctrl_max = 0, smem_max = 0;
+    for (int32_t q = 0; q < p->batch;) {
+        Wave w;
+        w.first = q;
+        size_t bytes = 0;
+        int64_t nmin = INT64_MAX;
+        while (q < p->batch && w.count < sms) {
+            const int32_t i = order[q];
+            const size_t b = align256(static_cast<size_t>(p->m[i]) * p->n[i] * sizeof(float));
+            if (w.count > 0 && bytes + b > kWaveBytes) break;
+            bytes += b;
+            nmin = std::min(nmin, p->n[i]);
+            ++w.count;
+            ++q;
+        }
+        w.gsize = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(sms / w.count, nmin)));
+        int64_t cpb = 1;
+        for (int32_t e = w.first; e < w.first + w.count; ++e)
+            cpb = std::max<int64_t>(cpb, (p->n[order[e]] + w.gsize - 1) / w.gsize);
+        w.smem = cpqr_grouped_smem(cpb, 0);
+        if (w.smem > static_cast<size_t>(device_info().max_smem_optin) - 8 * 1024) return false;
+        w.x_bytes = bytes;
+        w.ctrl_stride = align256(sizeof(CpqrCtrl) + 2 * static_cast<size_t>(w.gsize) * sizeof(Cand));
+        x_max = std::max(x_max, bytes);
+        ctrl_max = std::max(ctrl_max, w.ctrl_stride * w.count);
+        smem_max = std::max(smem_max, w.smem);
+        p->waves.push_back(w);
+    }
+
+    // workspace: tables (tasks, solve units, parameter blocks), then the wave's working
+    // copies and control words, R, selection flags
+    size_t off = 0;
+    p->off_tasks = off;
+    off = align256(off + p->tasks.size() * sizeof(BatchTask));
+    p->off_solve = off;
+    off = align256(off + p->solve_units.size() * sizeof(SolveUnit));
+    p->off_params = off;
+    off = align256(off + static_cast<size_t>(p->batch) * sizeof(CpqrParams<float>));
+    p->table_bytes = off;
+    p->off_x = off;
+    off = align256(off + x_max);
+    p->off_ctrl = off;
+    off = align256(off + ctrl_max);
+    p->off_r = off;
+    off = align256(off + static_cast<size_t>(rr) * sizeof(double));
+    p->off_sel = off;
+    off = align256(off + static_cast<size_t>(sel));
+    p->work_bytes = off;
+    p->tot.ntasks = p->batch;
+    p->tot.partial = 0;
+    p->tot.r = static_cast<int64_t>((p->off_sel - p->off_r) / sizeof(double));
+    p->tot.j = p->j_offsets.back();
+    p->tot.t = p->t_offsets.back();
+    p->tot.sel = static_cast<int64_t>(p->work_bytes - p->off_sel);
+    p->tables.assign(p->table_bytes, 0);
+    memcpy(p->tables.data() + p->off_tasks, p->tasks.data(), p->tasks.size() * sizeof(BatchTask));
+    memcpy(p->tables.data() + p->off_solve, p->solve_units.data(), p->solve_units.size() * sizeof(SolveUnit));
+    return true;
+}
+
+// PLAIN_F32: one parameter block per matrix, in wave order, for the bound matrices and
+// workspace (the outputs are the call's, added by the kernel from their bases).
+void write_params_plain32(id_batch_plan* p, const void* const* A, void* work) {
+    uint8_t* w = static_cast<uint8_t*>(work);
+    const int64_t ms = p->opts.watchdog_ms > 0 ? p->opts.watchdog_ms : 4000;
+    CpqrParams<float>* params = reinterpret_cast<CpqrParams<float>*>(p->tables.data() + p->off_params);
+    for (const Wave& wv : p->waves) {
+        size_t xoff = 0;
+        for (int32_t e = 0; e < wv.count; ++e) {
+            const int32_t i = p->wave_order[wv.first + e];
+            const BatchTask& t = p->tasks[i];
+            CpqrParams<float> P{};
+            P.X = reinterpret_cast<float*>(w + p->off_x + xoff);
+            xoff += align256(static_cast<size_t>(t.m) * t.n * sizeof(float));
+            P.r = t.m;
+            P.n = t.n;
+            P.ldx = t.m;
+            P.src = A[i];
+            P.src_f64 = p->a_f64;
+            P.ldsrc = t.lda;
+            P.kcap = t.kcap;
+            P.rel_tol = p->opts.rel_tol;
+            P.R = reinterpret_cast<double*>(w + p->off_r) + t.r_off;
+            P.ldr = t.kcap;
+            P.sel = w + p->off_sel + t.sel_off;
+            P.ctrl = reinterpret_cast<CpqrCtrl*>(w + p->off_ctrl + e * wv.ctrl_stride);
+            P.cand = reinterpret_cast<Cand*>(w + p->off_ctrl + e * wv.ctrl_stride + sizeof(CpqrCtrl));
+            P.resident = 0;
+            P.cpb_max = (t.n + wv.gsize - 1) / wv.gsize;
+            P.limit_ns = static_cast<uint64_t>(ms) * 1000000ull;
+            P.out_j = t.j_off;
+            P.out_i = i;
+            params[wv.first + e] = P;
+        }
+    }
 }
 
 uint64_t fnv1a(uint64_t h, const void* data, size_t len) {
@@ -535,11 +690,47 @@ id_status_t enqueue_plain(const id_batch_plan* p, const void* omega, int64_t ome
     return ID_OK;
 }
 
+// PLAIN_F32: per wave, zero the groups' control words and launch the grouped pivoted QR;
+// then the solve classes as in stage 3 of the mixed call.
+id_status_t enqueue_plain32(const id_batch_plan* p, int32_t* J, double* T, int32_t* k_out, int32_t* info, void* work,
+                            cudaStream_t s) {
+    uint8_t* w = static_cast<uint8_t*>(work);
+    const BatchTask* d_tasks = reinterpret_cast<const BatchTask*>(w + p->off_tasks);
+    const SolveUnit* d_solve = reinterpret_cast<const SolveUnit*>(w + p->off_solve);
+    const CpqrParams<float>* d_params = reinterpret_cast<const CpqrParams<float>*>(w + p->off_params);
+    const double* R = reinterpret_cast<const double*>(w + p->off_r);
+    record_stage(0, s);
+    if (cudaMemsetAsync(info, 0, sizeof(int32_t) * p->batch, s) != cudaSuccess) return ID_ERR_CUDA;
+    record_stage(1, s);
+    record_stage(2, s);
+    for (const Wave& wv : p->waves) {
+        if (cudaMemsetAsync(w + p->off_ctrl, 0, wv.ctrl_stride * wv.count, s) != cudaSuccess) return ID_ERR_CUDA;
+        if (launch_cpqr_grouped<float>(d_params + wv.first, wv.count, wv.gsize, wv.smem, J, k_out, info, s) !=
+            cudaSuccess)
+            return ID_ERR_CUDA;
+    }
+    record_stage(3, s);
+    for (const SolveClass& c : p->solve_classes)
+        if (launch_solve_T_batched(d_tasks, d_solve + c.first, c.count, c.kmax, p->tune.solve_warps, R, J, k_out,
+                                   info, T, p->tot, p->opts.refine_steps, s) != cudaSuccess)
+            return ID_ERR_CUDA;
+    record_stage(4, s);
+    record_stage(5, s);
+    return ID_OK;
+}
+
 id_status_t check_call(const id_batch_plan* p, const void* omega, int64_t omega_ld, const int32_t* J,
                        const double* T, const int32_t* k_out, const int32_t* info, const void* work,
                        size_t work_bytes) {
-    if (!p || !omega || !J || !T || !k_out || !info || !work) return ID_ERR_ARG;
+    if (!p || !J || !T || !k_out || !info || !work) return ID_ERR_ARG;
+    if (!omega && !p->plain32) return ID_ERR_ARG;
     if (work_bytes < p->work_bytes) return ID_ERR_WORKSPACE;
+    if (p->plain32) {
+        if (work != p->bound_work || p->mats.size() != static_cast<size_t>(p->batch)) return ID_ERR_ARG;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return ID_ERR_ARG;
+        return ID_OK;
+    }
     if (p->plain) {
         if (work != p->bound_work || p->mats.size() != static_cast<size_t>(p->batch) || omega_ld < p->m_max)
             return ID_ERR_ARG;
@@ -587,13 +778,18 @@ id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_
     if (a_dtype != ID_F64 && a_dtype != ID_F32) return ID_ERR_ARG;
     id_batch_opts_t o = opts ? *opts : id_batch_opts_default();
     const bool plain = o.precision == ID_PLAIN_F64;
-    if ((!is_mixed(o.precision) && !plain) || o.oversample < 0 || o.refine_steps < 0 || o.rel_tol < 0.0 ||
+    const bool plain32 = o.precision == ID_PLAIN_F32;
+    if ((!is_mixed(o.precision) && !plain && !plain32) || o.oversample < 0 || o.refine_steps < 0 || o.rel_tol < 0.0 ||
         !std::isfinite(o.rel_tol))
         return ID_ERR_ARG;
     if (plain && (a_dtype != ID_F64 || o.rel_tol > 0.0)) return ID_ERR_ARG;
     for (int32_t i = 0; i < batch; ++i) {
         if (m[i] < 1 || n[i] < 1 || lda[i] < m[i] || k[i] < 1 || k[i] > m[i] || k[i] > n[i]) return ID_ERR_ARG;
         if (plain) continue;   // the single-matrix FP64 path takes any shape
+        if (plain32) {
+            if (k[i] > 128) return ID_ERR_UNSUPPORTED;   // the batched solve's rank limit
+            continue;
+        }
         if (k[i] > 128 || n[i] > kMaxClusterBatch * 128 || m[i] > (int64_t(1) << 31) / 2) return ID_ERR_UNSUPPORTED;
         if (std::min<int64_t>(k[i] + o.oversample, m[i]) > 160) return ID_ERR_UNSUPPORTED;
     }
@@ -646,6 +842,15 @@ id_status_t id_batch_plan_create(int32_t batch, id_dtype_t a_dtype, const int64_
         *plan = p;
         return ID_OK;
     }
+    if (plain32) {
+        p->plain32 = true;
+        if (!build_plan_plain32(p)) {
+            delete p;
+            return ID_ERR_UNSUPPORTED;
+        }
+        *plan = p;
+        return ID_OK;
+    }
     if (o.tune_cache) read_cache(p, o.tune_cache);
     if (!build_plan(p)) {
         delete p;
@@ -684,6 +889,13 @@ int64_t id_batch_plan_describe(const id_batch_plan_t* p, char* buf, int64_t len)
     if (p->plain)
         os << "{\"precision\": \"plain_f64\", \"ids\": " << p->batch << ", \"work_bytes\": " << p->work_bytes
            << "}";
+    else if (p->plain32) {
+        os << "{\"precision\": \"plain_f32\", \"waves\": " << p->waves.size() << ", \"ids_per_wave\": [";
+        for (size_t i = 0; i < p->waves.size(); ++i) os << (i ? ", " : "") << p->waves[i].count;
+        os << "], \"ctas_per_id\": [";
+        for (size_t i = 0; i < p->waves.size(); ++i) os << (i ? ", " : "") << p->waves[i].gsize;
+        os << "], \"solve_units\": " << p->solve_units.size() << ", \"work_bytes\": " << p->work_bytes << "}";
+    }
     else
         os << "{" << tuning_json(p, 0.0).substr(0, tuning_json(p, 0.0).rfind(", \"ms\""))
        << ", \"sketch_units\": " << p->sunits.size()
@@ -708,12 +920,14 @@ id_status_t id_batch_bind(id_batch_plan_t* p, const void* const* A, void* work, 
     if (!p || !A || !work) return ID_ERR_ARG;
     if (work_bytes < p->work_bytes) return ID_ERR_WORKSPACE;
     if ((reinterpret_cast<uintptr_t>(work) & 255u) != 0) return ID_ERR_ARG;
-    if (p->plain) {
+    if (p->plain || p->plain32) {
         for (int32_t i = 0; i < p->batch; ++i)
             if (!A[i]) return ID_ERR_ARG;
         p->mats.assign(A, A + p->batch);
         p->bound_work = work;
-        return ID_OK;
+        if (!p->plain32) return ID_OK;
+        write_params_plain32(p, A, work);
+        return upload(p, work, static_cast<cudaStream_t>(stream));
     }
     std::vector<CUtensorMap> maps(p->batch);
     for (int32_t i = 0; i < p->batch; ++i)
@@ -728,6 +942,7 @@ id_status_t id_factor_batched(const id_batch_plan_t* p, const void* omega, int64
     const id_status_t st = check_call(p, omega, omega_ld, J, T, k_out, info, work, work_bytes);
     if (st != ID_OK) return st;
     if (p->plain) return enqueue_plain(p, omega, omega_ld, J, T, k_out, info, work, static_cast<cudaStream_t>(stream));
+    if (p->plain32) return enqueue_plain32(p, J, T, k_out, info, work, static_cast<cudaStream_t>(stream));
     if (!ensure_streams(const_cast<id_batch_plan*>(p))) return ID_ERR_CUDA;
     return enqueue(p, omega, omega_ld, J, T, k_out, info, work, static_cast<cudaStream_t>(stream));
 }
@@ -766,7 +981,7 @@ id_status_t id_batch_autotune(id_batch_plan_t* p, const void* omega, int64_t ome
                               const char* cache_path, double* best_ms) {
     id_status_t st = check_call(p, omega, omega_ld, J, T, k_out, info, work, work_bytes);
     if (st != ID_OK) return st;
-    if (p->plain) return ID_ERR_ARG;      // nothing to tune: the FP64 IDs run with their own shapes
+    if (p->plain || p->plain32) return ID_ERR_ARG;   // nothing to tune: the plain IDs run with their own shapes
     if (!ensure_streams(p)) return ID_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (reps < 1) reps = 5;

@@ -263,15 +263,16 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 // at 0 for the launch; `epoch` counts this CTA's barriers.  Returns false if the
 // grid-wide abort flag is up or the wait ran past limit_ns (then it raises the
 // flag so every CTA leaves).  Call from all threads of the CTA.
+// count: the CTAs taking part (the whole grid, or one group of a grouped launch).
 __device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t& epoch, int* abort,
-                                             uint64_t limit_ns, int* s_ok) {
+                                             uint64_t limit_ns, int* s_ok, uint32_t count) {
     __syncthreads();
     epoch += 1;
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
         atomicAdd(counter, 1u);
-        const uint32_t target = epoch * gridDim.x;
+        const uint32_t target = epoch * count;
         const uint64_t t0 = globaltimer_ns();
         while (ld_acquire_u32(counter) < target) {
             if (ld_volatile_i32(abort)) { ok = 0; break; }

@@ -106,12 +106,12 @@ __host__ __device__ inline size_t grid_smem_bytes(int64_t cpb) {
     return 2 * static_cast<size_t>(cpb) * sizeof(T) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
 }
 
+// The pivoted QR of one matrix by the G CTAs b = 0..G-1 (a whole grid, or one group of a
+// grouped launch).
 template <typename T>
-__global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> P) {
-    extern __shared__ __align__(16) uint8_t smem_dyn[];
-    __shared__ GridShared<T> G_;
-
-    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+__device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int G, const int b, GridShared<T>& G_,
+                                               uint8_t* smem_dyn) {
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int64_t c0 = P.n * b / G, c1 = P.n * (b + 1) / G;
     const int nc = static_cast<int>(c1 - c0);
@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
         const T tot = block_sum(tid == 0 ? local_total : T(0), G_.shs);
         publish(0, 0, static_cast<double>(tot));
     }
-    bool ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok);
+    bool ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok,
+                           static_cast<uint32_t>(G));
 
     int k = 0;
     double total = 0.0;
@@ -350,7 +351,8 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
             __syncthreads();
         }
         publish(slot ^ 1, j + 1, 0.0);
-        ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok);
+        ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok,
+                           static_cast<uint32_t>(G));
         k = j + 1;
     }
     if (!ok) {
@@ -358,6 +360,55 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> 
         return;
     }
     if (b == 0) list_complement(P.J, P.sel, P.n, k, P.k_out, G_.shi);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> P) {
+    extern __shared__ __align__(16) uint8_t smem_dyn[];
+    __shared__ GridShared<T> G_;
+    cpqr_grid_body<T>(P, static_cast<int>(gridDim.x), static_cast<int>(blockIdx.x), G_, smem_dyn);
+}
+
+// Grouped launch: CTAs [g gsize, (g + 1) gsize) factor the matrix of groups[g] on their own,
+// with the group's own candidate table and barrier counter.  The launch is cooperative, so
+// every group is resident at once and its barrier waits only on its own CTAs.
+template <typename T>
+__global__ void __launch_bounds__(kGridThreads) k_cpqr_grid_grouped(const CpqrParams<T>* __restrict__ groups,
+                                                                   int gsize, int32_t* J_base, int32_t* k_out_base,
+                                                                   int32_t* info_base) {
+    extern __shared__ __align__(16) uint8_t smem_dyn[];
+    __shared__ GridShared<T> G_;
+    __shared__ CpqrParams<T> sP;
+    if (threadIdx.x == 0) {
+        sP = groups[blockIdx.x / gsize];
+        sP.J = J_base + sP.out_j;
+        sP.k_out = k_out_base + sP.out_i;
+        sP.info = info_base + sP.out_i;
+    }
+    __syncthreads();
+    cpqr_grid_body<T>(sP, gsize, static_cast<int>(blockIdx.x % gsize), G_, smem_dyn);
+}
+
+template <typename T>
+cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gsize, size_t smem, int32_t* J_base,
+                                int32_t* k_out_base, int32_t* info_base, cudaStream_t s) {
+    void* kern = reinterpret_cast<void*>(k_cpqr_grid_grouped<T>);
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {const_cast<CpqrParams<T>**>(&groups), &gsize, &J_base, &k_out_base, &info_base};
+    return cudaLaunchCooperativeKernel(kern, dim3(static_cast<unsigned>(ngroups * gsize)), dim3(kGridThreads), args,
+                                       smem, s);
+}
+template cudaError_t launch_cpqr_grouped<float>(const CpqrParams<float>*, int, int, size_t, int32_t*, int32_t*,
+                                                int32_t*, cudaStream_t);
+template cudaError_t launch_cpqr_grouped<double>(const CpqrParams<double>*, int, int, size_t, int32_t*, int32_t*,
+                                                 int32_t*, cudaStream_t);
+
+size_t cpqr_grouped_smem(int64_t cpb, int f64) {
+    return f64 ? grid_smem_bytes<double>(cpb) : grid_smem_bytes<float>(cpb);
 }
 
 size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes) {

@@ -47,6 +47,8 @@ struct CpqrParams {
     int resident;
     int64_t cpb_max;   // columns per CTA at most (shared-memory layout)
     uint64_t limit_ns;
+    int64_t out_j;     // grouped launch: J = J_base + out_j, k_out / info = their base + out_i
+    int32_t out_i;
 };
 
 // Candidate entries written by other CTAs are read from L2 (never from a stale L1 line).
@@ -98,5 +100,16 @@ __host__ __device__ inline size_t resident_smem_bytes(int64_t cpb, int64_t r) {
 
 template <typename T>
 cudaError_t launch_cpqr_resident(const CpqrParams<T>& P, int grid, size_t smem, cudaStream_t s);
+
+// Grouped streaming pivoted QR: ngroups matrices, gsize CTAs each, in one cooperative
+// launch; groups (device) holds one parameter block per matrix, each with its own control
+// word and candidate table [2][gsize], zeroed before the launch.  The outputs of group g
+// are J_base + out_j, k_out_base[out_i] and info_base[out_i].  smem from
+// cpqr_grouped_smem(the largest columns per CTA of any group).
+template <typename T>
+cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gsize, size_t smem, int32_t* J_base,
+                                int32_t* k_out_base, int32_t* info_base, cudaStream_t s);
+size_t cpqr_grouped_smem(int64_t cpb, int f64);
+constexpr int kCpqrGroupedThreads = 512;
 
 }  // namespace gid

@@ -89,7 +89,6 @@ def test_plan_argument_errors(gid):
     assert plan_status(gid, [1000], [500], [129]) == 5        # k > 128
     assert plan_status(gid, [1000], [3000], [50]) == 5        # n > 2048
     assert plan_status(gid, [1000], [500], [128], oversample=40) == 5   # ell > 160
-    assert plan_status(gid, [100], [50], [5], precision=1) == 1         # single-matrix PLAIN_F32 only
     assert plan_status(gid, [100], [50], [5], slab_chunks=7) == 1       # not a tuner candidate
     assert plan_status(gid, [100], [50], [5], cpqr_tpc=3) == 1
 
@@ -132,3 +131,22 @@ def test_plan_plain_f64(gid):
     assert plan_status(gid, [1000], [3000], [129], precision=0) == 0     # beyond the mixed kernels' limits
     assert plan_status(gid, [100], [50], [5], precision=0, dtype=1) == 1  # FP32 input
     assert plan_status(gid, [100], [50], [5], precision=0, rel_tol=1e-6) == 1
+
+
+def test_plan_plain_f32_waves(gid):
+    """The unsketched FP32 plan: waves whose FP32 working copies fit 64 MiB, the SMs
+    shared evenly within a wave, and the packed offsets of the other plans."""
+    p = gid.BatchPlan([(2048, 512)] * 64, [32] * 64, dtype=torch.float32, precision="plain_f32", device="cpu")
+    d = p.describe()
+    assert d["precision"] == "plain_f32"
+    assert d["ids_per_wave"] == [16, 16, 16, 16]          # 4 MiB each
+    assert d["ctas_per_id"] == [9, 9, 9, 9]               # 152 SMs // 16
+    assert p.j_off[-1] == 64 * 512 and p.t_off[-1] == 64 * 32 * 480
+    q = gid.BatchPlan([(300, 3000), (5000, 40), (300, 7)], [128, 40, 7], precision="plain_f32", tol=1e-3,
+                      device="cpu")
+    d = q.describe()
+    assert d["waves"] == 1 and d["ids_per_wave"] == [3] and d["ctas_per_id"] == [7]   # at most n of the narrowest
+    assert q.t_off == [0, 128 * 2999, 128 * 2999 + 40 * 39, 128 * 2999 + 40 * 39 + 7 * 6]
+    assert plan_status(gid, [100], [50], [5], precision=1) == 0
+    assert plan_status(gid, [100], [50], [5], precision=1, dtype=1) == 0
+    assert plan_status(gid, [1000], [500], [129], precision=1) == 5      # the batched solve's rank limit

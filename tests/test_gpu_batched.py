@@ -288,3 +288,36 @@ def test_batched_plain_f64(gid, dev, orc):
         one = gid.id_factor(bufs[i][1], r, precision="plain_f64", omega=omd[:ell, :m])
         assert np.array_equal(one.J.cpu().numpy(), J), i
         assert np.array_equal(one.T.cpu().numpy(), T), i
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batched_plain_f32(gid, dev, orc, dtype):
+    """The unsketched FP32 plan (grouped pivoted QRs in waves, then the batched solve):
+    uneven shapes over two waves (six 4000 x 1000 working copies of 16 MB do not fit one
+    64 MB wave) plus ragged small ones.  Every matrix's pivots equal the oracle's
+    unsketched ID of the same data (separated columns), its 2-norm error meets
+    e <= 1.1 e_D + 10 u32, and J and T agree with one id_factor(plain_f32) call."""
+    shapes = [(4000, 1000, 30)] * 6 + [(300, 77, 12), (1000, 33, 33), (2048, 512, 32)]
+    mats = [wl.separated_matrix(m, n, seed=700 + i, decay=0.9).astype(dtype) for i, (m, n, _) in enumerate(shapes)]
+    ranks = [r for _, _, r in shapes]
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    plan = gid.BatchPlan([a.shape for a in mats], ranks, dtype=tdt, precision="plain_f32")
+    assert plan.describe()["waves"] >= 2
+    bufs = [to_dev(a, dev, dtype=dtype) for a in mats]
+    plan.bind([v for _, v in bufs])
+    plan.run()
+    torch.cuda.synchronize()
+    for i, (a, r, res) in enumerate(zip(mats, ranks, plan.results())):
+        a64 = a.astype(np.float32).astype(np.float64)      # the values the FP32 pivoting sees
+        ref = orc.interp_decomp(a64, k=r)
+        assert res.info == 0 and res.k == r, (i, res.info, res.k)
+        J, T = res.J.cpu().numpy(), res.T.cpu().numpy()
+        assert np.array_equal(J, ref["J"]), i
+        scale = max(1.0, np.max(np.abs(ref["T"])))
+        assert np.max(np.abs(T - ref["T"])) <= 1e-4 * scale, i
+        e_m = orc.rel_err(a64, J, T, r)
+        e_d = orc.rel_err(a64, ref["J"], ref["T"], r)
+        assert e_m <= 1.1 * e_d + 10 * 2.0 ** -24, (i, e_m, e_d)
+        one = gid.id_factor(bufs[i][1], r, precision="plain_f32")
+        assert np.array_equal(one.J.cpu().numpy(), J), i
+        assert np.max(np.abs(one.T.cpu().numpy() - T)) <= 1e-4 * scale, i
