@@ -674,6 +674,35 @@ def config5_leg(gid, wl, dev, peaks, reps=5):
                     "solve), the reconstruction, and the host read of the 64 ranks (one synchronisation)"}
 
 
+def profile_case(gid, wl, dev, which):
+    """One launch of each pivoted-QR kernel, in this order: the cluster kernel (config 2's
+    BF16x3 ID: its sketch 110 x 2000), the resident grid kernel (config 1 plain FP64,
+    1000 x 500, k = 50), the streaming grid kernel (plain FP64 16384 x 1000, k = 50,
+    sigma_i = i^-2: a 131 MB working copy) and the grouped kernel (one wave of 16 FP32
+    2048 x 512 matrices of config 5, k = 32)."""
+    import torch
+    cfg = wl.config2()
+    A = torch.from_numpy(cfg["A"]).to(dev)
+    om = torch.from_numpy(cfg["omega_bits"].view(np.int16)).to(dev).view(torch.bfloat16)
+    gid.id_factor(A, cfg["k"], precision="mixed_bf16x3", omega=om)
+    del A
+    torch.cuda.empty_cache()
+    c1 = wl.config1()
+    gid.id_factor(torch.from_numpy(c1["A"]).to(dev), c1["k"], precision="plain_f64")
+    a3 = wl.lowrank(16384, 1000, np.arange(1, 1001, dtype=np.float64) ** -2.0, 6)
+    gid.id_factor(torch.from_numpy(a3).to(dev), 50, precision="plain_f64")
+    c5 = wl.config5()
+    mats = [torch.from_numpy(np.asfortranarray(c5["A"][i])).to(dev) for i in range(16)]
+    plan = gid.BatchPlan([tuple(a.shape) for a in mats], [c5["k"]] * 16, dtype=torch.float32,
+                         precision="plain_f32")
+    plan.bind(mats)
+    plan.run()
+    torch.cuda.synchronize()
+    bad = [i for i, r in enumerate(plan.results()) if r.info != 0 or r.k != c5["k"]]
+    print(json.dumps({"profile_case": which, "grouped_plan": plan.describe(), "bad": bad}), flush=True)
+    return 1 if bad else 0
+
+
 def figures(gid, wl, dev, ks=tuple(range(1, 52, 5)), ns=(50, 100, 200, 300, 500, 700, 1000)):
     """The sweeps of the paper's Figs. 1-6 (Sec. 3): the paper's Slow / Medium / Fast
     matrices (1000 x 1000, sigma_i = i^-1, i^-2, i^-4), target rank k over `ks` with all
@@ -749,6 +778,8 @@ def main():
     ap.add_argument("--inflight", type=int, default=INFLIGHT, help="IDs in flight in the timed stream")
     ap.add_argument("--figures", action="store_true",
                     help="print the k and n sweeps of the paper's Figs. 1-6 as one JSON object and exit")
+    ap.add_argument("--profile-case", choices=["cpqr"],
+                    help="run one launch of each pivoted-QR kernel (a profiling case) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -773,6 +804,8 @@ def main():
             dist.barrier()
 
     gid.load()
+    if args.profile_case:
+        return profile_case(gid, wl, dev, args.profile_case)
     if args.figures:
         if rank == 0:
             print(json.dumps(figures(gid, wl, dev)), flush=True)
