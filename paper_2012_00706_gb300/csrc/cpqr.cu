@@ -32,7 +32,12 @@
 namespace gid {
 
 constexpr int kGridThreads = 512;
-constexpr int kColGroup = 8;                 // columns of one pass over the rows
+constexpr int kGridWarps = kGridThreads / 32;
+constexpr int kSuper = 256;                  // columns whose dot products share one CTA barrier
+// columns of one pass over the rows, and rows per thread unrolled: 32 loads in flight
+template <typename T> struct ColGroup;
+template <> struct ColGroup<double> { static constexpr int cols = 8, unroll = 4; };
+template <> struct ColGroup<float> { static constexpr int cols = 16, unroll = 2; };
 constexpr size_t kResidentSmem = 200 * 1024; // shared memory for resident columns
 
 template <typename T> struct SqrtU;
@@ -91,19 +96,20 @@ struct GridShared {
     double shv[33];
     int shi[33];
     T shs[33];
-    T red[kGridThreads / 32][kColGroup];
-    T sv[kColGroup];
-    int recompute[kColGroup];
     int ok;
     int p, pg;
     double alpha, s2, sumnu, total;
 };
 
-// Dynamic shared memory of a CTA: residual norms, reference norms and selection flags
-// of its (at most cpb) columns.
+// Dynamic shared memory of a CTA: residual norms and reference norms of its (at most cpb)
+// columns, the per-warp partial sums, reflector scalars and recompute flags of one
+// super-group of min(cpb, kSuper) columns, and the columns' selection flags.
+__host__ __device__ inline int64_t grid_super(int64_t cpb) { return cpb < kSuper ? cpb : kSuper; }
 template <typename T>
 __host__ __device__ inline size_t grid_smem_bytes(int64_t cpb) {
-    return 2 * static_cast<size_t>(cpb) * sizeof(T) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
+    const size_t sup = static_cast<size_t>(grid_super(cpb));
+    return (2 * static_cast<size_t>(cpb) + (kGridWarps + 1) * sup) * sizeof(T) + sup * sizeof(int) +
+           ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
 }
 
 // The pivoted QR of one matrix by the G CTAs b = 0..G-1 (a whole grid, or one group of a
@@ -117,9 +123,13 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     const int nc = static_cast<int>(c1 - c0);
     const int64_t r = P.r;
     const T sqrt_u = SqrtU<T>::v();
+    const int sup = static_cast<int>(grid_super(P.cpb_max));
     T* nu_s = reinterpret_cast<T*>(smem_dyn);
     T* nuref_s = nu_s + P.cpb_max;
-    uint8_t* sel_s = reinterpret_cast<uint8_t*>(nuref_s + P.cpb_max);
+    T* red_s = nuref_s + P.cpb_max;             // [kGridWarps][sup]
+    T* sv_s = red_s + kGridWarps * sup;
+    int* rec_s = reinterpret_cast<int*>(sv_s + sup);
+    uint8_t* sel_s = reinterpret_cast<uint8_t*>(rec_s + sup);
     uint32_t epoch = 0;
 
     // column c (local index) of the slice in the global working copy
@@ -259,40 +269,45 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             P.R[static_cast<int64_t>(p) * P.ldr + j] = static_cast<double>(beta);
         }
         __syncthreads();
-        // ---- the slice's unselected columns, kColGroup at a time
-        for (int g0 = 0; g0 < nc; g0 += kColGroup) {
-            const int gn = min(kColGroup, nc - g0);
+        // ---- the slice's unselected columns by super-groups of at most kSuper: the dot
+        // products of all of them (CG columns per pass over the rows), one barrier, their
+        // reflector scalars, one barrier, the updates, and the squared norms where the
+        // downdate was refused
+        constexpr int CG = ColGroup<T>::cols;
+        constexpr int UR = ColGroup<T>::unroll;
+        for (int s0 = 0; s0 < nc; s0 += sup) {
+            const int sn = min(sup, nc - s0);
             // pass 1: S_c = x_p(j:r)^T x_c(j:r)
-            bool act[kColGroup];
-            T* xc[kColGroup];
+            for (int g0 = s0; g0 < s0 + sn; g0 += CG) {
+                const int gn = min(CG, s0 + sn - g0);
+                const T* xg = col(g0);
+                bool act[CG];
+                T S[CG];
 #pragma unroll
-            for (int q = 0; q < kColGroup; ++q) {
-                act[q] = q < gn && !sel_s[g0 + q];
-                xc[q] = col(min(g0 + q, nc - 1));
-            }
-            T S[kColGroup];
+                for (int q = 0; q < CG; ++q) {
+                    act[q] = q < gn && !sel_s[g0 + q];
+                    S[q] = 0;
+                }
+#pragma unroll UR
+                for (int64_t t = j + tid; t < r; t += nt) {
+                    const T pv = __ldcg(xp + t);
 #pragma unroll
-            for (int q = 0; q < kColGroup; ++q) S[q] = 0;
-#pragma unroll 4
-            for (int64_t t = j + tid; t < r; t += nt) {
-                const T pv = __ldcg(xp + t);
+                    for (int q = 0; q < CG; ++q)
+                        if (act[q]) S[q] = fma(pv, xg[q * P.ldx + t], S[q]);
+                }
 #pragma unroll
-                for (int q = 0; q < kColGroup; ++q)
-                    if (act[q]) S[q] = fma(pv, xc[q][t], S[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < kColGroup; ++q) {
-                const T v = warp_sum(S[q]);
-                if (lane == 0) G_.red[warp][q] = v;
+                for (int q = 0; q < CG; ++q) {
+                    const T v = warp_sum(S[q]);
+                    if (lane == 0 && q < gn) red_s[warp * sup + (g0 - s0) + q] = v;
+                }
             }
             __syncthreads();
-            if (tid < gn) {
-                const int c = g0 + tid;
+            for (int c = s0 + tid; c < s0 + sn; c += nt) {
                 T sv = 0;
                 int rec = 0;
                 if (!sel_s[c]) {
                     T s = 0;
-                    for (int w = 0; w < (nt >> 5); ++w) s += G_.red[w][tid];
+                    for (int w = 0; w < kGridWarps; ++w) s += red_s[w * sup + (c - s0)];
                     const T X = col(c)[j];
                     s = fma(-beta, X, s);
                     const T tw = -s * rb;
@@ -307,45 +322,55 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                         else nu_s[c] = d;
                     }
                 }
-                G_.sv[tid] = sv;
-                G_.recompute[tid] = rec;
+                sv_s[c - s0] = sv;
+                rec_s[c - s0] = rec;
             }
             __syncthreads();
             // pass 2: x_c(t) -= sv_c x_p(t) for t > j; squared norms where recomputed
-            T msv[kColGroup], sq[kColGroup];
-            bool rec[kColGroup];
             bool any_rec = false;
+            for (int g0 = s0; g0 < s0 + sn; g0 += CG) {
+                const int gn = min(CG, s0 + sn - g0);
+                T* xg = col(g0);
+                T msv[CG], sq[CG];
+                bool act[CG], rec[CG];
+                bool grp_rec = false;
 #pragma unroll
-            for (int q = 0; q < kColGroup; ++q) {
-                msv[q] = -G_.sv[q];
-                rec[q] = act[q] && G_.recompute[q] != 0;
-                any_rec |= rec[q];
-                sq[q] = 0;
-            }
-#pragma unroll 4
-            for (int64_t t = j + 1 + tid; t < r; t += nt) {
-                const T pv = __ldcg(xp + t);
+                for (int q = 0; q < CG; ++q) {
+                    act[q] = q < gn && !sel_s[g0 + q];
+                    msv[q] = act[q] ? -sv_s[g0 - s0 + q] : T(0);
+                    rec[q] = act[q] && rec_s[g0 - s0 + q] != 0;
+                    grp_rec |= rec[q];
+                    sq[q] = 0;
+                }
+#pragma unroll UR
+                for (int64_t t = j + 1 + tid; t < r; t += nt) {
+                    const T pv = __ldcg(xp + t);
 #pragma unroll
-                for (int q = 0; q < kColGroup; ++q) {
-                    if (act[q]) {
-                        const T nx = fma(msv[q], pv, xc[q][t]);
-                        xc[q][t] = nx;
-                        if (rec[q]) sq[q] = fma(nx, nx, sq[q]);
+                    for (int q = 0; q < CG; ++q) {
+                        if (act[q]) {
+                            const T nx = fma(msv[q], pv, xg[q * P.ldx + t]);
+                            xg[q * P.ldx + t] = nx;
+                            if (rec[q]) sq[q] = fma(nx, nx, sq[q]);
+                        }
                     }
+                }
+                if (grp_rec) {
+#pragma unroll
+                    for (int q = 0; q < CG; ++q) {
+                        const T v = warp_sum(sq[q]);
+                        if (lane == 0 && q < gn) red_s[warp * sup + (g0 - s0) + q] = v;
+                    }
+                    any_rec = true;
                 }
             }
             if (any_rec) {
-#pragma unroll
-                for (int q = 0; q < kColGroup; ++q) {
-                    const T v = warp_sum(sq[q]);
-                    if (lane == 0) G_.red[warp][q] = v;
-                }
                 __syncthreads();
-                if (tid < gn && G_.recompute[tid]) {
+                for (int c = s0 + tid; c < s0 + sn; c += nt) {
+                    if (!rec_s[c - s0]) continue;
                     T s = 0;
-                    for (int w = 0; w < (nt >> 5); ++w) s += G_.red[w][tid];
-                    nu_s[g0 + tid] = s;
-                    nuref_s[g0 + tid] = s;
+                    for (int w = 0; w < kGridWarps; ++w) s += red_s[w * sup + (c - s0)];
+                    nu_s[c] = s;
+                    nuref_s[c] = s;
                 }
             }
             __syncthreads();
