@@ -494,7 +494,7 @@ def config1_leg(gid, wl, dev, peaks, reps=20):
         err = gid.id_factor(A, k, precision=prec, estimate_error=True).err
         out[prec] = {"ms_per_id": ms, "ids_per_s": 1e3 / ms, "tflops": flops / (ms / 1e3) / 1e12,
                      "stages_ms": stages, "k": kout, "err_fro": err,
-                     "cpqr_roofline": {"kernel": "k_cpqr_grid", "bound": "alu", "achieved": ach, "peak": peak,
+                     "cpqr_roofline": {"kernel": "k_cpqr_resident", "bound": "alu", "achieved": ach, "peak": peak,
                                        "unit": "TFLOP/s", "frac": ach / peak,
                                        "algorithmic_flops": cq_flops}}
     return out

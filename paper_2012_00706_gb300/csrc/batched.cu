@@ -383,10 +383,13 @@ bool build_plan_plain32(id_batch_plan* p) {
             ++q;
         }
         w.gsize = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(sms / w.count, nmin)));
-        int64_t cpb = 1;
-        for (int32_t e = w.first; e < w.first + w.count; ++e)
-            cpb = std::max<int64_t>(cpb, (p->n[order[e]] + w.gsize - 1) / w.gsize);
-        w.smem = cpqr_grouped_smem(cpb, 0);
+        int64_t cpb = 1, rst = 0;
+        for (int32_t e = w.first; e < w.first + w.count; ++e) {
+            const int64_t ci = (p->n[order[e]] + w.gsize - 1) / w.gsize;
+            cpb = std::max<int64_t>(cpb, ci);
+            rst = std::max<int64_t>(rst, cpqr_grouped_rstage(ci, p->m[order[e]], 4));
+        }
+        w.smem = cpqr_grouped_smem(cpb, rst, 0);
         if (w.smem > static_cast<size_t>(device_info().max_smem_optin) - 8 * 1024) return false;
         w.x_bytes = bytes;
         w.ctrl_stride = align256(sizeof(CpqrCtrl) + 2 * static_cast<size_t>(w.gsize) * sizeof(Cand));
@@ -456,6 +459,8 @@ void write_params_plain32(id_batch_plan* p, const void* const* A, void* work) {
             P.cand = reinterpret_cast<Cand*>(w + p->off_ctrl + e * wv.ctrl_stride + sizeof(CpqrCtrl));
             P.resident = 0;
             P.cpb_max = (t.n + wv.gsize - 1) / wv.gsize;
+            P.colmode = cpqr_grouped_colmode(P.cpb_max);
+            P.rstage = cpqr_grouped_rstage(P.cpb_max, t.m, 4);
             P.limit_ns = static_cast<uint64_t>(ms) * 1000000ull;
             P.out_j = t.j_off;
             P.out_i = i;

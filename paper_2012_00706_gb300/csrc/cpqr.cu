@@ -102,14 +102,23 @@ struct GridShared {
 };
 
 // Dynamic shared memory of a CTA: residual norms and reference norms of its (at most cpb)
-// columns, the per-warp partial sums, reflector scalars and recompute flags of one
-// super-group of min(cpb, kSuper) columns, and the columns' selection flags.
+// columns, the per-warp partial sums and reflector scalars of one super-group of
+// min(cpb, kSuper) columns, the staged pivot column (rstage rows, column mode), the
+// super-group's recompute flags, and the columns' selection flags.
 __host__ __device__ inline int64_t grid_super(int64_t cpb) { return cpb < kSuper ? cpb : kSuper; }
 template <typename T>
-__host__ __device__ inline size_t grid_smem_bytes(int64_t cpb) {
+__host__ __device__ inline size_t grid_smem_bytes(int64_t cpb, int64_t rstage) {
     const size_t sup = static_cast<size_t>(grid_super(cpb));
-    return (2 * static_cast<size_t>(cpb) + (kGridWarps + 1) * sup) * sizeof(T) + sup * sizeof(int) +
-           ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
+    return (2 * static_cast<size_t>(cpb) + (kGridWarps + 1) * sup + static_cast<size_t>(rstage)) * sizeof(T) +
+           sup * sizeof(int) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
+}
+
+// Column mode (a warp per column, no CTA barrier inside a step) when every warp has a
+// column; the pivot column is staged in shared memory when it takes at most 64 KB.
+constexpr size_t kStageBytes = 64 * 1024;
+inline bool grid_colmode(int64_t cpb) { return cpb >= kGridWarps; }
+inline int64_t grid_rstage(int64_t cpb, int64_t r, int elem_bytes) {
+    return grid_colmode(cpb) && static_cast<size_t>(r) * elem_bytes <= kStageBytes ? r : 0;
 }
 
 // The pivoted QR of one matrix by the G CTAs b = 0..G-1 (a whole grid, or one group of a
@@ -128,12 +137,16 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     T* nuref_s = nu_s + P.cpb_max;
     T* red_s = nuref_s + P.cpb_max;             // [kGridWarps][sup]
     T* sv_s = red_s + kGridWarps * sup;
-    int* rec_s = reinterpret_cast<int*>(sv_s + sup);
+    T* xps_s = sv_s + sup;                      // [rstage] staged pivot column (column mode)
+    int* rec_s = reinterpret_cast<int*>(xps_s + P.rstage);
     uint8_t* sel_s = reinterpret_cast<uint8_t*>(rec_s + sup);
     uint32_t epoch = 0;
 
-    // column c (local index) of the slice in the global working copy
-    auto col = [&](int c) -> T* { return P.X + (c0 + c) * P.ldx; };
+    // column c (local index) of the slice in the global working copy (the parameters may
+    // sit in shared memory, where stores through X could alias them: keep them local)
+    T* const Xs = P.X + c0 * P.ldx;
+    const int64_t ldx = P.ldx;
+    auto col = [&](int c) -> T* { return Xs + c * ldx; };
 
     // ---- init: copy the slice into the working copy (or take it there), exact squared norms
     T local_total = 0;
@@ -269,6 +282,78 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             P.R[static_cast<int64_t>(p) * P.ldr + j] = static_cast<double>(beta);
         }
         __syncthreads();
+        if (P.colmode) {
+            // ---- column mode: warp w takes columns w, w + 16, ...; per column the dot
+            // product (one warp reduction), the reflector scalars, the update and, where the
+            // downdate is refused, the exact squared norm, with no CTA barrier in between
+            // xp(t): the staged copy, or L2 (the column was written by another CTA)
+            auto run_cols = [&](auto xpv) {
+                for (int c = warp; c < nc; c += kGridWarps) {
+                    if (sel_s[c]) continue;
+                    T* x = col(c);
+                    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                    int64_t t = j + lane;
+                    for (; t + 96 < r; t += 128) {
+                        s0 = fma(xpv(t), x[t], s0);
+                        s1 = fma(xpv(t + 32), x[t + 32], s1);
+                        s2 = fma(xpv(t + 64), x[t + 64], s2);
+                        s3 = fma(xpv(t + 96), x[t + 96], s3);
+                    }
+                    for (; t < r; t += 32) s0 = fma(xpv(t), x[t], s0);
+                    T sdot = warp_sum((s0 + s1) + (s2 + s3));
+                    const T X = x[j];
+                    sdot = fma(-beta, X, sdot);
+                    const T tw = -sdot * rb;
+                    const T sv = tw * inv;
+                    const T rho = X - tw;
+                    const T nu = nu_s[c];
+                    bool rec = false;
+                    T d = nu;
+                    if (nu > T(0)) {
+                        d = fmax(nu - rho * rho, T(0));
+                        rec = d <= sqrt_u * nuref_s[c];
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                        if (nu > T(0) && !rec) nu_s[c] = d;
+                    }
+                    const T msv = -sv;
+                    T q0 = 0, q1 = 0;
+                    t = j + 1 + lane;
+                    for (; t + 32 < r; t += 64) {
+                        const T n0 = fma(msv, xpv(t), x[t]);
+                        const T n1 = fma(msv, xpv(t + 32), x[t + 32]);
+                        x[t] = n0;
+                        x[t + 32] = n1;
+                        if (rec) {
+                            q0 = fma(n0, n0, q0);
+                            q1 = fma(n1, n1, q1);
+                        }
+                    }
+                    for (; t < r; t += 32) {
+                        const T n0 = fma(msv, xpv(t), x[t]);
+                        x[t] = n0;
+                        if (rec) q0 = fma(n0, n0, q0);
+                    }
+                    if (rec) {
+                        const T sq = warp_sum(q0 + q1);
+                        if (lane == 0) {
+                            nu_s[c] = sq;
+                            nuref_s[c] = sq;
+                        }
+                    }
+                }
+            };
+            if (P.rstage > 0) {
+                for (int64_t t = j + tid; t < r; t += nt) xps_s[t] = __ldcg(xp + t);
+                __syncthreads();
+                run_cols([&](int64_t t) { return xps_s[t]; });
+            } else {
+                run_cols([&](int64_t t) { return __ldcg(xp + t); });
+            }
+            __syncthreads();
+        } else {
         // ---- the slice's unselected columns by super-groups of at most kSuper: the dot
         // products of all of them (CG columns per pass over the rows), one barrier, their
         // reflector scalars, one barrier, the updates, and the squared norms where the
@@ -280,12 +365,13 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             // pass 1: S_c = x_p(j:r)^T x_c(j:r)
             for (int g0 = s0; g0 < s0 + sn; g0 += CG) {
                 const int gn = min(CG, s0 + sn - g0);
-                const T* xg = col(g0);
                 bool act[CG];
+                const T* xc[CG];
                 T S[CG];
 #pragma unroll
                 for (int q = 0; q < CG; ++q) {
                     act[q] = q < gn && !sel_s[g0 + q];
+                    xc[q] = col(min(g0 + q, nc - 1));
                     S[q] = 0;
                 }
 #pragma unroll UR
@@ -293,7 +379,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     const T pv = __ldcg(xp + t);
 #pragma unroll
                     for (int q = 0; q < CG; ++q)
-                        if (act[q]) S[q] = fma(pv, xg[q * P.ldx + t], S[q]);
+                        if (act[q]) S[q] = fma(pv, xc[q][t], S[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < CG; ++q) {
@@ -330,13 +416,14 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             bool any_rec = false;
             for (int g0 = s0; g0 < s0 + sn; g0 += CG) {
                 const int gn = min(CG, s0 + sn - g0);
-                T* xg = col(g0);
+                T* xc[CG];
                 T msv[CG], sq[CG];
                 bool act[CG], rec[CG];
                 bool grp_rec = false;
 #pragma unroll
                 for (int q = 0; q < CG; ++q) {
                     act[q] = q < gn && !sel_s[g0 + q];
+                    xc[q] = col(min(g0 + q, nc - 1));
                     msv[q] = act[q] ? -sv_s[g0 - s0 + q] : T(0);
                     rec[q] = act[q] && rec_s[g0 - s0 + q] != 0;
                     grp_rec |= rec[q];
@@ -348,8 +435,8 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
 #pragma unroll
                     for (int q = 0; q < CG; ++q) {
                         if (act[q]) {
-                            const T nx = fma(msv[q], pv, xg[q * P.ldx + t]);
-                            xg[q * P.ldx + t] = nx;
+                            const T nx = fma(msv[q], pv, xc[q][t]);
+                            xc[q][t] = nx;
                             if (rec[q]) sq[q] = fma(nx, nx, sq[q]);
                         }
                     }
@@ -374,6 +461,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                 }
             }
             __syncthreads();
+        }
         }
         publish(slot ^ 1, j + 1, 0.0);
         ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok,
@@ -432,9 +520,12 @@ template cudaError_t launch_cpqr_grouped<float>(const CpqrParams<float>*, int, i
 template cudaError_t launch_cpqr_grouped<double>(const CpqrParams<double>*, int, int, size_t, int32_t*, int32_t*,
                                                  int32_t*, cudaStream_t);
 
-size_t cpqr_grouped_smem(int64_t cpb, int f64) {
-    return f64 ? grid_smem_bytes<double>(cpb) : grid_smem_bytes<float>(cpb);
+size_t cpqr_grouped_smem(int64_t cpb, int64_t rstage, int f64) {
+    return f64 ? grid_smem_bytes<double>(cpb, rstage) : grid_smem_bytes<float>(cpb, rstage);
 }
+
+int cpqr_grouped_colmode(int64_t cpb) { return grid_colmode(cpb) ? 1 : 0; }
+int64_t cpqr_grouped_rstage(int64_t cpb, int64_t r, int elem_bytes) { return grid_rstage(cpb, r, elem_bytes); }
 
 size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes) {
     size_t b = sizeof(CpqrCtrl) + 2 * static_cast<size_t>(plan.grid) * sizeof(Cand);
@@ -450,7 +541,8 @@ bool cpqr_plan(int64_t r, int64_t n, int elem_bytes, CpqrPlan* plan) {
     // shared memory beyond the static part (about 2 KB) and a margin
     const size_t budget = std::min<size_t>(kResidentSmem, static_cast<size_t>(dev.max_smem_optin) - 8 * 1024);
     const bool f64 = elem_bytes == 8;
-    const size_t lean = f64 ? grid_smem_bytes<double>(cpb) : grid_smem_bytes<float>(cpb);
+    const int64_t rst = grid_rstage(cpb, r, elem_bytes);
+    const size_t lean = f64 ? grid_smem_bytes<double>(cpb, rst) : grid_smem_bytes<float>(cpb, rst);
     const size_t full = f64 ? resident_smem_bytes<double>(cpb, r) : resident_smem_bytes<float>(cpb, r);
     // resident (warp per column, cpqr_resident.cu) when the slice's columns fit the shared
     // memory, streamed through the working copy otherwise
@@ -482,6 +574,8 @@ static cudaError_t launch_cpqr_t(void* W, int64_t r, int64_t n, int64_t ldw, con
         P.pub = reinterpret_cast<T*>(static_cast<char*>(ctrl) + off);
     }
     P.cpb_max = (n + plan.grid - 1) / plan.grid;
+    P.colmode = grid_colmode(P.cpb_max) ? 1 : 0;
+    P.rstage = grid_rstage(P.cpb_max, r, static_cast<int>(sizeof(T)));
     P.limit_ns = limit_ns;
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(CpqrCtrl), s);
     if (e != cudaSuccess) return e;

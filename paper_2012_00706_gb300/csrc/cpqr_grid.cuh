@@ -49,6 +49,8 @@ struct CpqrParams {
     uint64_t limit_ns;
     int64_t out_j;     // grouped launch: J = J_base + out_j, k_out / info = their base + out_i
     int32_t out_i;
+    int32_t colmode;   // streaming kernel: a warp per column (slices of at least a column per warp)
+    int64_t rstage;    // streaming kernel, column mode: rows of the pivot column staged in shared memory (0: none)
 };
 
 // Candidate entries written by other CTAs are read from L2 (never from a stale L1 line).
@@ -109,7 +111,11 @@ cudaError_t launch_cpqr_resident(const CpqrParams<T>& P, int grid, size_t smem, 
 template <typename T>
 cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gsize, size_t smem, int32_t* J_base,
                                 int32_t* k_out_base, int32_t* info_base, cudaStream_t s);
-size_t cpqr_grouped_smem(int64_t cpb, int f64);
+size_t cpqr_grouped_smem(int64_t cpb, int64_t rstage, int f64);
+// The streaming kernel's mode for a slice of at most cpb columns of r rows: a warp per
+// column, and the rows of the pivot column it stages in shared memory (0: none).
+int cpqr_grouped_colmode(int64_t cpb);
+int64_t cpqr_grouped_rstage(int64_t cpb, int64_t r, int elem_bytes);
 constexpr int kCpqrGroupedThreads = 512;
 
 }  // namespace gid

@@ -243,6 +243,26 @@ def test_plain_tall_streamed_matches_oracle(gid, dev, orc, m, n, k, dtype):
     assert np.max(np.abs(T - ref["T"])) <= tol * max(1.0, np.max(np.abs(ref["T"])))
 
 
+@pytest.mark.parametrize("m,n,k,dtype", [(3000, 2600, 20, np.float64), (9000, 2500, 16, np.float64),
+                                         (5000, 2500, 20, np.float32)])
+def test_plain_wide_column_mode_matches_oracle(gid, dev, orc, m, n, k, dtype):
+    """Wide matrices whose slices hold at least a column per warp take the streamed pivoted
+    QR's column mode (a warp per column, no CTA barrier inside a step), with the pivot column
+    staged in shared memory (3000 and 5000 rows) or read from L2 (9000 FP64 rows, 72 KB):
+    pivots equal the oracle's on separated inputs, T to the solve's accuracy."""
+    a = wl.separated_matrix(m, n, seed=m + n, decay=0.97)
+    a = a.astype(dtype).astype(np.float64)
+    ref = orc.interp_decomp(a, k=k)
+    assert np.min(ref["gaps"]) >= 1e-3
+    prec = "plain_f64" if dtype == np.float64 else "plain_f32"
+    res = gid.id_factor(torch.from_numpy(a.astype(dtype)).to(dev), k, precision=prec)
+    assert res.info == 0 and res.k == k
+    assert np.array_equal(res.J.cpu().numpy(), ref["J"])
+    T = res.T.cpu().numpy()
+    tol = 1e-9 if dtype == np.float64 else 1e-3
+    assert np.max(np.abs(T - ref["T"])) <= tol * max(1.0, np.max(np.abs(ref["T"])))
+
+
 def test_plain_f64_config1_full(gid, dev, orc):
     """Config 1 (1000 x 500, sigma_i = 10^(-i/25), k = 50): pivots equal the oracle's up
     to its first step whose two leading norms are within 1e-8 (none on this matrix),
