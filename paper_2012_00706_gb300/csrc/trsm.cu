@@ -71,7 +71,12 @@ k_solve_T(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__
     }
 }
 
-size_t solve_T_scratch_doubles(int kcap, int64_t n) { return static_cast<size_t>(kcap) * static_cast<size_t>(n); }
+// The thread-per-column solve's correction vectors (kcap per column), or the FP32 inverse
+// of R11 of the product solve (kp x kp floats).
+size_t solve_T_scratch_doubles(int kcap, int64_t n) {
+    const size_t kp = static_cast<size_t>((kcap + 3) & ~3);
+    return std::max(static_cast<size_t>(kcap) * static_cast<size_t>(n), (kp * kp + 1) / 2);
+}
 
 // ---- warp-per-column solve for k <= 32*KQ: lane l holds rows l, l+32, ... of its column.
 //
@@ -492,9 +497,201 @@ cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* unit
     }
 }
 
+// ---- FP32 coefficient solve as products (R from an FP32 pivoted QR, k <= 128, one
+// refinement step).  k_r11_inverse forms X = R11^-1 by k warp substitutions (X(:,j) solves
+// R11 x = e_j); k_solve_T_gemm then takes kGemmCols columns of T per CTA: T0 = X R12, the
+// residual E = R12 - R11 T0 with exact products summed as float pairs (as residual_pairs),
+// and T = T0 + X E, delivered in FP64.  The refinement is the same one step as the warp
+// solve's; the substitutions, a dependent chain per column of T there, run once per column
+// of R11 here, and the rest are register-tiled products (a 4 x 4 block per thread) that skip
+// the zero triangles of X and R11.  An ill-conditioned R11 (r11_ill_conditioned) takes the
+// FP64 solves of the warp kernel instead.
+constexpr int kGemmCols = 32;
+constexpr int kGemmThreads = 256;
+constexpr int kGemmMaxK = 128;
+
+__host__ __device__ inline int gemm_kp(int k) { return (k + 3) & ~3; }
+
+// X (kp x kp column-major, kp = k rounded up to 4): X(:, j) = R11^-1 e_j, zero below row j.
+template <int KQ>
+__global__ void __launch_bounds__(kWarpSolveWarps * 32)
+k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+              const int32_t* __restrict__ k_ptr, float* __restrict__ X) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int k = *k_ptr;
+    if (k <= 0 || static_cast<int>(blockIdx.x) * kWarpSolveWarps >= gemm_kp(k)) return;
+    const int kp = gemm_kp(k);
+    float* r11s = reinterpret_cast<float*>(sm);
+    float* rinv = r11s + static_cast<int64_t>(k) * k;
+    stage_r11<float>(R, ldr, J, k, r11s, rinv);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kWarpSolveWarps + (threadIdx.x >> 5);
+    if (j >= kp) return;
+    float t[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) t[q] = (lane + 32 * q == j) ? 1.f : 0.f;
+    if (j < k) warp_backsub<float, KQ>(t, SmemCols<float>{r11s, k}, rinv, k, lane);
+    float* xc = X + static_cast<int64_t>(j) * kp;
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        const int b = lane + 32 * q;
+        if (b < kp) xc[b] = (j < k && b <= j) ? t[q] : 0.f;
+    }
+}
+
+template <int KQ>
+__global__ void __launch_bounds__(kGemmThreads)
+k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+               const int32_t* __restrict__ k_ptr, int64_t n, const float* __restrict__ Xg, double* __restrict__ T,
+               int64_t ldt, int refine_steps, int64_t smem_bytes) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int k = *k_ptr;
+    if (k <= 0) return;
+    if (r11_ill_conditioned(R, ldr, J, k)) {
+        // every CTA takes part: the fallback's warps cover all columns of T by a grid stride
+        solve_fp64_fallback<KQ>(R, ldr, J, k, n, T, ldt, refine_steps, smem_bytes, sm);
+        return;
+    }
+    const int64_t nc = n - k;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kGemmCols;
+    if (c0 >= nc) return;
+    const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), nc - c0));
+    const int kp = gemm_kp(k);
+    float* Xs = reinterpret_cast<float*>(sm);        // kp x kp, column-major
+    float* Rs = Xs + kp * kp;                        // R11, kp x kp column-major, zero below the diagonal
+    float* Bt = Rs + kp * kp;                        // [kp][kGemmCols]: R12, then the residual E
+    float* Tt = Bt + kp * kGemmCols;                 // [kp][kGemmCols]: T0
+    for (int i = threadIdx.x; i < kp * kp; i += blockDim.x) Xs[i] = __ldg(Xg + i);
+    for (int i = threadIdx.x; i < kp * kp; i += blockDim.x) {
+        const int r = i % kp, b = i / kp;
+        Rs[i] = (b < k && r <= b) ? static_cast<float>(R[static_cast<int64_t>(__ldg(J + b)) * ldr + r]) : 0.f;
+    }
+    for (int i = threadIdx.x; i < kp * kGemmCols; i += blockDim.x) {
+        const int b = i % kp, c = i / kp;
+        Bt[b * kGemmCols + c] =
+            (b < k && c < ncols) ? static_cast<float>(R[static_cast<int64_t>(__ldg(J + k + c0 + c)) * ldr + b]) : 0.f;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;   // columns 4 tx .. 4 tx + 3, rows 4 ty .. 4 ty + 3
+    const int r0 = 4 * ty, cc = 4 * tx;
+    const bool live = r0 < kp;
+    float t0[4][4] = {};
+    if (live) {
+        // T0 = X R12: X(r, b) = 0 for b < r
+        for (int b = r0; b < kp; ++b) {
+            const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
+            const float4 bv = *reinterpret_cast<const float4*>(Bt + b * kGemmCols + cc);
+            const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ba[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) t0[i][jj] = fmaf(xa[i], ba[jj], t0[i][jj]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            *reinterpret_cast<float4*>(Tt + (r0 + i) * kGemmCols + cc) =
+                make_float4(t0[i][0], t0[i][1], t0[i][2], t0[i][3]);
+    }
+    __syncthreads();
+    float e[4][4] = {};
+    if (live) {
+        // E = R12 - R11 T0: exact products (p, fma error), float-pair sums (TwoSum)
+        float hi[4][4], lo[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 bv = *reinterpret_cast<const float4*>(Bt + (r0 + i) * kGemmCols + cc);
+            hi[i][0] = bv.x; hi[i][1] = bv.y; hi[i][2] = bv.z; hi[i][3] = bv.w;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) lo[i][jj] = 0.f;
+        }
+        for (int b = r0; b < kp; ++b) {
+            const float4 rv = *reinterpret_cast<const float4*>(Rs + b * kp + r0);
+            const float4 tv = *reinterpret_cast<const float4*>(Tt + b * kGemmCols + cc);
+            const float ra[4] = {-rv.x, -rv.y, -rv.z, -rv.w}, ta[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float pr = __fmul_rn(ra[i], ta[jj]);
+                    const float er = fmaf(ra[i], ta[jj], -pr);
+                    const float sum = __fadd_rn(hi[i][jj], pr);
+                    const float bp = __fsub_rn(sum, hi[i][jj]);
+                    const float err = __fadd_rn(__fsub_rn(hi[i][jj], __fsub_rn(sum, bp)), __fsub_rn(pr, bp));
+                    hi[i][jj] = sum;
+                    lo[i][jj] = __fadd_rn(lo[i][jj], __fadd_rn(err, er));
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                e[i][jj] = static_cast<float>(static_cast<double>(hi[i][jj]) + static_cast<double>(lo[i][jj]));
+    }
+    __syncthreads();    // every read of R12 is done before E takes its place
+    if (live) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            *reinterpret_cast<float4*>(Bt + (r0 + i) * kGemmCols + cc) = make_float4(e[i][0], e[i][1], e[i][2], e[i][3]);
+    }
+    __syncthreads();
+    if (!live) return;
+    // T = T0 + X E
+    float d[4][4] = {};
+    for (int b = r0; b < kp; ++b) {
+        const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
+        const float4 ev = *reinterpret_cast<const float4*>(Bt + b * kGemmCols + cc);
+        const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ea[4] = {ev.x, ev.y, ev.z, ev.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) d[i][jj] = fmaf(xa[i], ea[jj], d[i][jj]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = r0 + i;
+        if (row >= k) continue;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int c = cc + jj;
+            if (c < ncols) T[(c0 + c) * ldt + row] = static_cast<double>(t0[i][jj]) + static_cast<double>(d[i][jj]);
+        }
+    }
+}
+
+template <int KQ>
+static cudaError_t launch_gemm_solve(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
+                                     int64_t n, double* T, int64_t ldt, float* X, cudaStream_t s) {
+    const int kp = gemm_kp(kcap);
+    const size_t inv_smem = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(float) + 16;
+    auto kinv = k_r11_inverse<KQ>;
+    cudaError_t e = cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(inv_smem));
+    if (e != cudaSuccess) return e;
+    kinv<<<(kp + kWarpSolveWarps - 1) / kWarpSolveWarps, kWarpSolveWarps * 32, inv_smem, s>>>(R64, ldr, J, k_ptr, X);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (2 * static_cast<size_t>(kp) * kp + 2 * static_cast<size_t>(kp) * kGemmCols) * sizeof(float);
+    auto kern = k_solve_T_gemm<KQ>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t cols = std::max<int64_t>(1, n - 1);
+    const unsigned grid = static_cast<unsigned>((cols + kGemmCols - 1) / kGemmCols);
+    kern<<<grid, kGemmThreads, smem, s>>>(R64, ldr, J, k_ptr, n, X, T, ldt, 1, static_cast<int64_t>(smem));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
                            int64_t n, double* T, int64_t ldt, double* scratch, int refine_steps, int low_solve,
                            cudaStream_t s) {
+    if (low_solve && refine_steps == 1 && kcap <= kGemmMaxK) {
+        float* X = reinterpret_cast<float*>(scratch);
+        switch ((kcap + 31) / 32) {
+            case 1: return launch_gemm_solve<1>(R64, ldr, J, k_ptr, kcap, n, T, ldt, X, s);
+            case 2: return launch_gemm_solve<2>(R64, ldr, J, k_ptr, kcap, n, T, ldt, X, s);
+            case 3: return launch_gemm_solve<3>(R64, ldr, J, k_ptr, kcap, n, T, ldt, X, s);
+            default: return launch_gemm_solve<4>(R64, ldr, J, k_ptr, kcap, n, T, ldt, X, s);
+        }
+    }
     if (kcap <= 32 * kWarpSolveMaxQ) {
         const int kq = (kcap + 31) / 32;
         if (low_solve) return launch_warp_solve_kq<float>(kq, R64, ldr, J, k_ptr, kcap, n, T, ldt, refine_steps, s);
