@@ -71,11 +71,11 @@ k_solve_T(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__
     }
 }
 
-// The thread-per-column solve's correction vectors (kcap per column), or the FP32 inverse
-// of R11 of the product solve (kp x kp floats).
+// The thread-per-column solve's correction vectors (kcap per column), or the product
+// solve's FP32 R11 inverse, packed R11 and flag (2 kq^2 + 1 floats, kq = kcap rounded up to 4).
 size_t solve_T_scratch_doubles(int kcap, int64_t n) {
-    const size_t kp = static_cast<size_t>((kcap + 3) & ~3);
-    return std::max(static_cast<size_t>(kcap) * static_cast<size_t>(n), (kp * kp + 1) / 2);
+    const size_t kq = static_cast<size_t>((kcap + 3) & ~3);
+    return std::max(static_cast<size_t>(kcap) * static_cast<size_t>(n), kq * kq + 1);
 }
 
 // ---- warp-per-column solve for k <= 32*KQ: lane l holds rows l, l+32, ... of its column.
@@ -498,40 +498,95 @@ cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* unit
 }
 
 // ---- FP32 coefficient solve as products (R from an FP32 pivoted QR, k <= 128, one
-// refinement step).  k_r11_inverse forms X = R11^-1 by k warp substitutions (X(:,j) solves
-// R11 x = e_j); k_solve_T_gemm then takes kGemmCols columns of T per CTA: T0 = X R12, the
-// residual E = R12 - R11 T0 with exact products summed as float pairs (as residual_pairs),
-// and T = T0 + X E, delivered in FP64.  The refinement is the same one step as the warp
+// refinement step).  k_r11_inverse stages R11 once per CTA (every load in flight), forms
+// X = R11^-1 by warp substitutions (X(:,j) solves the leading (j+1) x (j+1) system for
+// e_j), and leaves in the scratch X, a packed FP32 copy of R11 and the ill-conditioning
+// flag.  k_solve_T_gemm then takes kGemmCols columns of T per CTA: T0 = X R12, the residual
+// E = R12 - R11 T0 with exact products summed as float pairs (as residual_pairs), and
+// T = T0 + X E, delivered in FP64.  The refinement is the same one step as the warp
 // solve's; the substitutions, a dependent chain per column of T there, run once per column
-// of R11 here, and the rest are register-tiled products (a 4 x 4 block per thread) that skip
+// of R11 here, and the rest are register-tiled products (a 4 x 2 block per thread) that skip
 // the zero triangles of X and R11.  An ill-conditioned R11 (r11_ill_conditioned) takes the
 // FP64 solves of the warp kernel instead.
-constexpr int kGemmCols = 32;
+//
+// Scratch (floats, kq = kcap rounded up to 4): X [kq x kq], R11 [kq x kq], flag; both
+// matrices are column-major with the device rank's kp = k rounded up to 4 as leading
+// dimension, zero below the diagonal and past k.
+constexpr int kGemmCols = 16;
 constexpr int kGemmThreads = 256;
 constexpr int kGemmMaxK = 128;
 
 __host__ __device__ inline int gemm_kp(int k) { return (k + 3) & ~3; }
 
-// X (kp x kp column-major, kp = k rounded up to 4): X(:, j) = R11^-1 e_j, zero below row j.
+// An FP32 value stored in an FP64 word, converted by its bits when it is a normal float
+// (the values R holds on this path), by the FP64 pipe otherwise.
+__device__ __forceinline__ float f32_of_exact(double x) {
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (e >= 897u && e <= 1150u && (lo & 0x1FFFFFFFu) == 0u)
+        return __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+    return __double2float_rn(x);
+}
+
 template <int KQ>
 __global__ void __launch_bounds__(kWarpSolveWarps * 32)
 k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
-              const int32_t* __restrict__ k_ptr, float* __restrict__ X) {
+              const int32_t* __restrict__ k_ptr, float* __restrict__ scr, int kq_cap) {
     extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int js[32 * KQ];
     const int k = *k_ptr;
-    if (k <= 0 || static_cast<int>(blockIdx.x) * kWarpSolveWarps >= gemm_kp(k)) return;
     const int kp = gemm_kp(k);
-    float* r11s = reinterpret_cast<float*>(sm);
+    if (k <= 0 || static_cast<int>(blockIdx.x) * kWarpSolveWarps >= kp) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* r11s = reinterpret_cast<float*>(sm);                 // k x k, column-major
     float* rinv = r11s + static_cast<int64_t>(k) * k;
-    stage_r11<float>(R, ldr, J, k, r11s, rinv);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) js[i] = __ldg(J + i);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * kWarpSolveWarps + (threadIdx.x >> 5);
+    // R11 by rounds of 4 columns per warp, the 4 KQ loads of a lane issued together
+    for (int a0 = warp; a0 < k; a0 += 4 * kWarpSolveWarps) {
+        double v[4][KQ];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int a = a0 + u * kWarpSolveWarps;
+            const double* col = R + static_cast<int64_t>(js[min(a, k - 1)]) * ldr;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                const int b = lane + 32 * q;
+                v[u][q] = (a < k && b <= a) ? col[b] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int a = a0 + u * kWarpSolveWarps;
+            if (a >= k) continue;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                const int b = lane + 32 * q;
+                if (b <= a) r11s[a * k + b] = f32_of_exact(v[u][q]);
+                if (b == a) rinv[a] = 1.f / f32_of_exact(v[u][q]);
+            }
+        }
+    }
+    float* X = scr;
+    float* R11p = scr + static_cast<int64_t>(kq_cap) * kq_cap;
+    if (blockIdx.x == 0) {
+        const bool ill = r11_ill_conditioned(R, ldr, J, k);     // CTA-wide (barriers inside)
+        if (threadIdx.x == 0) reinterpret_cast<int*>(R11p + static_cast<int64_t>(kq_cap) * kq_cap)[0] = ill ? 1 : 0;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        for (int a = warp; a < kp; a += kWarpSolveWarps)
+            for (int b = lane; b < kp; b += 32)
+                R11p[a * kp + b] = (a < k && b <= a) ? r11s[a * k + b] : 0.f;
+    }
+    const int j = blockIdx.x * kWarpSolveWarps + warp;
     if (j >= kp) return;
     float t[KQ];
 #pragma unroll
     for (int q = 0; q < KQ; ++q) t[q] = (lane + 32 * q == j) ? 1.f : 0.f;
-    if (j < k) warp_backsub<float, KQ>(t, SmemCols<float>{r11s, k}, rinv, k, lane);
+    // X(:, j) involves R11(0:j, 0:j) only: a chain of j + 1 steps
+    if (j < k) warp_backsub<float, KQ>(t, SmemCols<float>{r11s, k}, rinv, j + 1, lane);
     float* xc = X + static_cast<int64_t>(j) * kp;
 #pragma unroll
     for (int q = 0; q < KQ; ++q) {
@@ -543,12 +598,15 @@ k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restri
 template <int KQ>
 __global__ void __launch_bounds__(kGemmThreads)
 k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
-               const int32_t* __restrict__ k_ptr, int64_t n, const float* __restrict__ Xg, double* __restrict__ T,
-               int64_t ldt, int refine_steps, int64_t smem_bytes) {
+               const int32_t* __restrict__ k_ptr, int64_t n, const float* __restrict__ scr, int kq_cap,
+               double* __restrict__ T, int64_t ldt, int refine_steps, int64_t smem_bytes) {
     extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int jc[kGemmCols];
     const int k = *k_ptr;
     if (k <= 0) return;
-    if (r11_ill_conditioned(R, ldr, J, k)) {
+    const float* Xg = scr;
+    const float* Rg = scr + static_cast<int64_t>(kq_cap) * kq_cap;
+    if (__ldg(reinterpret_cast<const int*>(Rg + static_cast<int64_t>(kq_cap) * kq_cap))) {
         // every CTA takes part: the fallback's warps cover all columns of T by a grid stride
         solve_fp64_fallback<KQ>(R, ldr, J, k, n, T, ldt, refine_steps, smem_bytes, sm);
         return;
@@ -558,61 +616,83 @@ k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
     if (c0 >= nc) return;
     const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), nc - c0));
     const int kp = gemm_kp(k);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* Xs = reinterpret_cast<float*>(sm);        // kp x kp, column-major
-    float* Rs = Xs + kp * kp;                        // R11, kp x kp column-major, zero below the diagonal
+    float* Rs = Xs + kp * kp;                        // R11, kp x kp column-major
     float* Bt = Rs + kp * kp;                        // [kp][kGemmCols]: R12, then the residual E
     float* Tt = Bt + kp * kGemmCols;                 // [kp][kGemmCols]: T0
-    for (int i = threadIdx.x; i < kp * kp; i += blockDim.x) Xs[i] = __ldg(Xg + i);
-    for (int i = threadIdx.x; i < kp * kp; i += blockDim.x) {
-        const int r = i % kp, b = i / kp;
-        Rs[i] = (b < k && r <= b) ? static_cast<float>(R[static_cast<int64_t>(__ldg(J + b)) * ldr + r]) : 0.f;
-    }
-    for (int i = threadIdx.x; i < kp * kGemmCols; i += blockDim.x) {
-        const int b = i % kp, c = i / kp;
-        Bt[b * kGemmCols + c] =
-            (b < k && c < ncols) ? static_cast<float>(R[static_cast<int64_t>(__ldg(J + k + c0 + c)) * ldr + b]) : 0.f;
+    if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? __ldg(J + k + c0 + threadIdx.x) : 0;
+    {
+        const float4* xg4 = reinterpret_cast<const float4*>(Xg);
+        const float4* rg4 = reinterpret_cast<const float4*>(Rg);
+        float4* xs4 = reinterpret_cast<float4*>(Xs);
+        float4* rs4 = reinterpret_cast<float4*>(Rs);
+        const int n4 = kp * kp / 4;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < n4; i += kGemmThreads) {
+            const float4 x = __ldg(xg4 + i), r = __ldg(rg4 + i);
+            xs4[i] = x;
+            rs4[i] = r;
+        }
     }
     __syncthreads();
-    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;   // columns 4 tx .. 4 tx + 3, rows 4 ty .. 4 ty + 3
-    const int r0 = 4 * ty, cc = 4 * tx;
+    // R12 tile: warp w takes columns w and w + 8, its lanes the rows
+#pragma unroll
+    for (int u = 0; u < kGemmCols / kWarpSolveWarps; ++u) {
+        const int c = warp + u * kWarpSolveWarps;
+        const double* col = R + static_cast<int64_t>(jc[c]) * ldr;
+        double v[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            v[q] = (b < k && c < ncols) ? col[b] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            if (b < kp) Bt[b * kGemmCols + c] = f32_of_exact(v[q]);
+        }
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;   // columns 2 tx, 2 tx + 1; rows 4 ty .. 4 ty + 3
+    const int r0 = 4 * ty, cc = 2 * tx;
     const bool live = r0 < kp;
-    float t0[4][4] = {};
+    float t0[4][2] = {};
     if (live) {
         // T0 = X R12: X(r, b) = 0 for b < r
         for (int b = r0; b < kp; ++b) {
             const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
-            const float4 bv = *reinterpret_cast<const float4*>(Bt + b * kGemmCols + cc);
-            const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ba[4] = {bv.x, bv.y, bv.z, bv.w};
+            const float2 bv = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
+            const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ba[2] = {bv.x, bv.y};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) t0[i][jj] = fmaf(xa[i], ba[jj], t0[i][jj]);
+                for (int jj = 0; jj < 2; ++jj) t0[i][jj] = fmaf(xa[i], ba[jj], t0[i][jj]);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            *reinterpret_cast<float4*>(Tt + (r0 + i) * kGemmCols + cc) =
-                make_float4(t0[i][0], t0[i][1], t0[i][2], t0[i][3]);
+            *reinterpret_cast<float2*>(Tt + (r0 + i) * kGemmCols + cc) = make_float2(t0[i][0], t0[i][1]);
     }
     __syncthreads();
-    float e[4][4] = {};
+    float e[4][2] = {};
     if (live) {
         // E = R12 - R11 T0: exact products (p, fma error), float-pair sums (TwoSum)
-        float hi[4][4], lo[4][4];
+        float hi[4][2], lo[4][2];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float4 bv = *reinterpret_cast<const float4*>(Bt + (r0 + i) * kGemmCols + cc);
-            hi[i][0] = bv.x; hi[i][1] = bv.y; hi[i][2] = bv.z; hi[i][3] = bv.w;
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) lo[i][jj] = 0.f;
+            const float2 bv = *reinterpret_cast<const float2*>(Bt + (r0 + i) * kGemmCols + cc);
+            hi[i][0] = bv.x;
+            hi[i][1] = bv.y;
+            lo[i][0] = lo[i][1] = 0.f;
         }
         for (int b = r0; b < kp; ++b) {
             const float4 rv = *reinterpret_cast<const float4*>(Rs + b * kp + r0);
-            const float4 tv = *reinterpret_cast<const float4*>(Tt + b * kGemmCols + cc);
-            const float ra[4] = {-rv.x, -rv.y, -rv.z, -rv.w}, ta[4] = {tv.x, tv.y, tv.z, tv.w};
+            const float2 tv = *reinterpret_cast<const float2*>(Tt + b * kGemmCols + cc);
+            const float ra[4] = {-rv.x, -rv.y, -rv.z, -rv.w}, ta[2] = {tv.x, tv.y};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
+                for (int jj = 0; jj < 2; ++jj) {
                     const float pr = __fmul_rn(ra[i], ta[jj]);
                     const float er = fmaf(ra[i], ta[jj], -pr);
                     const float sum = __fadd_rn(hi[i][jj], pr);
@@ -622,37 +702,37 @@ k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
                     lo[i][jj] = __fadd_rn(lo[i][jj], __fadd_rn(err, er));
                 }
         }
+        // the pair's sum rounded once to FP32
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
-                e[i][jj] = static_cast<float>(static_cast<double>(hi[i][jj]) + static_cast<double>(lo[i][jj]));
+            for (int jj = 0; jj < 2; ++jj) e[i][jj] = __fadd_rn(hi[i][jj], lo[i][jj]);
     }
     __syncthreads();    // every read of R12 is done before E takes its place
     if (live) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            *reinterpret_cast<float4*>(Bt + (r0 + i) * kGemmCols + cc) = make_float4(e[i][0], e[i][1], e[i][2], e[i][3]);
+            *reinterpret_cast<float2*>(Bt + (r0 + i) * kGemmCols + cc) = make_float2(e[i][0], e[i][1]);
     }
     __syncthreads();
     if (!live) return;
     // T = T0 + X E
-    float d[4][4] = {};
+    float d[4][2] = {};
     for (int b = r0; b < kp; ++b) {
         const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
-        const float4 ev = *reinterpret_cast<const float4*>(Bt + b * kGemmCols + cc);
-        const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ea[4] = {ev.x, ev.y, ev.z, ev.w};
+        const float2 ev = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
+        const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ea[2] = {ev.x, ev.y};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) d[i][jj] = fmaf(xa[i], ea[jj], d[i][jj]);
+            for (int jj = 0; jj < 2; ++jj) d[i][jj] = fmaf(xa[i], ea[jj], d[i][jj]);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int row = r0 + i;
         if (row >= k) continue;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
+        for (int jj = 0; jj < 2; ++jj) {
             const int c = cc + jj;
             if (c < ncols) T[(c0 + c) * ldt + row] = static_cast<double>(t0[i][jj]) + static_cast<double>(d[i][jj]);
         }
@@ -661,22 +741,26 @@ k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
 
 template <int KQ>
 static cudaError_t launch_gemm_solve(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
-                                     int64_t n, double* T, int64_t ldt, float* X, cudaStream_t s) {
-    const int kp = gemm_kp(kcap);
+                                     int64_t n, double* T, int64_t ldt, float* scr, cudaStream_t s) {
+    const int kq = gemm_kp(kcap);
     const size_t inv_smem = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(float) + 16;
     auto kinv = k_r11_inverse<KQ>;
     cudaError_t e = cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(inv_smem));
     if (e != cudaSuccess) return e;
-    kinv<<<(kp + kWarpSolveWarps - 1) / kWarpSolveWarps, kWarpSolveWarps * 32, inv_smem, s>>>(R64, ldr, J, k_ptr, X);
+    kinv<<<(kq + kWarpSolveWarps - 1) / kWarpSolveWarps, kWarpSolveWarps * 32, inv_smem, s>>>(R64, ldr, J, k_ptr, scr,
+                                                                                                kq);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = (2 * static_cast<size_t>(kp) * kp + 2 * static_cast<size_t>(kp) * kGemmCols) * sizeof(float);
+    // the tiles' shared memory, or the FP64 fallback's copy of R11 if that is larger
+    const size_t tiles = (2 * static_cast<size_t>(kq) * kq + 2 * static_cast<size_t>(kq) * kGemmCols) * sizeof(float);
+    const size_t fb = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(double);
+    const size_t smem = std::max(tiles, fb) + 16;
     auto kern = k_solve_T_gemm<KQ>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int64_t cols = std::max<int64_t>(1, n - 1);
     const unsigned grid = static_cast<unsigned>((cols + kGemmCols - 1) / kGemmCols);
-    kern<<<grid, kGemmThreads, smem, s>>>(R64, ldr, J, k_ptr, n, X, T, ldt, 1, static_cast<int64_t>(smem));
+    kern<<<grid, kGemmThreads, smem, s>>>(R64, ldr, J, k_ptr, n, scr, kq, T, ldt, 1, static_cast<int64_t>(smem - 16));
     return cudaGetLastError();
 }
 
