@@ -570,18 +570,39 @@ k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restri
     }
     float* X = scr;
     float* R11p = scr + static_cast<int64_t>(kq_cap) * kq_cap;
-    if (blockIdx.x == 0) {
-        const bool ill = r11_ill_conditioned(R, ldr, J, k);     // CTA-wide (barriers inside)
-        if (threadIdx.x == 0) reinterpret_cast<int*>(R11p + static_cast<int64_t>(kq_cap) * kq_cap)[0] = ill ? 1 : 0;
-    }
     __syncthreads();
     if (blockIdx.x == 0) {
-        for (int a = warp; a < kp; a += kWarpSolveWarps)
-            for (int b = lane; b < kp; b += 32)
-                R11p[a * kp + b] = (a < k && b <= a) ? r11s[a * k + b] : 0.f;
+        // the test of r11_ill_conditioned on the staged diagonal (the same FP32 values)
+        __shared__ float s_mx[kWarpSolveWarps], s_mn[kWarpSolveWarps];
+        float mx = 0.f, mn = INFINITY;
+        for (int a = threadIdx.x; a < k; a += blockDim.x) {
+            const float d = fabsf(r11s[a * k + a]);
+            mx = fmaxf(mx, d);
+            mn = fminf(mn, d);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        }
+        if (lane == 0) {
+            s_mx[warp] = mx;
+            s_mn[warp] = mn;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 0; w < kWarpSolveWarps; ++w) {
+                mx = fmaxf(mx, s_mx[w]);
+                mn = fminf(mn, s_mn[w]);
+            }
+            const bool ill = static_cast<double>(mx) > kIllRatio * static_cast<double>(mn);
+            reinterpret_cast<int*>(R11p + static_cast<int64_t>(kq_cap) * kq_cap)[0] = ill ? 1 : 0;
+        }
     }
     const int j = blockIdx.x * kWarpSolveWarps + warp;
     if (j >= kp) return;
+    // the packed copy of R11 for the product kernel: each warp writes the column it inverts
+    for (int b = lane; b < kp; b += 32) R11p[j * kp + b] = (j < k && b <= j) ? r11s[j * k + b] : 0.f;
     float t[KQ];
 #pragma unroll
     for (int q = 0; q < KQ; ++q) t[q] = (lane + 32 * q == j) ? 1.f : 0.f;
