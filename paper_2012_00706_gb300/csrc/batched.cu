@@ -106,7 +106,8 @@ struct id_batch_plan {
     std::vector<int64_t> j_offsets, t_offsets;
     // workspace layout (bytes)
     size_t off_tasks = 0, off_maps = 0, off_sunits = 0, off_cq = 0, off_solve = 0, off_partial = 0, off_r = 0,
-           off_sel = 0;
+           off_sel = 0, off_inv = 0;
+    int kcap_max = 0;      // the largest rank cap of the batch (the product solve's inverses)
     BatchTotals tot;
     size_t work_bytes = 0;
     size_t table_bytes = 0;
@@ -241,7 +242,8 @@ bool build_plan(id_batch_plan* p) {
     p->tasks.assign(p->batch, BatchTask{});
     p->j_offsets.assign(p->batch + 1, 0);
     p->t_offsets.assign(p->batch + 1, 0);
-    int64_t partial = 0, rr = 0, sel = 0;
+    int64_t partial = 0, rr = 0, sel = 0, inv = 0;
+    p->kcap_max = 0;
     p->ell_max = 0;
     p->m_max = 0;
     for (int32_t i = 0; i < p->batch; ++i) {
@@ -262,6 +264,9 @@ bool build_plan(id_batch_plan* p) {
         rr += static_cast<int64_t>(t.kcap) * t.n;
         t.sel_off = sel;
         sel += (t.n + 15) / 16 * 16;
+        t.inv_off = inv;
+        inv += static_cast<int64_t>(batch_inverse_floats(t.kcap));
+        p->kcap_max = std::max(p->kcap_max, t.kcap);
         t.j_off = p->j_offsets[i];
         p->j_offsets[i + 1] = p->j_offsets[i] + t.n;
         t.tcols = p->opts.rel_tol > 0.0 ? t.n - 1 : t.n - t.kcap;
@@ -310,13 +315,16 @@ bool build_plan(id_batch_plan* p) {
     off = align256(off + static_cast<size_t>(rr) * sizeof(double));
     p->off_sel = off;
     off = align256(off + static_cast<size_t>(sel));
+    p->off_inv = off;
+    off = align256(off + static_cast<size_t>(inv) * sizeof(float));
     p->work_bytes = off;
     p->tot.ntasks = p->batch;
     p->tot.partial = static_cast<int64_t>((p->off_r - p->off_partial) / sizeof(float));
     p->tot.r = static_cast<int64_t>((p->off_sel - p->off_r) / sizeof(double));
     p->tot.j = p->j_offsets.back();
     p->tot.t = p->t_offsets.back();
-    p->tot.sel = static_cast<int64_t>(p->work_bytes - p->off_sel);
+    p->tot.sel = static_cast<int64_t>(p->off_inv - p->off_sel);
+    p->tot.inv = static_cast<int64_t>((p->work_bytes - p->off_inv) / sizeof(float));
 
     // host image of the table region
     p->tables.assign(p->table_bytes, 0);
@@ -338,7 +346,8 @@ bool build_plan_plain32(id_batch_plan* p) {
     p->tasks.assign(p->batch, BatchTask{});
     p->j_offsets.assign(p->batch + 1, 0);
     p->t_offsets.assign(p->batch + 1, 0);
-    int64_t rr = 0, sel = 0;
+    int64_t rr = 0, sel = 0, inv = 0;
+    p->kcap_max = 0;
     p->ell_max = 0;
     p->m_max = 0;
     for (int32_t i = 0; i < p->batch; ++i) {
@@ -351,6 +360,9 @@ bool build_plan_plain32(id_batch_plan* p) {
         rr += static_cast<int64_t>(t.kcap) * t.n;
         t.sel_off = sel;
         sel += (t.n + 15) / 16 * 16;
+        t.inv_off = inv;
+        inv += static_cast<int64_t>(batch_inverse_floats(t.kcap));
+        p->kcap_max = std::max(p->kcap_max, t.kcap);
         t.j_off = p->j_offsets[i];
         p->j_offsets[i + 1] = p->j_offsets[i] + t.n;
         t.tcols = p->opts.rel_tol > 0.0 ? t.n - 1 : t.n - t.kcap;
@@ -417,13 +429,16 @@ bool build_plan_plain32(id_batch_plan* p) {
     off = align256(off + static_cast<size_t>(rr) * sizeof(double));
     p->off_sel = off;
     off = align256(off + static_cast<size_t>(sel));
+    p->off_inv = off;
+    off = align256(off + static_cast<size_t>(inv) * sizeof(float));
     p->work_bytes = off;
     p->tot.ntasks = p->batch;
     p->tot.partial = 0;
     p->tot.r = static_cast<int64_t>((p->off_sel - p->off_r) / sizeof(double));
     p->tot.j = p->j_offsets.back();
     p->tot.t = p->t_offsets.back();
-    p->tot.sel = static_cast<int64_t>(p->work_bytes - p->off_sel);
+    p->tot.sel = static_cast<int64_t>(p->off_inv - p->off_sel);
+    p->tot.inv = static_cast<int64_t>((p->work_bytes - p->off_inv) / sizeof(float));
     p->tables.assign(p->table_bytes, 0);
     memcpy(p->tables.data() + p->off_tasks, p->tasks.data(), p->tasks.size() * sizeof(BatchTask));
     memcpy(p->tables.data() + p->off_solve, p->solve_units.data(), p->solve_units.size() * sizeof(SolveUnit));
@@ -633,6 +648,11 @@ id_status_t enqueue(const id_batch_plan* p, const void* omega, int64_t omega_ld,
         }
     }
     record_stage(3, s);
+    // one refinement step: the solve as products, every R11 inverted first
+    float* inv = reinterpret_cast<float*>(w + p->off_inv);
+    const bool product = p->opts.refine_steps == 1;
+    if (product && launch_r11_inverse_batched(d_tasks, p->batch, p->kcap_max, R, J, k_out, p->tot, inv, s) != cudaSuccess)
+        return ID_ERR_CUDA;
     // solve classes (by rank) run concurrently on the plan's streams as well
     const int nsc = static_cast<int>(p->solve_classes.size());
     const int naux2 = std::min(nsc, kMaxAuxStreams);
@@ -644,8 +664,10 @@ id_status_t enqueue(const id_batch_plan* p, const void* omega, int64_t omega_ld,
     for (int ci = 0; ci < nsc; ++ci) {
         const SolveClass& c = p->solve_classes[ci];
         cudaStream_t cs = naux2 > 1 ? p->aux[ci % naux2] : s;
-        e = launch_solve_T_batched(d_tasks, d_solve + c.first, c.count, c.kmax, p->tune.solve_warps, R, J, k_out,
-                                   info, T, p->tot, p->opts.refine_steps, cs);
+        e = product ? launch_solve_T_batched_product(d_tasks, d_solve + c.first, c.count, c.kmax, R, J, k_out, info, T,
+                                                     p->tot, p->opts.refine_steps, inv, cs)
+                    : launch_solve_T_batched(d_tasks, d_solve + c.first, c.count, c.kmax, p->tune.solve_warps, R, J,
+                                             k_out, info, T, p->tot, p->opts.refine_steps, cs);
         if (e != cudaSuccess) return ID_ERR_CUDA;
     }
     if (naux2 > 1) {
@@ -715,10 +737,18 @@ id_status_t enqueue_plain32(const id_batch_plan* p, int32_t* J, double* T, int32
             return ID_ERR_CUDA;
     }
     record_stage(3, s);
-    for (const SolveClass& c : p->solve_classes)
-        if (launch_solve_T_batched(d_tasks, d_solve + c.first, c.count, c.kmax, p->tune.solve_warps, R, J, k_out,
-                                   info, T, p->tot, p->opts.refine_steps, s) != cudaSuccess)
-            return ID_ERR_CUDA;
+    float* inv = reinterpret_cast<float*>(w + p->off_inv);
+    const bool product = p->opts.refine_steps == 1;
+    if (product && launch_r11_inverse_batched(d_tasks, p->batch, p->kcap_max, R, J, k_out, p->tot, inv, s) != cudaSuccess)
+        return ID_ERR_CUDA;
+    for (const SolveClass& c : p->solve_classes) {
+        const cudaError_t e =
+            product ? launch_solve_T_batched_product(d_tasks, d_solve + c.first, c.count, c.kmax, R, J, k_out, info, T,
+                                                     p->tot, p->opts.refine_steps, inv, s)
+                    : launch_solve_T_batched(d_tasks, d_solve + c.first, c.count, c.kmax, p->tune.solve_warps, R, J,
+                                             k_out, info, T, p->tot, p->opts.refine_steps, s);
+        if (e != cudaSuccess) return ID_ERR_CUDA;
+    }
     record_stage(4, s);
     record_stage(5, s);
     return ID_OK;

@@ -57,11 +57,12 @@ struct BatchTask {
     int64_t tcols;
     int64_t sel_off;       // bytes: selected-column flags (n)
     double rel_tol;
+    int64_t inv_off;       // floats: the product solve's R11 inverse, packed R11 and flag
 };
 // Element counts of the batch workspace regions and outputs (bounds the kernels check
 // every table entry against before using it).
 struct BatchTotals {
-    int64_t ntasks = 0, partial = 0, r = 0, j = 0, t = 0, sel = 0;
+    int64_t ntasks = 0, partial = 0, r = 0, j = 0, t = 0, sel = 0, inv = 0;
 };
 struct SolveUnit {
     int32_t task, c0, ncols, pad;   // columns [c0, c0 + ncols) of T
@@ -171,6 +172,17 @@ cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* unit
                                    int warps, const double* R_base, const int32_t* J_base,
                                    const int32_t* k_out, int32_t* infos, double* T_base,
                                    const BatchTotals& tot, int refine_steps, cudaStream_t s);
+// The batch's solve as products (one refinement step, ranks <= 128): the inverses of every
+// task's R11 (kmax bounds all ranks of the batch), then the listed units (kmax bounds theirs).
+// inv: the workspace's inverse region, batch_inverse_floats(kcap) floats per task.
+size_t batch_inverse_floats(int kcap);
+cudaError_t launch_r11_inverse_batched(const BatchTask* tasks, int ntasks, int kmax, const double* R_base,
+                                       const int32_t* J_base, const int32_t* k_out, const BatchTotals& tot, float* inv,
+                                       cudaStream_t s);
+cudaError_t launch_solve_T_batched_product(const BatchTask* tasks, const SolveUnit* units, int nunits, int kmax,
+                                           const double* R_base, const int32_t* J_base, const int32_t* k_out,
+                                           int32_t* infos, double* T_base, const BatchTotals& tot, int refine_steps,
+                                           const float* inv, cudaStream_t s);
 cudaError_t launch_reconstruct_one(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, const int32_t* J,
                                    int k, const double* T, int64_t ldt, void* Ahat, int64_t ldh, cudaStream_t s);
 cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,

@@ -378,6 +378,57 @@ static cudaError_t launch_warp_solve_kq(int kq, const double* R64, int64_t ldr, 
     }
 }
 
+// The warp-per-column solve of columns [c0, c_end) of T of one matrix of the batch (T with
+// leading dimension ldr): R11 staged in FP32, FP32 solves, `steps` refinement steps with the
+// float-pair residual.
+template <int KQ>
+__device__ __forceinline__ void batched_warp_columns(const double* __restrict__ R, int ldr,
+                                                     const int32_t* __restrict__ J, int k, int64_t c0, int64_t c_end,
+                                                     double* __restrict__ T, int steps, uint8_t* sm) {
+    float* r11s = reinterpret_cast<float*>(sm);                         // k x k, column-major
+    float* rinv = r11s + static_cast<int64_t>(k) * k;
+    stage_r11<float>(R, ldr, J, k, r11s, rinv);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t c = c0 + (threadIdx.x >> 5); c < c_end; c += blockDim.x >> 5) {
+        const double* r12 = R + static_cast<int64_t>(J[k + c]) * ldr;
+        double rhs[KQ];
+        float t[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            rhs[q] = b < k ? r12[b] : 0.0;
+            t[q] = static_cast<float>(rhs[q]);
+        }
+        warp_backsub<float, KQ>(t, SmemCols<float>{r11s, k}, rinv, k, lane);
+        double tt[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
+        for (int it = 0; it < steps; ++it) {
+            double res[KQ];
+            float th[KQ], tl[KQ];
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                th[q] = static_cast<float>(tt[q]);
+                tl[q] = static_cast<float>(tt[q] - static_cast<double>(th[q]));
+            }
+            residual_pairs<KQ>(rhs, th, tl, it > 0, r11s, k, lane, res);
+            float d[KQ];
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) d[q] = static_cast<float>(res[q]);
+            warp_backsub<float, KQ>(d, SmemCols<float>{r11s, k}, rinv, k, lane);
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) tt[q] += static_cast<double>(d[q]);
+        }
+        double* out = T + c * ldr;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int b = lane + 32 * q;
+            if (b < k) out[b] = tt[q];
+        }
+    }
+}
+
 // ---- batched solve: CTA b solves columns [c0, c0 + ncols) of T of task units[b].task,
 // with the warp-per-column scheme above (FP32 solves, FP64 refinement residual).
 constexpr int kBatchSolveMaxWarps = 16;
@@ -420,49 +471,7 @@ k_solve_T_batched(const BatchTask* __restrict__ tasks, const SolveUnit* __restri
     // an ill-conditioned R11 takes more refinement steps (each cuts the error by kappa u32)
     const int steps = (refine_steps > 0 && r11_ill_conditioned(R, ldr, J, k))
                           ? max(refine_steps, kIllRefineSteps) : refine_steps;
-    float* r11s = reinterpret_cast<float*>(sm);                         // k x k, column-major
-    float* rinv = r11s + static_cast<int64_t>(k) * k;
-    stage_r11<float>(R, ldr, J, k, r11s, rinv);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    double* T = T_base + bt.t_off;
-    for (int64_t c = su.c0 + (threadIdx.x >> 5); c < c_end; c += blockDim.x >> 5) {
-        const double* r12 = R + static_cast<int64_t>(J[k + c]) * ldr;
-        double rhs[KQ];
-        float t[KQ];
-#pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            const int b = lane + 32 * q;
-            rhs[q] = b < k ? r12[b] : 0.0;
-            t[q] = static_cast<float>(rhs[q]);
-        }
-        warp_backsub<float, KQ>(t, SmemCols<float>{r11s, k}, rinv, k, lane);
-        double tt[KQ];
-#pragma unroll
-        for (int q = 0; q < KQ; ++q) tt[q] = static_cast<double>(t[q]);
-        for (int it = 0; it < steps; ++it) {
-            double res[KQ];
-            float th[KQ], tl[KQ];
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                th[q] = static_cast<float>(tt[q]);
-                tl[q] = static_cast<float>(tt[q] - static_cast<double>(th[q]));
-            }
-            residual_pairs<KQ>(rhs, th, tl, it > 0, r11s, k, lane, res);
-            float d[KQ];
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) d[q] = static_cast<float>(res[q]);
-            warp_backsub<float, KQ>(d, SmemCols<float>{r11s, k}, rinv, k, lane);
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) tt[q] += static_cast<double>(d[q]);
-        }
-        double* out = T + c * ldr;
-#pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            const int b = lane + 32 * q;
-            if (b < k) out[b] = tt[q];
-        }
-    }
+    batched_warp_columns<KQ>(R, ldr, J, k, su.c0, c_end, T_base + bt.t_off, steps, sm);
 }
 
 template <int KQ>
@@ -529,20 +538,29 @@ __device__ __forceinline__ float f32_of_exact(double x) {
     return __double2float_rn(x);
 }
 
+// The inverse of R11 for columns j = jb * 8 + warp of X (this CTA's block jb): stage R11 once
+// (every load in flight), test its conditioning (block 0), and leave X(:, j) and the packed
+// R11(:, j) in the scratch (layout above).  R11(a, b) = R(a, J[b]).  Returns false (nothing
+// written) when a pivot index is out of range [0, n).
 template <int KQ>
-__global__ void __launch_bounds__(kWarpSolveWarps * 32)
-k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
-              const int32_t* __restrict__ k_ptr, float* __restrict__ scr, int kq_cap) {
-    extern __shared__ __align__(16) uint8_t sm[];
+__device__ __forceinline__ bool r11_inverse_body(const double* __restrict__ R, int64_t ldr,
+                                                 const int32_t* __restrict__ J, int64_t n, int k, int jb,
+                                                 float* __restrict__ scr, int kq_cap, uint8_t* sm) {
     __shared__ int js[32 * KQ];
-    const int k = *k_ptr;
+    __shared__ int s_bad;
     const int kp = gemm_kp(k);
-    if (k <= 0 || static_cast<int>(blockIdx.x) * kWarpSolveWarps >= kp) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* r11s = reinterpret_cast<float*>(sm);                 // k x k, column-major
     float* rinv = r11s + static_cast<int64_t>(k) * k;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) js[i] = __ldg(J + i);
+    if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int v = __ldg(J + i);
+        js[i] = v;
+        if (v < 0 || v >= n) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) return false;
     // R11 by rounds of 4 columns per warp, the 4 KQ loads of a lane issued together
     for (int a0 = warp; a0 < k; a0 += 4 * kWarpSolveWarps) {
         double v[4][KQ];
@@ -571,9 +589,9 @@ k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restri
     float* X = scr;
     float* R11p = scr + static_cast<int64_t>(kq_cap) * kq_cap;
     __syncthreads();
-    if (blockIdx.x == 0) {
+    if (jb == 0) {
         // the test of r11_ill_conditioned on the staged diagonal (the same FP32 values)
-        __shared__ float s_mx[kWarpSolveWarps], s_mn[kWarpSolveWarps];
+        __shared__ float s_mx[kGemmThreads / 32], s_mn[kGemmThreads / 32];
         float mx = 0.f, mn = INFINITY;
         for (int a = threadIdx.x; a < k; a += blockDim.x) {
             const float d = fabsf(r11s[a * k + a]);
@@ -591,7 +609,7 @@ k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restri
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int w = 0; w < kWarpSolveWarps; ++w) {
+            for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
                 mx = fmaxf(mx, s_mx[w]);
                 mn = fminf(mn, s_mn[w]);
             }
@@ -599,8 +617,8 @@ k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restri
             reinterpret_cast<int*>(R11p + static_cast<int64_t>(kq_cap) * kq_cap)[0] = ill ? 1 : 0;
         }
     }
-    const int j = blockIdx.x * kWarpSolveWarps + warp;
-    if (j >= kp) return;
+    const int j = jb * kWarpSolveWarps + warp;
+    if (j >= kp) return true;
     // the packed copy of R11 for the product kernel: each warp writes the column it inverts
     for (int b = lane; b < kp; b += 32) R11p[j * kp + b] = (j < k && b <= j) ? r11s[j * k + b] : 0.f;
     float t[KQ];
@@ -614,54 +632,39 @@ k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restri
         const int b = lane + 32 * q;
         if (b < kp) xc[b] = (j < k && b <= j) ? t[q] : 0.f;
     }
+    return true;
 }
 
 template <int KQ>
-__global__ void __launch_bounds__(kGemmThreads)
-k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
-               const int32_t* __restrict__ k_ptr, int64_t n, const float* __restrict__ scr, int kq_cap,
-               double* __restrict__ T, int64_t ldt, int refine_steps, int64_t smem_bytes) {
+__global__ void __launch_bounds__(kWarpSolveWarps * 32)
+k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+              const int32_t* __restrict__ k_ptr, int64_t n, float* __restrict__ scr, int kq_cap) {
     extern __shared__ __align__(16) uint8_t sm[];
-    __shared__ int jc[kGemmCols];
     const int k = *k_ptr;
-    if (k <= 0) return;
-    const float* Xg = scr;
-    const float* Rg = scr + static_cast<int64_t>(kq_cap) * kq_cap;
-    if (__ldg(reinterpret_cast<const int*>(Rg + static_cast<int64_t>(kq_cap) * kq_cap))) {
-        // every CTA takes part: the fallback's warps cover all columns of T by a grid stride
-        solve_fp64_fallback<KQ>(R, ldr, J, k, n, T, ldt, refine_steps, smem_bytes, sm);
-        return;
-    }
-    const int64_t nc = n - k;
-    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kGemmCols;
-    if (c0 >= nc) return;
-    const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), nc - c0));
-    const int kp = gemm_kp(k);
+    if (k <= 0 || static_cast<int>(blockIdx.x) * kWarpSolveWarps >= gemm_kp(k)) return;
+    r11_inverse_body<KQ>(R, ldr, J, n, k, blockIdx.x, scr, kq_cap, sm);
+}
+
+// Shared memory of the product tiles for a scratch capacity kq: X and R11 (kq x kq each), the
+// R12 / residual tile and the T0 tile (kq x kGemmCols each), in floats.
+__host__ __device__ inline size_t gemm_tile_floats(int kq) {
+    return 2 * static_cast<size_t>(kq) * kq + 2 * static_cast<size_t>(kq) * kGemmCols;
+}
+
+// Columns [c0, c0 + ncols) of T (ncols <= kGemmCols) from the staged X and R11 (kp x kp in
+// Xs, Rs): stage R12 (column c of the tile is R(:, jcol[c])), T0 = X R12, E = R12 - R11 T0
+// (exact products, float-pair sums), T = T0 + X E written as T[(c0 + c) ldt + row].  All
+// threads of the CTA (kGemmThreads) call it; it ends with a barrier.
+template <int KQ>
+__device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t ldr, const int* jcol, int k, int kp,
+                                          int ncols, const float* Xs, const float* Rs, float* Bt, float* Tt,
+                                          double* __restrict__ T, int64_t c0, int64_t ldt) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* Xs = reinterpret_cast<float*>(sm);        // kp x kp, column-major
-    float* Rs = Xs + kp * kp;                        // R11, kp x kp column-major
-    float* Bt = Rs + kp * kp;                        // [kp][kGemmCols]: R12, then the residual E
-    float* Tt = Bt + kp * kGemmCols;                 // [kp][kGemmCols]: T0
-    if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? __ldg(J + k + c0 + threadIdx.x) : 0;
-    {
-        const float4* xg4 = reinterpret_cast<const float4*>(Xg);
-        const float4* rg4 = reinterpret_cast<const float4*>(Rg);
-        float4* xs4 = reinterpret_cast<float4*>(Xs);
-        float4* rs4 = reinterpret_cast<float4*>(Rs);
-        const int n4 = kp * kp / 4;
-#pragma unroll 4
-        for (int i = threadIdx.x; i < n4; i += kGemmThreads) {
-            const float4 x = __ldg(xg4 + i), r = __ldg(rg4 + i);
-            xs4[i] = x;
-            rs4[i] = r;
-        }
-    }
-    __syncthreads();
     // R12 tile: warp w takes columns w and w + 8, its lanes the rows
 #pragma unroll
     for (int u = 0; u < kGemmCols / kWarpSolveWarps; ++u) {
         const int c = warp + u * kWarpSolveWarps;
-        const double* col = R + static_cast<int64_t>(jc[c]) * ldr;
+        const double* col = R + static_cast<int64_t>(jcol[c]) * ldr;
         double v[KQ];
 #pragma unroll
         for (int q = 0; q < KQ; ++q) {
@@ -736,28 +739,75 @@ k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
             *reinterpret_cast<float2*>(Bt + (r0 + i) * kGemmCols + cc) = make_float2(e[i][0], e[i][1]);
     }
     __syncthreads();
-    if (!live) return;
-    // T = T0 + X E
-    float d[4][2] = {};
-    for (int b = r0; b < kp; ++b) {
-        const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
-        const float2 ev = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
-        const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ea[2] = {ev.x, ev.y};
+    if (live) {
+        // T = T0 + X E
+        float d[4][2] = {};
+        for (int b = r0; b < kp; ++b) {
+            const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
+            const float2 ev = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
+            const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ea[2] = {ev.x, ev.y};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int jj = 0; jj < 2; ++jj) d[i][jj] = fmaf(xa[i], ea[jj], d[i][jj]);
-    }
+                for (int jj = 0; jj < 2; ++jj) d[i][jj] = fmaf(xa[i], ea[jj], d[i][jj]);
+        }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int row = r0 + i;
-        if (row >= k) continue;
+        for (int i = 0; i < 4; ++i) {
+            const int row = r0 + i;
+            if (row >= k) continue;
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int c = cc + jj;
-            if (c < ncols) T[(c0 + c) * ldt + row] = static_cast<double>(t0[i][jj]) + static_cast<double>(d[i][jj]);
+            for (int jj = 0; jj < 2; ++jj) {
+                const int c = cc + jj;
+                if (c < ncols)
+                    T[(c0 + c) * ldt + row] = static_cast<double>(t0[i][jj]) + static_cast<double>(d[i][jj]);
+            }
         }
     }
+    __syncthreads();    // the tiles are free for the next call
+}
+
+// X and R11 from the scratch into shared memory (kp x kp each, float4 copies).
+__device__ __forceinline__ void stage_x_r11(const float* __restrict__ scr, int kq_cap, int kp, float* Xs, float* Rs) {
+    const float4* xg4 = reinterpret_cast<const float4*>(scr);
+    const float4* rg4 = reinterpret_cast<const float4*>(scr + static_cast<int64_t>(kq_cap) * kq_cap);
+    float4* xs4 = reinterpret_cast<float4*>(Xs);
+    float4* rs4 = reinterpret_cast<float4*>(Rs);
+    const int n4 = kp * kp / 4;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        const float4 x = __ldg(xg4 + i), r = __ldg(rg4 + i);
+        xs4[i] = x;
+        rs4[i] = r;
+    }
+}
+
+template <int KQ>
+__global__ void __launch_bounds__(kGemmThreads)
+k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
+               const int32_t* __restrict__ k_ptr, int64_t n, const float* __restrict__ scr, int kq_cap,
+               double* __restrict__ T, int64_t ldt, int refine_steps, int64_t smem_bytes) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int jc[kGemmCols];
+    const int k = *k_ptr;
+    if (k <= 0) return;
+    if (__ldg(reinterpret_cast<const int*>(scr + 2 * static_cast<int64_t>(kq_cap) * kq_cap))) {
+        // every CTA takes part: the fallback's warps cover all columns of T by a grid stride
+        solve_fp64_fallback<KQ>(R, ldr, J, k, n, T, ldt, refine_steps, smem_bytes, sm);
+        return;
+    }
+    const int64_t nc = n - k;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kGemmCols;
+    if (c0 >= nc) return;
+    const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), nc - c0));
+    const int kp = gemm_kp(k);
+    float* Xs = reinterpret_cast<float*>(sm);        // kp x kp, column-major
+    float* Rs = Xs + kp * kp;                        // R11, kp x kp column-major
+    float* Bt = Rs + kp * kp;                        // [kp][kGemmCols]: R12, then the residual E
+    float* Tt = Bt + kp * kGemmCols;                 // [kp][kGemmCols]: T0
+    if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? __ldg(J + k + c0 + threadIdx.x) : 0;
+    stage_x_r11(scr, kq_cap, kp, Xs, Rs);
+    __syncthreads();
+    gemm_tile<KQ>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, c0, ldt);
 }
 
 template <int KQ>
@@ -768,12 +818,12 @@ static cudaError_t launch_gemm_solve(const double* R64, int64_t ldr, const int32
     auto kinv = k_r11_inverse<KQ>;
     cudaError_t e = cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(inv_smem));
     if (e != cudaSuccess) return e;
-    kinv<<<(kq + kWarpSolveWarps - 1) / kWarpSolveWarps, kWarpSolveWarps * 32, inv_smem, s>>>(R64, ldr, J, k_ptr, scr,
-                                                                                                kq);
+    kinv<<<(kq + kWarpSolveWarps - 1) / kWarpSolveWarps, kWarpSolveWarps * 32, inv_smem, s>>>(R64, ldr, J, k_ptr, n,
+                                                                                                scr, kq);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the tiles' shared memory, or the FP64 fallback's copy of R11 if that is larger
-    const size_t tiles = (2 * static_cast<size_t>(kq) * kq + 2 * static_cast<size_t>(kq) * kGemmCols) * sizeof(float);
+    const size_t tiles = gemm_tile_floats(kq) * sizeof(float);
     const size_t fb = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(double);
     const size_t smem = std::max(tiles, fb) + 16;
     auto kern = k_solve_T_gemm<KQ>;
@@ -784,6 +834,158 @@ static cudaError_t launch_gemm_solve(const double* R64, int64_t ldr, const int32
     kern<<<grid, kGemmThreads, smem, s>>>(R64, ldr, J, k_ptr, n, scr, kq, T, ldt, 1, static_cast<int64_t>(smem - 16));
     return cudaGetLastError();
 }
+
+// ---- the batch's solve as products: k_r11_inverse_batched forms every matrix's X, packed
+// R11 and flag in its slice of the inverse region (BatchTask::inv_off, the layout above with
+// kq = kcap rounded up to 4), CTA (matrix, 8-column block of X); k_solve_T_batched_gemm then
+// runs the unit's columns by tiles of kGemmCols, or the warp-per-column solve with extra
+// refinement steps for an ill-conditioned R11.
+__host__ __device__ inline int64_t batch_inv_floats(int kcap) {
+    const int64_t kq = gemm_kp(kcap);
+    return 2 * kq * kq + 4;
+}
+
+// A table entry whose regions all lie inside the workspace and the outputs.
+__device__ __forceinline__ bool batch_entry_ok(const BatchTask& bt, int k, int kmax, const BatchTotals& tot) {
+    return k <= bt.kcap && k <= kmax && bt.r_off >= 0 && bt.r_off + static_cast<int64_t>(bt.kcap) * bt.n <= tot.r &&
+           bt.j_off >= 0 && bt.j_off + bt.n <= tot.j && bt.t_off >= 0 &&
+           bt.t_off + static_cast<int64_t>(bt.kcap) * bt.tcols <= tot.t && bt.inv_off >= 0 &&
+           bt.inv_off + batch_inv_floats(bt.kcap) <= tot.inv;
+}
+
+template <int KQ>
+__global__ void __launch_bounds__(kWarpSolveWarps * 32)
+k_r11_inverse_batched(const BatchTask* __restrict__ tasks, const double* __restrict__ R_base,
+                      const int32_t* __restrict__ J_base, const int32_t* __restrict__ k_out, BatchTotals tot,
+                      float* __restrict__ inv_base) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int task = blockIdx.x;
+    if (task >= tot.ntasks) return;
+    const BatchTask& bt = tasks[task];
+    const int k = k_out[task];
+    if (k <= 0 || static_cast<int>(blockIdx.y) * kWarpSolveWarps >= gemm_kp(k)) return;
+    if (!batch_entry_ok(bt, k, 32 * KQ, tot)) return;     // the product kernel reports it
+    r11_inverse_body<KQ>(R_base + bt.r_off, bt.kcap, J_base + bt.j_off, bt.n, k, blockIdx.y,
+                         inv_base + bt.inv_off, gemm_kp(bt.kcap), sm);
+}
+
+template <int KQ>
+__global__ void __launch_bounds__(kGemmThreads)
+k_solve_T_batched_gemm(const BatchTask* __restrict__ tasks, const SolveUnit* __restrict__ units,
+                       const double* __restrict__ R_base, const int32_t* __restrict__ J_base,
+                       const int32_t* __restrict__ k_out, int32_t* infos, double* __restrict__ T_base,
+                       BatchTotals tot, int kmax, int refine_steps, const float* __restrict__ inv_base) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int s_bad;
+    __shared__ int jc[kGemmCols];
+    const SolveUnit su = units[blockIdx.x];
+    if (su.task < 0 || su.task >= tot.ntasks) return;
+    const BatchTask& bt = tasks[su.task];
+    const int k = k_out[su.task];
+    const int64_t c_end = min(min(static_cast<int64_t>(su.c0) + su.ncols, bt.n - k), bt.tcols);
+    if (k <= 0 || su.c0 < 0 || su.c0 >= c_end) return;
+    const double* R = R_base + bt.r_off;
+    const int32_t* J = J_base + bt.j_off;
+    const int ldr = bt.kcap;
+    // every index below stays inside this task's regions: check the entry and the pivot list
+    if (threadIdx.x == 0) s_bad = !batch_entry_ok(bt, k, kmax, tot);
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0) set_info(infos + su.task, kInfoBadTable);
+        return;
+    }
+    for (int64_t a = threadIdx.x; a < bt.n; a += blockDim.x)
+        if (J[a] < 0 || J[a] >= bt.n) s_bad = 1;
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0) set_info(infos + su.task, kInfoBadTable);
+        return;
+    }
+    const float* scr = inv_base + bt.inv_off;
+    const int kq = gemm_kp(bt.kcap);
+    double* T = T_base + bt.t_off;
+    if (__ldg(reinterpret_cast<const int*>(scr + 2 * static_cast<int64_t>(kq) * kq))) {
+        // an ill-conditioned R11 takes more refinement steps (each cuts the error by kappa u32)
+        batched_warp_columns<KQ>(R, ldr, J, k, su.c0, c_end, T, max(refine_steps, kIllRefineSteps), sm);
+        return;
+    }
+    const int kp = gemm_kp(k);
+    float* Xs = reinterpret_cast<float*>(sm);
+    float* Rs = Xs + kp * kp;
+    float* Bt = Rs + kp * kp;
+    float* Tt = Bt + kp * kGemmCols;
+    stage_x_r11(scr, kq, kp, Xs, Rs);
+    for (int64_t t0 = su.c0; t0 < c_end; t0 += kGemmCols) {
+        const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), c_end - t0));
+        if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? J[k + t0 + threadIdx.x] : 0;
+        __syncthreads();
+        gemm_tile<KQ>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, t0, ldr);
+    }
+}
+
+template <int KQ>
+static cudaError_t launch_batched_product(const BatchTask* tasks, int ntasks, const SolveUnit* units, int nunits,
+                                          int kmax, const double* R_base, const int32_t* J_base, const int32_t* k_out,
+                                          int32_t* infos, double* T_base, const BatchTotals& tot, int refine_steps,
+                                          float* inv, bool with_inverse, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (with_inverse) {
+        const size_t inv_smem = (static_cast<size_t>(32 * KQ) * 32 * KQ + 32 * KQ) * sizeof(float) + 16;
+        auto kinv = k_r11_inverse_batched<KQ>;
+        e = cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(inv_smem));
+        if (e != cudaSuccess) return e;
+        const dim3 grid(static_cast<unsigned>(ntasks), static_cast<unsigned>((gemm_kp(kmax) + kWarpSolveWarps - 1) /
+                                                                             kWarpSolveWarps));
+        kinv<<<grid, kWarpSolveWarps * 32, inv_smem, s>>>(tasks, R_base, J_base, k_out, tot, inv);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || nunits <= 0) return e;
+    }
+    const size_t smem = gemm_tile_floats(gemm_kp(kmax)) * sizeof(float) + 16;
+    auto kern = k_solve_T_batched_gemm<KQ>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<nunits, kGemmThreads, smem, s>>>(tasks, units, R_base, J_base, k_out, infos, T_base, tot, kmax,
+                                            refine_steps, inv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_r11_inverse_batched(const BatchTask* tasks, int ntasks, int kmax, const double* R_base,
+                                       const int32_t* J_base, const int32_t* k_out, const BatchTotals& tot, float* inv,
+                                       cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (kmax < 1 || kmax > kGemmMaxK) return cudaErrorInvalidValue;
+    switch ((kmax + 31) / 32) {
+        case 1: return launch_batched_product<1>(tasks, ntasks, nullptr, 0, kmax, R_base, J_base, k_out, nullptr,
+                                                 nullptr, tot, 1, inv, true, s);
+        case 2: return launch_batched_product<2>(tasks, ntasks, nullptr, 0, kmax, R_base, J_base, k_out, nullptr,
+                                                 nullptr, tot, 1, inv, true, s);
+        case 3: return launch_batched_product<3>(tasks, ntasks, nullptr, 0, kmax, R_base, J_base, k_out, nullptr,
+                                                 nullptr, tot, 1, inv, true, s);
+        default: return launch_batched_product<4>(tasks, ntasks, nullptr, 0, kmax, R_base, J_base, k_out, nullptr,
+                                                  nullptr, tot, 1, inv, true, s);
+    }
+}
+
+cudaError_t launch_solve_T_batched_product(const BatchTask* tasks, const SolveUnit* units, int nunits, int kmax,
+                                           const double* R_base, const int32_t* J_base, const int32_t* k_out,
+                                           int32_t* infos, double* T_base, const BatchTotals& tot, int refine_steps,
+                                           const float* inv, cudaStream_t s) {
+    if (nunits <= 0) return cudaSuccess;
+    if (kmax < 1 || kmax > kGemmMaxK) return cudaErrorInvalidValue;
+    float* iv = const_cast<float*>(inv);
+    switch ((kmax + 31) / 32) {
+        case 1: return launch_batched_product<1>(tasks, 0, units, nunits, kmax, R_base, J_base, k_out, infos, T_base,
+                                                 tot, refine_steps, iv, false, s);
+        case 2: return launch_batched_product<2>(tasks, 0, units, nunits, kmax, R_base, J_base, k_out, infos, T_base,
+                                                 tot, refine_steps, iv, false, s);
+        case 3: return launch_batched_product<3>(tasks, 0, units, nunits, kmax, R_base, J_base, k_out, infos, T_base,
+                                                 tot, refine_steps, iv, false, s);
+        default: return launch_batched_product<4>(tasks, 0, units, nunits, kmax, R_base, J_base, k_out, infos, T_base,
+                                                  tot, refine_steps, iv, false, s);
+    }
+}
+
+size_t batch_inverse_floats(int kcap) { return static_cast<size_t>(batch_inv_floats(kcap)); }
 
 cudaError_t launch_solve_T(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
                            int64_t n, double* T, int64_t ldt, double* scratch, int refine_steps, int low_solve,

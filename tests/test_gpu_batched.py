@@ -321,3 +321,30 @@ def test_batched_plain_f32(gid, dev, orc, dtype):
         one = gid.id_factor(bufs[i][1], r, precision="plain_f32")
         assert np.array_equal(one.J.cpu().numpy(), J), i
         assert np.max(np.abs(one.T.cpu().numpy() - T), initial=0.0) <= 1e-4 * scale, i
+
+
+def test_batched_solve_ill_conditioned_r11(gid, dev, orc):
+    """The batch's solve takes the products for well-conditioned R11 and the warp solve with
+    six refinement steps where the largest diagonal of R11 exceeds 2^24 / 100 times the
+    smallest: a PLAIN_F32 batch holding a matrix whose Householder QR is exact in FP32 (so
+    the GPU's R equals the oracle's) with diagonal ratio 2^19 between two separated ones.
+    Every T equals the oracle's; the ill-conditioned one to 1e-6 of its largest entry."""
+    w, perm = wl.exact_triangular_id_matrix(k=20, n=150, rows=40)
+    mats = [wl.separated_matrix(300, 80, seed=91, decay=0.9).astype(np.float32), w,
+            wl.separated_matrix(500, 120, seed=92, decay=0.9).astype(np.float32)]
+    ranks = [10, 20, 15]
+    plan = gid.BatchPlan([a.shape for a in mats], ranks, dtype=torch.float32, precision="plain_f32")
+    bufs = [to_dev(a, dev, dtype=np.float32) for a in mats]
+    plan.bind([v for _, v in bufs])
+    plan.run()
+    torch.cuda.synchronize()
+    for i, (a, r, res) in enumerate(zip(mats, ranks, plan.results())):
+        a64 = a.astype(np.float64)
+        ref = orc.interp_decomp(a64, k=r)
+        assert res.info == 0 and res.k == r, (i, res.info, res.k)
+        assert np.array_equal(res.J.cpu().numpy(), ref["J"]), i
+        tol = 1e-6 if i == 1 else 1e-4
+        T = res.T.cpu().numpy()
+        assert np.max(np.abs(T - ref["T"])) <= tol * max(1.0, np.max(np.abs(ref["T"]))), (i, np.max(np.abs(T - ref["T"])))
+    d = np.abs(np.diag(w.astype(np.float64)[:20, perm[:20]]))
+    assert d.max() / d.min() > 2.0 ** 24 / 100
