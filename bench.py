@@ -295,7 +295,8 @@ def batched_leg(gid, wl, dev, stream, count=512, loops=True, lean_steps=0, world
         gid.set_stage_events(None)
         torch.cuda.synchronize()
         stages = {"sketch": evs[0].elapsed_time(evs[1]), "cpqr": evs[2].elapsed_time(evs[3]),
-                  "solve_T": evs[3].elapsed_time(evs[4])}
+                  "solve_T": evs[3].elapsed_time(evs[5]), "solve_inverses": evs[3].elapsed_time(evs[4]),
+                  "solve_products": evs[4].elapsed_time(evs[5])}
         info = plan.info.cpu()
         with tempfile.TemporaryDirectory() as td:
             best = plan.autotune(omega, reps=3, cache_path=os.path.join(td, "tune.jsonl"))

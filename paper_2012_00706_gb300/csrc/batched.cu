@@ -653,6 +653,7 @@ id_status_t enqueue(const id_batch_plan* p, const void* omega, int64_t omega_ld,
     const bool product = p->opts.refine_steps == 1;
     if (product && launch_r11_inverse_batched(d_tasks, p->batch, p->kcap_max, R, J, k_out, p->tot, inv, s) != cudaSuccess)
         return ID_ERR_CUDA;
+    record_stage(4, s);     // the inverses (nothing on the warp solve's path)
     // solve classes (by rank) run concurrently on the plan's streams as well
     const int nsc = static_cast<int>(p->solve_classes.size());
     const int naux2 = std::min(nsc, kMaxAuxStreams);
@@ -676,7 +677,6 @@ id_status_t enqueue(const id_batch_plan* p, const void* omega, int64_t omega_ld,
             if (cudaStreamWaitEvent(s, p->join[i], 0) != cudaSuccess) return ID_ERR_CUDA;
         }
     }
-    record_stage(4, s);
     record_stage(5, s);
     return ID_OK;
 }
@@ -741,6 +741,7 @@ id_status_t enqueue_plain32(const id_batch_plan* p, int32_t* J, double* T, int32
     const bool product = p->opts.refine_steps == 1;
     if (product && launch_r11_inverse_batched(d_tasks, p->batch, p->kcap_max, R, J, k_out, p->tot, inv, s) != cudaSuccess)
         return ID_ERR_CUDA;
+    record_stage(4, s);     // the inverses (nothing on the warp solve's path)
     for (const SolveClass& c : p->solve_classes) {
         const cudaError_t e =
             product ? launch_solve_T_batched_product(d_tasks, d_solve + c.first, c.count, c.kmax, R, J, k_out, info, T,
@@ -749,7 +750,6 @@ id_status_t enqueue_plain32(const id_batch_plan* p, int32_t* J, double* T, int32
                                              k_out, info, T, p->tot, p->opts.refine_steps, s);
         if (e != cudaSuccess) return ID_ERR_CUDA;
     }
-    record_stage(4, s);
     record_stage(5, s);
     return ID_OK;
 }
