@@ -676,12 +676,26 @@ def config5_leg(gid, wl, dev, peaks, reps=5):
 
 
 def profile_case(gid, wl, dev, which):
-    """One launch of each pivoted-QR kernel, in this order: the cluster kernel (config 2's
+    """`bwd`: one forward and one backward of the differentiable ID on config 5's 64 FP32
+    2048 x 512 matrices (k = 32, loss ||A_hat - B||_F^2).
+
+    `cpqr`: one launch of each pivoted-QR kernel, in this order: the cluster kernel (config 2's
     BF16x3 ID: its sketch 110 x 2000), the resident grid kernel (config 1 plain FP64,
     1000 x 500, k = 50), the streaming grid kernel (plain FP64 16384 x 1000, k = 50,
     sigma_i = i^-2: a 131 MB working copy) and the grouped kernel (one wave of 16 FP32
     2048 x 512 matrices of config 5, k = 32)."""
     import torch
+    if which == "bwd":
+        c = wl.config5()
+        A = torch.from_numpy(np.ascontiguousarray(c["A"].transpose(0, 2, 1))).to(dev).transpose(1, 2)
+        B = torch.from_numpy(c["B"]).to(dev)
+        A.requires_grad_(True)
+        Ahat, T, J = gid.IDFunction.apply(A, c["k"])
+        ((Ahat - B) ** 2).sum().backward()
+        torch.cuda.synchronize()
+        ok = bool(torch.isfinite(A.grad).all())
+        print(json.dumps({"profile_case": which, "grad_finite": ok}), flush=True)
+        return 0 if ok else 1
     cfg = wl.config2()
     A = torch.from_numpy(cfg["A"]).to(dev)
     om = torch.from_numpy(cfg["omega_bits"].view(np.int16)).to(dev).view(torch.bfloat16)
@@ -779,8 +793,9 @@ def main():
     ap.add_argument("--inflight", type=int, default=INFLIGHT, help="IDs in flight in the timed stream")
     ap.add_argument("--figures", action="store_true",
                     help="print the k and n sweeps of the paper's Figs. 1-6 as one JSON object and exit")
-    ap.add_argument("--profile-case", choices=["cpqr"],
-                    help="run one launch of each pivoted-QR kernel (a profiling case) and exit")
+    ap.add_argument("--profile-case", choices=["cpqr", "bwd"],
+                    help="profiling cases: cpqr runs one launch of each pivoted-QR kernel; bwd one forward and "
+                         "backward of the 64 x 2048 x 512 differentiable ID")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

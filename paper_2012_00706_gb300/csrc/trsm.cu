@@ -684,6 +684,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
     float t0[4][2] = {};
     if (live) {
         // T0 = X R12: X(r, b) = 0 for b < r
+#pragma unroll 4
         for (int b = r0; b < kp; ++b) {
             const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
             const float2 bv = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
@@ -709,6 +710,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
             hi[i][1] = bv.y;
             lo[i][0] = lo[i][1] = 0.f;
         }
+#pragma unroll 2
         for (int b = r0; b < kp; ++b) {
             const float4 rv = *reinterpret_cast<const float4*>(Rs + b * kp + r0);
             const float2 tv = *reinterpret_cast<const float2*>(Tt + b * kGemmCols + cc);
@@ -742,6 +744,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
     if (live) {
         // T = T0 + X E
         float d[4][2] = {};
+#pragma unroll 4
         for (int b = r0; b < kp; ++b) {
             const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
             const float2 ev = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
@@ -773,7 +776,7 @@ __device__ __forceinline__ void stage_x_r11(const float* __restrict__ scr, int k
     float4* xs4 = reinterpret_cast<float4*>(Xs);
     float4* rs4 = reinterpret_cast<float4*>(Rs);
     const int n4 = kp * kp / 4;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = threadIdx.x; i < n4; i += blockDim.x) {
         const float4 x = __ldg(xg4 + i), r = __ldg(rg4 + i);
         xs4[i] = x;
