@@ -49,55 +49,106 @@ struct GemmArgs {
     float alpha, beta;
 };
 
-__device__ __forceinline__ float gop_at(const GOp& o, int64_t b, int64_t i, int64_t j) {
-    const int64_t c = o.map ? static_cast<int64_t>(o.map[b * o.mstride + o.moff + j]) : j;
-    return o.base[b * o.bstride + i * o.rs + c * o.cs];
-}
+// Register-tiled FP32 gather GEMM, D (M x N) = alpha A (M x K) B (K x N) + beta D, batched over
+// blockIdx.z.  The tile is TM x TN with 256 threads (16 x 16, MR x NR outputs each) and TK-deep
+// chunks; the next chunk is fetched into registers while the current one is multiplied, and
+// the gathered indices (A's K-index map, B's and D's N-index maps) are read once per tile into
+// shared memory.  Consecutive threads walk the unit-stride dimension of each operand.
+constexpr int kGK = 32;
 
-constexpr int kGT = 64, kGK = 16;
-
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) k_gemm_gather(const GemmArgs g) {
-    __shared__ float As[kGK][kGT + 4];
-    __shared__ float Bs[kGK][kGT + 4];
+    constexpr int MR = TM / 16, NR = TN / 16;
+    constexpr int LA = TM * kGK / 256, LB = TN * kGK / 256;   // elements per thread per chunk
+    __shared__ __align__(16) float As[kGK][TM + 4];
+    __shared__ __align__(16) float Bs[kGK][TN + 4];
+    __shared__ int64_t amap[kGK];         // A column offsets (col(k) * cs) of the current chunk
+    __shared__ int64_t bmap[TN], dmap[TN];
     const int64_t b = blockIdx.z;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t i0 = static_cast<int64_t>(blockIdx.y) * kGT, j0 = static_cast<int64_t>(blockIdx.x) * kGT;
-    float acc[4][4] = {};
-    for (int64_t k0 = 0; k0 < g.K; k0 += kGK) {
-        for (int idx = threadIdx.x; idx < kGK * kGT; idx += 256) {
-            // consecutive threads walk the dimension with unit stride where the operand has one
-            int kk, ii;
-            if (g.a.rs == 1) { ii = idx % kGT; kk = idx / kGT; } else { kk = idx % kGK; ii = idx / kGK; }
-            const int64_t gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < g.M && gk < g.K) ? gop_at(g.a, b, gi, gk) : 0.f;
-            int jj, kb;
-            if (g.b.rs == 1) { kb = idx % kGK; jj = idx / kGK; } else { jj = idx % kGT; kb = idx / kGT; }
-            const int64_t gj = j0 + jj, gk2 = k0 + kb;
-            Bs[kb][jj] = (gj < g.N && gk2 < g.K) ? gop_at(g.b, b, gk2, gj) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGK; ++kk) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { av[q] = As[kk][ty * 4 + q]; bv[q] = Bs[kk][tx * 4 + q]; }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
-        }
-        __syncthreads();
+    const int64_t i0 = static_cast<int64_t>(blockIdx.y) * TM, j0 = static_cast<int64_t>(blockIdx.x) * TN;
+    const float* abase = g.a.base + b * g.a.bstride;
+    const float* bbase = g.b.base + b * g.b.bstride;
+    for (int t = threadIdx.x; t < TN; t += 256) {
+        const int64_t j = min(j0 + t, g.N - 1);
+        bmap[t] = (g.b.map ? static_cast<int64_t>(g.b.map[b * g.b.mstride + g.b.moff + j]) : j) * g.b.cs;
+        dmap[t] = (g.d.map ? static_cast<int64_t>(g.d.map[b * g.d.mstride + g.d.moff + j]) : j) * g.d.cs;
     }
+    // element e of this thread's share of a chunk: (row, k) of A and (k, column) of B
+    auto a_rc = [&](int e, int& ii, int& kk) {
+        const int idx = threadIdx.x + 256 * e;
+        if (g.a.rs == 1) { ii = idx % TM; kk = idx / TM; } else { kk = idx % kGK; ii = idx / kGK; }
+    };
+    auto b_rc = [&](int e, int& kk, int& jj) {
+        const int idx = threadIdx.x + 256 * e;
+        if (g.b.rs == 1) { kk = idx % kGK; jj = idx / kGK; } else { jj = idx % TN; kk = idx / TN; }
+    };
+    float ra[LA], rb[LB];
+    auto fetch = [&](int64_t k0) {
+        // amap for this chunk: written by the first kGK threads, read after a barrier
+        __syncthreads();
+        if (threadIdx.x < kGK) {
+            const int64_t kg = min(k0 + threadIdx.x, g.K - 1);
+            amap[threadIdx.x] =
+                (g.a.map ? static_cast<int64_t>(g.a.map[b * g.a.mstride + g.a.moff + kg]) : kg) * g.a.cs;
+        }
+        __syncthreads();
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int64_t gi = i0 + ty * 4 + p;
+        for (int e = 0; e < LA; ++e) {
+            int ii, kk;
+            a_rc(e, ii, kk);
+            const int64_t gi = i0 + ii, gk = k0 + kk;
+            ra[e] = (gi < g.M && gk < g.K) ? abase[gi * g.a.rs + amap[kk]] : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < LB; ++e) {
+            int kk, jj;
+            b_rc(e, kk, jj);
+            const int64_t gj = j0 + jj, gk = k0 + kk;
+            rb[e] = (gj < g.N && gk < g.K) ? bbase[gk * g.b.rs + bmap[jj]] : 0.f;
+        }
+    };
+    float acc[MR][NR] = {};
+    fetch(0);
+    for (int64_t k0 = 0; k0 < g.K; k0 += kGK) {
+        __syncthreads();     // the previous chunk's reads of As / Bs are done
+#pragma unroll
+        for (int e = 0; e < LA; ++e) {
+            int ii, kk;
+            a_rc(e, ii, kk);
+            As[kk][ii] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < LB; ++e) {
+            int kk, jj;
+            b_rc(e, kk, jj);
+            Bs[kk][jj] = rb[e];
+        }
+        if (k0 + kGK < g.K) fetch(k0 + kGK);   // in flight during the products below
+        else __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kGK; ++kk) {
+            float av[MR], bv[NR];
+#pragma unroll
+            for (int p = 0; p < MR; ++p) av[p] = As[kk][ty * MR + p];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) bv[q] = Bs[kk][tx * NR + q];
+#pragma unroll
+            for (int p = 0; p < MR; ++p)
+#pragma unroll
+                for (int q = 0; q < NR; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+        }
+    }
+    float* dbase = g.d.base + b * g.d.bstride;
+#pragma unroll
+    for (int p = 0; p < MR; ++p) {
+        const int64_t gi = i0 + ty * MR + p;
         if (gi >= g.M) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t gj = j0 + tx * 4 + q;
-            if (gj >= g.N) continue;
-            const int64_t c = g.d.map ? static_cast<int64_t>(g.d.map[b * g.d.mstride + g.d.moff + gj]) : gj;
-            float* dst = g.d.base + b * g.d.bstride + gi * g.d.rs + c * g.d.cs;
+        for (int q = 0; q < NR; ++q) {
+            const int jj = tx * NR + q;
+            if (j0 + jj >= g.N) continue;
+            float* dst = dbase + gi * g.d.rs + dmap[jj];
             *dst = g.beta == 0.f ? g.alpha * acc[p][q] : fmaf(g.alpha, acc[p][q], g.beta * *dst);
         }
     }
@@ -105,9 +156,18 @@ __global__ void __launch_bounds__(256) k_gemm_gather(const GemmArgs g) {
 
 static cudaError_t gemm(const GemmArgs& g, int64_t batch, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-    dim3 grid(static_cast<unsigned>((g.N + kGT - 1) / kGT), static_cast<unsigned>((g.M + kGT - 1) / kGT),
-              static_cast<unsigned>(batch));
-    k_gemm_gather<<<grid, 256, 0, s>>>(g);
+    const unsigned z = static_cast<unsigned>(batch);
+    // tile shapes for the ranks of the adjoint's products (one side often k <= 32)
+    if (g.M <= 32) {
+        dim3 grid(static_cast<unsigned>((g.N + 127) / 128), static_cast<unsigned>((g.M + 31) / 32), z);
+        k_gemm_gather<32, 128><<<grid, 256, 0, s>>>(g);
+    } else if (g.N <= 32) {
+        dim3 grid(static_cast<unsigned>((g.N + 31) / 32), static_cast<unsigned>((g.M + 127) / 128), z);
+        k_gemm_gather<128, 32><<<grid, 256, 0, s>>>(g);
+    } else {
+        dim3 grid(static_cast<unsigned>((g.N + 63) / 64), static_cast<unsigned>((g.M + 63) / 64), z);
+        k_gemm_gather<64, 64><<<grid, 256, 0, s>>>(g);
+    }
     return cudaGetLastError();
 }
 

@@ -521,7 +521,8 @@ cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* unit
 // Scratch (floats, kq = kcap rounded up to 4): X [kq x kq], R11 [kq x kq], flag; both
 // matrices are column-major with the device rank's kp = k rounded up to 4 as leading
 // dimension, zero below the diagonal and past k.
-constexpr int kGemmCols = 16;
+constexpr int kGemmCols = 16;          // tile width of the single ID (256 threads)
+constexpr int kGemmColsBatch = 32;     // tile width of the batch's units (512 threads)
 constexpr int kGemmThreads = 256;
 constexpr int kGemmMaxK = 128;
 
@@ -591,7 +592,7 @@ __device__ __forceinline__ bool r11_inverse_body(const double* __restrict__ R, i
     __syncthreads();
     if (jb == 0) {
         // the test of r11_ill_conditioned on the staged diagonal (the same FP32 values)
-        __shared__ float s_mx[kGemmThreads / 32], s_mn[kGemmThreads / 32];
+        __shared__ float s_mx[kWarpSolveWarps], s_mn[kWarpSolveWarps];
         float mx = 0.f, mn = INFINITY;
         for (int a = threadIdx.x; a < k; a += blockDim.x) {
             const float d = fabsf(r11s[a * k + a]);
@@ -645,25 +646,28 @@ k_r11_inverse(const double* __restrict__ R, int64_t ldr, const int32_t* __restri
     r11_inverse_body<KQ>(R, ldr, J, n, k, blockIdx.x, scr, kq_cap, sm);
 }
 
-// Shared memory of the product tiles for a scratch capacity kq: X and R11 (kq x kq each), the
-// R12 / residual tile and the T0 tile (kq x kGemmCols each), in floats.
-__host__ __device__ inline size_t gemm_tile_floats(int kq) {
-    return 2 * static_cast<size_t>(kq) * kq + 2 * static_cast<size_t>(kq) * kGemmCols;
+// Shared memory of the product tiles for a scratch capacity kq and tiles of `cols` columns: X
+// and R11 (kq x kq each), the R12 / residual tile and the T0 tile (kq rows of cols + 2 floats:
+// the padding spreads the column-wise stores of the R12 staging over the banks), in floats.
+__host__ __device__ inline int gemm_ld(int cols) { return cols + 2; }
+__host__ __device__ inline size_t gemm_tile_floats(int kq, int cols) {
+    return 2 * static_cast<size_t>(kq) * kq + 2 * static_cast<size_t>(kq) * gemm_ld(cols);
 }
 
-// Columns [c0, c0 + ncols) of T (ncols <= kGemmCols) from the staged X and R11 (kp x kp in
-// Xs, Rs): stage R12 (column c of the tile is R(:, jcol[c])), T0 = X R12, E = R12 - R11 T0
-// (exact products, float-pair sums), T = T0 + X E written as T[(c0 + c) ldt + row].  All
-// threads of the CTA (kGemmThreads) call it; it ends with a barrier.
-template <int KQ>
+// Columns [c0, c0 + ncols) of T (ncols <= COLS) from the staged X and R11 (kp x kp in Xs,
+// Rs): stage R12 (column c of the tile is R(:, jcol[c])), T0 = X R12, E = R12 - R11 T0 (exact
+// products, float-pair sums), T = T0 + X E written as T[(c0 + c) ldt + row].  All 16 COLS
+// threads of the CTA call it (32 row groups x COLS / 2 column pairs); it ends with a barrier.
+template <int KQ, int COLS>
 __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t ldr, const int* jcol, int k, int kp,
                                           int ncols, const float* Xs, const float* Rs, float* Bt, float* Tt,
                                           double* __restrict__ T, int64_t c0, int64_t ldt) {
+    constexpr int LD = COLS + 2, NCG = COLS / 2, NW = COLS / 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // R12 tile: warp w takes columns w and w + 8, its lanes the rows
+    // R12 tile: warp w takes columns w and w + NW, its lanes the rows
 #pragma unroll
-    for (int u = 0; u < kGemmCols / kWarpSolveWarps; ++u) {
-        const int c = warp + u * kWarpSolveWarps;
+    for (int u = 0; u < 2; ++u) {
+        const int c = warp + u * NW;
         const double* col = R + static_cast<int64_t>(jcol[c]) * ldr;
         double v[KQ];
 #pragma unroll
@@ -674,11 +678,11 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
 #pragma unroll
         for (int q = 0; q < KQ; ++q) {
             const int b = lane + 32 * q;
-            if (b < kp) Bt[b * kGemmCols + c] = f32_of_exact(v[q]);
+            if (b < kp) Bt[b * LD + c] = f32_of_exact(v[q]);
         }
     }
     __syncthreads();
-    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;   // columns 2 tx, 2 tx + 1; rows 4 ty .. 4 ty + 3
+    const int tx = threadIdx.x % NCG, ty = threadIdx.x / NCG;   // columns 2 tx, 2 tx + 1; rows 4 ty .. 4 ty + 3
     const int r0 = 4 * ty, cc = 2 * tx;
     const bool live = r0 < kp;
     float t0[4][2] = {};
@@ -687,7 +691,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
 #pragma unroll 4
         for (int b = r0; b < kp; ++b) {
             const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
-            const float2 bv = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
+            const float2 bv = *reinterpret_cast<const float2*>(Bt + b * LD + cc);
             const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ba[2] = {bv.x, bv.y};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -696,7 +700,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            *reinterpret_cast<float2*>(Tt + (r0 + i) * kGemmCols + cc) = make_float2(t0[i][0], t0[i][1]);
+            *reinterpret_cast<float2*>(Tt + (r0 + i) * LD + cc) = make_float2(t0[i][0], t0[i][1]);
     }
     __syncthreads();
     float e[4][2] = {};
@@ -705,7 +709,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
         float hi[4][2], lo[4][2];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float2 bv = *reinterpret_cast<const float2*>(Bt + (r0 + i) * kGemmCols + cc);
+            const float2 bv = *reinterpret_cast<const float2*>(Bt + (r0 + i) * LD + cc);
             hi[i][0] = bv.x;
             hi[i][1] = bv.y;
             lo[i][0] = lo[i][1] = 0.f;
@@ -713,7 +717,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
 #pragma unroll 2
         for (int b = r0; b < kp; ++b) {
             const float4 rv = *reinterpret_cast<const float4*>(Rs + b * kp + r0);
-            const float2 tv = *reinterpret_cast<const float2*>(Tt + b * kGemmCols + cc);
+            const float2 tv = *reinterpret_cast<const float2*>(Tt + b * LD + cc);
             const float ra[4] = {-rv.x, -rv.y, -rv.z, -rv.w}, ta[2] = {tv.x, tv.y};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -738,7 +742,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
     if (live) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            *reinterpret_cast<float2*>(Bt + (r0 + i) * kGemmCols + cc) = make_float2(e[i][0], e[i][1]);
+            *reinterpret_cast<float2*>(Bt + (r0 + i) * LD + cc) = make_float2(e[i][0], e[i][1]);
     }
     __syncthreads();
     if (live) {
@@ -747,7 +751,7 @@ __device__ __forceinline__ void gemm_tile(const double* __restrict__ R, int64_t 
 #pragma unroll 4
         for (int b = r0; b < kp; ++b) {
             const float4 xv = *reinterpret_cast<const float4*>(Xs + b * kp + r0);
-            const float2 ev = *reinterpret_cast<const float2*>(Bt + b * kGemmCols + cc);
+            const float2 ev = *reinterpret_cast<const float2*>(Bt + b * LD + cc);
             const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ea[2] = {ev.x, ev.y};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -805,12 +809,12 @@ k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
     const int kp = gemm_kp(k);
     float* Xs = reinterpret_cast<float*>(sm);        // kp x kp, column-major
     float* Rs = Xs + kp * kp;                        // R11, kp x kp column-major
-    float* Bt = Rs + kp * kp;                        // [kp][kGemmCols]: R12, then the residual E
-    float* Tt = Bt + kp * kGemmCols;                 // [kp][kGemmCols]: T0
+    float* Bt = Rs + kp * kp;                        // [kp][gemm_ld]: R12, then the residual E
+    float* Tt = Bt + kp * gemm_ld(kGemmCols);        // [kp][gemm_ld]: T0
     if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? __ldg(J + k + c0 + threadIdx.x) : 0;
     stage_x_r11(scr, kq_cap, kp, Xs, Rs);
     __syncthreads();
-    gemm_tile<KQ>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, c0, ldt);
+    gemm_tile<KQ, kGemmCols>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, c0, ldt);
 }
 
 template <int KQ>
@@ -826,7 +830,7 @@ static cudaError_t launch_gemm_solve(const double* R64, int64_t ldr, const int32
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the tiles' shared memory, or the FP64 fallback's copy of R11 if that is larger
-    const size_t tiles = gemm_tile_floats(kq) * sizeof(float);
+    const size_t tiles = gemm_tile_floats(kq, kGemmCols) * sizeof(float);
     const size_t fb = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(double);
     const size_t smem = std::max(tiles, fb) + 16;
     auto kern = k_solve_T_gemm<KQ>;
@@ -873,14 +877,14 @@ k_r11_inverse_batched(const BatchTask* __restrict__ tasks, const double* __restr
 }
 
 template <int KQ>
-__global__ void __launch_bounds__(kGemmThreads)
+__global__ void __launch_bounds__(16 * kGemmColsBatch)
 k_solve_T_batched_gemm(const BatchTask* __restrict__ tasks, const SolveUnit* __restrict__ units,
                        const double* __restrict__ R_base, const int32_t* __restrict__ J_base,
                        const int32_t* __restrict__ k_out, int32_t* infos, double* __restrict__ T_base,
                        BatchTotals tot, int kmax, int refine_steps, const float* __restrict__ inv_base) {
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ int s_bad;
-    __shared__ int jc[kGemmCols];
+    __shared__ int jc[kGemmColsBatch];
     const SolveUnit su = units[blockIdx.x];
     if (su.task < 0 || su.task >= tot.ntasks) return;
     const BatchTask& bt = tasks[su.task];
@@ -916,13 +920,13 @@ k_solve_T_batched_gemm(const BatchTask* __restrict__ tasks, const SolveUnit* __r
     float* Xs = reinterpret_cast<float*>(sm);
     float* Rs = Xs + kp * kp;
     float* Bt = Rs + kp * kp;
-    float* Tt = Bt + kp * kGemmCols;
+    float* Tt = Bt + kp * gemm_ld(kGemmColsBatch);
     stage_x_r11(scr, kq, kp, Xs, Rs);
-    for (int64_t t0 = su.c0; t0 < c_end; t0 += kGemmCols) {
-        const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), c_end - t0));
-        if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? J[k + t0 + threadIdx.x] : 0;
+    for (int64_t t0 = su.c0; t0 < c_end; t0 += kGemmColsBatch) {
+        const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmColsBatch), c_end - t0));
+        if (threadIdx.x < kGemmColsBatch) jc[threadIdx.x] = threadIdx.x < ncols ? J[k + t0 + threadIdx.x] : 0;
         __syncthreads();
-        gemm_tile<KQ>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, t0, ldr);
+        gemm_tile<KQ, kGemmColsBatch>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, t0, ldr);
     }
 }
 
@@ -943,11 +947,11 @@ static cudaError_t launch_batched_product(const BatchTask* tasks, int ntasks, co
         e = cudaGetLastError();
         if (e != cudaSuccess || nunits <= 0) return e;
     }
-    const size_t smem = gemm_tile_floats(gemm_kp(kmax)) * sizeof(float) + 16;
+    const size_t smem = gemm_tile_floats(gemm_kp(kmax), kGemmColsBatch) * sizeof(float) + 16;
     auto kern = k_solve_T_batched_gemm<KQ>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<nunits, kGemmThreads, smem, s>>>(tasks, units, R_base, J_base, k_out, infos, T_base, tot, kmax,
+    kern<<<nunits, 16 * kGemmColsBatch, smem, s>>>(tasks, units, R_base, J_base, k_out, infos, T_base, tot, kmax,
                                             refine_steps, inv);
     return cudaGetLastError();
 }
