@@ -16,7 +16,7 @@
 //
 // The heavy terms are gather-GEMMs (columns selected through J) done by one
 // batched, register-tiled FP32 kernel; the thin QR is classical Gram-Schmidt
-// applied twice, one CTA per matrix; the k x k pieces are small kernels.
+// applied twice, one CTA per matrix; the substitutions with R and R^T run a warp per column.
 #include "common.cuh"
 #include "internal.h"
 
@@ -231,58 +231,155 @@ __global__ void __launch_bounds__(512) k_cgs2(const float* __restrict__ A, int64
 
 // ------------------------------------------------------------------ small k x k pieces
 
-// B1 = B0 + R^-T Tb (column by column, forward substitution with R^T), then B2 = R^-1 B1.
-// One thread per column of (n - k) columns; R in shared memory.  Tb (k x (n-k), ld ldtb) nullable.
-__global__ void k_bwd_b(const float* __restrict__ R, int k, int64_t ncols, const float* __restrict__ B0,
-                        const float* __restrict__ Tb, int64_t ldtb, int64_t strideTb, float* __restrict__ B1,
-                        float* __restrict__ B2) {
-    extern __shared__ float rs[];
-    const int64_t b = blockIdx.y;
-    const float* rb = R + b * k * k;
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) rs[idx] = rb[idx];
-    __syncthreads();
-    const int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
-    const float* b0 = B0 + (b * ncols + c) * k;
-    float* b1 = B1 + (b * ncols + c) * k;
-    float* b2 = B2 + (b * ncols + c) * k;
-    // y = R^-T tb: R^T is lower triangular, R^T(a, i) = R(i, a) = rs[a * k + i]
-    for (int a = 0; a < k; ++a) {
-        float v = 0.f;
-        if (Tb) {
-            v = Tb[b * strideTb + c * ldtb + a];
-            for (int i = 0; i < a; ++i) v = fmaf(-rs[a * k + i], b1[i] - b0[i], v);
-            v /= rs[a * k + a];
-        }
-        b1[a] = b0[a] + v;
-    }
-    for (int a = k - 1; a >= 0; --a) {
-        float v = b1[a];
-        for (int i = a + 1; i < k; ++i) v = fmaf(-rs[i * k + a], b2[i], v);
-        b2[a] = v / rs[a * k + a];
+// Warp-per-column substitutions with R (k x k upper, FP32) staged in shared memory twice: rc
+// column-major (column a contiguous: R(0:a, a)) and rt row-major (row a contiguous: R(a, a:k)),
+// so that every step's reads are contiguous across the lanes.  Lane l holds rows l, l + 32, ...
+// (KQ blocks of 32); the steps run by block from a compile-time register index.
+__device__ __forceinline__ void stage_r_both(const float* __restrict__ R, int k, float* rc, float* rt) {
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int a = idx / k, r = idx - a * k;          // R(r, a) = R[a k + r]
+        const float v = R[idx];
+        rc[idx] = v;
+        rt[r * k + a] = v;
     }
 }
 
-// K2 = H + R^-T E for one matrix per block (k x k, column-major; E nullable).
-__global__ void k_bwd_k2(const float* __restrict__ R, int k, const float* __restrict__ H,
-                         const float* __restrict__ E, float* __restrict__ K2) {
-    const int64_t b = blockIdx.x;
-    const float* rb = R + b * k * k;
-    const float* hb = H + b * k * k;
-    float* kb = K2 + b * k * k;
-    const int c = threadIdx.x;
-    if (c >= k) return;
-    const float* e = E ? E + b * k * k + static_cast<int64_t>(c) * k : nullptr;
-    float* out = kb + static_cast<int64_t>(c) * k;
-    // y = R^-T e (forward substitution), out = h + y
-    for (int a = 0; a < k; ++a) {
-        float v = 0.f;
-        if (e) {
-            v = e[a];
-            for (int i = 0; i < a; ++i) v = fmaf(-rb[static_cast<int64_t>(a) * k + i], out[i] - hb[static_cast<int64_t>(c) * k + i], v);
-            v /= rb[static_cast<int64_t>(a) * k + a];
+// y = R^-T t (forward substitution: y_a = (t_a - sum_{i<a} R(i,a) y_i) / R(a,a)).
+template <int KQ>
+__device__ __forceinline__ void warp_fwd_rt(float (&t)[KQ], const float* rc, const float* rt, int k, int lane) {
+#pragma unroll
+    for (int qa = 0; qa < KQ; ++qa) {
+        const int a_end = min(32 * qa + 32, k);
+        for (int a = 32 * qa; a < a_end; ++a) {
+            const int i = a - 32 * qa;
+            const float ya = __shfl_sync(0xffffffffu, t[qa], i) / rc[a * k + a];
+            const float* row = rt + a * k + lane;           // R(a, lane + 32 q)
+            if (lane == i) t[qa] = ya;
+            else if (lane > i && lane + 32 * qa < k) t[qa] = fmaf(-row[32 * qa], ya, t[qa]);
+#pragma unroll
+            for (int q = qa + 1; q < KQ; ++q)
+                if (lane + 32 * q < k) t[q] = fmaf(-row[32 * q], ya, t[q]);
         }
-        out[a] = hb[static_cast<int64_t>(c) * k + a] + v;
+    }
+}
+
+// x = R^-1 t (back substitution).
+template <int KQ>
+__device__ __forceinline__ void warp_back_r(float (&t)[KQ], const float* rc, int k, int lane) {
+#pragma unroll
+    for (int qa = KQ - 1; qa >= 0; --qa) {
+        for (int a = min(32 * qa + 31, k - 1); a >= 32 * qa; --a) {
+            const int i = a - 32 * qa;
+            const float xa = __shfl_sync(0xffffffffu, t[qa], i) / rc[a * k + a];
+            const float* col = rc + a * k + lane;           // R(lane + 32 q, a)
+            if (lane == i) t[qa] = xa;
+            else if (lane < i) t[qa] = fmaf(-col[32 * qa], xa, t[qa]);
+#pragma unroll
+            for (int q = 0; q < qa; ++q) t[q] = fmaf(-col[32 * q], xa, t[q]);
+        }
+    }
+}
+
+// B1 = B0 + R^-T Tb (Tb nullable), then B2 = R^-1 B1, for the columns of one matrix
+// (blockIdx.y): a warp per column.
+template <int KQ>
+__global__ void __launch_bounds__(256) k_bwd_b(const float* __restrict__ R, int k, int64_t ncols,
+                                               const float* __restrict__ B0, const float* __restrict__ Tb, int64_t ldtb,
+                                               int64_t strideTb, float* __restrict__ B1, float* __restrict__ B2) {
+    extern __shared__ float rs[];
+    const int64_t b = blockIdx.y;
+    float* rc = rs;
+    float* rt = rs + k * k;
+    stage_r_both(R + b * k * k, k, rc, rt);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncols;
+         c += nwarps) {
+        const float* b0 = B0 + (b * ncols + c) * k;
+        float y[KQ], x[KQ];
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int r = lane + 32 * q;
+            y[q] = (Tb && r < k) ? Tb[b * strideTb + c * ldtb + r] : 0.f;
+        }
+        if (Tb) warp_fwd_rt<KQ>(y, rc, rt, k, lane);
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int r = lane + 32 * q;
+            x[q] = r < k ? b0[r] + y[q] : 0.f;
+            if (r < k) B1[(b * ncols + c) * k + r] = x[q];
+        }
+        warp_back_r<KQ>(x, rc, k, lane);
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int r = lane + 32 * q;
+            if (r < k) B2[(b * ncols + c) * k + r] = x[q];
+        }
+    }
+}
+
+// K2 = H + R^-T E (k x k column-major per matrix; E nullable): a warp per column.
+template <int KQ>
+__global__ void __launch_bounds__(256) k_bwd_k2(const float* __restrict__ R, int k, const float* __restrict__ H,
+                                                const float* __restrict__ E, float* __restrict__ K2) {
+    extern __shared__ float rs[];
+    const int64_t b = blockIdx.y;
+    float* rc = rs;
+    float* rt = rs + k * k;
+    stage_r_both(R + b * k * k, k, rc, rt);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= k) return;
+    const float* hb = H + b * k * k + static_cast<int64_t>(c) * k;
+    float y[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        const int r = lane + 32 * q;
+        y[q] = (E && r < k) ? E[b * k * k + static_cast<int64_t>(c) * k + r] : 0.f;
+    }
+    if (E) warp_fwd_rt<KQ>(y, rc, rt, k, lane);
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        const int r = lane + 32 * q;
+        if (r < k) K2[b * k * k + static_cast<int64_t>(c) * k + r] = hb[r] + y[q];
+    }
+}
+
+template <int KQ>
+static cudaError_t launch_bwd_small(bool is_b, const float* R, int k, int64_t ncols, const float* B0, const float* Tb,
+                                    int64_t ldtb, int64_t strideTb, float* B1, float* B2, const float* H,
+                                    const float* E, float* K2, int64_t batch, cudaStream_t s) {
+    const size_t smem = 2 * static_cast<size_t>(k) * k * sizeof(float);
+    cudaError_t e;
+    if (is_b) {
+        auto kern = k_bwd_b<KQ>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
+            cudaSuccess)
+            return e;
+        const int64_t blocks = std::min<int64_t>((ncols + 7) / 8, 64);
+        kern<<<dim3(static_cast<unsigned>(blocks), static_cast<unsigned>(batch)), 256, smem, s>>>(
+            R, k, ncols, B0, Tb, ldtb, strideTb, B1, B2);
+    } else {
+        auto kern = k_bwd_k2<KQ>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
+            cudaSuccess)
+            return e;
+        kern<<<dim3(static_cast<unsigned>((k + 7) / 8), static_cast<unsigned>(batch)), 256, smem, s>>>(R, k, H, E,
+                                                                                                   K2);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t bwd_small(bool is_b, const float* R, int k, int64_t ncols, const float* B0, const float* Tb,
+                             int64_t ldtb, int64_t strideTb, float* B1, float* B2, const float* H, const float* E,
+                             float* K2, int64_t batch, cudaStream_t s) {
+    switch ((k + 31) / 32) {
+        case 1: return launch_bwd_small<1>(is_b, R, k, ncols, B0, Tb, ldtb, strideTb, B1, B2, H, E, K2, batch, s);
+        case 2: return launch_bwd_small<2>(is_b, R, k, ncols, B0, Tb, ldtb, strideTb, B1, B2, H, E, K2, batch, s);
+        case 3: return launch_bwd_small<3>(is_b, R, k, ncols, B0, Tb, ldtb, strideTb, B1, B2, H, E, K2, batch, s);
+        default: return launch_bwd_small<4>(is_b, R, k, ncols, B0, Tb, ldtb, strideTb, B1, B2, H, E, K2, batch, s);
     }
 }
 
@@ -381,15 +478,9 @@ cudaError_t launch_backward(int64_t batch, const float* A, int64_t m, int64_t n,
             if ((e = cudaMemsetAsync(w.B0, 0, sizeof(float) * batch * nc * k, s)) != cudaSuccess) return e;
         }
         // B1 = B0 + R^-T Tb, B2 = R^-1 B1
-        dim3 gb(static_cast<unsigned>((nc + 127) / 128), static_cast<unsigned>(batch));
-        const size_t rsm = static_cast<size_t>(k) * k * sizeof(float);
-        if (rsm > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_bwd_b, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(rsm))) !=
-                cudaSuccess)
+        if ((e = bwd_small(true, w.R, k, nc, w.B0, Tb, ldtb, strideTb, w.B1, w.B2, nullptr, nullptr, nullptr, batch,
+                           s)) != cudaSuccess)
             return e;
-        k_bwd_b<<<gb, 128, rsm, s>>>(w.R, k, nc, w.B0, Tb, ldtb, strideTb, w.B1,
-                                                                             w.B2);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // Z = G_c T^T + C B2^T  accumulated into X_bar (= dA(:, J[0:k]))
         const GOut Xb{dA, strideD, 1, ldd, J, strideJ, 0};
         if (G) {
@@ -420,8 +511,9 @@ cudaError_t launch_backward(int64_t batch, const float* A, int64_t m, int64_t n,
         }
     }
     // K2 = H + R^-T E
-    k_bwd_k2<<<static_cast<unsigned>(batch), 128, 0, s>>>(w.R, k, w.H, (Tb && nc > 0) ? w.E : nullptr, w.K2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = bwd_small(false, w.R, k, 0, nullptr, nullptr, 0, 0, nullptr, nullptr, w.H, (Tb && nc > 0) ? w.E : nullptr,
+                       w.K2, batch, s)) != cudaSuccess)
+        return e;
     // X_bar -= Q K2
     {
         const GOut Xb{dA, strideD, 1, ldd, J, strideJ, 0};
