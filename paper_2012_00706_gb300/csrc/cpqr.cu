@@ -106,12 +106,47 @@ struct GridShared {
 // min(cpb, kSuper) columns, the staged pivot column (rstage rows, column mode), the
 // super-group's recompute flags, and the columns' selection flags.
 __host__ __device__ inline int64_t grid_super(int64_t cpb) { return cpb < kSuper ? cpb : kSuper; }
+// The staged pivot column comes first (16-byte aligned for vector reads), rounded up to 16 bytes.
+__host__ __device__ inline int64_t grid_rstage_padded(int64_t rstage, int elem_bytes) {
+    const int64_t per = 16 / elem_bytes;
+    return (rstage + per - 1) / per * per;
+}
 template <typename T>
 __host__ __device__ inline size_t grid_smem_bytes(int64_t cpb, int64_t rstage) {
     const size_t sup = static_cast<size_t>(grid_super(cpb));
-    return (2 * static_cast<size_t>(cpb) + (kGridWarps + 1) * sup + static_cast<size_t>(rstage)) * sizeof(T) +
+    return (2 * static_cast<size_t>(cpb) + (kGridWarps + 1) * sup +
+            static_cast<size_t>(grid_rstage_padded(rstage, sizeof(T)))) * sizeof(T) +
            sup * sizeof(int) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
 }
+
+// 16-byte vectors of the column mode's vector path.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using V = float4;
+    static constexpr int E = 4;
+    static __device__ __forceinline__ float dot(const float4 a, const float4 b, float s) {
+        return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+    }
+    static __device__ __forceinline__ float4 axpy(float m, const float4 p, const float4 x) {
+        return make_float4(fmaf(m, p.x, x.x), fmaf(m, p.y, x.y), fmaf(m, p.z, x.z), fmaf(m, p.w, x.w));
+    }
+    static __device__ __forceinline__ float sq(const float4 a, float s) { return dot(a, a, s); }
+    static __device__ __forceinline__ float4 ldcg(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+};
+template <> struct Vec16<double> {
+    using V = double2;
+    static constexpr int E = 2;
+    static __device__ __forceinline__ double dot(const double2 a, const double2 b, double s) {
+        return fma(a.y, b.y, fma(a.x, b.x, s));
+    }
+    static __device__ __forceinline__ double2 axpy(double m, const double2 p, const double2 x) {
+        return make_double2(fma(m, p.x, x.x), fma(m, p.y, x.y));
+    }
+    static __device__ __forceinline__ double sq(const double2 a, double s) { return dot(a, a, s); }
+    static __device__ __forceinline__ double2 ldcg(const double* p) {
+        return __ldcg(reinterpret_cast<const double2*>(p));
+    }
+};
 
 // Column mode (a warp per column, no CTA barrier inside a step) when every warp has a
 // column; the pivot column is staged in shared memory when it takes at most 64 KB.
@@ -133,12 +168,12 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     const int64_t r = P.r;
     const T sqrt_u = SqrtU<T>::v();
     const int sup = static_cast<int>(grid_super(P.cpb_max));
-    T* nu_s = reinterpret_cast<T*>(smem_dyn);
+    T* xps_s = reinterpret_cast<T*>(smem_dyn);  // [rstage] staged pivot column (column mode)
+    T* nu_s = xps_s + grid_rstage_padded(P.rstage, sizeof(T));
     T* nuref_s = nu_s + P.cpb_max;
     T* red_s = nuref_s + P.cpb_max;             // [kGridWarps][sup]
     T* sv_s = red_s + kGridWarps * sup;
-    T* xps_s = sv_s + sup;                      // [rstage] staged pivot column (column mode)
-    int* rec_s = reinterpret_cast<int*>(xps_s + P.rstage);
+    int* rec_s = reinterpret_cast<int*>(sv_s + sup);
     uint8_t* sel_s = reinterpret_cast<uint8_t*>(rec_s + sup);
     uint32_t epoch = 0;
 
@@ -345,12 +380,123 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     }
                 }
             };
+            // the same column work with 16-byte vectors (columns 16-byte aligned): a scalar head
+            // up to the first aligned row, vectors, a scalar tail; several vectors in flight
+            using VT = Vec16<T>;
+            using V = typename VT::V;
+            constexpr int E = VT::E;
+            auto run_cols_vec = [&](auto xpv, auto xpw) {
+                const int64_t hd = min(r, (static_cast<int64_t>(j) + E - 1) / E * E);
+                const int64_t rd = hd + (r - hd) / E * E;
+                const int64_t hu = min(r, (static_cast<int64_t>(j) + E) / E * E);     // after row j
+                const int64_t ru = hu + (r - hu) / E * E;
+                for (int c = warp; c < nc; c += kGridWarps) {
+                    if (sel_s[c]) continue;
+                    T* x = col(c);
+                    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                    if (j + lane < hd) s0 = xpv(j + lane) * x[j + lane];
+                    if (rd + lane < r) s1 = xpv(rd + lane) * x[rd + lane];
+                    {
+                        const V* xv = reinterpret_cast<const V*>(x + hd);
+                        const int64_t nv = (rd - hd) / E;
+                        int64_t v = lane;
+                        for (; v + 224 < nv; v += 256) {
+                            V a[8], q[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                a[u] = xv[v + 32 * u];
+                                q[u] = xpw(hd + (v + 32 * u) * E);
+                            }
+                            s0 = VT::dot(a[0], q[0], s0);
+                            s1 = VT::dot(a[1], q[1], s1);
+                            s2 = VT::dot(a[2], q[2], s2);
+                            s3 = VT::dot(a[3], q[3], s3);
+                            s0 = VT::dot(a[4], q[4], s0);
+                            s1 = VT::dot(a[5], q[5], s1);
+                            s2 = VT::dot(a[6], q[6], s2);
+                            s3 = VT::dot(a[7], q[7], s3);
+                        }
+                        for (; v < nv; v += 32) s0 = VT::dot(xv[v], xpw(hd + v * E), s0);
+                    }
+                    T sdot = warp_sum((s0 + s1) + (s2 + s3));
+                    const T X = x[j];
+                    sdot = fma(-beta, X, sdot);
+                    const T tw = -sdot * rb;
+                    const T sv = tw * inv;
+                    const T rho = X - tw;
+                    const T nu = nu_s[c];
+                    bool rec = false;
+                    T d = nu;
+                    if (nu > T(0)) {
+                        d = fmax(nu - rho * rho, T(0));
+                        rec = d <= sqrt_u * nuref_s[c];
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                        if (nu > T(0) && !rec) nu_s[c] = d;
+                    }
+                    const T msv = -sv;
+                    T q0 = 0, q1 = 0;
+                    if (j + 1 + lane < hu) {
+                        const int64_t t = j + 1 + lane;
+                        const T n0 = fma(msv, xpv(t), x[t]);
+                        x[t] = n0;
+                        q0 = n0 * n0;
+                    }
+                    if (ru + lane < r) {
+                        const int64_t t = ru + lane;
+                        const T n0 = fma(msv, xpv(t), x[t]);
+                        x[t] = n0;
+                        q1 = n0 * n0;
+                    }
+                    {
+                        V* xv = reinterpret_cast<V*>(x + hu);
+                        const int64_t nv = (ru - hu) / E;
+                        int64_t v = lane;
+                        for (; v + 96 < nv; v += 128) {
+                            V a[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) a[u] = VT::axpy(msv, xpw(hu + (v + 32 * u) * E), xv[v + 32 * u]);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) xv[v + 32 * u] = a[u];
+                            if (rec) {
+                                q0 = VT::sq(a[0], q0);
+                                q1 = VT::sq(a[1], q1);
+                                q0 = VT::sq(a[2], q0);
+                                q1 = VT::sq(a[3], q1);
+                            }
+                        }
+                        for (; v < nv; v += 32) {
+                            const V a = VT::axpy(msv, xpw(hu + v * E), xv[v]);
+                            xv[v] = a;
+                            if (rec) q0 = VT::sq(a, q0);
+                        }
+                    }
+                    if (rec) {
+                        const T sq = warp_sum(q0 + q1);
+                        if (lane == 0) {
+                            nu_s[c] = sq;
+                            nuref_s[c] = sq;
+                        }
+                    }
+                }
+            };
+            const bool vec = (ldx * static_cast<int64_t>(sizeof(T))) % 16 == 0 &&
+                             (reinterpret_cast<uintptr_t>(Xs) & 15u) == 0;
             if (P.rstage > 0) {
                 for (int64_t t = j + tid; t < r; t += nt) xps_s[t] = __ldcg(xp + t);
                 __syncthreads();
-                run_cols([&](int64_t t) { return xps_s[t]; });
+                if (vec)
+                    run_cols_vec([&](int64_t t) { return xps_s[t]; },
+                                 [&](int64_t t) { return *reinterpret_cast<const V*>(xps_s + t); });
+                else
+                    run_cols([&](int64_t t) { return xps_s[t]; });
             } else {
-                run_cols([&](int64_t t) { return __ldcg(xp + t); });
+                if (vec && (reinterpret_cast<uintptr_t>(xp) & 15u) == 0)
+                    run_cols_vec([&](int64_t t) { return __ldcg(xp + t); }, [&](int64_t t) { return VT::ldcg(xp + t); });
+                else
+                    run_cols([&](int64_t t) { return __ldcg(xp + t); });
             }
             __syncthreads();
         } else {
