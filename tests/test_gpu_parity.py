@@ -244,12 +244,13 @@ def test_plain_tall_streamed_matches_oracle(gid, dev, orc, m, n, k, dtype):
 
 
 @pytest.mark.parametrize("m,n,k,dtype", [(3000, 2600, 20, np.float64), (9000, 2500, 16, np.float64),
-                                         (5000, 2500, 20, np.float32)])
+                                         (5000, 2500, 20, np.float32), (3001, 2600, 20, np.float32)])
 def test_plain_wide_column_mode_matches_oracle(gid, dev, orc, m, n, k, dtype):
     """Wide matrices whose slices hold at least a column per warp take the streamed pivoted
     QR's column mode (a warp per column, no CTA barrier inside a step), with the pivot column
-    staged in shared memory (3000 and 5000 rows) or read from L2 (9000 FP64 rows, 72 KB):
-    pivots equal the oracle's on separated inputs, T to the solve's accuracy."""
+    staged in shared memory (3000 and 5000 rows) or read from L2 (9000 FP64 rows, 72 KB), by
+    16-byte vectors where the columns are aligned and element by element where they are not
+    (3001 FP32 rows): pivots equal the oracle's on separated inputs, T to the solve's accuracy."""
     a = wl.separated_matrix(m, n, seed=m + n, decay=0.97)
     a = a.astype(dtype).astype(np.float64)
     ref = orc.interp_decomp(a, k=k)
