@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
     // the step's decision, written by warp 0 before the CTA barrier
     __shared__ double s_alpha, s_s2;
     __shared__ int s_p, s_go;   // s_go: 1 carry on, 0 stop (rank reached or tolerance met), -1 watchdog
+    __shared__ int s_src;       // the table entry (CTA) whose published column is the pivot
 
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
 
     // ---- warp 0: wait (bounded) until every record of step `step` carries its stamp,
     // reduce the table in a fixed order (ties to the smaller CTA, hence column) and, unless
-    // `final`, decide the step and stage the winner's rows step..r-1 in shared memory.
+    // `final`, decide the step; the whole CTA then stages the winner's rows step..r-1.
     // s_go: 1 carry on, 0 stop (tolerance met, or zero residual: info = step + 1), -1 watchdog
     double total = 0.0;   // warp 0: ||W||_F^2, from the first table
     auto decide = [&](int step, bool final_wait) {
@@ -230,12 +231,10 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         } else if (p < 0 || !(bv > 0.0) || !(s2 > 0.0)) {
             go = 0;
             if (b == 0 && lane == 0) set_info(P.info, step + 1);
-        } else {
-            const T* src = P.pub + (static_cast<int64_t>(slot) * G + bg) * r;
-            for (int64_t t = step + lane; t < r; t += 32) xps[t] = __ldcg(src + t);
         }
         if (lane == 0) {
             s_go = go;
+            s_src = bg;
             s_p = p;
             s_alpha = alpha;
             s_s2 = s2;
@@ -249,6 +248,12 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         __syncthreads();
         go = s_go;
         if (go <= 0) break;
+        {
+            // the pivot column's rows j..r-1 from the table, every thread a few of them
+            const T* src = P.pub + (static_cast<int64_t>(j & 1) * G + s_src) * r;
+            for (int64_t t = j + tid; t < r; t += kResWarps * 32) xps[t] = __ldcg(src + t);
+            __syncthreads();
+        }
         // ---- reflector scalars; the pivot column staged in xps (not modified in this step)
         const int p = s_p;
         const T alpha = static_cast<T>(s_alpha);
