@@ -123,19 +123,21 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         }
         if (lane == 0) { w_nu[warp] = v; w_idx[warp] = ci; w_sum[warp] = part; }
         __syncthreads();
+        // every warp finds the CTA's best the same way; all threads copy its rows
+        double bv = lane < kResWarps ? w_nu[lane] : -1.0;
+        int bi = lane < kResWarps ? w_idx[lane] : -1;
+        warp_argmax(bv, bi);
+        if (bi >= 0 && step < r) {
+            const T* x = xs + static_cast<int64_t>(bi) * r;
+            T* dst = P.pub + (static_cast<int64_t>(slot) * G + b) * r;
+            for (int64_t t = step + tid; t < r; t += kResWarps * 32) dst[t] = x[t];
+        }
+        // the column's stores, observed through the barrier, before the record's stamp
+        __syncthreads();
         if (warp == 0) {
-            double bv = lane < kResWarps ? w_nu[lane] : -1.0;
-            int bi = lane < kResWarps ? w_idx[lane] : -1;
             double sum = lane < kResWarps ? w_sum[lane] : 0.0;
-            warp_argmax(bv, bi);
             sum = warp_sum(sum);
-            T alpha = 0;
-            if (bi >= 0 && step < r) {
-                const T* x = xs + static_cast<int64_t>(bi) * r;
-                T* dst = P.pub + (static_cast<int64_t>(slot) * G + b) * r;
-                for (int64_t t = step + lane; t < r; t += 32) dst[t] = x[t];
-                alpha = x[step];
-            }
+            const T alpha = (bi >= 0 && step < r) ? xs[static_cast<int64_t>(bi) * r + step] : T(0);
             Cand* rec = P.cand + slot * G + b;
             if (lane == 0) {
                 rec->nu = bv;
@@ -144,11 +146,9 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
                 rec->s2 = bi >= 0 && step < r ? bv : 0.0;   // nu is the exact norm of rows step..r-1
                 rec->alpha = static_cast<double>(alpha);
                 rec->idx = bi >= 0 ? static_cast<int>(c0 + bi) : -1;
+                __threadfence();
+                st_release_s32(&rec->stamp, step + 1);
             }
-            // every lane's stores (column and record) before the stamp
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) st_release_s32(&rec->stamp, step + 1);
         }
     };
 
