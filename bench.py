@@ -791,6 +791,8 @@ def main():
                     help="run only the batched leg (a profiling case) and print its JSON")
     ap.add_argument("--batch-count", type=int, default=512, help="matrices in the batched leg")
     ap.add_argument("--inflight", type=int, default=INFLIGHT, help="IDs in flight in the timed stream")
+    ap.add_argument("--inflight-groups", type=int, default=INFLIGHT_GROUPS,
+                    help="CUDA graphs the in-flight IDs are issued as, replayed in turn")
     ap.add_argument("--figures", action="store_true",
                     help="print the k and n sweeps of the paper's Figs. 1-6 as one JSON object and exit")
     ap.add_argument("--profile-case", choices=["cpqr", "bwd"],
@@ -958,8 +960,8 @@ def main():
         return t0.elapsed_time(t1)
 
     def run_inflight(precision, om, steps, warmup, depth):
-        """`steps` IDs with `depth` of them in flight, issued as INFLIGHT_GROUPS CUDA graphs of
-        depth / INFLIGHT_GROUPS IDs each, replayed in turn on their own streams: a graph holds
+        """`steps` IDs with `depth` of them in flight, issued as `--inflight-groups` CUDA graphs
+        of depth / groups IDs each, replayed in turn on their own streams: a graph holds
         its IDs on forked streams (each with its own copy of A, workspace and outputs, so
         nothing is shared through L2), and while one group's pivoted QRs run on 16-SM
         clusters the next group's sketches fill the other SMs.  A graph of the remaining
@@ -991,7 +993,7 @@ def main():
             torch.cuda.synchronize()
             return g
 
-        ngroups = max(1, min(INFLIGHT_GROUPS, depth))
+        ngroups = max(1, min(args.inflight_groups, depth))
         per = depth // ngroups
         bounds = [(gi * per, depth if gi == ngroups - 1 else (gi + 1) * per) for gi in range(ngroups)]
         groups = [capture(range(lo, hi)) for lo, hi in bounds]
@@ -1083,8 +1085,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "ell": ELL, "precision": args.precision,
-                   "launch": f"a stream of IDs, {args.inflight} in flight: {min(INFLIGHT_GROUPS, args.inflight)} "
-                             f"CUDA graphs of {args.inflight // min(INFLIGHT_GROUPS, args.inflight)} IDs on forked "
+                   "launch": f"a stream of IDs, {args.inflight} in flight: {min(args.inflight_groups, args.inflight)} "
+                             f"CUDA graphs of {args.inflight // min(args.inflight_groups, args.inflight)} IDs on forked "
                              f"streams (own A copy, workspace, outputs each), replayed in turn on their own "
                              f"streams; single-ID latency in latency_ms_per_id; e2e double-buffers A",
                    "l2": "inputs larger than L2 (A is 320 MB vs 129 MB L2); no flush needed"},
