@@ -189,6 +189,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     for (int c = 0; c < nc; ++c) {
         T* x = col(c);
         T s = 0;
+#pragma unroll 8
         for (int64_t t = tid; t < r; t += nt) {
             T a;
             if (P.src) {
@@ -231,12 +232,20 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
         T s2 = 0;
         T alpha = 0;
         if (bl >= 0 && row < r) {
+            // the candidate's exact squared norm: eight independent sums keep eight loads in
+            // flight per thread (this pass is on every step's critical path)
             const T* x = col(bl);
-            T s = 0;
-            for (int64_t t = row + tid; t < r; t += nt) {
-                const T a = x[t];
-                s += a * a;
+            T sa[8] = {};
+            int64_t t = row + tid;
+            for (; t + 7 * nt < r; t += 8 * nt) {
+                T a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = x[t + u * nt];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sa[u] = fma(a[u], a[u], sa[u]);
             }
+            for (; t < r; t += nt) sa[0] = fma(x[t], x[t], sa[0]);
+            const T s = ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
             s2 = block_sum(s, G_.shs);
             alpha = x[row];
         }
