@@ -288,7 +288,8 @@ id_status_t id_factor(const void* A, id_dtype_t a_dtype, int64_t m, int64_t n, i
                            s);
     record_stage(4, s);
     if (e == cudaSuccess && opts->estimate_error)
-        e = launch_residual_fro(A, a_f64, m, n, lda, J, k_out, T, ldt, f.acc, err_out, s);
+        e = launch_residual_fro(A, a_f64, m, n, lda, J, k_out, T, ldt, p.kcap, f.acc, err_out,
+                                reinterpret_cast<float*>(f.tscr), s);
     record_stage(5, s);
     return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
 }
@@ -467,7 +468,9 @@ id_status_t id_factor_adaptive(const void* A, id_dtype_t a_dtype, int64_t m, int
         if (e == cudaSuccess)
             e = launch_solve_T(f.R64, opts->k_max, J, k_out, k, n, T, ldt, f.tscr, opts->refine_steps,
                                p.w_f64 ? 0 : 1, s);
-        if (e == cudaSuccess) e = launch_residual_fro(A, a_f64, m, n, lda, J, k_out, T, ldt, f.acc, err_out, s);
+        if (e == cudaSuccess)
+            e = launch_residual_fro(A, a_f64, m, n, lda, J, k_out, T, ldt, k, f.acc, err_out,
+                                    reinterpret_cast<float*>(f.tscr), s);
         double h_err = 0.0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err_out, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h_info, info, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -185,9 +185,13 @@ cudaError_t launch_solve_T_batched_product(const BatchTask* tasks, const SolveUn
                                            const float* inv, cudaStream_t s);
 cudaError_t launch_reconstruct_one(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, const int32_t* J,
                                    int k, const double* T, int64_t ldt, void* Ahat, int64_t ldh, cudaStream_t s);
+// ||A - A(:,J) P||_F / ||A||_F into err_out (acc2: 4 doubles of scratch).  FP32 A: the
+// products in exact float pairs, with T split into FP32 parts in tsplit (2 kcap (n - 1) floats,
+// free space such as the solve's scratch once the solve has run); FP64 A: DFMA (tsplit unused).
 cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda,
                                 const int32_t* J, const int32_t* k_ptr, const double* T,
-                                int64_t ldt, double* acc2, double* err_out, cudaStream_t s);
+                                int64_t ldt, int kcap, double* acc2, double* err_out, float* tsplit,
+                                cudaStream_t s);
 
 // ---- transpose and column gather (transform.cu)
 cudaError_t launch_transpose(const void* A, int f64, int64_t m, int64_t n, int64_t lda, void* B, int64_t ldb,

@@ -1087,6 +1087,104 @@ k_residual_tiles(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda, co
     }
 }
 
+// FP32 A: the same residual with exact FP32 products.  T is split once into FP32 parts
+// (Th + Tl = T to about 2^-48, k_split_T); every product a Th splits exactly into two floats
+// (p = fl(a Th), e = fma(a, Th, -p)), the sums are kept as unevaluated float pairs (TwoSum)
+// and a Tl goes into the low part.  The pair carries about 48 bits: the residual, even where
+// it is 1e-6 of the data, keeps about nine digits, and the FP32 pipe runs it at some sixty
+// times the FP64 pipe's rate.  The squares of the residual entries are summed in FP64.
+__global__ void k_split_T(const double* __restrict__ T, int64_t ldt, const int32_t* __restrict__ k_ptr, int64_t n,
+                          int ld, float* __restrict__ Th, float* __restrict__ Tl) {
+    const int k = *k_ptr;
+    const int64_t nc = n - k;
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < nc * k;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t c = idx / k, b = idx - c * k;
+        const double t = T[c * ldt + b];
+        const float h = static_cast<float>(t);
+        Th[c * ld + b] = h;
+        Tl[c * ld + b] = static_cast<float>(t - static_cast<double>(h));
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_residual_tiles_pair(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const int32_t* __restrict__ J,
+                      const int32_t* __restrict__ k_ptr, const float* __restrict__ Th, const float* __restrict__ Tl,
+                      int ld, double* acc2) {
+    __shared__ float As[kResK][kResTile + 1];
+    __shared__ float Hs[kResK][kResTile + 1];
+    __shared__ float Ls[kResK][kResTile + 1];
+    __shared__ double red[8];
+    const int k = *k_ptr;
+    const int64_t nc = n - k;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kResTile;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.y) * kResTile;
+    if (k <= 0 || q0 >= nc) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int64_t c = q0 + tx * 4 + v;
+        const float* col = c < nc ? A + static_cast<int64_t>(J[k + c]) * lda : nullptr;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t row = r0 + ty * 4 + u;
+            hi[u][v] = (col && row < m) ? col[row] : 0.f;
+            lo[u][v] = 0.f;
+        }
+    }
+    for (int b0 = 0; b0 < k; b0 += kResK) {
+        for (int idx = threadIdx.x; idx < kResK * kResTile; idx += 256) {
+            const int bb = idx / kResTile, i = idx % kResTile;
+            const int b = b0 + bb;
+            const int64_t row = r0 + i, c = q0 + i;
+            As[bb][i] = (b < k && row < m) ? A[static_cast<int64_t>(J[b]) * lda + row] : 0.f;
+            Hs[bb][i] = (b < k && c < nc) ? Th[c * ld + b] : 0.f;
+            Ls[bb][i] = (b < k && c < nc) ? Tl[c * ld + b] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int bb = 0; bb < kResK; ++bb) {
+            float na[4], th[4], tl[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                na[u] = -As[bb][ty * 4 + u];
+                th[u] = Hs[bb][tx * 4 + u];
+                tl[u] = Ls[bb][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float p = __fmul_rn(na[u], th[v]);
+                    const float e = fmaf(na[u], th[v], -p);
+                    const float sum = __fadd_rn(hi[u][v], p);
+                    const float bp = __fsub_rn(sum, hi[u][v]);
+                    const float err = __fadd_rn(__fsub_rn(hi[u][v], __fsub_rn(sum, bp)), __fsub_rn(p, bp));
+                    hi[u][v] = sum;
+                    lo[u][v] = fmaf(na[u], tl[v], __fadd_rn(lo[u][v], __fadd_rn(err, e)));
+                }
+        }
+        __syncthreads();
+    }
+    double sq = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const double r = static_cast<double>(hi[u][v]) + static_cast<double>(lo[u][v]);
+            sq = fma(r, r, sq);
+        }
+    sq = warp_sum(sq);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        atomicAdd(acc2, tot);
+    }
+}
+
 // acc2[1] += ||A||_F^2 (grid-stride over the columns, warp per column).
 template <typename TA>
 __global__ void k_sumsq(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda, double* acc2) {
@@ -1110,8 +1208,8 @@ __global__ void k_residual_finish(const double* acc2, double* err_out) {
 }
 
 cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, int64_t lda, const int32_t* J,
-                                const int32_t* k_ptr, const double* T, int64_t ldt, double* acc2,
-                                double* err_out, cudaStream_t s) {
+                                const int32_t* k_ptr, const double* T, int64_t ldt, int kcap, double* acc2,
+                                double* err_out, float* tsplit, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(acc2, 0, 2 * sizeof(double), s);
     if (e != cudaSuccess) return e;
     const int64_t ncmax = std::max<int64_t>(1, n - 1);
@@ -1122,7 +1220,13 @@ cudaError_t launch_residual_fro(const void* A, int a_f64, int64_t m, int64_t n, 
         k_residual_tiles<double><<<g, 256, 0, s>>>(static_cast<const double*>(A), m, n, lda, J, k_ptr, T, ldt, acc2);
         k_sumsq<double><<<gs, 256, 0, s>>>(static_cast<const double*>(A), m, n, lda, acc2);
     } else {
-        k_residual_tiles<float><<<g, 256, 0, s>>>(static_cast<const float*>(A), m, n, lda, J, k_ptr, T, ldt, acc2);
+        // T split into FP32 parts (kcap x (n - 1) each, ld kcap), then the float-pair tiles
+        float* Th = tsplit;
+        float* Tl = tsplit + static_cast<int64_t>(kcap) * ncmax;
+        const unsigned gsp = static_cast<unsigned>(std::min<int64_t>((ncmax * kcap + 255) / 256, 8LL * device_info().sm_count));
+        k_split_T<<<gsp, 256, 0, s>>>(T, ldt, k_ptr, n, kcap, Th, Tl);
+        k_residual_tiles_pair<<<g, 256, 0, s>>>(static_cast<const float*>(A), m, n, lda, J, k_ptr, Th, Tl, kcap,
+                                                 acc2);
         k_sumsq<float><<<gs, 256, 0, s>>>(static_cast<const float*>(A), m, n, lda, acc2);
     }
     e = cudaGetLastError();
