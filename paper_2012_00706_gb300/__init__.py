@@ -502,6 +502,30 @@ def id_backward(A: torch.Tensor, J: torch.Tensor, T: torch.Tensor, k: int, dAhat
     return out[0] if squeeze else out
 
 
+_PLAN_CACHE: "dict" = {}
+_PLAN_CACHE_SIZE = 4
+
+
+def _forward_plan(ac: torch.Tensor, k: int, lda: int) -> "BatchPlan":
+    """The bound PLAIN_F32 batch plan of IDFunction's forward for these matrices, kept for
+    the most recent few (shape, rank, strides, address): a repeated forward on the same
+    buffers only launches (no host tables, no table upload).  The plan keeps the matrices'
+    addresses only (they are part of the key), not the tensors, so the cache holds no
+    caller memory alive; the caller copies J and T out before the plan can run again."""
+    batch, m, n = ac.shape
+    key = (batch, m, n, k, lda, tuple(ac.stride()), ac.data_ptr(), ac.dtype, str(ac.device))
+    plan = _PLAN_CACHE.pop(key, None)
+    if plan is None:
+        plan = BatchPlan([(m, n)] * batch, [k] * batch, dtype=ac.dtype, precision="plain_f32",
+                         lda=[lda] * batch, device=ac.device)
+        plan.bind([ac[b] for b in range(batch)])
+        plan.mats = None
+    _PLAN_CACHE[key] = plan
+    while len(_PLAN_CACHE) > _PLAN_CACHE_SIZE:
+        _PLAN_CACHE.pop(next(iter(_PLAN_CACHE)))
+    return plan
+
+
 class IDFunction(torch.autograd.Function):
     """Differentiable column ID with the pivots held fixed.
 
@@ -522,13 +546,11 @@ class IDFunction(torch.autograd.Function):
             # the whole batch in one launch sequence: grouped pivoted QRs in waves, then
             # one batched solve; the ranks are read back once
             ac, lda, _ = _batched_colmajor(a, m)
-            plan = BatchPlan([(m, n)] * batch, [k] * batch, dtype=a.dtype, precision="plain_f32",
-                             lda=[lda] * batch, device=dev)
-            plan.bind([ac[b] for b in range(batch)])
+            plan = _forward_plan(ac, k, lda)
             plan.run()
             kinfo = torch.stack([plan.k_out, plan.info], dim=1).cpu()
-            Jt = plan.J[: batch * n].view(batch, n)
-            Tt = plan.T[: batch * k * (n - k)].view(batch, n - k, k).transpose(1, 2)
+            Jt = plan.J[: batch * n].view(batch, n).clone()
+            Tt = plan.T[: batch * k * (n - k)].view(batch, n - k, k).clone().transpose(1, 2)
         else:
             ws = torch.empty(id_workspace_size(m, n, a.dtype, k=k, precision="plain_f32"), dtype=torch.uint8,
                              device=dev)

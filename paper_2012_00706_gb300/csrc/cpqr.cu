@@ -131,6 +131,7 @@ template <> struct Vec16<float> {
         return make_float4(fmaf(m, p.x, x.x), fmaf(m, p.y, x.y), fmaf(m, p.z, x.z), fmaf(m, p.w, x.w));
     }
     static __device__ __forceinline__ float sq(const float4 a, float s) { return dot(a, a, s); }
+    static __device__ __forceinline__ void zero_first(float4& a) { a.x = 0.f; }
     static __device__ __forceinline__ float4 ldcg(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
 };
 template <> struct Vec16<double> {
@@ -143,6 +144,7 @@ template <> struct Vec16<double> {
         return make_double2(fma(m, p.x, x.x), fma(m, p.y, x.y));
     }
     static __device__ __forceinline__ double sq(const double2 a, double s) { return dot(a, a, s); }
+    static __device__ __forceinline__ void zero_first(double2& a) { a.x = 0.0; }
     static __device__ __forceinline__ double2 ldcg(const double* p) {
         return __ldcg(reinterpret_cast<const double2*>(p));
     }
@@ -491,12 +493,105 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     }
                 }
             };
+            // short FP32 columns (at most 16 vectors per lane): the column is read once into
+            // registers during the dot product and updated from there, one read and one write
+            // per step
+            constexpr int NVR = 16;
+            auto run_cols_reg = [&](auto xpv, auto xpw) {
+                const int64_t hd = min(r, (static_cast<int64_t>(j) + E - 1) / E * E);
+                const int64_t rd = hd + (r - hd) / E * E;
+                const int64_t nv = (rd - hd) / E;
+                for (int c = warp; c < nc; c += kGridWarps) {
+                    if (sel_s[c]) continue;
+                    T* x = col(c);
+                    V* xv = reinterpret_cast<V*>(x + hd);
+                    V xr[NVR];
+                    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+                    for (int u = 0; u < NVR; ++u) {
+                        const int64_t v = lane + 32 * u;
+                        if (v < nv) xr[u] = xv[v];
+                    }
+#pragma unroll
+                    for (int u = 0; u < NVR; ++u) {
+                        const int64_t v = lane + 32 * u;
+                        if (v < nv) {
+                            const V q = xpw(hd + v * E);
+                            if ((u & 3) == 0) s0 = VT::dot(xr[u], q, s0);
+                            else if ((u & 3) == 1) s1 = VT::dot(xr[u], q, s1);
+                            else if ((u & 3) == 2) s2 = VT::dot(xr[u], q, s2);
+                            else s3 = VT::dot(xr[u], q, s3);
+                        }
+                    }
+                    // the scalar head rows [j, hd) and tail rows [rd, r)
+                    const int64_t th = j + lane, tt = rd + lane;
+                    const bool in_h = th < hd, in_t = tt < r;
+                    const T xh = in_h ? x[th] : T(0), xt = in_t ? x[tt] : T(0);
+                    if (in_h) s0 = fma(xpv(th), xh, s0);
+                    if (in_t) s1 = fma(xpv(tt), xt, s1);
+                    T sdot = warp_sum((s0 + s1) + (s2 + s3));
+                    const T X = x[j];
+                    sdot = fma(-beta, X, sdot);
+                    const T tw = -sdot * rb;
+                    const T sv = tw * inv;
+                    const T rho = X - tw;
+                    const T nu = nu_s[c];
+                    bool rec = false;
+                    T d = nu;
+                    if (nu > T(0)) {
+                        d = fmax(nu - rho * rho, T(0));
+                        rec = d <= sqrt_u * nuref_s[c];
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                        if (nu > T(0) && !rec) nu_s[c] = d;
+                    }
+                    const T msv = -sv;
+                    T q0 = 0, q1 = 0;
+                    // rows above j + 1 leave the computation: row j is set to zero (its R entry is
+                    // out), so that the recomputed norm covers rows j + 1 .. r - 1 only
+                    if (in_h) {
+                        const T n0 = th == j ? T(0) : fma(msv, xpv(th), xh);
+                        x[th] = n0;
+                        q0 = n0 * n0;
+                    }
+                    if (in_t) {
+                        const T n0 = fma(msv, xpv(tt), xt);
+                        x[tt] = n0;
+                        q1 = n0 * n0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < NVR; ++u) {
+                        const int64_t v = lane + 32 * u;
+                        if (v < nv) {
+                            V a = VT::axpy(msv, xpw(hd + v * E), xr[u]);
+                            if (u == 0 && lane == 0 && hd == j) VT::zero_first(a);
+                            xv[v] = a;
+                            if (rec) q0 = VT::sq(a, q0);
+                        }
+                    }
+                    if (rec) {
+                        const T sq = warp_sum(q0 + q1);
+                        if (lane == 0) {
+                            nu_s[c] = sq;
+                            nuref_s[c] = sq;
+                        }
+                    }
+                }
+            };
             const bool vec = (ldx * static_cast<int64_t>(sizeof(T))) % 16 == 0 &&
                              (reinterpret_cast<uintptr_t>(Xs) & 15u) == 0;
             if (P.rstage > 0) {
                 for (int64_t t = j + tid; t < r; t += nt) xps_s[t] = __ldcg(xp + t);
                 __syncthreads();
-                if (vec)
+                bool reg = false;
+                if constexpr (sizeof(T) == 4) reg = vec && r - j <= static_cast<int64_t>(32) * NVR * E;
+                if (reg) {
+                    if constexpr (sizeof(T) == 4)
+                        run_cols_reg([&](int64_t t) { return xps_s[t]; },
+                                     [&](int64_t t) { return *reinterpret_cast<const V*>(xps_s + t); });
+                } else if (vec)
                     run_cols_vec([&](int64_t t) { return xps_s[t]; },
                                  [&](int64_t t) { return *reinterpret_cast<const V*>(xps_s + t); });
                 else
