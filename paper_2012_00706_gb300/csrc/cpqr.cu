@@ -62,6 +62,40 @@ __device__ T block_sum(T v, T* sh) {
     return sh[32];
 }
 
+// argmax of (value, index) with ties to the smaller index and a sum, in one pass (three
+// barriers); returns to all threads.
+__device__ void block_argmax_sum(double v, int idx, double part, double* shv, int* shi, double* shp, double* outv,
+                                 int* outi, double* outp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
+    }
+    __syncthreads();
+    if (lane == 0) { shv[warp] = v; shi[warp] = idx; shp[warp] = part; }
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? shv[lane] : -1.0;
+        idx = lane < nw ? shi[lane] : -1;
+        part = lane < nw ? shp[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
+        }
+        if (lane == 0) { shv[32] = v; shi[32] = idx; shp[32] = part; }
+    }
+    __syncthreads();
+    *outv = shv[32];
+    *outi = shi[32];
+    *outp = shp[32];
+}
+
 // argmax of (value, index) with ties to the smaller index; returns to all threads.
 __device__ void block_argmax(double v, int idx, double* shv, int* shi, double* outv, int* outi) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -96,13 +130,14 @@ struct GridShared {
     double shv[33];
     int shi[33];
     T shs[33];
+    double shp[33];
     int ok;
     int p, pg;
     double alpha, s2, sumnu, total;
 };
 
-// Dynamic shared memory of a CTA: residual norms and reference norms of its (at most cpb)
-// columns, the per-warp partial sums and reflector scalars of one super-group of
+// Dynamic shared memory of a CTA: residual norms, reference norms and (column mode) exact
+// squared norms below the step's row of its (at most cpb) columns, the per-warp partial sums and reflector scalars of one super-group of
 // min(cpb, kSuper) columns, the staged pivot column (rstage rows, column mode), the
 // super-group's recompute flags, and the columns' selection flags.
 __host__ __device__ inline int64_t grid_super(int64_t cpb) { return cpb < kSuper ? cpb : kSuper; }
@@ -114,7 +149,7 @@ __host__ __device__ inline int64_t grid_rstage_padded(int64_t rstage, int elem_b
 template <typename T>
 __host__ __device__ inline size_t grid_smem_bytes(int64_t cpb, int64_t rstage) {
     const size_t sup = static_cast<size_t>(grid_super(cpb));
-    return (2 * static_cast<size_t>(cpb) + (kGridWarps + 1) * sup +
+    return (3 * static_cast<size_t>(cpb) + (kGridWarps + 1) * sup +
             static_cast<size_t>(grid_rstage_padded(rstage, sizeof(T)))) * sizeof(T) +
            sup * sizeof(int) + ((static_cast<size_t>(cpb) + 15) & ~size_t(15));
 }
@@ -173,7 +208,8 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     T* xps_s = reinterpret_cast<T*>(smem_dyn);  // [rstage] staged pivot column (column mode)
     T* nu_s = xps_s + grid_rstage_padded(P.rstage, sizeof(T));
     T* nuref_s = nu_s + P.cpb_max;
-    T* red_s = nuref_s + P.cpb_max;             // [kGridWarps][sup]
+    T* s2_s = nuref_s + P.cpb_max;              // column mode: exact ||x(j+1:r)||^2 after step j
+    T* red_s = s2_s + P.cpb_max;                // [kGridWarps][sup]
     T* sv_s = red_s + kGridWarps * sup;
     int* rec_s = reinterpret_cast<int*>(sv_s + sup);
     uint8_t* sel_s = reinterpret_cast<uint8_t*>(rec_s + sup);
@@ -208,6 +244,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             if (!isfinite(static_cast<double>(s))) bad = true;
             nu_s[c] = s;
             nuref_s[c] = s;
+            s2_s[c] = s;
             sel_s[c] = 0;
             P.sel[c0 + c] = 0;
             local_total += s;
@@ -227,13 +264,17 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             part += nu_s[c];
             if (v > best) { best = v; bi = c; }
         }
-        double bv;
+        double bv, sumd;
         int bl;
-        block_argmax(best, bi, G_.shv, G_.shi, &bv, &bl);
-        const T sum = block_sum(part, G_.shs);
+        block_argmax_sum(best, bi, static_cast<double>(part), G_.shv, G_.shi, G_.shp, &bv, &bl, &sumd);
+        const T sum = static_cast<T>(sumd);
         T s2 = 0;
         T alpha = 0;
-        if (bl >= 0 && row < r) {
+        if (bl >= 0 && row < r && P.colmode) {
+            // column mode: the exact norm below the row, left by the column's warp
+            s2 = s2_s[bl];
+            alpha = col(bl)[row];
+        } else if (bl >= 0 && row < r) {
             // the candidate's exact squared norm: eight independent sums keep eight loads in
             // flight per thread (this pass is on every step's critical path)
             const T* x = col(bl);
@@ -285,10 +326,9 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                 sn += c.sumnu;
                 tt += c.total;
             }
-            double gv;
+            double gv, gsn;
             int gg;
-            block_argmax(bv, bg, G_.shv, G_.shi, &gv, &gg);
-            const double gsn = block_sum(sn, G_.shv);
+            block_argmax_sum(bv, bg, sn, G_.shv, G_.shi, G_.shp, &gv, &gg, &gsn);
             const double gtt = j == 0 ? block_sum(tt, G_.shv) : 0.0;
             if (tid == 0) {
                 G_.pg = gg;
@@ -372,19 +412,20 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                         const T n1 = fma(msv, xpv(t + 32), x[t + 32]);
                         x[t] = n0;
                         x[t + 32] = n1;
-                        if (rec) {
-                            q0 = fma(n0, n0, q0);
-                            q1 = fma(n1, n1, q1);
-                        }
+                        q0 = fma(n0, n0, q0);
+                        q1 = fma(n1, n1, q1);
                     }
                     for (; t < r; t += 32) {
                         const T n0 = fma(msv, xpv(t), x[t]);
                         x[t] = n0;
-                        if (rec) q0 = fma(n0, n0, q0);
+                        q0 = fma(n0, n0, q0);
                     }
-                    if (rec) {
-                        const T sq = warp_sum(q0 + q1);
-                        if (lane == 0) {
+                    // the exact squared norm below row j, for this step's record and, where
+                    // the downdate was refused, as the new norm
+                    const T sq = warp_sum(q0 + q1);
+                    if (lane == 0) {
+                        s2_s[c] = sq;
+                        if (rec) {
                             nu_s[c] = sq;
                             nuref_s[c] = sq;
                         }
@@ -471,22 +512,23 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                             for (int u = 0; u < 4; ++u) a[u] = VT::axpy(msv, xpw(hu + (v + 32 * u) * E), xv[v + 32 * u]);
 #pragma unroll
                             for (int u = 0; u < 4; ++u) xv[v + 32 * u] = a[u];
-                            if (rec) {
-                                q0 = VT::sq(a[0], q0);
-                                q1 = VT::sq(a[1], q1);
-                                q0 = VT::sq(a[2], q0);
-                                q1 = VT::sq(a[3], q1);
-                            }
+                            q0 = VT::sq(a[0], q0);
+                            q1 = VT::sq(a[1], q1);
+                            q0 = VT::sq(a[2], q0);
+                            q1 = VT::sq(a[3], q1);
                         }
                         for (; v < nv; v += 32) {
                             const V a = VT::axpy(msv, xpw(hu + v * E), xv[v]);
                             xv[v] = a;
-                            if (rec) q0 = VT::sq(a, q0);
+                            q0 = VT::sq(a, q0);
                         }
                     }
-                    if (rec) {
-                        const T sq = warp_sum(q0 + q1);
-                        if (lane == 0) {
+                    // the exact squared norm below row j, for this step's record and, where
+                    // the downdate was refused, as the new norm
+                    const T sq = warp_sum(q0 + q1);
+                    if (lane == 0) {
+                        s2_s[c] = sq;
+                        if (rec) {
                             nu_s[c] = sq;
                             nuref_s[c] = sq;
                         }
@@ -568,12 +610,15 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                             V a = VT::axpy(msv, xpw(hd + v * E), xr[u]);
                             if (u == 0 && lane == 0 && hd == j) VT::zero_first(a);
                             xv[v] = a;
-                            if (rec) q0 = VT::sq(a, q0);
+                            q0 = VT::sq(a, q0);
                         }
                     }
-                    if (rec) {
-                        const T sq = warp_sum(q0 + q1);
-                        if (lane == 0) {
+                    // the exact squared norm below row j, for this step's record and, where
+                    // the downdate was refused, as the new norm
+                    const T sq = warp_sum(q0 + q1);
+                    if (lane == 0) {
+                        s2_s[c] = sq;
+                        if (rec) {
                             nu_s[c] = sq;
                             nuref_s[c] = sq;
                         }
