@@ -450,6 +450,14 @@ id_status_t id_set_stage_events(void* const* events, int32_t count);
  * Synchronises the stream.  Errors: ID_ERR_ARG, ID_ERR_CUDA. */
 id_status_t id_probe_fma_peak(int32_t which, double* tflops, void* stream);
 
+/* Self-check (not part of the computation): widens every one of the 2^32 FP32 bit
+ * patterns to FP64 with the integer routine the FP32 pivoted-QR kernels use to store
+ * their R entries (IEEE 754 binary32 -> binary64: exponent rebiased, significand moved,
+ * subnormals normalised) and with the hardware conversion, and writes to *mismatches
+ * (host output) how many differ in bits (a NaN need only stay a NaN).  About 10 ms;
+ * synchronises the stream.  Errors: ID_ERR_ARG (mismatches NULL), ID_ERR_CUDA. */
+id_status_t id_check_widen(uint64_t* mismatches, void* stream);
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char* id_status_string(id_status_t status);
 

@@ -20,7 +20,7 @@ import torch
 __all__ = [
     "PRECISIONS", "IDResult", "load", "id_factor", "id_sketch", "id_scale_cast", "id_workspace_size",
     "status_string", "lib_path", "set_stage_events", "id_backward", "id_reconstruct", "IDFunction",
-    "BatchPlan", "shard_batch", "probe_fma_peak", "low_cast", "reconstruct", "id_factor_adaptive",
+    "BatchPlan", "shard_batch", "probe_fma_peak", "check_widen", "low_cast", "reconstruct", "id_factor_adaptive",
     "id_factor_rows", "id_factor_two_sided",
 ]
 
@@ -110,6 +110,8 @@ def load():
         lib.id_batch_shard.argtypes = [i32, p, p, p, i32, i32, p, p]
         lib.id_probe_fma_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), p]
         lib.id_probe_fma_peak.restype = ctypes.c_int
+        lib.id_check_widen.argtypes = [ctypes.POINTER(ctypes.c_uint64), p]
+        lib.id_check_widen.restype = ctypes.c_int
         lib.id_adaptive_workspace_size.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(IDOpts), i32, i32,
                                                    ctypes.POINTER(sz)]
         lib.id_adaptive_workspace_size.restype = ctypes.c_int
@@ -266,6 +268,15 @@ def probe_fma_peak(which: str = "fp32", stream=None) -> float:
     _check(load().id_probe_fma_peak({"fp32": 0, "fp64": 1}[which], ctypes.byref(t), _stream_ptr(stream)),
            "id_probe_fma_peak")
     return t.value
+
+
+def check_widen(stream=None) -> int:
+    """Number of FP32 bit patterns (of all 2^32) whose integer widening to FP64, the one
+    the FP32 pivoted-QR kernels store R with, differs from the hardware conversion
+    (a self-check; 0 expected).  Synchronises."""
+    n = ctypes.c_uint64(0)
+    _check(load().id_check_widen(ctypes.byref(n), _stream_ptr(stream)), "id_check_widen")
+    return int(n.value)
 
 
 def id_factor_adaptive(A: torch.Tensor, tol: float, k_max: int, omega: torch.Tensor, *, block: int = 16,

@@ -238,6 +238,38 @@ __device__ __forceinline__ void tmem_st_wait() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// ------------------------------------------------- FP32 -> FP64 in integers
+
+// Exact widening of an IEEE binary32 value to binary64 by its bits: the exponent is
+// rebiased from 127 to 1023 (+896) and the 23-bit significand moves to the top of the
+// 52-bit one; a subnormal float is normalised by its leading zeros; zeros, infinities
+// and NaNs keep their class.  GB300's FP64 pipe converts at a small fraction of the
+// FP32 rate, so kernels that compute in FP32 and store FP64 (the R factors) widen here
+// on the integer pipe instead of stalling a warp on the FP64 pipe every pivot step.
+__device__ __forceinline__ double f64_of_f32(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t a = u & 0x7fffffffu;
+    uint32_t hi = (a >> 3) + (896u << 20);
+    uint32_t lo = a << 29;
+    if (a - 0x00800000u >= 0x7f000000u) {     // not a normal float
+        if (a >= 0x7f800000u) {
+            hi = 0x7ff00000u | ((a & 0x007fffffu) >> 3);
+        } else if (a == 0u) {
+            hi = 0u;
+        } else {
+            const int sh = __clz(static_cast<int>(a)) - 8;          // bit 23 after the shift
+            const uint32_t m = (a << sh) & 0x007fffffu;
+            hi = ((897u - static_cast<uint32_t>(sh)) << 20) | (m >> 3);
+            lo = m << 29;
+        }
+    }
+    return __hiloint2double(static_cast<int>(hi | (u & 0x80000000u)), static_cast<int>(lo));
+}
+
+// R entries and candidate records are FP64 whatever the working precision.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f64_of_f32(x); }
+
 // ------------------------------------------------------------ warp helpers
 
 template <typename T>

@@ -255,18 +255,20 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     // ---- publish this slice's best candidate for the step with row `row` (exact squared
     // norm of its rows row..r-1, its entry on row `row`)
     auto publish = [&](int slot, int row, double total) {
-        double best = -1.0;
+        // compared in the working precision (widening is exact and monotone), widened once
+        T bestw = T(-1);
         int bi = -1;
         T part = 0;
         for (int c = tid; c < nc; c += nt) {
             if (sel_s[c]) continue;
-            const double v = static_cast<double>(nu_s[c]);
-            part += nu_s[c];
-            if (v > best) { best = v; bi = c; }
+            const T v = nu_s[c];
+            part += v;
+            if (v > bestw) { bestw = v; bi = c; }
         }
         double bv, sumd;
         int bl;
-        block_argmax_sum(best, bi, static_cast<double>(part), G_.shv, G_.shi, G_.shp, &bv, &bl, &sumd);
+        block_argmax_sum(bi >= 0 ? to_f64(bestw) : -1.0, bi, to_f64(part), G_.shv, G_.shi, G_.shp, &bv, &bl,
+                         &sumd);
         const T sum = static_cast<T>(sumd);
         T s2 = 0;
         T alpha = 0;
@@ -295,10 +297,10 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
         if (tid == 0) {
             Cand cd;
             cd.nu = bv;
-            cd.sumnu = static_cast<double>(sum);
+            cd.sumnu = to_f64(sum);
             cd.total = total;
-            cd.s2 = static_cast<double>(s2);
-            cd.alpha = static_cast<double>(alpha);
+            cd.s2 = to_f64(s2);
+            cd.alpha = to_f64(alpha);
             cd.idx = bl >= 0 ? static_cast<int>(c0 + bl) : -1;
             cd.stamp = 0;
             P.cand[slot * G + b] = cd;
@@ -365,7 +367,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             sel_s[p - c0] = 1;
             P.sel[p] = 1;
             P.J[j] = p;
-            P.R[static_cast<int64_t>(p) * P.ldr + j] = static_cast<double>(beta);
+            P.R[static_cast<int64_t>(p) * P.ldr + j] = to_f64(beta);
         }
         __syncthreads();
         if (P.colmode) {
@@ -401,7 +403,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     }
                     __syncwarp();
                     if (lane == 0) {
-                        P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                        P.R[(c0 + c) * P.ldr + j] = to_f64(rho);
                         if (nu > T(0) && !rec) nu_s[c] = d;
                     }
                     const T msv = -sv;
@@ -485,7 +487,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     }
                     __syncwarp();
                     if (lane == 0) {
-                        P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                        P.R[(c0 + c) * P.ldr + j] = to_f64(rho);
                         if (nu > T(0) && !rec) nu_s[c] = d;
                     }
                     const T msv = -sv;
@@ -586,7 +588,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     }
                     __syncwarp();
                     if (lane == 0) {
-                        P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                        P.R[(c0 + c) * P.ldr + j] = to_f64(rho);
                         if (nu > T(0) && !rec) nu_s[c] = d;
                     }
                     const T msv = -sv;
@@ -694,7 +696,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     const T tw = -s * rb;
                     sv = tw * inv;
                     const T rho = X - tw;
-                    P.R[(c0 + c) * P.ldr + j] = static_cast<double>(rho);
+                    P.R[(c0 + c) * P.ldr + j] = to_f64(rho);
                     // downdate; an exact recompute where cancellation has eaten sqrt(u)
                     const T nu = nu_s[c];
                     if (nu > T(0)) {

@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
     const int rb = qq * RPT;                 // first row of this thread's block
     const float sqrt_u = 2.44140625e-04f;    // sqrt of the FP32 unit round-off 2^-24
     const bool need_sum = W.rel_tol > 0.0;
+    const float rtol = static_cast<float>(W.rel_tol);   // converted once, off the FP64 pipe's per-step path
 
     if (t == 0) {
         mbar_init(&recv_bar[0], 1);
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         const int p = key_index(best);
         const float hv = best ? key_norm(best) : -1.f;
         if (total < 0.f) total = hs;
-        if (need_sum && sqrtf(fmaxf(hs, 0.f)) <= static_cast<float>(W.rel_tol) * sqrtf(total)) break;
+        if (need_sum && sqrtf(fmaxf(hs, 0.f)) <= rtol * sqrtf(total)) break;
         if (p < 0 || !(hv > 0.f)) {
             if (me == 0 && t == 0) set_info(W.info, j + 1);
             break;
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         if (valid && i == p) {
             selected = true;
             if (qq == 0) {
-                W.R[i * W.ldr + j] = static_cast<double>(beta);
+                W.R[i * W.ldr + j] = f64_of_f32(beta);
                 W.J[j] = p;
                 W.sel[i] = 1;
             }
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         const float tw = -S * rbeta;                        // tau w
         const float sv = selected ? 0.f : tw * inv;         // the pivot column itself stays
         const float rho = X - tw;
-        if (!selected && qq == 0) W.R[i * W.ldr + j] = static_cast<double>(rho);
+        if (!selected && qq == 0) W.R[i * W.ldr + j] = f64_of_f32(rho);
         // norm downdate nu - rho^2 = nu (1 - (rho / sqrt(nu))^2); an exact recompute where
         // cancellation has left at most sqrt(u) of the reference norm
         bool recompute = false;

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
                 rec->sumnu = sum;
                 rec->total = step == 0 ? sum : 0.0;
                 rec->s2 = bi >= 0 && step < r ? bv : 0.0;   // nu is the exact norm of rows step..r-1
-                rec->alpha = static_cast<double>(alpha);
+                rec->alpha = to_f64(alpha);
                 rec->idx = bi >= 0 ? static_cast<int>(c0 + bi) : -1;
                 __threadfence();
                 st_release_s32(&rec->stamp, step + 1);
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
             sel_s[cp] = 1;
             P.sel[p] = 1;
             P.J[j] = p;
-            P.R[static_cast<int64_t>(p) * P.ldr + j] = static_cast<double>(beta);
+            P.R[static_cast<int64_t>(p) * P.ldr + j] = to_f64(beta);
         }
         // ---- this warp's unselected columns
         for (int c = warp; c < nc; c += kResWarps) {
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
             S = fma(-beta, X, S);
             const T tw = -S * rbeta;
             const T sv = tw * inv;
-            if (lane == 0) P.R[(c0 + c) * P.ldr + j] = static_cast<double>(X - tw);
+            if (lane == 0) P.R[(c0 + c) * P.ldr + j] = to_f64(X - tw);
             T q0 = 0, q1 = 0;
             t = j + 1 + lane;
             for (; t + 32 < r; t += 64) {

@@ -59,8 +59,43 @@ cudaError_t probe(int iters, double* tflops, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// Every float bit pattern u = base + i (i < count) widened by f64_of_f32 and by the
+// hardware conversion: the bits must agree, except that a NaN need only stay a NaN (the
+// hardware may return a canonical NaN).  The mismatches are counted.
+__global__ void k_widen_check(uint64_t base, uint64_t count, unsigned long long* mismatches) {
+    unsigned long long bad = 0;
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < count;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const float x = __uint_as_float(static_cast<uint32_t>(base + i));
+        const double a = f64_of_f32(x);
+        const double b = static_cast<double>(x);
+        if (isnan(x) ? !isnan(a) : __double_as_longlong(a) != __double_as_longlong(b)) ++bad;
+    }
+    if (bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace
 }  // namespace gid
+
+extern "C" id_status_t id_check_widen(uint64_t* mismatches, void* stream) {
+    if (!mismatches) return ID_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        const gid::DeviceInfo& dev = gid::device_info();
+        gid::k_widen_check<<<dev.sm_count * 8, 256, 0, s>>>(0ull, 1ull << 32, d);
+        e = cudaGetLastError();
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (d) cudaFreeAsync(d, s);
+    if (e != cudaSuccess) return ID_ERR_CUDA;
+    *mismatches = h;
+    return ID_OK;
+}
 
 extern "C" id_status_t id_probe_fma_peak(int32_t which, double* tflops, void* stream) {
     if (!tflops || (which != 0 && which != 1)) return ID_ERR_ARG;

@@ -93,3 +93,7 @@ def test_factor_rejects_null_outputs(lib):
     o.k = 3
     code = lib.id_factor(None, 0, 10, 5, 10, ctypes.byref(o), None, None, 3, None, None, None, None, 0, None)
     assert code == 1
+
+
+def test_check_widen_rejects_null_output(lib):
+    assert lib.id_check_widen(None, None) == 1

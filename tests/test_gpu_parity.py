@@ -145,6 +145,12 @@ def test_sketch_identity_reproduces_cast(gid, dev, orc, precision):
     assert bad.size == 0, (int(bad.size), np.argwhere(normal)[bad[:5]].tolist())
 
 
+def test_widen_f32_to_f64_matches_hardware(gid, dev):
+    """The integer FP32 -> FP64 widening the FP32 pivoted-QR kernels store R with equals the
+    hardware conversion on all 2^32 bit patterns (zeros, subnormals, infinities, NaNs)."""
+    assert gid.check_widen() == 0
+
+
 def test_scale_cast_nonfinite(gid, dev):
     a = np.ones((70, 4))
     a[65, 2] = np.inf
