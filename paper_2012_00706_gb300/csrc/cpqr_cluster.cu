@@ -161,179 +161,93 @@ __device__ __forceinline__ void st_async_peer(uint32_t dst_cluster, float4 v, ui
                  : "memory");
 }
 
-// x[u] for a warp-uniform u (a uniform switch, no local memory).
+// End of a pivot step for a warp-uniform register index u (a uniform switch, no local
+// memory): x[u] = 0 where `own` holds (the step's row leaves the column), and x[(u + 1) % RPT]
+// is returned (the next step's row, held by this thread or by the next one of the group).
 template <int RPT>
-__device__ __forceinline__ float pick_row(const float (&x)[RPT], int u) {
+__device__ __forceinline__ float zero_and_next(float (&x)[RPT], int u, bool own) {
     switch (u) {
-        case 0: if constexpr (RPT > 0) return x[0]; else return 0.f;
-        case 1: if constexpr (RPT > 1) return x[1]; else return 0.f;
-        case 2: if constexpr (RPT > 2) return x[2]; else return 0.f;
-        case 3: if constexpr (RPT > 3) return x[3]; else return 0.f;
-        case 4: if constexpr (RPT > 4) return x[4]; else return 0.f;
-        case 5: if constexpr (RPT > 5) return x[5]; else return 0.f;
-        case 6: if constexpr (RPT > 6) return x[6]; else return 0.f;
-        case 7: if constexpr (RPT > 7) return x[7]; else return 0.f;
-        case 8: if constexpr (RPT > 8) return x[8]; else return 0.f;
-        case 9: if constexpr (RPT > 9) return x[9]; else return 0.f;
-        case 10: if constexpr (RPT > 10) return x[10]; else return 0.f;
-        case 11: if constexpr (RPT > 11) return x[11]; else return 0.f;
-        case 12: if constexpr (RPT > 12) return x[12]; else return 0.f;
-        case 13: if constexpr (RPT > 13) return x[13]; else return 0.f;
-        case 14: if constexpr (RPT > 14) return x[14]; else return 0.f;
-        case 15: if constexpr (RPT > 15) return x[15]; else return 0.f;
-        case 16: if constexpr (RPT > 16) return x[16]; else return 0.f;
-        case 17: if constexpr (RPT > 17) return x[17]; else return 0.f;
-        case 18: if constexpr (RPT > 18) return x[18]; else return 0.f;
-        case 19: if constexpr (RPT > 19) return x[19]; else return 0.f;
-        case 20: if constexpr (RPT > 20) return x[20]; else return 0.f;
-        case 21: if constexpr (RPT > 21) return x[21]; else return 0.f;
-        case 22: if constexpr (RPT > 22) return x[22]; else return 0.f;
-        case 23: if constexpr (RPT > 23) return x[23]; else return 0.f;
-        case 24: if constexpr (RPT > 24) return x[24]; else return 0.f;
-        case 25: if constexpr (RPT > 25) return x[25]; else return 0.f;
-        case 26: if constexpr (RPT > 26) return x[26]; else return 0.f;
-        case 27: if constexpr (RPT > 27) return x[27]; else return 0.f;
-        case 28: if constexpr (RPT > 28) return x[28]; else return 0.f;
-        case 29: if constexpr (RPT > 29) return x[29]; else return 0.f;
-        case 30: if constexpr (RPT > 30) return x[30]; else return 0.f;
-        case 31: if constexpr (RPT > 31) return x[31]; else return 0.f;
-        case 32: if constexpr (RPT > 32) return x[32]; else return 0.f;
-        case 33: if constexpr (RPT > 33) return x[33]; else return 0.f;
-        case 34: if constexpr (RPT > 34) return x[34]; else return 0.f;
-        case 35: if constexpr (RPT > 35) return x[35]; else return 0.f;
-        case 36: if constexpr (RPT > 36) return x[36]; else return 0.f;
-        case 37: if constexpr (RPT > 37) return x[37]; else return 0.f;
-        case 38: if constexpr (RPT > 38) return x[38]; else return 0.f;
-        case 39: if constexpr (RPT > 39) return x[39]; else return 0.f;
-        case 40: if constexpr (RPT > 40) return x[40]; else return 0.f;
-        case 41: if constexpr (RPT > 41) return x[41]; else return 0.f;
-        case 42: if constexpr (RPT > 42) return x[42]; else return 0.f;
-        case 43: if constexpr (RPT > 43) return x[43]; else return 0.f;
-        case 44: if constexpr (RPT > 44) return x[44]; else return 0.f;
-        case 45: if constexpr (RPT > 45) return x[45]; else return 0.f;
-        case 46: if constexpr (RPT > 46) return x[46]; else return 0.f;
-        case 47: if constexpr (RPT > 47) return x[47]; else return 0.f;
-        case 48: if constexpr (RPT > 48) return x[48]; else return 0.f;
-        case 49: if constexpr (RPT > 49) return x[49]; else return 0.f;
-        case 50: if constexpr (RPT > 50) return x[50]; else return 0.f;
-        case 51: if constexpr (RPT > 51) return x[51]; else return 0.f;
-        case 52: if constexpr (RPT > 52) return x[52]; else return 0.f;
-        case 53: if constexpr (RPT > 53) return x[53]; else return 0.f;
-        case 54: if constexpr (RPT > 54) return x[54]; else return 0.f;
-        case 55: if constexpr (RPT > 55) return x[55]; else return 0.f;
-        case 56: if constexpr (RPT > 56) return x[56]; else return 0.f;
-        case 57: if constexpr (RPT > 57) return x[57]; else return 0.f;
-        case 58: if constexpr (RPT > 58) return x[58]; else return 0.f;
-        case 59: if constexpr (RPT > 59) return x[59]; else return 0.f;
-        case 60: if constexpr (RPT > 60) return x[60]; else return 0.f;
-        case 61: if constexpr (RPT > 61) return x[61]; else return 0.f;
-        case 62: if constexpr (RPT > 62) return x[62]; else return 0.f;
-        case 63: if constexpr (RPT > 63) return x[63]; else return 0.f;
-        case 64: if constexpr (RPT > 64) return x[64]; else return 0.f;
-        case 65: if constexpr (RPT > 65) return x[65]; else return 0.f;
-        case 66: if constexpr (RPT > 66) return x[66]; else return 0.f;
-        case 67: if constexpr (RPT > 67) return x[67]; else return 0.f;
-        case 68: if constexpr (RPT > 68) return x[68]; else return 0.f;
-        case 69: if constexpr (RPT > 69) return x[69]; else return 0.f;
-        case 70: if constexpr (RPT > 70) return x[70]; else return 0.f;
-        case 71: if constexpr (RPT > 71) return x[71]; else return 0.f;
-        case 72: if constexpr (RPT > 72) return x[72]; else return 0.f;
-        case 73: if constexpr (RPT > 73) return x[73]; else return 0.f;
-        case 74: if constexpr (RPT > 74) return x[74]; else return 0.f;
-        case 75: if constexpr (RPT > 75) return x[75]; else return 0.f;
-        case 76: if constexpr (RPT > 76) return x[76]; else return 0.f;
-        case 77: if constexpr (RPT > 77) return x[77]; else return 0.f;
-        case 78: if constexpr (RPT > 78) return x[78]; else return 0.f;
-        case 79: if constexpr (RPT > 79) return x[79]; else return 0.f;
+        case 0: if constexpr (RPT > 0) { x[0] = own ? 0.f : x[0]; return x[(0 + 1) % RPT]; } return 0.f;
+        case 1: if constexpr (RPT > 1) { x[1] = own ? 0.f : x[1]; return x[(1 + 1) % RPT]; } return 0.f;
+        case 2: if constexpr (RPT > 2) { x[2] = own ? 0.f : x[2]; return x[(2 + 1) % RPT]; } return 0.f;
+        case 3: if constexpr (RPT > 3) { x[3] = own ? 0.f : x[3]; return x[(3 + 1) % RPT]; } return 0.f;
+        case 4: if constexpr (RPT > 4) { x[4] = own ? 0.f : x[4]; return x[(4 + 1) % RPT]; } return 0.f;
+        case 5: if constexpr (RPT > 5) { x[5] = own ? 0.f : x[5]; return x[(5 + 1) % RPT]; } return 0.f;
+        case 6: if constexpr (RPT > 6) { x[6] = own ? 0.f : x[6]; return x[(6 + 1) % RPT]; } return 0.f;
+        case 7: if constexpr (RPT > 7) { x[7] = own ? 0.f : x[7]; return x[(7 + 1) % RPT]; } return 0.f;
+        case 8: if constexpr (RPT > 8) { x[8] = own ? 0.f : x[8]; return x[(8 + 1) % RPT]; } return 0.f;
+        case 9: if constexpr (RPT > 9) { x[9] = own ? 0.f : x[9]; return x[(9 + 1) % RPT]; } return 0.f;
+        case 10: if constexpr (RPT > 10) { x[10] = own ? 0.f : x[10]; return x[(10 + 1) % RPT]; } return 0.f;
+        case 11: if constexpr (RPT > 11) { x[11] = own ? 0.f : x[11]; return x[(11 + 1) % RPT]; } return 0.f;
+        case 12: if constexpr (RPT > 12) { x[12] = own ? 0.f : x[12]; return x[(12 + 1) % RPT]; } return 0.f;
+        case 13: if constexpr (RPT > 13) { x[13] = own ? 0.f : x[13]; return x[(13 + 1) % RPT]; } return 0.f;
+        case 14: if constexpr (RPT > 14) { x[14] = own ? 0.f : x[14]; return x[(14 + 1) % RPT]; } return 0.f;
+        case 15: if constexpr (RPT > 15) { x[15] = own ? 0.f : x[15]; return x[(15 + 1) % RPT]; } return 0.f;
+        case 16: if constexpr (RPT > 16) { x[16] = own ? 0.f : x[16]; return x[(16 + 1) % RPT]; } return 0.f;
+        case 17: if constexpr (RPT > 17) { x[17] = own ? 0.f : x[17]; return x[(17 + 1) % RPT]; } return 0.f;
+        case 18: if constexpr (RPT > 18) { x[18] = own ? 0.f : x[18]; return x[(18 + 1) % RPT]; } return 0.f;
+        case 19: if constexpr (RPT > 19) { x[19] = own ? 0.f : x[19]; return x[(19 + 1) % RPT]; } return 0.f;
+        case 20: if constexpr (RPT > 20) { x[20] = own ? 0.f : x[20]; return x[(20 + 1) % RPT]; } return 0.f;
+        case 21: if constexpr (RPT > 21) { x[21] = own ? 0.f : x[21]; return x[(21 + 1) % RPT]; } return 0.f;
+        case 22: if constexpr (RPT > 22) { x[22] = own ? 0.f : x[22]; return x[(22 + 1) % RPT]; } return 0.f;
+        case 23: if constexpr (RPT > 23) { x[23] = own ? 0.f : x[23]; return x[(23 + 1) % RPT]; } return 0.f;
+        case 24: if constexpr (RPT > 24) { x[24] = own ? 0.f : x[24]; return x[(24 + 1) % RPT]; } return 0.f;
+        case 25: if constexpr (RPT > 25) { x[25] = own ? 0.f : x[25]; return x[(25 + 1) % RPT]; } return 0.f;
+        case 26: if constexpr (RPT > 26) { x[26] = own ? 0.f : x[26]; return x[(26 + 1) % RPT]; } return 0.f;
+        case 27: if constexpr (RPT > 27) { x[27] = own ? 0.f : x[27]; return x[(27 + 1) % RPT]; } return 0.f;
+        case 28: if constexpr (RPT > 28) { x[28] = own ? 0.f : x[28]; return x[(28 + 1) % RPT]; } return 0.f;
+        case 29: if constexpr (RPT > 29) { x[29] = own ? 0.f : x[29]; return x[(29 + 1) % RPT]; } return 0.f;
+        case 30: if constexpr (RPT > 30) { x[30] = own ? 0.f : x[30]; return x[(30 + 1) % RPT]; } return 0.f;
+        case 31: if constexpr (RPT > 31) { x[31] = own ? 0.f : x[31]; return x[(31 + 1) % RPT]; } return 0.f;
+        case 32: if constexpr (RPT > 32) { x[32] = own ? 0.f : x[32]; return x[(32 + 1) % RPT]; } return 0.f;
+        case 33: if constexpr (RPT > 33) { x[33] = own ? 0.f : x[33]; return x[(33 + 1) % RPT]; } return 0.f;
+        case 34: if constexpr (RPT > 34) { x[34] = own ? 0.f : x[34]; return x[(34 + 1) % RPT]; } return 0.f;
+        case 35: if constexpr (RPT > 35) { x[35] = own ? 0.f : x[35]; return x[(35 + 1) % RPT]; } return 0.f;
+        case 36: if constexpr (RPT > 36) { x[36] = own ? 0.f : x[36]; return x[(36 + 1) % RPT]; } return 0.f;
+        case 37: if constexpr (RPT > 37) { x[37] = own ? 0.f : x[37]; return x[(37 + 1) % RPT]; } return 0.f;
+        case 38: if constexpr (RPT > 38) { x[38] = own ? 0.f : x[38]; return x[(38 + 1) % RPT]; } return 0.f;
+        case 39: if constexpr (RPT > 39) { x[39] = own ? 0.f : x[39]; return x[(39 + 1) % RPT]; } return 0.f;
+        case 40: if constexpr (RPT > 40) { x[40] = own ? 0.f : x[40]; return x[(40 + 1) % RPT]; } return 0.f;
+        case 41: if constexpr (RPT > 41) { x[41] = own ? 0.f : x[41]; return x[(41 + 1) % RPT]; } return 0.f;
+        case 42: if constexpr (RPT > 42) { x[42] = own ? 0.f : x[42]; return x[(42 + 1) % RPT]; } return 0.f;
+        case 43: if constexpr (RPT > 43) { x[43] = own ? 0.f : x[43]; return x[(43 + 1) % RPT]; } return 0.f;
+        case 44: if constexpr (RPT > 44) { x[44] = own ? 0.f : x[44]; return x[(44 + 1) % RPT]; } return 0.f;
+        case 45: if constexpr (RPT > 45) { x[45] = own ? 0.f : x[45]; return x[(45 + 1) % RPT]; } return 0.f;
+        case 46: if constexpr (RPT > 46) { x[46] = own ? 0.f : x[46]; return x[(46 + 1) % RPT]; } return 0.f;
+        case 47: if constexpr (RPT > 47) { x[47] = own ? 0.f : x[47]; return x[(47 + 1) % RPT]; } return 0.f;
+        case 48: if constexpr (RPT > 48) { x[48] = own ? 0.f : x[48]; return x[(48 + 1) % RPT]; } return 0.f;
+        case 49: if constexpr (RPT > 49) { x[49] = own ? 0.f : x[49]; return x[(49 + 1) % RPT]; } return 0.f;
+        case 50: if constexpr (RPT > 50) { x[50] = own ? 0.f : x[50]; return x[(50 + 1) % RPT]; } return 0.f;
+        case 51: if constexpr (RPT > 51) { x[51] = own ? 0.f : x[51]; return x[(51 + 1) % RPT]; } return 0.f;
+        case 52: if constexpr (RPT > 52) { x[52] = own ? 0.f : x[52]; return x[(52 + 1) % RPT]; } return 0.f;
+        case 53: if constexpr (RPT > 53) { x[53] = own ? 0.f : x[53]; return x[(53 + 1) % RPT]; } return 0.f;
+        case 54: if constexpr (RPT > 54) { x[54] = own ? 0.f : x[54]; return x[(54 + 1) % RPT]; } return 0.f;
+        case 55: if constexpr (RPT > 55) { x[55] = own ? 0.f : x[55]; return x[(55 + 1) % RPT]; } return 0.f;
+        case 56: if constexpr (RPT > 56) { x[56] = own ? 0.f : x[56]; return x[(56 + 1) % RPT]; } return 0.f;
+        case 57: if constexpr (RPT > 57) { x[57] = own ? 0.f : x[57]; return x[(57 + 1) % RPT]; } return 0.f;
+        case 58: if constexpr (RPT > 58) { x[58] = own ? 0.f : x[58]; return x[(58 + 1) % RPT]; } return 0.f;
+        case 59: if constexpr (RPT > 59) { x[59] = own ? 0.f : x[59]; return x[(59 + 1) % RPT]; } return 0.f;
+        case 60: if constexpr (RPT > 60) { x[60] = own ? 0.f : x[60]; return x[(60 + 1) % RPT]; } return 0.f;
+        case 61: if constexpr (RPT > 61) { x[61] = own ? 0.f : x[61]; return x[(61 + 1) % RPT]; } return 0.f;
+        case 62: if constexpr (RPT > 62) { x[62] = own ? 0.f : x[62]; return x[(62 + 1) % RPT]; } return 0.f;
+        case 63: if constexpr (RPT > 63) { x[63] = own ? 0.f : x[63]; return x[(63 + 1) % RPT]; } return 0.f;
+        case 64: if constexpr (RPT > 64) { x[64] = own ? 0.f : x[64]; return x[(64 + 1) % RPT]; } return 0.f;
+        case 65: if constexpr (RPT > 65) { x[65] = own ? 0.f : x[65]; return x[(65 + 1) % RPT]; } return 0.f;
+        case 66: if constexpr (RPT > 66) { x[66] = own ? 0.f : x[66]; return x[(66 + 1) % RPT]; } return 0.f;
+        case 67: if constexpr (RPT > 67) { x[67] = own ? 0.f : x[67]; return x[(67 + 1) % RPT]; } return 0.f;
+        case 68: if constexpr (RPT > 68) { x[68] = own ? 0.f : x[68]; return x[(68 + 1) % RPT]; } return 0.f;
+        case 69: if constexpr (RPT > 69) { x[69] = own ? 0.f : x[69]; return x[(69 + 1) % RPT]; } return 0.f;
+        case 70: if constexpr (RPT > 70) { x[70] = own ? 0.f : x[70]; return x[(70 + 1) % RPT]; } return 0.f;
+        case 71: if constexpr (RPT > 71) { x[71] = own ? 0.f : x[71]; return x[(71 + 1) % RPT]; } return 0.f;
+        case 72: if constexpr (RPT > 72) { x[72] = own ? 0.f : x[72]; return x[(72 + 1) % RPT]; } return 0.f;
+        case 73: if constexpr (RPT > 73) { x[73] = own ? 0.f : x[73]; return x[(73 + 1) % RPT]; } return 0.f;
+        case 74: if constexpr (RPT > 74) { x[74] = own ? 0.f : x[74]; return x[(74 + 1) % RPT]; } return 0.f;
+        case 75: if constexpr (RPT > 75) { x[75] = own ? 0.f : x[75]; return x[(75 + 1) % RPT]; } return 0.f;
+        case 76: if constexpr (RPT > 76) { x[76] = own ? 0.f : x[76]; return x[(76 + 1) % RPT]; } return 0.f;
+        case 77: if constexpr (RPT > 77) { x[77] = own ? 0.f : x[77]; return x[(77 + 1) % RPT]; } return 0.f;
+        case 78: if constexpr (RPT > 78) { x[78] = own ? 0.f : x[78]; return x[(78 + 1) % RPT]; } return 0.f;
+        case 79: if constexpr (RPT > 79) { x[79] = own ? 0.f : x[79]; return x[(79 + 1) % RPT]; } return 0.f;
         default: return 0.f;
-    }
-}
-
-// x[u] = 0 where `own` holds (u warp-uniform).
-template <int RPT>
-__device__ __forceinline__ void zero_row(float (&x)[RPT], int u, bool own) {
-    switch (u) {
-        case 0: if constexpr (RPT > 0) x[0] = own ? 0.f : x[0]; break;
-        case 1: if constexpr (RPT > 1) x[1] = own ? 0.f : x[1]; break;
-        case 2: if constexpr (RPT > 2) x[2] = own ? 0.f : x[2]; break;
-        case 3: if constexpr (RPT > 3) x[3] = own ? 0.f : x[3]; break;
-        case 4: if constexpr (RPT > 4) x[4] = own ? 0.f : x[4]; break;
-        case 5: if constexpr (RPT > 5) x[5] = own ? 0.f : x[5]; break;
-        case 6: if constexpr (RPT > 6) x[6] = own ? 0.f : x[6]; break;
-        case 7: if constexpr (RPT > 7) x[7] = own ? 0.f : x[7]; break;
-        case 8: if constexpr (RPT > 8) x[8] = own ? 0.f : x[8]; break;
-        case 9: if constexpr (RPT > 9) x[9] = own ? 0.f : x[9]; break;
-        case 10: if constexpr (RPT > 10) x[10] = own ? 0.f : x[10]; break;
-        case 11: if constexpr (RPT > 11) x[11] = own ? 0.f : x[11]; break;
-        case 12: if constexpr (RPT > 12) x[12] = own ? 0.f : x[12]; break;
-        case 13: if constexpr (RPT > 13) x[13] = own ? 0.f : x[13]; break;
-        case 14: if constexpr (RPT > 14) x[14] = own ? 0.f : x[14]; break;
-        case 15: if constexpr (RPT > 15) x[15] = own ? 0.f : x[15]; break;
-        case 16: if constexpr (RPT > 16) x[16] = own ? 0.f : x[16]; break;
-        case 17: if constexpr (RPT > 17) x[17] = own ? 0.f : x[17]; break;
-        case 18: if constexpr (RPT > 18) x[18] = own ? 0.f : x[18]; break;
-        case 19: if constexpr (RPT > 19) x[19] = own ? 0.f : x[19]; break;
-        case 20: if constexpr (RPT > 20) x[20] = own ? 0.f : x[20]; break;
-        case 21: if constexpr (RPT > 21) x[21] = own ? 0.f : x[21]; break;
-        case 22: if constexpr (RPT > 22) x[22] = own ? 0.f : x[22]; break;
-        case 23: if constexpr (RPT > 23) x[23] = own ? 0.f : x[23]; break;
-        case 24: if constexpr (RPT > 24) x[24] = own ? 0.f : x[24]; break;
-        case 25: if constexpr (RPT > 25) x[25] = own ? 0.f : x[25]; break;
-        case 26: if constexpr (RPT > 26) x[26] = own ? 0.f : x[26]; break;
-        case 27: if constexpr (RPT > 27) x[27] = own ? 0.f : x[27]; break;
-        case 28: if constexpr (RPT > 28) x[28] = own ? 0.f : x[28]; break;
-        case 29: if constexpr (RPT > 29) x[29] = own ? 0.f : x[29]; break;
-        case 30: if constexpr (RPT > 30) x[30] = own ? 0.f : x[30]; break;
-        case 31: if constexpr (RPT > 31) x[31] = own ? 0.f : x[31]; break;
-        case 32: if constexpr (RPT > 32) x[32] = own ? 0.f : x[32]; break;
-        case 33: if constexpr (RPT > 33) x[33] = own ? 0.f : x[33]; break;
-        case 34: if constexpr (RPT > 34) x[34] = own ? 0.f : x[34]; break;
-        case 35: if constexpr (RPT > 35) x[35] = own ? 0.f : x[35]; break;
-        case 36: if constexpr (RPT > 36) x[36] = own ? 0.f : x[36]; break;
-        case 37: if constexpr (RPT > 37) x[37] = own ? 0.f : x[37]; break;
-        case 38: if constexpr (RPT > 38) x[38] = own ? 0.f : x[38]; break;
-        case 39: if constexpr (RPT > 39) x[39] = own ? 0.f : x[39]; break;
-        case 40: if constexpr (RPT > 40) x[40] = own ? 0.f : x[40]; break;
-        case 41: if constexpr (RPT > 41) x[41] = own ? 0.f : x[41]; break;
-        case 42: if constexpr (RPT > 42) x[42] = own ? 0.f : x[42]; break;
-        case 43: if constexpr (RPT > 43) x[43] = own ? 0.f : x[43]; break;
-        case 44: if constexpr (RPT > 44) x[44] = own ? 0.f : x[44]; break;
-        case 45: if constexpr (RPT > 45) x[45] = own ? 0.f : x[45]; break;
-        case 46: if constexpr (RPT > 46) x[46] = own ? 0.f : x[46]; break;
-        case 47: if constexpr (RPT > 47) x[47] = own ? 0.f : x[47]; break;
-        case 48: if constexpr (RPT > 48) x[48] = own ? 0.f : x[48]; break;
-        case 49: if constexpr (RPT > 49) x[49] = own ? 0.f : x[49]; break;
-        case 50: if constexpr (RPT > 50) x[50] = own ? 0.f : x[50]; break;
-        case 51: if constexpr (RPT > 51) x[51] = own ? 0.f : x[51]; break;
-        case 52: if constexpr (RPT > 52) x[52] = own ? 0.f : x[52]; break;
-        case 53: if constexpr (RPT > 53) x[53] = own ? 0.f : x[53]; break;
-        case 54: if constexpr (RPT > 54) x[54] = own ? 0.f : x[54]; break;
-        case 55: if constexpr (RPT > 55) x[55] = own ? 0.f : x[55]; break;
-        case 56: if constexpr (RPT > 56) x[56] = own ? 0.f : x[56]; break;
-        case 57: if constexpr (RPT > 57) x[57] = own ? 0.f : x[57]; break;
-        case 58: if constexpr (RPT > 58) x[58] = own ? 0.f : x[58]; break;
-        case 59: if constexpr (RPT > 59) x[59] = own ? 0.f : x[59]; break;
-        case 60: if constexpr (RPT > 60) x[60] = own ? 0.f : x[60]; break;
-        case 61: if constexpr (RPT > 61) x[61] = own ? 0.f : x[61]; break;
-        case 62: if constexpr (RPT > 62) x[62] = own ? 0.f : x[62]; break;
-        case 63: if constexpr (RPT > 63) x[63] = own ? 0.f : x[63]; break;
-        case 64: if constexpr (RPT > 64) x[64] = own ? 0.f : x[64]; break;
-        case 65: if constexpr (RPT > 65) x[65] = own ? 0.f : x[65]; break;
-        case 66: if constexpr (RPT > 66) x[66] = own ? 0.f : x[66]; break;
-        case 67: if constexpr (RPT > 67) x[67] = own ? 0.f : x[67]; break;
-        case 68: if constexpr (RPT > 68) x[68] = own ? 0.f : x[68]; break;
-        case 69: if constexpr (RPT > 69) x[69] = own ? 0.f : x[69]; break;
-        case 70: if constexpr (RPT > 70) x[70] = own ? 0.f : x[70]; break;
-        case 71: if constexpr (RPT > 71) x[71] = own ? 0.f : x[71]; break;
-        case 72: if constexpr (RPT > 72) x[72] = own ? 0.f : x[72]; break;
-        case 73: if constexpr (RPT > 73) x[73] = own ? 0.f : x[73]; break;
-        case 74: if constexpr (RPT > 74) x[74] = own ? 0.f : x[74]; break;
-        case 75: if constexpr (RPT > 75) x[75] = own ? 0.f : x[75]; break;
-        case 76: if constexpr (RPT > 76) x[76] = own ? 0.f : x[76]; break;
-        case 77: if constexpr (RPT > 77) x[77] = own ? 0.f : x[77]; break;
-        case 78: if constexpr (RPT > 78) x[78] = own ? 0.f : x[78]; break;
-        case 79: if constexpr (RPT > 79) x[79] = own ? 0.f : x[79]; break;
-        default: break;
     }
 }
 
@@ -363,6 +277,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
     __shared__ float wsum[MAXW];
     __shared__ float wnorm[MAXW];
     __shared__ __align__(8) uint64_t recv_bar[2];
+    __shared__ int wait_abort;                  // a thread whose exchange wait timed out sets it
 
     const uint32_t me = cluster_rank(), C = cluster_nrank();
     const CqTask W = cq_task<MAXR>(P, C);
@@ -388,6 +303,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         mbar_init(&recv_bar[0], 1);
         mbar_init(&recv_bar[1], 1);
         cta_key[0] = cta_key[1] = cta_key[2] = 0ull;
+        wait_abort = 0;
         fence_barrier_init();
     }
     cluster_sync_all();
@@ -408,6 +324,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
 #pragma unroll
     for (int o = 1; o < TPC; o <<= 1) nu += __shfl_xor_sync(0xffffffffu, nu, o);
     float nuref = nu;
+    float xnext = x[0];       // this thread's candidate for the next step's row (row 0: thread 0)
     bool selected = !valid;
     if (valid && qq == 0) {
         if (!isfinite(nu)) set_info(W.info, kInfoNonFinite);
@@ -478,8 +395,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         }
     };
     auto wait_exchange = [&](int q) -> bool {
-        volatile int keep = 0;
-        return mbar_wait(&recv_bar[q & 1], static_cast<uint32_t>((q >> 1) & 1), &keep, P.limit_ns);
+        return mbar_wait(&recv_bar[q & 1], static_cast<uint32_t>((q >> 1) & 1), &wait_abort, P.limit_ns);
     };
 
     {
@@ -535,9 +451,9 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
         float S = (S0 + S1) + (S2 + S3);
 #pragma unroll
         for (int o = 1; o < TPC; o <<= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-        // X = x_j, held by thread qj of the group at register uj
+        // X = x_j: thread qj of the group picked it (register uj) at the end of the last step
         const int qj = j / RPT, uj = j - qj * RPT;
-        const float X = __shfl_sync(0xffffffffu, pick_row<RPT>(x, uj), gbase + qj);
+        const float X = __shfl_sync(0xffffffffu, xnext, gbase + qj);
         S = fmaf(-beta, X, S);
         if (valid && i == p) {
             selected = true;
@@ -571,7 +487,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
                 x[u + 2] = fmaf(-sv, v4.z, x[u + 2]);
                 x[u + 3] = fmaf(-sv, v4.w, x[u + 3]);
             }
-            zero_row<RPT>(x, uj, qq == qj);
+            xnext = zero_and_next<RPT>(x, uj, qq == qj);
             float sq = 0.f;
 #pragma unroll
             for (int u = 0; u < RPT; ++u) sq = fmaf(x[u], x[u], sq);
@@ -593,7 +509,7 @@ __global__ void __launch_bounds__(kCqMaxThreads, (MAXR <= 64 && TPC == 4) ? 2 : 
                 x[u + 2] = fmaf(-sv, v4.z, x[u + 2]);
                 x[u + 3] = fmaf(-sv, v4.w, x[u + 3]);
             }
-            zero_row<RPT>(x, uj, qq == qj);
+            xnext = zero_and_next<RPT>(x, uj, qq == qj);
         }
         send_best(j + 1, key, part);
         ok = wait_exchange(j + 1);

@@ -521,9 +521,10 @@ cudaError_t launch_solve_T_batched(const BatchTask* tasks, const SolveUnit* unit
 // Scratch (floats, kq = kcap rounded up to 4): X [kq x kq], R11 [kq x kq], flag; both
 // matrices are column-major with the device rank's kp = k rounded up to 4 as leading
 // dimension, zero below the diagonal and past k.
-constexpr int kGemmCols = 16;          // tile width of the single ID (256 threads)
-constexpr int kGemmColsBatch = 32;     // tile width of the batch's units (512 threads)
-constexpr int kGemmThreads = 256;
+// Tile width of T (512 threads: 32 row groups x 16 column pairs).  In the in-flight stream
+// 32-column tiles beat 16-column ones (half the CTAs, each hiding its latency with twice
+// the warps) at 4 us more solve latency.
+constexpr int kGemmCols = 32;
 constexpr int kGemmMaxK = 128;
 
 __host__ __device__ inline int gemm_kp(int k) { return (k + 3) & ~3; }
@@ -788,13 +789,13 @@ __device__ __forceinline__ void stage_x_r11(const float* __restrict__ scr, int k
     }
 }
 
-template <int KQ>
-__global__ void __launch_bounds__(kGemmThreads)
+template <int KQ, int COLS>
+__global__ void __launch_bounds__(16 * COLS)
 k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ J,
                const int32_t* __restrict__ k_ptr, int64_t n, const float* __restrict__ scr, int kq_cap,
                double* __restrict__ T, int64_t ldt, int refine_steps, int64_t smem_bytes) {
     extern __shared__ __align__(16) uint8_t sm[];
-    __shared__ int jc[kGemmCols];
+    __shared__ int jc[COLS];
     const int k = *k_ptr;
     if (k <= 0) return;
     if (__ldg(reinterpret_cast<const int*>(scr + 2 * static_cast<int64_t>(kq_cap) * kq_cap))) {
@@ -803,18 +804,35 @@ k_solve_T_gemm(const double* __restrict__ R, int64_t ldr, const int32_t* __restr
         return;
     }
     const int64_t nc = n - k;
-    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kGemmCols;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * COLS;
     if (c0 >= nc) return;
-    const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), nc - c0));
+    const int ncols = static_cast<int>(min(static_cast<int64_t>(COLS), nc - c0));
     const int kp = gemm_kp(k);
     float* Xs = reinterpret_cast<float*>(sm);        // kp x kp, column-major
     float* Rs = Xs + kp * kp;                        // R11, kp x kp column-major
     float* Bt = Rs + kp * kp;                        // [kp][gemm_ld]: R12, then the residual E
-    float* Tt = Bt + kp * gemm_ld(kGemmCols);        // [kp][gemm_ld]: T0
-    if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? __ldg(J + k + c0 + threadIdx.x) : 0;
+    float* Tt = Bt + kp * gemm_ld(COLS);             // [kp][gemm_ld]: T0
+    if (threadIdx.x < COLS) jc[threadIdx.x] = threadIdx.x < ncols ? __ldg(J + k + c0 + threadIdx.x) : 0;
     stage_x_r11(scr, kq_cap, kp, Xs, Rs);
     __syncthreads();
-    gemm_tile<KQ, kGemmCols>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, c0, ldt);
+    gemm_tile<KQ, COLS>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, c0, ldt);
+}
+
+template <int KQ, int COLS>
+static cudaError_t launch_gemm_tiles(const double* R64, int64_t ldr, const int32_t* J, const int32_t* k_ptr, int kcap,
+                                     int64_t n, double* T, int64_t ldt, float* scr, cudaStream_t s) {
+    const int kq = gemm_kp(kcap);
+    // the tiles' shared memory, or the FP64 fallback's copy of R11 if that is larger
+    const size_t tiles = gemm_tile_floats(kq, COLS) * sizeof(float);
+    const size_t fb = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(double);
+    const size_t smem = std::max(tiles, fb) + 16;
+    auto kern = k_solve_T_gemm<KQ, COLS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t cols = std::max<int64_t>(1, n - 1);
+    const unsigned grid = static_cast<unsigned>((cols + COLS - 1) / COLS);
+    kern<<<grid, 16 * COLS, smem, s>>>(R64, ldr, J, k_ptr, n, scr, kq, T, ldt, 1, static_cast<int64_t>(smem - 16));
+    return cudaGetLastError();
 }
 
 template <int KQ>
@@ -829,17 +847,7 @@ static cudaError_t launch_gemm_solve(const double* R64, int64_t ldr, const int32
                                                                                                 scr, kq);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the tiles' shared memory, or the FP64 fallback's copy of R11 if that is larger
-    const size_t tiles = gemm_tile_floats(kq, kGemmCols) * sizeof(float);
-    const size_t fb = (static_cast<size_t>(kcap) * kcap + kcap) * sizeof(double);
-    const size_t smem = std::max(tiles, fb) + 16;
-    auto kern = k_solve_T_gemm<KQ>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    const int64_t cols = std::max<int64_t>(1, n - 1);
-    const unsigned grid = static_cast<unsigned>((cols + kGemmCols - 1) / kGemmCols);
-    kern<<<grid, kGemmThreads, smem, s>>>(R64, ldr, J, k_ptr, n, scr, kq, T, ldt, 1, static_cast<int64_t>(smem - 16));
-    return cudaGetLastError();
+    return launch_gemm_tiles<KQ, kGemmCols>(R64, ldr, J, k_ptr, kcap, n, T, ldt, scr, s);
 }
 
 // ---- the batch's solve as products: k_r11_inverse_batched forms every matrix's X, packed
@@ -877,14 +885,14 @@ k_r11_inverse_batched(const BatchTask* __restrict__ tasks, const double* __restr
 }
 
 template <int KQ>
-__global__ void __launch_bounds__(16 * kGemmColsBatch)
+__global__ void __launch_bounds__(16 * kGemmCols)
 k_solve_T_batched_gemm(const BatchTask* __restrict__ tasks, const SolveUnit* __restrict__ units,
                        const double* __restrict__ R_base, const int32_t* __restrict__ J_base,
                        const int32_t* __restrict__ k_out, int32_t* infos, double* __restrict__ T_base,
                        BatchTotals tot, int kmax, int refine_steps, const float* __restrict__ inv_base) {
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ int s_bad;
-    __shared__ int jc[kGemmColsBatch];
+    __shared__ int jc[kGemmCols];
     const SolveUnit su = units[blockIdx.x];
     if (su.task < 0 || su.task >= tot.ntasks) return;
     const BatchTask& bt = tasks[su.task];
@@ -920,13 +928,13 @@ k_solve_T_batched_gemm(const BatchTask* __restrict__ tasks, const SolveUnit* __r
     float* Xs = reinterpret_cast<float*>(sm);
     float* Rs = Xs + kp * kp;
     float* Bt = Rs + kp * kp;
-    float* Tt = Bt + kp * gemm_ld(kGemmColsBatch);
+    float* Tt = Bt + kp * gemm_ld(kGemmCols);
     stage_x_r11(scr, kq, kp, Xs, Rs);
-    for (int64_t t0 = su.c0; t0 < c_end; t0 += kGemmColsBatch) {
-        const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmColsBatch), c_end - t0));
-        if (threadIdx.x < kGemmColsBatch) jc[threadIdx.x] = threadIdx.x < ncols ? J[k + t0 + threadIdx.x] : 0;
+    for (int64_t t0 = su.c0; t0 < c_end; t0 += kGemmCols) {
+        const int ncols = static_cast<int>(min(static_cast<int64_t>(kGemmCols), c_end - t0));
+        if (threadIdx.x < kGemmCols) jc[threadIdx.x] = threadIdx.x < ncols ? J[k + t0 + threadIdx.x] : 0;
         __syncthreads();
-        gemm_tile<KQ, kGemmColsBatch>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, t0, ldr);
+        gemm_tile<KQ, kGemmCols>(R, ldr, jc, k, kp, ncols, Xs, Rs, Bt, Tt, T, t0, ldr);
     }
 }
 
@@ -947,11 +955,11 @@ static cudaError_t launch_batched_product(const BatchTask* tasks, int ntasks, co
         e = cudaGetLastError();
         if (e != cudaSuccess || nunits <= 0) return e;
     }
-    const size_t smem = gemm_tile_floats(gemm_kp(kmax), kGemmColsBatch) * sizeof(float) + 16;
+    const size_t smem = gemm_tile_floats(gemm_kp(kmax), kGemmCols) * sizeof(float) + 16;
     auto kern = k_solve_T_batched_gemm<KQ>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<nunits, 16 * kGemmColsBatch, smem, s>>>(tasks, units, R_base, J_base, k_out, infos, T_base, tot, kmax,
+    kern<<<nunits, 16 * kGemmCols, smem, s>>>(tasks, units, R_base, J_base, k_out, infos, T_base, tot, kmax,
                                             refine_steps, inv);
     return cudaGetLastError();
 }
