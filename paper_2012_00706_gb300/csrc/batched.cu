@@ -384,13 +384,14 @@ bool build_plan_plain32(id_batch_plan* p) {
         Wave w;
         w.first = q;
         size_t bytes = 0;
-        int64_t nmin = INT64_MAX;
+        int64_t nmin = INT64_MAX, mmax = 1;
         while (q < p->batch && w.count < sms) {
             const int32_t i = order[q];
             const size_t b = align256(static_cast<size_t>(p->m[i]) * p->n[i] * sizeof(float));
             if (w.count > 0 && bytes + b > kWaveBytes) break;
             bytes += b;
             nmin = std::min(nmin, p->n[i]);
+            mmax = std::max(mmax, p->m[i]);
             ++w.count;
             ++q;
         }
@@ -404,7 +405,8 @@ bool build_plan_plain32(id_batch_plan* p) {
         w.smem = cpqr_grouped_smem(cpb, rst, 0);
         if (w.smem > static_cast<size_t>(device_info().max_smem_optin) - 8 * 1024) return false;
         w.x_bytes = bytes;
-        w.ctrl_stride = align256(sizeof(CpqrCtrl) + 2 * static_cast<size_t>(w.gsize) * sizeof(Cand));
+        // barrier word and candidate tables, then the row mode's two pivot-column slots
+        w.ctrl_stride = cpqr_pub_offset(w.gsize) + align256(2 * static_cast<size_t>(mmax) * sizeof(float));
         x_max = std::max(x_max, bytes);
         ctrl_max = std::max(ctrl_max, w.ctrl_stride * w.count);
         smem_max = std::max(smem_max, w.smem);
@@ -472,6 +474,7 @@ void write_params_plain32(id_batch_plan* p, const void* const* A, void* work) {
             P.sel = w + p->off_sel + t.sel_off;
             P.ctrl = reinterpret_cast<CpqrCtrl*>(w + p->off_ctrl + e * wv.ctrl_stride);
             P.cand = reinterpret_cast<Cand*>(w + p->off_ctrl + e * wv.ctrl_stride + sizeof(CpqrCtrl));
+            P.pub = reinterpret_cast<float*>(w + p->off_ctrl + e * wv.ctrl_stride + cpqr_pub_offset(wv.gsize));
             P.resident = 0;
             P.cpb_max = (t.n + wv.gsize - 1) / wv.gsize;
             P.colmode = cpqr_grouped_colmode(P.cpb_max);

@@ -133,7 +133,7 @@ struct GridShared {
     double shp[33];
     int ok;
     int p, pg;
-    double alpha, s2, sumnu, total;
+    double alpha, s2, sumnu, total, sv_p;
 };
 
 // Dynamic shared memory of a CTA: residual norms, reference norms and (column mode) exact
@@ -205,6 +205,12 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     const int64_t r = P.r;
     const T sqrt_u = SqrtU<T>::v();
     const int sup = static_cast<int>(grid_super(P.cpb_max));
+    if (!P.colmode && !P.pub) {
+        // row mode needs the pivot-column slots (every CTA sees the same parameters and
+        // leaves before the first grid barrier)
+        if (b == 0 && tid == 0) set_info(P.info, kInfoBadTable);
+        return;
+    }
     T* xps_s = reinterpret_cast<T*>(smem_dyn);  // [rstage] staged pivot column (column mode)
     T* nu_s = xps_s + grid_rstage_padded(P.rstage, sizeof(T));
     T* nuref_s = nu_s + P.cpb_max;
@@ -252,9 +258,23 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     }
     if (bad) set_info(P.info, kInfoNonFinite);
 
+    // Row mode keeps each column one update behind: step j's update is applied by step j + 1's
+    // pass.  The pivot column of step j brought up to date at row t is
+    // fma(-sv_p, xprev[t], xq[t]) (xq: its stored copy, xprev: step j - 1's pivot column,
+    // kept in pub by its owner); candidates read after step j add their own pending update.
+    const T* pf_xq = nullptr;
+    const T* pf_xprev = nullptr;
+    T pf_msvp = 0;
+    bool pf_pend = false;
+    auto pivot_at = [&](int64_t t) -> T {
+        const T q = __ldcg(pf_xq + t);
+        return pf_pend ? fma(pf_msvp, __ldcg(pf_xprev + t), q) : q;
+    };
+
     // ---- publish this slice's best candidate for the step with row `row` (exact squared
-    // norm of its rows row..r-1, its entry on row `row`)
-    auto publish = [&](int slot, int row, double total) {
+    // norm of its rows row..r-1, its entry on row `row`; `lagging`: row mode after a step,
+    // whose update the candidate's values take on the fly)
+    auto publish = [&](int slot, int row, double total, bool lagging) {
         // compared in the working precision (widening is exact and monotone), widened once
         T bestw = T(-1);
         int bi = -1;
@@ -276,6 +296,27 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             // column mode: the exact norm below the row, left by the column's warp
             s2 = s2_s[bl];
             alpha = col(bl)[row];
+        } else if (bl >= 0 && row < r && lagging) {
+            // as below, on the values after the pending update
+            const T* x = col(bl);
+            const T msv = -sv_s[bl];
+            auto cur = [&](int64_t t) { return fma(msv, pivot_at(t), x[t]); };
+            T sa[8] = {};
+            int64_t t = row + tid;
+            for (; t + 7 * nt < r; t += 8 * nt) {
+                T a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = cur(t + u * nt);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sa[u] = fma(a[u], a[u], sa[u]);
+            }
+            for (; t < r; t += nt) {
+                const T a = cur(t);
+                sa[0] = fma(a, a, sa[0]);
+            }
+            const T s = ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
+            s2 = block_sum(s, G_.shs);
+            alpha = cur(row);
         } else if (bl >= 0 && row < r) {
             // the candidate's exact squared norm: eight independent sums keep eight loads in
             // flight per thread (this pass is on every step's critical path)
@@ -301,6 +342,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             cd.total = total;
             cd.s2 = to_f64(s2);
             cd.alpha = to_f64(alpha);
+            cd.sv = (lagging && bl >= 0) ? to_f64(sv_s[bl]) : 0.0;
             cd.idx = bl >= 0 ? static_cast<int>(c0 + bl) : -1;
             cd.stamp = 0;
             P.cand[slot * G + b] = cd;
@@ -309,7 +351,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
 
     {
         const T tot = block_sum(tid == 0 ? local_total : T(0), G_.shs);
-        publish(0, 0, static_cast<double>(tot));
+        publish(0, 0, static_cast<double>(tot), false);
     }
     bool ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok,
                            static_cast<uint32_t>(G));
@@ -340,6 +382,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
                     G_.p = w.idx;
                     G_.alpha = w.alpha;
                     G_.s2 = w.s2;
+                    G_.sv_p = w.sv;
                     gv = w.nu;
                 }
                 G_.shv[32] = gv;
@@ -651,116 +694,138 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             }
             __syncthreads();
         } else {
-        // ---- the slice's unselected columns by super-groups of at most kSuper: the dot
-        // products of all of them (CG columns per pass over the rows), one barrier, their
-        // reflector scalars, one barrier, the updates, and the squared norms where the
-        // downdate was refused
+        // ---- row mode (fewer columns than warps: all threads split the rows).  One pass over
+        // rows j..r-1 applies step j - 1's update to the slice's unselected columns (their
+        // coefficients in sv_s, step j - 1's pivot column from pub) and forms this step's dot
+        // products S_c = x_p(j:r)^T x_c(j:r) with the pivot column brought up to date on the
+        // fly; the pivot's owner keeps that column in pub for step j + 1.  One barrier, the
+        // reflector scalars (this step's update coefficients replace the applied ones), and the
+        // exact norms where the downdate was refused.  Step j's update waits for step j + 1's
+        // pass: a column is read and written once per step.
         constexpr int CG = ColGroup<T>::cols;
         constexpr int UR = ColGroup<T>::unroll;
-        for (int s0 = 0; s0 < nc; s0 += sup) {
-            const int sn = min(sup, nc - s0);
-            // pass 1: S_c = x_p(j:r)^T x_c(j:r)
-            for (int g0 = s0; g0 < s0 + sn; g0 += CG) {
-                const int gn = min(CG, s0 + sn - g0);
-                bool act[CG];
-                const T* xc[CG];
-                T S[CG];
+        const bool pend = j > 0;
+        pf_xq = xp;
+        pf_xprev = P.pub + static_cast<int64_t>((j + 1) & 1) * r;     // step j - 1's slot
+        pf_msvp = pend ? -static_cast<T>(G_.sv_p) : T(0);
+        pf_pend = pend;
+        T* const xcur = P.pub + static_cast<int64_t>(j & 1) * r;
+        const bool own_p = p >= c0 && p < c1;
+        for (int g0 = 0; g0 < nc; g0 += CG) {
+            const int gn = min(CG, nc - g0);
+            bool act[CG];
+            T* xc[CG];
+            T msv[CG], S[CG];
 #pragma unroll
-                for (int q = 0; q < CG; ++q) {
-                    act[q] = q < gn && !sel_s[g0 + q];
-                    xc[q] = col(min(g0 + q, nc - 1));
-                    S[q] = 0;
-                }
-#pragma unroll UR
-                for (int64_t t = j + tid; t < r; t += nt) {
-                    const T pv = __ldcg(xp + t);
-#pragma unroll
-                    for (int q = 0; q < CG; ++q)
-                        if (act[q]) S[q] = fma(pv, xc[q][t], S[q]);
-                }
-#pragma unroll
-                for (int q = 0; q < CG; ++q) {
-                    const T v = warp_sum(S[q]);
-                    if (lane == 0 && q < gn) red_s[warp * sup + (g0 - s0) + q] = v;
-                }
+            for (int q = 0; q < CG; ++q) {
+                act[q] = q < gn && !sel_s[g0 + q];
+                xc[q] = col(min(g0 + q, nc - 1));
+                msv[q] = (act[q] && pend) ? -sv_s[g0 + q] : T(0);
+                S[q] = 0;
             }
-            __syncthreads();
-            for (int c = s0 + tid; c < s0 + sn; c += nt) {
-                T sv = 0;
-                int rec = 0;
-                if (!sel_s[c]) {
-                    T s = 0;
-                    for (int w = 0; w < kGridWarps; ++w) s += red_s[w * sup + (c - s0)];
-                    const T X = col(c)[j];
-                    s = fma(-beta, X, s);
-                    const T tw = -s * rb;
-                    sv = tw * inv;
-                    const T rho = X - tw;
-                    P.R[(c0 + c) * P.ldr + j] = to_f64(rho);
-                    // downdate; an exact recompute where cancellation has eaten sqrt(u)
-                    const T nu = nu_s[c];
-                    if (nu > T(0)) {
-                        const T d = fmax(nu - rho * rho, T(0));
-                        if (d <= sqrt_u * nuref_s[c]) rec = 1;
-                        else nu_s[c] = d;
+            const bool keep = own_p && g0 == 0;
+            bool any = keep;
+#pragma unroll
+            for (int q = 0; q < CG; ++q) any |= act[q];
+            if (!any) continue;     // every column of the group is selected: nothing reads its sums
+#pragma unroll UR
+            for (int64_t t = j + tid; t < r; t += nt) {
+                const T pp = pend ? __ldcg(pf_xprev + t) : T(0);
+                const T q0 = __ldcg(xp + t);
+                const T pv = pend ? fma(pf_msvp, pp, q0) : q0;
+                if (keep) xcur[t] = pv;
+#pragma unroll
+                for (int q = 0; q < CG; ++q) {
+                    if (act[q]) {
+                        T v = xc[q][t];
+                        if (pend) {
+                            v = fma(msv[q], pp, v);
+                            xc[q][t] = v;
+                        }
+                        S[q] = fma(pv, v, S[q]);
                     }
                 }
-                sv_s[c - s0] = sv;
-                rec_s[c - s0] = rec;
             }
-            __syncthreads();
-            // pass 2: x_c(t) -= sv_c x_p(t) for t > j; squared norms where recomputed
-            bool any_rec = false;
-            for (int g0 = s0; g0 < s0 + sn; g0 += CG) {
-                const int gn = min(CG, s0 + sn - g0);
-                T* xc[CG];
+#pragma unroll
+            for (int q = 0; q < CG; ++q) {
+                const T v = warp_sum(S[q]);
+                if (lane == 0 && q < gn) red_s[warp * sup + g0 + q] = v;
+            }
+        }
+        __syncthreads();
+        for (int c = tid; c < nc; c += nt) {
+            T sv = 0;
+            int rec = 0;
+            if (!sel_s[c]) {
+                T s = 0;
+                for (int w = 0; w < kGridWarps; ++w) s += red_s[w * sup + c];
+                const T X = col(c)[j];
+                s = fma(-beta, X, s);
+                const T tw = -s * rb;
+                sv = tw * inv;
+                const T rho = X - tw;
+                P.R[(c0 + c) * P.ldr + j] = to_f64(rho);
+                // downdate; an exact recompute where cancellation has eaten sqrt(u)
+                const T nu = nu_s[c];
+                if (nu > T(0)) {
+                    const T d = fmax(nu - rho * rho, T(0));
+                    if (d <= sqrt_u * nuref_s[c]) rec = 1;
+                    else nu_s[c] = d;
+                }
+            }
+            sv_s[c] = sv;
+            rec_s[c] = rec;
+        }
+        __syncthreads();
+        // the refused downdates: exact squared norms of x_c(j+1:r) after this step's update
+        // (rare; the values are taken on the fly like the candidate's below)
+        bool any_rec = false;
+        for (int c = 0; c < nc; ++c) any_rec |= rec_s[c] != 0;
+        if (any_rec) {
+            for (int g0 = 0; g0 < nc; g0 += CG) {
+                const int gn = min(CG, nc - g0);
+                bool act[CG];
+                const T* xc[CG];
                 T msv[CG], sq[CG];
-                bool act[CG], rec[CG];
-                bool grp_rec = false;
+                bool grp = false;
 #pragma unroll
                 for (int q = 0; q < CG; ++q) {
-                    act[q] = q < gn && !sel_s[g0 + q];
+                    act[q] = q < gn && rec_s[g0 + q] != 0;
                     xc[q] = col(min(g0 + q, nc - 1));
-                    msv[q] = act[q] ? -sv_s[g0 - s0 + q] : T(0);
-                    rec[q] = act[q] && rec_s[g0 - s0 + q] != 0;
-                    grp_rec |= rec[q];
+                    msv[q] = act[q] ? -sv_s[g0 + q] : T(0);
+                    grp |= act[q];
                     sq[q] = 0;
                 }
+                if (!grp) continue;
 #pragma unroll UR
                 for (int64_t t = j + 1 + tid; t < r; t += nt) {
-                    const T pv = __ldcg(xp + t);
+                    const T pv = pivot_at(t);
 #pragma unroll
                     for (int q = 0; q < CG; ++q) {
                         if (act[q]) {
                             const T nx = fma(msv[q], pv, xc[q][t]);
-                            xc[q][t] = nx;
-                            if (rec[q]) sq[q] = fma(nx, nx, sq[q]);
+                            sq[q] = fma(nx, nx, sq[q]);
                         }
                     }
                 }
-                if (grp_rec) {
 #pragma unroll
-                    for (int q = 0; q < CG; ++q) {
-                        const T v = warp_sum(sq[q]);
-                        if (lane == 0 && q < gn) red_s[warp * sup + (g0 - s0) + q] = v;
-                    }
-                    any_rec = true;
+                for (int q = 0; q < CG; ++q) {
+                    const T v = warp_sum(sq[q]);
+                    if (lane == 0 && q < gn) red_s[warp * sup + g0 + q] = v;
                 }
             }
-            if (any_rec) {
-                __syncthreads();
-                for (int c = s0 + tid; c < s0 + sn; c += nt) {
-                    if (!rec_s[c - s0]) continue;
-                    T s = 0;
-                    for (int w = 0; w < kGridWarps; ++w) s += red_s[w * sup + (c - s0)];
-                    nu_s[c] = s;
-                    nuref_s[c] = s;
-                }
+            __syncthreads();
+            for (int c = tid; c < nc; c += nt) {
+                if (!rec_s[c]) continue;
+                T s = 0;
+                for (int w = 0; w < kGridWarps; ++w) s += red_s[w * sup + c];
+                nu_s[c] = s;
+                nuref_s[c] = s;
             }
             __syncthreads();
         }
         }
-        publish(slot ^ 1, j + 1, 0.0);
+        publish(slot ^ 1, j + 1, 0.0, !P.colmode);
         ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok,
                            static_cast<uint32_t>(G));
         k = j + 1;
@@ -824,10 +889,17 @@ size_t cpqr_grouped_smem(int64_t cpb, int64_t rstage, int f64) {
 int cpqr_grouped_colmode(int64_t cpb) { return grid_colmode(cpb) ? 1 : 0; }
 int64_t cpqr_grouped_rstage(int64_t cpb, int64_t r, int elem_bytes) { return grid_rstage(cpb, r, elem_bytes); }
 
+// Control region: the barrier word, the two candidate tables, then (at a 256-byte offset)
+// the resident kernel's published columns [2][grid][r] or the streaming kernel's two
+// pivot-column slots [2][r].
 size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes) {
-    size_t b = sizeof(CpqrCtrl) + 2 * static_cast<size_t>(plan.grid) * sizeof(Cand);
-    if (plan.resident) b = ((b + 255) & ~size_t(255)) + 2 * static_cast<size_t>(plan.grid) * r * elem_bytes;
+    size_t b = cpqr_pub_offset(plan.grid);
+    b += (plan.resident ? 2 * static_cast<size_t>(plan.grid) : size_t(2)) * r * elem_bytes;
     return b;
+}
+
+size_t cpqr_pub_offset(int grid) {
+    return (sizeof(CpqrCtrl) + 2 * static_cast<size_t>(grid) * sizeof(Cand) + 255) & ~size_t(255);
 }
 
 bool cpqr_plan(int64_t r, int64_t n, int elem_bytes, CpqrPlan* plan) {
@@ -865,11 +937,7 @@ static cudaError_t launch_cpqr_t(void* W, int64_t r, int64_t n, int64_t ldw, con
     P.ctrl = static_cast<CpqrCtrl*>(ctrl);
     P.cand = reinterpret_cast<Cand*>(static_cast<char*>(ctrl) + sizeof(CpqrCtrl));
     P.resident = plan.resident;
-    if (P.resident) {
-        const size_t off = (sizeof(CpqrCtrl) + 2 * static_cast<size_t>(plan.grid) * sizeof(Cand) + 255) &
-                           ~size_t(255);
-        P.pub = reinterpret_cast<T*>(static_cast<char*>(ctrl) + off);
-    }
+    P.pub = reinterpret_cast<T*>(static_cast<char*>(ctrl) + cpqr_pub_offset(plan.grid));
     P.cpb_max = (n + plan.grid - 1) / plan.grid;
     P.colmode = grid_colmode(P.cpb_max) ? 1 : 0;
     P.rstage = grid_rstage(P.cpb_max, r, static_cast<int>(sizeof(T)));

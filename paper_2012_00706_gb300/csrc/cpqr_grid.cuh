@@ -16,6 +16,7 @@ struct Cand {
     double total;   // initial sum of squares of the slice (first table only)
     double s2;      // exact squared norm of the best column below the next step's row
     double alpha;   // the best column's entry on the next step's row
+    double sv;      // streaming kernel, row mode: the best column's pending update coefficient
     int idx;        // column of the best norm (-1 if none)
     int stamp;      // resident kernel: step + 1 the record is for, stored last (release)
 };
@@ -43,7 +44,8 @@ struct CpqrParams {
     uint8_t* sel;
     CpqrCtrl* ctrl;
     Cand* cand;        // [2][gridDim.x]
-    T* pub;            // resident kernel: [2][gridDim.x][r] published candidate columns
+    T* pub;            // resident kernel: [2][gridDim.x][r] published candidate columns; streaming
+                       // kernel, row mode: [2][r] each step's pivot column brought up to date
     int resident;
     int64_t cpb_max;   // columns per CTA at most (shared-memory layout)
     uint64_t limit_ns;
@@ -61,6 +63,7 @@ __device__ __forceinline__ Cand load_cand(const Cand* p) {
     c.total = __ldcg(&p->total);
     c.s2 = __ldcg(&p->s2);
     c.alpha = __ldcg(&p->alpha);
+    c.sv = __ldcg(&p->sv);
     c.idx = __ldcg(&p->idx);
     c.stamp = 0;
     return c;

@@ -131,6 +131,7 @@ struct CpqrPlan {
 };
 bool cpqr_plan(int64_t r, int64_t n, int elem_bytes, CpqrPlan* plan);
 size_t cpqr_ctrl_bytes(const CpqrPlan& plan, int64_t r, int elem_bytes);
+size_t cpqr_pub_offset(int grid);   // offset of the column slots in the control region
 cudaError_t launch_cpqr(void* W, int w_f64, int64_t r, int64_t n, int64_t ldw, const void* src,
                         int src_f64, int64_t ldsrc, int kcap, double rel_tol, int32_t* J,
                         int32_t* k_out, int32_t* info, double* R64, int64_t ldr, void* nu,
