@@ -77,7 +77,7 @@ struct SolveClass {
 // PLAIN_F32: matrices wave_order[first, first + count) in one grouped launch of gsize
 // CTAs per matrix.
 struct Wave {
-    int32_t first = 0, count = 0, gsize = 1;
+    int32_t first = 0, count = 0, gsize = 1, colmode = 0;
     size_t smem = 0;
     size_t x_bytes = 0, ctrl_stride = 0;
 };
@@ -402,6 +402,9 @@ bool build_plan_plain32(id_batch_plan* p) {
             cpb = std::max<int64_t>(cpb, ci);
             rst = std::max<int64_t>(rst, cpqr_grouped_rstage(ci, p->m[order[e]], 4));
         }
+        // one mode per wave (a launch): a warp per column when any matrix has a column per
+        // warp (the others leave warps idle), else the rows split over all threads
+        w.colmode = cpqr_grouped_colmode(cpb);
         w.smem = cpqr_grouped_smem(cpb, rst, 0);
         if (w.smem > static_cast<size_t>(device_info().max_smem_optin) - 8 * 1024) return false;
         w.x_bytes = bytes;
@@ -477,7 +480,7 @@ void write_params_plain32(id_batch_plan* p, const void* const* A, void* work) {
             P.pub = reinterpret_cast<float*>(w + p->off_ctrl + e * wv.ctrl_stride + cpqr_pub_offset(wv.gsize));
             P.resident = 0;
             P.cpb_max = (t.n + wv.gsize - 1) / wv.gsize;
-            P.colmode = cpqr_grouped_colmode(P.cpb_max);
+            P.colmode = wv.colmode;
             P.rstage = cpqr_grouped_rstage(P.cpb_max, t.m, 4);
             P.limit_ns = static_cast<uint64_t>(ms) * 1000000ull;
             P.out_j = t.j_off;
@@ -735,7 +738,8 @@ id_status_t enqueue_plain32(const id_batch_plan* p, int32_t* J, double* T, int32
     record_stage(2, s);
     for (const Wave& wv : p->waves) {
         if (cudaMemsetAsync(w + p->off_ctrl, 0, wv.ctrl_stride * wv.count, s) != cudaSuccess) return ID_ERR_CUDA;
-        if (launch_cpqr_grouped<float>(d_params + wv.first, wv.count, wv.gsize, wv.smem, J, k_out, info, s) !=
+        if (launch_cpqr_grouped<float>(d_params + wv.first, wv.count, wv.gsize, wv.colmode, wv.smem, J, k_out, info,
+                                       s) !=
             cudaSuccess)
             return ID_ERR_CUDA;
     }

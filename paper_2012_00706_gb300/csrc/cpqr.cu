@@ -195,7 +195,7 @@ inline int64_t grid_rstage(int64_t cpb, int64_t r, int elem_bytes) {
 
 // The pivoted QR of one matrix by the G CTAs b = 0..G-1 (a whole grid, or one group of a
 // grouped launch).
-template <typename T>
+template <typename T, bool COLMODE>
 __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int G, const int b, GridShared<T>& G_,
                                                uint8_t* smem_dyn) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -205,9 +205,9 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     const int64_t r = P.r;
     const T sqrt_u = SqrtU<T>::v();
     const int sup = static_cast<int>(grid_super(P.cpb_max));
-    if (!P.colmode && !P.pub) {
-        // row mode needs the pivot-column slots (every CTA sees the same parameters and
-        // leaves before the first grid barrier)
+    if ((P.colmode != 0) != COLMODE || (!COLMODE && !P.pub)) {
+        // the parameters name the other mode, or row mode lacks its pivot-column slots (every
+        // CTA of the matrix sees the same parameters and leaves before the first grid barrier)
         if (b == 0 && tid == 0) set_info(P.info, kInfoBadTable);
         return;
     }
@@ -292,7 +292,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
         const T sum = static_cast<T>(sumd);
         T s2 = 0;
         T alpha = 0;
-        if (bl >= 0 && row < r && P.colmode) {
+        if (COLMODE && bl >= 0 && row < r) {
             // column mode: the exact norm below the row, left by the column's warp
             s2 = s2_s[bl];
             alpha = col(bl)[row];
@@ -413,7 +413,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             P.R[static_cast<int64_t>(p) * P.ldr + j] = to_f64(beta);
         }
         __syncthreads();
-        if (P.colmode) {
+        if constexpr (COLMODE) {
             // ---- column mode: warp w takes columns w, w + 16, ...; per column the dot
             // product (one warp reduction), the reflector scalars, the update and, where the
             // downdate is refused, the exact squared norm, with no CTA barrier in between
@@ -825,7 +825,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
             __syncthreads();
         }
         }
-        publish(slot ^ 1, j + 1, 0.0, !P.colmode);
+        publish(slot ^ 1, j + 1, 0.0, !COLMODE);
         ok = grid_barrier(&P.ctrl->counter, epoch, &P.ctrl->abort, P.limit_ns, &G_.ok,
                            static_cast<uint32_t>(G));
         k = j + 1;
@@ -837,17 +837,20 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     if (b == 0) list_complement(P.J, P.sel, P.n, k, P.k_out, G_.shi);
 }
 
-template <typename T>
+// COLMODE: the slice's mode (a warp per column, or the rows split over all threads),
+// fixed per launch so that each mode's registers are allocated on their own.
+template <typename T, bool COLMODE>
 __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid(const CpqrParams<T> P) {
     extern __shared__ __align__(16) uint8_t smem_dyn[];
     __shared__ GridShared<T> G_;
-    cpqr_grid_body<T>(P, static_cast<int>(gridDim.x), static_cast<int>(blockIdx.x), G_, smem_dyn);
+    cpqr_grid_body<T, COLMODE>(P, static_cast<int>(gridDim.x), static_cast<int>(blockIdx.x), G_, smem_dyn);
 }
 
 // Grouped launch: CTAs [g gsize, (g + 1) gsize) factor the matrix of groups[g] on their own,
 // with the group's own candidate table and barrier counter.  The launch is cooperative, so
-// every group is resident at once and its barrier waits only on its own CTAs.
-template <typename T>
+// every group is resident at once and its barrier waits only on its own CTAs.  Every
+// group's parameters name the launch's mode.
+template <typename T, bool COLMODE>
 __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid_grouped(const CpqrParams<T>* __restrict__ groups,
                                                                    int gsize, int32_t* J_base, int32_t* k_out_base,
                                                                    int32_t* info_base) {
@@ -861,13 +864,14 @@ __global__ void __launch_bounds__(kGridThreads) k_cpqr_grid_grouped(const CpqrPa
         sP.info = info_base + sP.out_i;
     }
     __syncthreads();
-    cpqr_grid_body<T>(sP, gsize, static_cast<int>(blockIdx.x % gsize), G_, smem_dyn);
+    cpqr_grid_body<T, COLMODE>(sP, gsize, static_cast<int>(blockIdx.x % gsize), G_, smem_dyn);
 }
 
 template <typename T>
-cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gsize, size_t smem, int32_t* J_base,
-                                int32_t* k_out_base, int32_t* info_base, cudaStream_t s) {
-    void* kern = reinterpret_cast<void*>(k_cpqr_grid_grouped<T>);
+cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gsize, int colmode, size_t smem,
+                                int32_t* J_base, int32_t* k_out_base, int32_t* info_base, cudaStream_t s) {
+    void* kern = colmode ? reinterpret_cast<void*>(k_cpqr_grid_grouped<T, true>)
+                         : reinterpret_cast<void*>(k_cpqr_grid_grouped<T, false>);
     if (smem > 48 * 1024) {
         const cudaError_t e =
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -877,9 +881,9 @@ cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gs
     return cudaLaunchCooperativeKernel(kern, dim3(static_cast<unsigned>(ngroups * gsize)), dim3(kGridThreads), args,
                                        smem, s);
 }
-template cudaError_t launch_cpqr_grouped<float>(const CpqrParams<float>*, int, int, size_t, int32_t*, int32_t*,
+template cudaError_t launch_cpqr_grouped<float>(const CpqrParams<float>*, int, int, int, size_t, int32_t*, int32_t*,
                                                 int32_t*, cudaStream_t);
-template cudaError_t launch_cpqr_grouped<double>(const CpqrParams<double>*, int, int, size_t, int32_t*, int32_t*,
+template cudaError_t launch_cpqr_grouped<double>(const CpqrParams<double>*, int, int, int, size_t, int32_t*, int32_t*,
                                                  int32_t*, cudaStream_t);
 
 size_t cpqr_grouped_smem(int64_t cpb, int64_t rstage, int f64) {
@@ -945,7 +949,7 @@ static cudaError_t launch_cpqr_t(void* W, int64_t r, int64_t n, int64_t ldw, con
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(CpqrCtrl), s);
     if (e != cudaSuccess) return e;
     if (P.resident) return launch_cpqr_resident<T>(P, plan.grid, plan.smem, s);
-    void* kern = reinterpret_cast<void*>(k_cpqr_grid<T>);
+    void* kern = P.colmode ? reinterpret_cast<void*>(k_cpqr_grid<T, true>) : reinterpret_cast<void*>(k_cpqr_grid<T, false>);
     if (plan.smem > 48 * 1024) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(plan.smem));
         if (e != cudaSuccess) return e;

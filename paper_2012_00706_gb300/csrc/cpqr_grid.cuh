@@ -110,10 +110,11 @@ cudaError_t launch_cpqr_resident(const CpqrParams<T>& P, int grid, size_t smem, 
 // launch; groups (device) holds one parameter block per matrix, each with its own control
 // word and candidate table [2][gsize], zeroed before the launch.  The outputs of group g
 // are J_base + out_j, k_out_base[out_i] and info_base[out_i].  smem from
-// cpqr_grouped_smem(the largest columns per CTA of any group).
+// cpqr_grouped_smem(the largest columns per CTA of any group).  colmode: the mode every
+// group's parameters name (a group whose parameters differ reports -3 in its info).
 template <typename T>
-cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gsize, size_t smem, int32_t* J_base,
-                                int32_t* k_out_base, int32_t* info_base, cudaStream_t s);
+cudaError_t launch_cpqr_grouped(const CpqrParams<T>* groups, int ngroups, int gsize, int colmode, size_t smem,
+                                int32_t* J_base, int32_t* k_out_base, int32_t* info_base, cudaStream_t s);
 size_t cpqr_grouped_smem(int64_t cpb, int64_t rstage, int f64);
 // The streaming kernel's mode for a slice of at most cpb columns of r rows: a warp per
 // column, and the rows of the pivot column it stages in shared memory (0: none).
