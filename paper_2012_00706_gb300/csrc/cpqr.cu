@@ -62,66 +62,40 @@ __device__ T block_sum(T v, T* sh) {
     return sh[32];
 }
 
-// argmax of (value, index) with ties to the smaller index and a sum, in one pass (three
-// barriers); returns to all threads.
-__device__ void block_argmax_sum(double v, int idx, double part, double* shv, int* shi, double* shp, double* outv,
-                                 int* outi, double* outp) {
+// argmax of pivot keys (norm_bits_key) with ties to the smaller index and, when with_sum,
+// a sum, in one pass (three barriers); returns to all threads.  The keys compare on the
+// integer pipe, so a step's reductions need no FP64 instruction unless sums are asked for.
+__device__ void block_argmax_key(uint64_t key, int idx, bool with_sum, double part, uint64_t* shk, int* shi,
+                                 double* shp, uint64_t* outk, int* outi, double* outp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (!key) idx = -1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const uint64_t ok = __shfl_xor_sync(0xffffffffu, key, o);
         const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
+        if (with_sum) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (ok > key || (ok == key && oi >= 0 && (idx < 0 || oi < idx))) { key = ok; idx = oi; }
     }
     __syncthreads();
-    if (lane == 0) { shv[warp] = v; shi[warp] = idx; shp[warp] = part; }
+    if (lane == 0) { shk[warp] = key; shi[warp] = idx; shp[warp] = part; }
     __syncthreads();
     if (warp == 0) {
-        v = lane < nw ? shv[lane] : -1.0;
+        key = lane < nw ? shk[lane] : 0ull;
         idx = lane < nw ? shi[lane] : -1;
         part = lane < nw ? shp[lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const uint64_t ok = __shfl_xor_sync(0xffffffffu, key, o);
             const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
+            if (with_sum) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (ok > key || (ok == key && oi >= 0 && (idx < 0 || oi < idx))) { key = ok; idx = oi; }
         }
-        if (lane == 0) { shv[32] = v; shi[32] = idx; shp[32] = part; }
+        if (lane == 0) { shk[32] = key; shi[32] = idx; shp[32] = part; }
     }
     __syncthreads();
-    *outv = shv[32];
+    *outk = shk[32];
     *outi = shi[32];
     *outp = shp[32];
-}
-
-// argmax of (value, index) with ties to the smaller index; returns to all threads.
-__device__ void block_argmax(double v, int idx, double* shv, int* shi, double* outv, int* outi) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
-    }
-    __syncthreads();
-    if (lane == 0) { shv[warp] = v; shi[warp] = idx; }
-    __syncthreads();
-    if (warp == 0) {
-        v = lane < nw ? shv[lane] : -1.0;
-        idx = lane < nw ? shi[lane] : -1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
-        }
-        if (lane == 0) { shv[32] = v; shi[32] = idx; }
-    }
-    __syncthreads();
-    *outv = shv[32];
-    *outi = shi[32];
 }
 
 // Per-CTA state in shared memory (static part).
@@ -205,6 +179,8 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     const int64_t r = P.r;
     const T sqrt_u = SqrtU<T>::v();
     const int sup = static_cast<int>(grid_super(P.cpb_max));
+    const bool tol_mode = P.rel_tol > 0.0;     // sums of norms are formed only for the tolerance test
+    uint64_t* const shk = reinterpret_cast<uint64_t*>(G_.shv);
     if ((P.colmode != 0) != COLMODE || (!COLMODE && !P.pub)) {
         // the parameters name the other mode, or row mode lacks its pivot-column slots (every
         // CTA of the matrix sees the same parameters and leaves before the first grid barrier)
@@ -275,21 +251,21 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
     // norm of its rows row..r-1, its entry on row `row`; `lagging`: row mode after a step,
     // whose update the candidate's values take on the fly)
     auto publish = [&](int slot, int row, double total, bool lagging) {
-        // compared in the working precision (widening is exact and monotone), widened once
-        T bestw = T(-1);
+        uint64_t bestk = 0ull;
         int bi = -1;
         T part = 0;
         for (int c = tid; c < nc; c += nt) {
             if (sel_s[c]) continue;
             const T v = nu_s[c];
-            part += v;
-            if (v > bestw) { bestw = v; bi = c; }
+            if (tol_mode) part += v;
+            const uint64_t key = norm_bits_key(v);
+            if (key > bestk) { bestk = key; bi = c; }      // c ascends: ties keep the smaller
         }
-        double bv, sumd;
+        uint64_t bk;
+        double sumd;
         int bl;
-        block_argmax_sum(bi >= 0 ? to_f64(bestw) : -1.0, bi, to_f64(part), G_.shv, G_.shi, G_.shp, &bv, &bl,
-                         &sumd);
-        const T sum = static_cast<T>(sumd);
+        block_argmax_key(bestk, bi, tol_mode, tol_mode ? to_f64(part) : 0.0, shk, G_.shi, G_.shp, &bk, &bl, &sumd);
+        const double bv = key_norm_f64(bk, T(0));
         T s2 = 0;
         T alpha = 0;
         if (COLMODE && bl >= 0 && row < r) {
@@ -338,7 +314,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
         if (tid == 0) {
             Cand cd;
             cd.nu = bv;
-            cd.sumnu = to_f64(sum);
+            cd.sumnu = tol_mode ? to_f64(static_cast<T>(sumd)) : 0.0;
             cd.total = total;
             cd.s2 = to_f64(s2);
             cd.alpha = to_f64(alpha);
@@ -362,18 +338,24 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
         const int slot = j & 1;
         // ---- global pivot: identical reduction of the candidate table in every CTA
         {
-            double bv = -1.0, sn = 0.0, tt = 0.0;
+            uint64_t bk = 0ull;
+            double sn = 0.0, tt = 0.0;
             int bg = -1;
             for (int g = tid; g < G; g += nt) {
                 const Cand c = load_cand(P.cand + slot * G + g);
-                if (c.idx >= 0 && (c.nu > bv || (c.nu == bv && (bg < 0 || g < bg)))) { bv = c.nu; bg = g; }
-                sn += c.sumnu;
-                tt += c.total;
+                const uint64_t key = c.idx >= 0 ? norm_bits_key(c.nu) : 0ull;
+                if (key > bk) { bk = key; bg = g; }          // g ascends: ties keep the smaller CTA
+                if (tol_mode) {
+                    sn += c.sumnu;
+                    tt += c.total;
+                }
             }
-            double gv, gsn;
+            uint64_t gk;
+            double gsn;
             int gg;
-            block_argmax_sum(bv, bg, sn, G_.shv, G_.shi, G_.shp, &gv, &gg, &gsn);
-            const double gtt = j == 0 ? block_sum(tt, G_.shv) : 0.0;
+            block_argmax_key(bk, bg, tol_mode, sn, shk, G_.shi, G_.shp, &gk, &gg, &gsn);
+            double gv = -1.0;
+            const double gtt = (j == 0 && tol_mode) ? block_sum(tt, G_.shv) : 0.0;
             if (tid == 0) {
                 G_.pg = gg;
                 G_.p = -1;
@@ -394,14 +376,14 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
         if (j == 0) total = G_.total;
         const int p = G_.p;
         const double best = G_.shv[32];
-        if (P.rel_tol > 0.0 && sqrt(fmax(G_.sumnu, 0.0)) <= P.rel_tol * sqrt(total)) break;
-        if (p < 0 || !(best > 0.0) || !(G_.s2 > 0.0)) {
+        if (tol_mode && sqrt(fmax(G_.sumnu, 0.0)) <= P.rel_tol * sqrt(total)) break;
+        if (p < 0 || !positive_bits(best) || !positive_bits(G_.s2)) {
             if (b == 0 && tid == 0) set_info(P.info, j + 1);
             break;
         }
         // ---- reflector scalars (the pivot column is not modified in this step)
-        const T alpha = static_cast<T>(G_.alpha);
-        const T snorm = sqrt(static_cast<T>(G_.s2));
+        const T alpha = narrow_exact(G_.alpha, T(0));
+        const T snorm = sqrt(narrow_exact(G_.s2, T(0)));
         const T beta = alpha >= T(0) ? -snorm : snorm;
         const T rb = T(1) / beta;
         const T inv = T(1) / (alpha - beta);
@@ -707,7 +689,7 @@ __device__ __forceinline__ void cpqr_grid_body(const CpqrParams<T>& P, const int
         const bool pend = j > 0;
         pf_xq = xp;
         pf_xprev = P.pub + static_cast<int64_t>((j + 1) & 1) * r;     // step j - 1's slot
-        pf_msvp = pend ? -static_cast<T>(G_.sv_p) : T(0);
+        pf_msvp = pend ? -narrow_exact(G_.sv_p, T(0)) : T(0);
         pf_pend = pend;
         T* const xcur = P.pub + static_cast<int64_t>(j & 1) * r;
         const bool own_p = p >= c0 && p < c1;

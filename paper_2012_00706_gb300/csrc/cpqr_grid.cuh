@@ -55,6 +55,43 @@ struct CpqrParams {
     int64_t rstage;    // streaming kernel, column mode: rows of the pivot column staged in shared memory (0: none)
 };
 
+// The FP64 fields of the records hold FP32 values exactly on the FP32 path; they come back
+// by their bits (GB300's FP64 pipe would take a conversion per thread and step).  Values
+// outside the normal float range go through the hardware conversion (exact as well).
+__device__ __forceinline__ float narrow_exact(double x, float) {
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (e >= 897u && e <= 1150u)
+        return __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+    if (((hi & 0x7FFFFFFFu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return __double2float_rn(x);
+}
+__device__ __forceinline__ double narrow_exact(double x, double) { return x; }
+
+// Pivot keys: the bits of a residual norm (non-negative; the sign bit of a -0 cleared) plus
+// one compare as unsigned integers in the order of the values, on the integer pipe; 0 means
+// "no candidate", and a NaN norm (a non-finite input, reported in info) is none.
+__device__ __forceinline__ uint64_t norm_bits_key(float v) {
+    const uint32_t a = __float_as_uint(v) & 0x7FFFFFFFu;
+    return a > 0x7F800000u ? 0ull : static_cast<uint64_t>(a) + 1ull;
+}
+__device__ __forceinline__ uint64_t norm_bits_key(double v) {
+    const uint64_t a = static_cast<uint64_t>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
+    return a > 0x7FF0000000000000ull ? 0ull : a + 1ull;
+}
+__device__ __forceinline__ double key_norm_f64(uint64_t key, float) {
+    return key ? f64_of_f32(__uint_as_float(static_cast<uint32_t>(key - 1ull))) : -1.0;
+}
+__device__ __forceinline__ double key_norm_f64(uint64_t key, double) {
+    return key ? __longlong_as_double(static_cast<long long>(key - 1ull)) : -1.0;
+}
+// x > 0 for a double, on the integer pipe (false for zeros, negatives and NaNs).
+__device__ __forceinline__ bool positive_bits(double x) {
+    const long long u = __double_as_longlong(x);
+    return u > 0 && u <= 0x7FF0000000000000ll;
+}
+
 // Candidate entries written by other CTAs are read from L2 (never from a stale L1 line).
 __device__ __forceinline__ Cand load_cand(const Cand* p) {
     Cand c;
