@@ -936,6 +936,8 @@ int64_t id_batch_plan_describe(const id_batch_plan_t* p, char* buf, int64_t len)
         for (size_t i = 0; i < p->waves.size(); ++i) os << (i ? ", " : "") << p->waves[i].count;
         os << "], \"ctas_per_id\": [";
         for (size_t i = 0; i < p->waves.size(); ++i) os << (i ? ", " : "") << p->waves[i].gsize;
+        os << "], \"column_mode\": [";
+        for (size_t i = 0; i < p->waves.size(); ++i) os << (i ? ", " : "") << p->waves[i].colmode;
         os << "], \"solve_units\": " << p->solve_units.size() << ", \"work_bytes\": " << p->work_bytes << "}";
     }
     else

@@ -146,6 +146,12 @@ def test_plan_plain_f32_waves(gid):
                       device="cpu")
     d = q.describe()
     assert d["waves"] == 1 and d["ids_per_wave"] == [3] and d["ctas_per_id"] == [7]   # at most n of the narrowest
+    # one slice mode per wave (a launch): a warp per column as soon as one matrix has a column
+    # per warp (429 columns per CTA here), rows split over all threads only when none has
+    assert d["column_mode"] == [1]
+    assert p.describe()["column_mode"] == [1, 1, 1, 1]     # 57 columns per CTA
+    r = gid.BatchPlan([(5000, 40)] * 4, [8] * 4, precision="plain_f32", device="cpu")
+    assert r.describe()["ctas_per_id"] == [38] and r.describe()["column_mode"] == [0]   # 2 columns per CTA
     assert q.t_off == [0, 128 * 2999, 128 * 2999 + 40 * 39, 128 * 2999 + 40 * 39 + 7 * 6]
     assert plan_status(gid, [100], [50], [5], precision=1) == 0
     assert plan_status(gid, [100], [50], [5], precision=1, dtype=1) == 0

@@ -323,6 +323,32 @@ def test_batched_plain_f32(gid, dev, orc, dtype):
         assert np.max(np.abs(one.T.cpu().numpy() - T), initial=0.0) <= 1e-4 * scale, i
 
 
+def test_batched_plain_f32_row_mode(gid, dev, orc):
+    """A PLAIN_F32 wave whose slices are narrower than a CTA's warps runs the grouped kernel in
+    row mode (each column one update behind, the pivot column brought up to date on the fly and
+    kept in the group's two pivot-column slots): pivots equal the oracle's on separated columns,
+    T agrees with the oracle's, tall ragged shapes included."""
+    shapes = [(5000, 40, 8), (4099, 37, 12), (6001, 45, 20), (3000, 33, 33)]
+    mats = [wl.separated_matrix(m, n, seed=760 + i, decay=0.9).astype(np.float32)
+            for i, (m, n, _) in enumerate(shapes)]
+    ranks = [r for _, _, r in shapes]
+    plan = gid.BatchPlan([a.shape for a in mats], ranks, dtype=torch.float32, precision="plain_f32")
+    d = plan.describe()
+    assert d["column_mode"] == [0] and d["waves"] == 1, d
+    bufs = [to_dev(a, dev, dtype=np.float32) for a in mats]
+    plan.bind([v for _, v in bufs])
+    plan.run()
+    torch.cuda.synchronize()
+    for i, (a, r, res) in enumerate(zip(mats, ranks, plan.results())):
+        a64 = a.astype(np.float64)
+        ref = orc.interp_decomp(a64, k=r)
+        assert res.info == 0 and res.k == r, (i, res.info, res.k)
+        J, T = res.J.cpu().numpy(), res.T.cpu().numpy()
+        assert np.array_equal(J, ref["J"]), i
+        scale = max(1.0, np.max(np.abs(ref["T"]), initial=0.0))
+        assert np.max(np.abs(T - ref["T"]), initial=0.0) <= 1e-4 * scale, i
+
+
 def test_batched_solve_ill_conditioned_r11(gid, dev, orc):
     """The batch's solve takes the products for well-conditioned R11 and the warp solve with
     six refinement steps where the largest diagonal of R11 exceeds 2^24 / 100 times the
