@@ -39,29 +39,50 @@ __device__ __forceinline__ void st_release_s32(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// (value, index) warp argmax, ties to the smaller index; lane 0's result goes to every
-// lane.  Values must be ordered (no NaN: callers map non-finite norms to -1), so that
-// every lane and every warp reducing the same entries takes the same decision: the
-// warps of a CTA branch on it independently, and must meet at the same barriers.
-__device__ __forceinline__ void warp_argmax(double& v, int& idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (oi >= 0 && (idx < 0 || ov > v || (ov == v && oi < idx))) { v = ov; idx = oi; }
-    }
-    v = __shfl_sync(0xffffffffu, v, 0);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-}
-
 // A residual norm as a pivot key: non-finite values (a non-finite input, reported in
 // info) order below every real norm.
 __device__ __forceinline__ double norm_key(double nu) { return isfinite(nu) ? nu : -1.0; }
 
+// The same order on the integer pipe: a finite norm's bits plus two (a -0 counts as +0), 1 for
+// a non-finite norm or the -1 a record carries for one, 0 for "no candidate"; keys compare as
+// unsigned integers, so a step's reductions need no FP64 instruction.
+__device__ __forceinline__ uint64_t res_key(float v) {
+    const uint32_t a = __float_as_uint(v) & 0x7FFFFFFFu;
+    return a >= 0x7F800000u ? 1ull : static_cast<uint64_t>(a) + 2ull;
+}
+__device__ __forceinline__ uint64_t res_key(double v) {
+    const uint64_t u = static_cast<uint64_t>(__double_as_longlong(v));
+    const uint64_t a = u & 0x7FFFFFFFFFFFFFFFull;
+    if (a >= 0x7FF0000000000000ull || ((u >> 63) != 0ull && a != 0ull)) return 1ull;
+    return a + 2ull;
+}
+// The norm a key stands for, as the record's FP64 value (-1 for keys 0 and 1).
+__device__ __forceinline__ double res_key_value(uint64_t key, float) {
+    return key >= 2ull ? f64_of_f32(__uint_as_float(static_cast<uint32_t>(key - 2ull))) : -1.0;
+}
+__device__ __forceinline__ double res_key_value(uint64_t key, double) {
+    return key >= 2ull ? __longlong_as_double(static_cast<long long>(key - 2ull)) : -1.0;
+}
+
+// Warp argmax of keys with ties to the smaller index; lane 0's result goes to every lane, so
+// that every warp reducing the same entries takes the same decision (the warps of a CTA
+// branch on it independently and must meet at the same barriers).
+__device__ __forceinline__ void warp_argmax_key(uint64_t& key, int& idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (oi >= 0 && (idx < 0 || ok > key || (ok == key && oi < idx))) { key = ok; idx = oi; }
+    }
+    key = __shfl_sync(0xffffffffu, key, 0);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrParams<T> P) {
     extern __shared__ __align__(16) uint8_t smem_dyn[];
-    __shared__ double w_nu[kResWarps], w_sum[kResWarps];
+    __shared__ unsigned long long w_key[kResWarps];
+    __shared__ double w_sum[kResWarps];
     __shared__ int w_idx[kResWarps];
     __shared__ int cnt[kResWarps];
     // the step's decision, written by warp 0 before the CTA barrier
@@ -71,6 +92,7 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
 
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const bool tol_mode = P.rel_tol > 0.0;     // sums of norms are formed only for the tolerance test
     const int64_t c0 = P.n * b / G, c1 = P.n * (b + 1) / G;
     const int nc = static_cast<int>(c1 - c0);
     const int64_t r = P.r;
@@ -113,20 +135,22 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
     // also the slice's total), and stamps the record with step + 1 after a fence
     auto publish = [&](int step) {
         const int slot = step & 1;
-        double v = -1.0, part = 0.0;
+        uint64_t v = 0ull;
+        double part = 0.0;
         int ci = -1;
         for (int c = warp; c < nc; c += kResWarps) {
             if (sel_s[c]) continue;
-            const double nu = norm_key(static_cast<double>(nu_s[c]));
-            part += nu;
-            if (ci < 0 || nu > v) { v = nu; ci = c; }     // c ascends: ties keep the smaller
+            const uint64_t key = res_key(nu_s[c]);
+            if (tol_mode) part += norm_key(to_f64(nu_s[c]));
+            if (ci < 0 || key > v) { v = key; ci = c; }     // c ascends: ties keep the smaller
         }
-        if (lane == 0) { w_nu[warp] = v; w_idx[warp] = ci; w_sum[warp] = part; }
+        if (lane == 0) { w_key[warp] = v; w_idx[warp] = ci; w_sum[warp] = part; }
         __syncthreads();
         // every warp finds the CTA's best the same way; all threads copy its rows
-        double bv = lane < kResWarps ? w_nu[lane] : -1.0;
+        uint64_t bk = lane < kResWarps ? w_key[lane] : 0ull;
         int bi = lane < kResWarps ? w_idx[lane] : -1;
-        warp_argmax(bv, bi);
+        warp_argmax_key(bk, bi);
+        const double bv = res_key_value(bk, T(0));
         if (bi >= 0 && step < r) {
             const T* x = xs + static_cast<int64_t>(bi) * r;
             T* dst = P.pub + (static_cast<int64_t>(slot) * G + b) * r;
@@ -135,8 +159,8 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         // the column's stores, observed through the barrier, before the record's stamp
         __syncthreads();
         if (warp == 0) {
-            double sum = lane < kResWarps ? w_sum[lane] : 0.0;
-            sum = warp_sum(sum);
+            double sum = 0.0;
+            if (tol_mode) sum = warp_sum(lane < kResWarps ? w_sum[lane] : 0.0);
             const T alpha = (bi >= 0 && step < r) ? xs[static_cast<int64_t>(bi) * r + step] : T(0);
             Cand* rec = P.cand + slot * G + b;
             if (lane == 0) {
@@ -198,7 +222,8 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
             if (lane == 0) s_go = 0;
             return;
         }
-        double bv = -1.0, sn = 0.0, tt = 0.0, wa = 0.0, ws = 0.0;
+        uint64_t bk = 0ull;
+        double sn = 0.0, tt = 0.0, wa = 0.0, ws = 0.0;
         int bg = -1, wi = -1;
         Cand e[kTableLanes];
 #pragma unroll
@@ -211,24 +236,29 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         for (int q = 0; q < kTableLanes; ++q) {
             const int g = 32 * q + lane;
             if (g >= G) continue;
-            const double nu = norm_key(e[q].nu);
-            if (e[q].idx >= 0 && (bg < 0 || nu > bv)) {   // g ascends per lane
-                bv = nu; bg = g; wa = e[q].alpha; ws = e[q].s2; wi = e[q].idx;
+            const uint64_t key = res_key(e[q].nu);
+            if (e[q].idx >= 0 && (bg < 0 || key > bk)) {   // g ascends per lane
+                bk = key; bg = g; wa = e[q].alpha; ws = e[q].s2; wi = e[q].idx;
             }
-            sn += e[q].sumnu;
-            tt += e[q].total;
+            if (tol_mode) {
+                sn += e[q].sumnu;
+                tt += e[q].total;
+            }
         }
-        warp_argmax(bv, bg);
-        sn = __shfl_sync(0xffffffffu, warp_sum(sn), 0);
-        if (step == 0) total = __shfl_sync(0xffffffffu, warp_sum(tt), 0);
+        warp_argmax_key(bk, bg);
+        if (tol_mode) {
+            sn = __shfl_sync(0xffffffffu, warp_sum(sn), 0);
+            if (step == 0) total = __shfl_sync(0xffffffffu, warp_sum(tt), 0);
+        }
+        const double bv = res_key_value(bk, 0.0);
         const int src_lane = bg >= 0 ? (bg & 31) : 0;
         const double alpha = __shfl_sync(0xffffffffu, wa, src_lane);
         const double s2 = __shfl_sync(0xffffffffu, ws, src_lane);
         const int p = bg >= 0 ? __shfl_sync(0xffffffffu, wi, src_lane) : -1;
         int go = 1;
-        if (P.rel_tol > 0.0 && sqrt(fmax(sn, 0.0)) <= P.rel_tol * sqrt(total)) {
+        if (tol_mode && sqrt(fmax(sn, 0.0)) <= P.rel_tol * sqrt(total)) {
             go = 0;
-        } else if (p < 0 || !(bv > 0.0) || !(s2 > 0.0)) {
+        } else if (p < 0 || !positive_bits(bv) || !positive_bits(s2)) {
             go = 0;
             if (b == 0 && lane == 0) set_info(P.info, step + 1);
         }
@@ -256,8 +286,8 @@ __global__ void __launch_bounds__(kResWarps * 32) k_cpqr_resident(const CpqrPara
         }
         // ---- reflector scalars; the pivot column staged in xps (not modified in this step)
         const int p = s_p;
-        const T alpha = static_cast<T>(s_alpha);
-        const T snorm = sqrt(static_cast<T>(s_s2));
+        const T alpha = narrow_exact(s_alpha, T(0));
+        const T snorm = sqrt(narrow_exact(s_s2, T(0)));
         const T beta = alpha >= T(0) ? -snorm : snorm;
         const T rbeta = T(1) / beta;
         const T inv = T(1) / (alpha - beta);
