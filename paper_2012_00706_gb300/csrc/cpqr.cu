@@ -16,14 +16,16 @@
 // so the pivot column itself, unscaled, is all a step needs besides two scalars.
 //
 // CTA b owns the contiguous column slice [n b / G, n (b + 1) / G) of the working copy
-// in global memory and updates it in place.  A step is two coalesced row-parallel passes
-// over the CTA's unselected columns, all its threads splitting the rows (several loads in
-// flight per thread): the dot products S_i (CTA reduction), then the update.  The pivot
-// column is read straight from the working copy (it is not modified in the step it is
-// chosen).  The CTA then publishes its best remaining candidate (norm, index, sum of
-// norms, and the candidate's exact squared norm and next-row entry, the reflector scalars
-// of the next step); after one bounded grid barrier every CTA reduces the same candidate
-// table in the same order and agrees on the next pivot.  Matrices whose columns fit the
+// in global memory and updates it in place, in one of two modes fixed per launch.  Column
+// mode (a warp per column): dot product, scalars and update of a column by one warp with
+// no CTA barrier.  Row mode (fewer columns than warps, all threads splitting the rows with
+// several loads in flight per thread): each column stays one update behind, and one pass
+// per step applies the previous step's update and forms this step's dot products S_i, with
+// the pivot column brought up to date on the fly.  The CTA then publishes its best
+// remaining candidate (norm, index, sum of norms, and the candidate's exact squared norm
+// and next-row entry, the reflector scalars of the next step); after one bounded grid
+// barrier every CTA reduces the same candidate table in the same order, on integer keys
+// of the norms' bits, and agrees on the next pivot.  Matrices whose columns fit the
 // grid's shared memory go to the resident kernel instead (cpqr_resident.cu).
 #include "cpqr_grid.cuh"
 

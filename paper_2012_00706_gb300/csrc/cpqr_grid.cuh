@@ -51,7 +51,8 @@ struct CpqrParams {
     uint64_t limit_ns;
     int64_t out_j;     // grouped launch: J = J_base + out_j, k_out / info = their base + out_i
     int32_t out_i;
-    int32_t colmode;   // streaming kernel: a warp per column (slices of at least a column per warp)
+    int32_t colmode;   // streaming kernel: a warp per column (else the rows split over all threads);
+                       // must equal the launch's mode
     int64_t rstage;    // streaming kernel, column mode: rows of the pivot column staged in shared memory (0: none)
 };
 
