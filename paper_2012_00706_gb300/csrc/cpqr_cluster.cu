@@ -5,13 +5,13 @@
 // threads: TPC threads own one column, each a contiguous block of MAXR / TPC
 // rows.  The n columns are split over the C CTAs of a cluster (up to 16).
 //
-// Every pivot step needs one global argmax.  Each CTA stages its best candidate
-// (norm, index, sum of norms) and that candidate's current column in its own
-// shared memory and bulk-copies the record into every peer's shared memory
-// (cp.async.bulk shared::cta -> shared::cluster), completing on the peer's
-// mbarrier in bytes.  Each CTA waits (bounded) on its own mbarrier, reduces the
-// C records in the same order, and so all CTAs agree on the pivot and hold its
-// column locally: one exchange per step, no grid barrier and no memory fences.
+// Every pivot step needs one global argmax.  Each warp stages its best candidate's
+// current column in shared memory; after one CTA barrier the CTA's best record (norm,
+// index, sum of norms, exact squared norm, then the column) goes into every peer's shared
+// memory by 16-byte st.async stores, completing on the peer's mbarrier in bytes.  Each
+// CTA waits (bounded) on its own mbarrier, reduces the C records in the same order, and
+// so all CTAs agree on the pivot and hold its column locally: one exchange per step, no
+// grid barrier and no memory fences.
 //
 // Per step each column forms w = v^T x(j:r) with the reflector
 // v = x_p / (alpha - beta) (v_j = 1), applies x -= tau w v, records
@@ -115,17 +115,6 @@ __device__ __forceinline__ uint32_t map_peer(uint32_t local_addr, uint32_t rank)
     uint32_t out;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(local_addr), "r"(rank));
     return out;
-}
-
-// Bulk copy of `bytes` from this CTA's shared memory into a peer's shared memory,
-// counted in bytes on the peer's mbarrier.
-__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
-                                            uint32_t bar_cluster) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst_cluster),
-        "r"(src_cta), "r"(bytes), "r"(bar_cluster)
-        : "memory");
 }
 
 __device__ __forceinline__ void cluster_sync_all() {
