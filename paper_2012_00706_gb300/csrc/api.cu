@@ -76,6 +76,7 @@ struct FactorPlan {
     CpqrPlan cp;
     ClusterCpqrPlan ccp;
     int use_cluster = 0;    // FP32 pivoting of at most 128 rows: one thread-block cluster
+    size_t ctrl_bytes = 0;  // the grid kernels' control region (the largest any launch of the plan needs)
     size_t bytes = 0;
 };
 
@@ -95,7 +96,7 @@ size_t carve_factor(void* base, int64_t n, const FactorPlan& p, FactorPtrs* out)
     Carver c(base);
     const int elem = p.w_f64 ? 8 : 4;
     FactorPtrs f{};
-    f.ctrl = c.take<uint8_t>(cpqr_ctrl_bytes(p.cp, p.rows, elem));
+    f.ctrl = c.take<uint8_t>(p.ctrl_bytes);
     f.sel = c.take<uint8_t>(static_cast<size_t>(n));
     f.nu = c.take<uint8_t>(static_cast<size_t>(n) * elem);
     f.nuref = c.take<uint8_t>(static_cast<size_t>(n) * elem);
@@ -159,6 +160,7 @@ id_status_t plan_factor(id_dtype_t a_dtype, int64_t m, int64_t n, int64_t lda, c
     // sketch), or the sketch Y, or the cast A_L
     const bool short_f32 = !p.w_f64 && (p.sketch || p.low || a_dtype == ID_F32);
     p.use_cluster = short_f32 && cpqr_cluster_plan(p.rows, n, &p.ccp) ? 1 : 0;
+    p.ctrl_bytes = cpqr_ctrl_bytes(p.cp, p.rows, p.w_f64 ? 8 : 4);
     p.bytes = carve_factor(nullptr, n, p, nullptr);
     *plan = p;
     return ID_OK;
@@ -385,6 +387,15 @@ id_status_t plan_adaptive(id_dtype_t a_dtype, int64_t m, int64_t n, const id_opt
     const id_status_t st = plan_factor(a_dtype, m, n, m, &fo, &p.f);
     if (st != ID_OK) return st;
     const size_t elem = p.f.w_f64 ? 8 : 4;
+    // the rounds pivot ell = block, 2 block, ..., ell_max rows: a shorter round may take the
+    // resident kernel, whose control region holds published columns, where ell_max does not
+    for (int64_t e = std::min<int64_t>(block, o->ell);; e = std::min<int64_t>(e + block, o->ell)) {
+        CpqrPlan cp;
+        if (cpqr_plan(e, n, static_cast<int>(elem), &cp))
+            p.f.ctrl_bytes = std::max(p.f.ctrl_bytes, cpqr_ctrl_bytes(cp, e, static_cast<int>(elem)));
+        if (e >= o->ell) break;
+    }
+    p.f.bytes = carve_factor(nullptr, n, p.f, nullptr);
     // the rounds sketch `block` rows, the last one the remainder
     const int rem = static_cast<int>(o->ell % block);
     size_t part = adaptive_partial_bytes(a_dtype, m, n, std::min<int>(block, o->ell), o->precision);
